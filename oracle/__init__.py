@@ -1,0 +1,132 @@
+"""Huskysort oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain CPU reference implementations used to check the CUDA library.  Only the
+test-suite, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline / reference
+arm import this package; the product path never does.  It shares no code with
+the CUDA library (``paper_2012_00866_gb300``) and imports nothing from it.
+
+  husky_oracle.c  Algorithm 4 encoder, Algorithms 2/3 array encoding, stable
+                  lexicographic argsort, sortedness/stability property check.
+  rmi_oracle.py   FP64 learned-bucketer model (forward, gradient, SGD step,
+                  least-squares leaf fit, bucket function).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "husky_oracle.c")
+_LIB = os.path.join(_HERE, "libhusky_oracle.so")
+_lib = None
+
+CODER_ASCII7 = 1
+CODER_BYTE8 = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile husky_oracle.c into libhusky_oracle.so beside it."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                           "-pthread", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        u64, vp, ci = ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+        lib.oracle_string_to_long.restype = u64
+        lib.oracle_string_to_long.argtypes = [vp, u64, ci, ci, u64]
+        lib.oracle_encode.restype = ci
+        lib.oracle_encode.argtypes = [vp, vp, u64, ci, vp, vp, vp]
+        lib.oracle_string_compare.restype = ci
+        lib.oracle_string_compare.argtypes = [vp, vp, u64, u64]
+        lib.oracle_stable_argsort.restype = ci
+        lib.oracle_stable_argsort.argtypes = [vp, vp, u64, vp, ci, ci]
+        lib.oracle_check_sorted.restype = ctypes.c_int64
+        lib.oracle_check_sorted.argtypes = [vp, vp, u64, vp, ci, ci]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data if a.size else 0
+
+
+def _threads(threads):
+    return threads if threads else (os.cpu_count() or 1)
+
+
+def string_to_long(s: bytes, max_length: int, bit_width: int, mask: int) -> int:
+    """Algorithm 4 on one string."""
+    buf = np.frombuffer(s, dtype=np.uint8) if s else np.zeros(1, np.uint8)
+    return int(_load().oracle_string_to_long(_ptr(buf), len(s), max_length,
+                                             bit_width, mask))
+
+
+def ascii_to_long(s: bytes) -> int:
+    """The ASCII coder: 7 bits x 64/7 = 9 chars, mask 0x7F."""
+    return string_to_long(s, 64 // 7, 7, 0x7F)
+
+
+def byte_to_long(s: bytes) -> int:
+    """The byte coder: 8 bits x 8 chars, no mask."""
+    return string_to_long(s, 8, 8, 0)
+
+
+def encode(data: np.ndarray, offsets: np.ndarray, coder: int = CODER_ASCII7):
+    """Algorithms 2/3: (codes uint64[n], exact uint8[n], perfect bool)."""
+    n = offsets.shape[0] - 1
+    codes = np.empty(n, dtype=np.uint64)
+    exact = np.empty(n, dtype=np.uint8)
+    perfect = ctypes.c_int(0)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    _load().oracle_encode(_ptr(data), _ptr(offsets), n, coder, _ptr(codes),
+                          _ptr(exact), ctypes.addressof(perfect))
+    return codes, exact, bool(perfect.value)
+
+
+def stable_argsort(data: np.ndarray, offsets: np.ndarray, index_u64: bool = False,
+                   threads: int | None = None) -> np.ndarray:
+    """Stable argsort of the strings, unsigned-byte lexicographic order."""
+    n = offsets.shape[0] - 1
+    perm = np.empty(n, dtype=np.uint64 if index_u64 else np.uint32)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    rc = _load().oracle_stable_argsort(_ptr(data), _ptr(offsets), n, _ptr(perm),
+                                       1 if index_u64 else 0, _threads(threads))
+    if rc != 0:
+        raise MemoryError("oracle_stable_argsort: out of memory")
+    return perm
+
+
+def check_sorted(data: np.ndarray, offsets: np.ndarray, perm: np.ndarray,
+                 threads: int | None = None) -> int:
+    """-1 if perm is the stable argsort, else the first failing position."""
+    n = offsets.shape[0] - 1
+    if perm.shape[0] != n:
+        return 0
+    perm = np.ascontiguousarray(perm)
+    if perm.dtype not in (np.uint32, np.uint64):
+        raise TypeError("perm must be uint32 or uint64")
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    return int(_load().oracle_check_sorted(_ptr(data), _ptr(offsets), n,
+                                           _ptr(perm),
+                                           1 if perm.dtype == np.uint64 else 0,
+                                           _threads(threads)))
+
+
+def string_compare(data: np.ndarray, offsets: np.ndarray, i: int, j: int) -> int:
+    return int(_load().oracle_string_compare(_ptr(data), _ptr(offsets), i, j))

@@ -1,0 +1,358 @@
+/*
+ * Huskysort oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously-correct CPU reference for what the GPU path computes.
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * arm may load this library.  It shares no code, header or constant table with
+ * the CUDA library; the two are compiled from disjoint sources.
+ *
+ * Contents
+ *   oracle_string_to_long   Algorithm 4 (stringToLong), literally.
+ *   oracle_encode           Algorithms 2/3 (huskyEncode over an array, with
+ *                           the per-element perfection test).
+ *   oracle_stable_argsort   The result the whole method must reach: the stable
+ *                           argsort of the strings under unsigned-byte
+ *                           lexicographic order (Section 3.1 Step 3: the final
+ *                           Timsort pass is stable; a proper prefix is smaller).
+ *   oracle_check_sorted     Property check usable at any size: a permutation
+ *                           that is sorted and stable on ties is THE stable
+ *                           argsort (unique), so this pins results too large to
+ *                           re-sort on the host.
+ *
+ * Readings of the paper taken here (each listed in the design doc):
+ *   - a "char" is one byte of the input buffer (charAt on ASCII text);
+ *   - perfectForLength(len) is undefined in the paper; an element is exactly
+ *     represented iff len <= maxLength and (len == 0 or its last byte != 0),
+ *     because "a" and "a\0" share a code;
+ *   - Java shifts are taken mod 64; the only shift that can reach 64 here is
+ *     the padding shift of an empty string, whose result is 0 either way.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Algorithm 4: pack min(len, max_length) chars, bit_width bits each, most
+ * significant first, each ANDed with mask when mask != 0, then shift left by
+ * bit_width * padding so that short strings are zero-padded on the right. */
+uint64_t oracle_string_to_long(const uint8_t *s, uint64_t len, int max_length,
+                               int bit_width, uint64_t mask)
+{
+    uint64_t length = len < (uint64_t)max_length ? len : (uint64_t)max_length;
+    uint64_t padding = (uint64_t)max_length - length;
+    uint64_t result = 0;
+    for (uint64_t i = 0; i < length; i++) {
+        uint64_t c = s[i];
+        if (mask != 0)
+            c = c & mask;
+        result = (result << bit_width) | c;
+    }
+    uint64_t shift = (uint64_t)bit_width * padding;
+    if (shift >= 64)
+        result = 0; /* only reached when length == 0, where result is 0 */
+    else
+        result = result << shift;
+    return result;
+}
+
+/* Coder constants (Section 4.3 "Constants" listing): ASCII uses 7 bits per
+ * char and 64/7 = 9 chars with mask 0x7F.  BYTE8 (8 bits x 8 chars, no mask)
+ * is this project's order-preserving coder for arbitrary bytes. */
+enum { ORACLE_CODER_ASCII7 = 1, ORACLE_CODER_BYTE8 = 2 };
+
+static void coder_params(int coder, int *max_length, int *bit_width,
+                         uint64_t *mask)
+{
+    if (coder == ORACLE_CODER_BYTE8) {
+        *max_length = 64 / 8;
+        *bit_width = 8;
+        *mask = 0;
+    } else {
+        *max_length = 64 / 7;
+        *bit_width = 7;
+        *mask = 0x7F;
+    }
+}
+
+/* perfectForLength (Algorithm 3), in this project's reading. */
+static int exactly_represented(const uint8_t *s, uint64_t len, int max_length)
+{
+    if (len > (uint64_t)max_length)
+        return 0;
+    if (len == 0)
+        return 1;
+    return s[len - 1] != 0;
+}
+
+/* Algorithms 2/3: encode every element; *perfect = all elements exact.
+ * exact_out (nullable) receives the per-element flag.  Returns 0. */
+int oracle_encode(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
+                  int coder, uint64_t *codes_out, uint8_t *exact_out,
+                  int *perfect)
+{
+    int max_length, bit_width;
+    uint64_t mask;
+    coder_params(coder, &max_length, &bit_width, &mask);
+    int is_perfect = 1;
+    for (uint64_t i = 0; i < n; i++) {
+        const uint8_t *s = bytes + offsets[i];
+        uint64_t len = offsets[i + 1] - offsets[i];
+        int ex = exactly_represented(s, len, max_length);
+        if (!ex)
+            is_perfect = 0;
+        if (exact_out)
+            exact_out[i] = (uint8_t)ex;
+        codes_out[i] = oracle_string_to_long(s, len, max_length, bit_width, mask);
+    }
+    if (perfect)
+        *perfect = is_perfect;
+    return 0;
+}
+
+/* Unsigned-byte lexicographic comparison; a proper prefix is smaller. */
+static int string_compare(const uint8_t *bytes, const uint64_t *offsets,
+                          uint64_t i, uint64_t j)
+{
+    uint64_t la = offsets[i + 1] - offsets[i];
+    uint64_t lb = offsets[j + 1] - offsets[j];
+    uint64_t m = la < lb ? la : lb;
+    int c = memcmp(bytes + offsets[i], bytes + offsets[j], (size_t)m);
+    if (c != 0)
+        return c < 0 ? -1 : 1;
+    if (la < lb)
+        return -1;
+    if (la > lb)
+        return 1;
+    return 0;
+}
+
+/* Public for tests: sign of the comparison of strings i and j. */
+int oracle_string_compare(const uint8_t *bytes, const uint64_t *offsets,
+                          uint64_t i, uint64_t j)
+{
+    return string_compare(bytes, offsets, i, j);
+}
+
+/* ---- stable merge sort of an index array ------------------------------- */
+
+typedef struct {
+    const uint8_t *bytes;
+    const uint64_t *offsets;
+} str_ctx;
+
+/* Merge a[lo..mid) and a[mid..hi) into tmp, left side first on ties, which is
+ * what makes merge sort stable. */
+static void merge_runs(const str_ctx *c, uint64_t *a, uint64_t *tmp,
+                       uint64_t lo, uint64_t mid, uint64_t hi)
+{
+    uint64_t i = lo, j = mid, k = lo;
+    while (i < mid && j < hi) {
+        if (string_compare(c->bytes, c->offsets, a[j], a[i]) < 0)
+            tmp[k++] = a[j++];
+        else
+            tmp[k++] = a[i++];
+    }
+    while (i < mid)
+        tmp[k++] = a[i++];
+    while (j < hi)
+        tmp[k++] = a[j++];
+    memcpy(a + lo, tmp + lo, (size_t)(hi - lo) * sizeof(uint64_t));
+}
+
+/* Bottom-up merge sort of a[lo..hi): widths 1, 2, 4, ... */
+static void merge_sort(const str_ctx *c, uint64_t *a, uint64_t *tmp,
+                       uint64_t lo, uint64_t hi)
+{
+    uint64_t n = hi - lo;
+    for (uint64_t width = 1; width < n; width *= 2) {
+        for (uint64_t s = lo; s < hi; s += 2 * width) {
+            uint64_t mid = s + width;
+            if (mid >= hi)
+                break;
+            uint64_t e = mid + width < hi ? mid + width : hi;
+            merge_runs(c, a, tmp, s, mid, e);
+        }
+    }
+}
+
+typedef struct {
+    const str_ctx *c;
+    uint64_t *a, *tmp;
+    uint64_t lo, hi;
+} sort_job;
+
+static void *sort_job_run(void *p)
+{
+    sort_job *j = (sort_job *)p;
+    merge_sort(j->c, j->a, j->tmp, j->lo, j->hi);
+    return NULL;
+}
+
+typedef struct {
+    const str_ctx *c;
+    uint64_t *a, *tmp;
+    uint64_t lo, mid, hi;
+} merge_job;
+
+static void *merge_job_run(void *p)
+{
+    merge_job *j = (merge_job *)p;
+    merge_runs(j->c, j->a, j->tmp, j->lo, j->mid, j->hi);
+    return NULL;
+}
+
+/* Stable argsort: perm receives the string indices in ascending order, equal
+ * strings in input order.  The index array starts as 0..n-1 and is merge
+ * sorted; with `threads` > 1, contiguous chunks are sorted concurrently and
+ * then merged pairwise (lower chunk first on ties), which is still exactly a
+ * stable merge sort.  perm_u64 selects a uint64 (1) or uint32 (0) output.
+ * Returns 0, or -1 when memory runs out. */
+int oracle_stable_argsort(const uint8_t *bytes, const uint64_t *offsets,
+                          uint64_t n, void *perm, int perm_u64, int threads)
+{
+    if (n == 0)
+        return 0;
+    uint64_t *a = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    uint64_t *tmp = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    if (!a || !tmp) {
+        free(a);
+        free(tmp);
+        return -1;
+    }
+    for (uint64_t i = 0; i < n; i++)
+        a[i] = i;
+    str_ctx c = {bytes, offsets};
+    if (threads < 1)
+        threads = 1;
+    if ((uint64_t)threads > n)
+        threads = (int)n;
+    if (threads > 256)
+        threads = 256;
+
+    uint64_t bounds[257];
+    for (int t = 0; t <= threads; t++)
+        bounds[t] = n * (uint64_t)t / (uint64_t)threads;
+
+    if (threads == 1) {
+        merge_sort(&c, a, tmp, 0, n);
+    } else {
+        pthread_t tid[256];
+        sort_job jobs[256];
+        for (int t = 0; t < threads; t++) {
+            jobs[t] = (sort_job){&c, a, tmp, bounds[t], bounds[t + 1]};
+            pthread_create(&tid[t], NULL, sort_job_run, &jobs[t]);
+        }
+        for (int t = 0; t < threads; t++)
+            pthread_join(tid[t], NULL);
+        /* Pairwise merge tree over the sorted chunks. */
+        int chunks = threads;
+        while (chunks > 1) {
+            merge_job mj[128];
+            int pairs = 0, out = 0;
+            for (int t = 0; t + 1 < chunks; t += 2) {
+                mj[pairs] = (merge_job){&c, a, tmp, bounds[t], bounds[t + 1],
+                                        bounds[t + 2]};
+                pthread_create(&tid[pairs], NULL, merge_job_run, &mj[pairs]);
+                pairs++;
+            }
+            for (int p = 0; p < pairs; p++)
+                pthread_join(tid[p], NULL);
+            for (int t = 0; t < chunks; t += 2)
+                bounds[out++] = bounds[t];
+            bounds[out] = n;
+            chunks = out;
+        }
+    }
+
+    if (perm_u64) {
+        memcpy(perm, a, (size_t)n * sizeof(uint64_t));
+    } else {
+        uint32_t *p32 = (uint32_t *)perm;
+        for (uint64_t i = 0; i < n; i++)
+            p32[i] = (uint32_t)a[i];
+    }
+    free(a);
+    free(tmp);
+    return 0;
+}
+
+/* ---- property check ------------------------------------------------------
+ *
+ * perm is THE stable argsort iff
+ *   (1) every entry is < n,
+ *   (2) for every adjacent pair (p, q) = (perm[j-1], perm[j]):
+ *       string(p) < string(q), or string(p) == string(q) and p < q.
+ * (2) makes the sequence strictly increasing under the total order
+ * (string, index), so no value repeats; n distinct values below n are a
+ * permutation of 0..n-1; a strictly increasing arrangement under a total
+ * order is unique.  Returns -1 when perm passes, else the first failing
+ * position j (for a range failure, the position of the bad entry). */
+
+typedef struct {
+    const str_ctx *c;
+    const void *perm;
+    int perm_u64;
+    uint64_t n, lo, hi;
+    int64_t bad;
+} check_job;
+
+static inline uint64_t perm_at(const void *perm, int perm_u64, uint64_t j)
+{
+    return perm_u64 ? ((const uint64_t *)perm)[j] : ((const uint32_t *)perm)[j];
+}
+
+static void *check_job_run(void *p)
+{
+    check_job *j = (check_job *)p;
+    j->bad = -1;
+    for (uint64_t k = j->lo; k < j->hi; k++) {
+        uint64_t q = perm_at(j->perm, j->perm_u64, k);
+        if (q >= j->n) {
+            j->bad = (int64_t)k;
+            return NULL;
+        }
+        if (k == 0)
+            continue;
+        uint64_t p0 = perm_at(j->perm, j->perm_u64, k - 1);
+        if (p0 >= j->n) {
+            j->bad = (int64_t)(k - 1);
+            return NULL;
+        }
+        int s = string_compare(j->c->bytes, j->c->offsets, p0, q);
+        if (s > 0 || (s == 0 && !(p0 < q))) {
+            j->bad = (int64_t)k;
+            return NULL;
+        }
+    }
+    return NULL;
+}
+
+int64_t oracle_check_sorted(const uint8_t *bytes, const uint64_t *offsets,
+                            uint64_t n, const void *perm, int perm_u64,
+                            int threads)
+{
+    if (n == 0)
+        return -1;
+    str_ctx c = {bytes, offsets};
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    if ((uint64_t)threads > n)
+        threads = (int)n;
+    pthread_t tid[256];
+    check_job jobs[256];
+    for (int t = 0; t < threads; t++) {
+        jobs[t] = (check_job){&c, perm, perm_u64, n,
+                              n * (uint64_t)t / (uint64_t)threads,
+                              n * (uint64_t)(t + 1) / (uint64_t)threads, -1};
+        pthread_create(&tid[t], NULL, check_job_run, &jobs[t]);
+    }
+    int64_t bad = -1;
+    for (int t = 0; t < threads; t++) {
+        pthread_join(tid[t], NULL);
+        if (bad < 0 && jobs[t].bad >= 0)
+            bad = jobs[t].bad;
+    }
+    return bad;
+}

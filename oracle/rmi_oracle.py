@@ -1,0 +1,156 @@
+"""Learned-bucketer (RMI) oracle -- TEST INFRASTRUCTURE ONLY.
+
+FP64 numpy restatement of the recursive-model index that steers the learned
+sort path.  The paper has no learned model: Huskysort's only requirement on a
+bucketing of the codes is the one it states for husky codes themselves
+(Section 3.2): whenever x > y the sort key of x must not be below that of y.
+A bucket function that is monotone non-decreasing in the code therefore leaves
+only equal-bucket elements to be ordered, which is exactly what the learned
+path relies on.  The model below is built so that monotonicity holds by
+construction, in FP64 here and in FP32 on the device:
+
+  feature    x(code) = ((code - cmin) >> shift) * 2**-24, shift chosen so the
+             shifted range fits in 24 bits (exact in FP32 and FP64);
+  root       y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, 1 -> 32 -> 32 -> 1,
+             with W1, W2, w3 >= 0 (projected after every SGD step), so y is
+             non-decreasing in x;
+  training   full-batch gradient descent on mean squared error against the
+             empirical CDF targets t_j = j / m of the sorted sample;
+  leaves     leaf(x) = clamp(floor(y(x) * L), 0, L - 1), L linear leaves;
+             leaf l is fitted by least squares to the sample points routed to
+             it, slope clamped >= 0, and its output is clamped into the band
+             [c_l, c_{l+1}] where c_l is the fraction of sample points routed
+             to leaves below l;
+  bucket     bucket(x) = min(B - 1, floor(pos(x) * B)).
+
+Nothing here is shared with the CUDA library.  The derivative of relu at 0 is
+taken as 0.
+"""
+
+import numpy as np
+
+HIDDEN = 32
+FEATURE_BITS = 24
+
+
+def feature_shift(cmin: int, cmax: int) -> int:
+    """Right shift that brings (cmax - cmin) below 2**24."""
+    span = int(cmax) - int(cmin)
+    return max(0, span.bit_length() - FEATURE_BITS)
+
+
+def feature(codes: np.ndarray, cmin: int, shift: int) -> np.ndarray:
+    """x = ((code - cmin) >> shift) * 2**-24 as float64 (exact)."""
+    c = codes.astype(np.uint64)
+    q = (c - np.uint64(cmin)) >> np.uint64(shift)
+    return q.astype(np.float64) * (2.0 ** -FEATURE_BITS)
+
+
+def init_params(seed: int = 0) -> dict:
+    """A monotone starting point: unit first-layer slopes with breakpoints
+    spread over [0, 1), small positive second layer, positive readout."""
+    rng = np.random.default_rng(seed)
+    W1 = np.ones(HIDDEN)
+    b1 = -np.arange(HIDDEN) / HIDDEN
+    W2 = rng.uniform(0.0, 2.0 / HIDDEN, size=(HIDDEN, HIDDEN))
+    b2 = np.zeros(HIDDEN)
+    w3 = np.full(HIDDEN, 1.0 / HIDDEN)
+    b3 = 0.0
+    return dict(W1=W1, b1=b1, W2=W2, b2=b2, w3=w3, b3=np.float64(b3))
+
+
+def forward(p: dict, x: np.ndarray):
+    """Root network output y for every x, plus the activations."""
+    z1 = np.outer(x, p["W1"]) + p["b1"]          # (m, 32)
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ p["W2"].T + p["b2"]                # (m, 32)
+    h2 = np.maximum(z2, 0.0)
+    y = h2 @ p["w3"] + p["b3"]                   # (m,)
+    return y, (z1, h1, z2, h2)
+
+
+def loss_and_grad(p: dict, x: np.ndarray, t: np.ndarray):
+    """Mean squared error (1/m) sum (y - t)^2 and its exact gradient by the
+    chain rule through both relu layers."""
+    m = x.shape[0]
+    y, (z1, h1, z2, h2) = forward(p, x)
+    r = y - t
+    loss = float(np.mean(r * r))
+    dy = 2.0 * r / m                             # dL/dy
+    g = {}
+    g["w3"] = h2.T @ dy
+    g["b3"] = np.float64(dy.sum())
+    dz2 = np.outer(dy, p["w3"]) * (z2 > 0.0)     # dL/dz2
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ p["W2"]) * (z1 > 0.0)           # dL/dz1
+    g["W1"] = dz1.T @ x
+    g["b1"] = dz1.sum(axis=0)
+    return loss, g
+
+
+def sgd_step(p: dict, g: dict, lr: float) -> dict:
+    """theta <- theta - lr * grad, then clamp the weights (not the biases) to
+    be non-negative so the root stays monotone."""
+    q = {k: p[k] - lr * g[k] for k in p}
+    for k in ("W1", "W2", "w3"):
+        q[k] = np.maximum(q[k], 0.0)
+    q["b3"] = np.float64(q["b3"])
+    return q
+
+
+def leaf_of(y: np.ndarray, leaves: int) -> np.ndarray:
+    """Leaf index clamp(floor(y * L), 0, L - 1)."""
+    v = np.floor(y * leaves)
+    return np.clip(v, 0, leaves - 1).astype(np.int64)
+
+
+def leaf_fit(x: np.ndarray, t: np.ndarray, leaf_start: np.ndarray):
+    """Least-squares line per leaf over contiguous point ranges.
+
+    leaf_start has L + 1 entries; leaf l owns points leaf_start[l] ..
+    leaf_start[l+1] - 1.  Returns (slope, intercept, band_lo, band_hi), each of
+    length L.  Normal equations: slope = (S Sxy - Sx Sy) / (S Sxx - Sx^2),
+    intercept = (Sy - slope Sx) / S.  A leaf with fewer than two points, no
+    spread in x, or a negative fitted slope gets slope 0 and intercept mean(t)
+    (or its band start when empty).  Bands: c_l = leaf_start[l] / m.
+    """
+    L = leaf_start.shape[0] - 1
+    m = leaf_start[-1]
+    slope = np.zeros(L)
+    icept = np.zeros(L)
+    lo = leaf_start[:-1].astype(np.float64) / max(m, 1)
+    hi = leaf_start[1:].astype(np.float64) / max(m, 1)
+    for l in range(L):
+        a, b = leaf_start[l], leaf_start[l + 1]
+        S = b - a
+        if S == 0:
+            icept[l] = lo[l]
+            continue
+        xs, ts = x[a:b], t[a:b]
+        Sx, Sy = xs.sum(), ts.sum()
+        Sxx, Sxy = (xs * xs).sum(), (xs * ts).sum()
+        den = S * Sxx - Sx * Sx
+        if S >= 2 and den > 0.0:
+            k = (S * Sxy - Sx * Sy) / den
+        else:
+            k = 0.0
+        if k < 0.0:
+            k = 0.0
+        slope[l] = k
+        icept[l] = (Sy - k * Sx) / S
+    return slope, icept, lo, hi
+
+
+def position(p: dict, leaf_params, x: np.ndarray, leaves: int) -> np.ndarray:
+    """pos(x) = clamp(a_l x + b_l, c_l, c_{l+1}) with l = leaf(root(x))."""
+    slope, icept, lo, hi = leaf_params
+    y, _ = forward(p, x)
+    l = leaf_of(y, leaves)
+    return np.clip(slope[l] * x + icept[l], lo[l], hi[l])
+
+
+def bucket_of(pos: np.ndarray, buckets: int) -> np.ndarray:
+    """bucket = min(B - 1, floor(pos * B)), pos in [0, 1]."""
+    b = np.floor(pos * buckets).astype(np.int64)
+    return np.clip(b, 0, buckets - 1)

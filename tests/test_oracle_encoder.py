@@ -1,0 +1,109 @@
+"""Pins for the oracle's encoder (Algorithm 4 and Algorithms 2/3).
+
+The encoder is pinned to things other than itself: codes worked by hand
+(tests/golden/husky_codes.txt), the order property of Section 3.2 brute-forced
+over every short string on small alphabets, the perfectness claim of Section 5
+("for ASCII strings, it is nine"), and the exactness reading for NUL bytes.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from conftest import literal, read_golden
+
+
+def _code(coder, s):
+    return oracle.ascii_to_long(s) if coder == "ASCII7" else oracle.byte_to_long(s)
+
+
+@pytest.mark.parametrize("row", read_golden("husky_codes.txt"),
+                         ids=lambda r: f"{r[0]}:{r[1]}")
+def test_hand_worked_codes(row):
+    coder, text, expected = row[0], literal(row[1]), int(row[2], 16)
+    assert _code(coder, text) == expected
+
+
+def _all_strings(alphabet, max_len, min_len=0):
+    out = []
+    for L in range(min_len, max_len + 1):
+        out.extend(bytes(t) for t in itertools.product(alphabet, repeat=L))
+    return out
+
+
+ALPHABETS_ASCII = [b"abcd", bytes([0x00, 0x01, 0x7E, 0x7F])]
+ALPHABETS_BYTE = [b"abcd", bytes([0x00, 0x01, 0x80, 0xFF])]
+
+
+@pytest.mark.parametrize("coder,alphabet",
+                         [("ASCII7", a) for a in ALPHABETS_ASCII] +
+                         [("BYTE8", a) for a in ALPHABETS_BYTE])
+def test_order_property_pairwise(coder, alphabet):
+    """Section 3.2 with p applying only to ties: for every ordered pair,
+    code(a) < code(b) implies a < b, and a < b implies code(a) <= code(b);
+    a == b implies equal codes.  85 strings, 7,225 pairs per alphabet."""
+    strs = _all_strings(alphabet, 3)
+    codes = [_code(coder, s) for s in strs]
+    for a, ca in zip(strs, codes):
+        for b, cb in zip(strs, codes):
+            if ca < cb:
+                assert a < b, (a, b)
+            if a < b:
+                assert ca <= cb, (a, b)
+            if a == b:
+                assert ca == cb
+
+
+@pytest.mark.parametrize("coder,alphabet,lengths", [
+    ("ASCII7", b"ab", (8, 11)),
+    ("BYTE8", b"ab", (7, 10)),
+    ("ASCII7", bytes([0x00, 0x7F]), (7, 10)),
+])
+def test_order_property_across_truncation(coder, alphabet, lengths):
+    """Strings straddling the 9-char (8-byte) cap: codes are non-decreasing
+    along the sorted order, which is equivalent to the pairwise property."""
+    strs = sorted(_all_strings(alphabet, lengths[1], lengths[0]))
+    codes = np.array([_code(coder, s) for s in strs], dtype=np.uint64)
+    assert np.all(codes[1:] >= codes[:-1])
+
+
+def test_ascii_perfect_up_to_nine():
+    """Section 5: nine ASCII chars fit; distinct NUL-free strings of length
+    <= 9 never collide (all 1,023 strings over {a, b})."""
+    strs = _all_strings(b"ab", 9)
+    codes = {oracle.ascii_to_long(s) for s in strs}
+    assert len(codes) == len(strs)
+
+
+def test_byte8_perfect_up_to_eight():
+    strs = _all_strings(bytes([0x01, 0xFF]), 8)
+    codes = {oracle.byte_to_long(s) for s in strs}
+    assert len(codes) == len(strs)
+
+
+def test_nul_shares_code_and_is_not_exact():
+    """'a' and 'a\\0' share a code, so exactness must look at the last byte."""
+    w = workloads.from_strings([b"a", b"a\x00", b"", b"abcdefghi",
+                                b"abcdefghij", b"\x00"])
+    codes, exact, perfect = oracle.encode(w.bytes, w.offsets, oracle.CODER_ASCII7)
+    assert codes[0] == codes[1]
+    assert list(exact) == [1, 0, 1, 1, 0, 0]
+    assert not perfect
+
+
+def test_perfect_flag_short_strings():
+    w = workloads.from_strings([b"abc", b"xyz", b"", b"abcdefghi"])
+    _, exact, perfect = oracle.encode(w.bytes, w.offsets, oracle.CODER_ASCII7)
+    assert perfect and exact.all()
+    _, _, perfect8 = oracle.encode(w.bytes, w.offsets, oracle.CODER_BYTE8)
+    assert not perfect8  # 9 chars exceed the 8-byte cap
+
+
+def test_array_encoder_matches_scalar():
+    w = workloads.generate(1, 2000, 11)
+    codes, _, _ = oracle.encode(w.bytes, w.offsets, oracle.CODER_ASCII7)
+    for i in range(0, 2000, 37):
+        assert codes[i] == oracle.ascii_to_long(w.string(i))
