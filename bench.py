@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 Huskysort string argsort.
+
+One step = one full stable argsort (encode, radix sort of the codes, tie
+fix-up) of the 1e7-string English-like workload (Zipf(1.1) draws over a
+50,000-word synthetic vocabulary), inputs resident in HBM.  Prints one JSON
+line.  `--impl reference` times the CPU oracle (the plain stable merge sort)
+on the host cores instead.
+
+Under torchrun (N > 1) every rank sorts its own copy of the workload
+(replicas: a single sort has no shard-local form without an exchange step);
+value = strings sorted by all ranks / max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "strings sorted/sec (M keys/s) and % of HBM roofline, learned/batched vs plain radix"
+UNIT = "M keys/s"
+DEFAULT_WORKLOAD = "zipf_words_1e7"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--mode", default="plain", choices=["plain", "learned"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--stats", default=None, help="write per-kernel stats JSON here")
+    return p.parse_args()
+
+
+# ---- distributed plumbing ---------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, local, backend="nccl"):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks -------------------------------------------------------------------
+
+REASONS = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) of the bench GPU during the timed region."""
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, seen = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(REASONS[1:], r[5:9]):
+                if v.lower() in ("active", "0x1", "1", "yes"):
+                    seen.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(seen)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def profile_traffic(kernel_source: str, key: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        with open(os.path.join(ROOT, kernel_source), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    entry = data.get(key)
+    if not entry or entry.get("source_sha256") != digest:
+        return None
+    return entry.get("dram_bytes_per_launch_full")
+
+
+# ---- our arm --------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    import workloads
+    import paper_2012_00866_gb300 as hs
+
+    dist_init(world, local)
+    device = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(device)
+    hs.load()
+    mode = hs.MODE_LEARNED if args.mode == "learned" else hs.MODE_PLAIN
+
+    w = workloads.standard(args.workload)
+    n = w.n
+    data = torch.from_numpy(w.bytes).to(device)
+    off = torch.from_numpy(w.offsets.view(np.int64)).to(device)
+    perm = torch.empty(n, dtype=torch.int32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    for _ in range(args.warmup):
+        hs.argsort_device(data, off, mode=mode, out=perm)
+    torch.cuda.synchronize(device)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(device).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    hs.stats_enable(True)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(device)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hs.argsort_device(data, off, mode=mode, out=perm)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize(device)
+    barrier(world)
+    clock_info = clocks.stop()
+    kstats = hs.stats_read()
+    hs.stats_enable(False)
+
+    ms = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(ms, world, device)
+    value = n * world / (ms / 1e3) / 1e6
+
+    # end to end through the public API: pinned host inputs in, host perm out
+    h_data = torch.from_numpy(w.bytes).pin_memory()
+    h_off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        hs.argsort(h_data, h_off, mode=mode)
+    torch.cuda.synchronize(device)
+    barrier(world)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        host_perm = hs.argsort(h_data, h_off, mode=mode)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    barrier(world)
+    e2e = sum(e2e_ms) / len(e2e_ms)
+    e2e = max_over_ranks(e2e, world, device)
+    e2e_value = n * world / (e2e / 1e3) / 1e6
+    del host_perm
+
+    peaks, peak_src = measured_peaks()
+    os_stat = kstats.get("onesweep", {})
+    launches = sum(v["launches"] for v in kstats.values())
+    roofline = None
+    if os_stat.get("launches"):
+        achieved = os_stat["algo_bytes"] / (os_stat["total_ms"] / 1e3) / 1e9
+        per_launch = os_stat["algo_bytes"] / os_stat["launches"]
+        roofline = {"kernel": "onesweep_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(achieved / peaks["hbm_gbs"], 4),
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                    "algo_bytes_per_launch": per_launch,
+                    "launch_ms": round(os_stat["total_ms"] / os_stat["launches"], 5),
+                    "traffic": profile_traffic("paper_2012_00866_gb300/csrc/sort.cu", f"onesweep/{args.workload}")}
+
+    stages = {k: {"launches_per_step": v["launches"] / args.steps,
+                  "ms_per_step": round(v["total_ms"] / args.steps, 4),
+                  "GBps": round(v["algo_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1) if v["total_ms"] > 0 else None}
+              for k, v in kstats.items() if v["launches"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        oracle.stable_argsort(w.bytes, w.offsets, threads=threads)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(n / dt / 1e6, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the full {args.workload} workload ({n} strings), one run, "
+                         f"stable merge sort on {threads} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "bytes": int(w.bytes.size),
+                       "mode": args.mode, "index": "u32", "coder": "auto(ascii7)",
+                       "l2": "flushed by a 256 MiB write before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(w.bytes.nbytes + w.offsets.nbytes),
+                    "d2h_bytes_per_step": int(n * 4), "ms_per_step": round(e2e, 3)},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clock_info,
+            "stages": stages,
+        }
+        print(json.dumps(line), flush=True)
+        if args.stats:
+            with open(args.stats, "w") as f:
+                json.dump({"kernels": kstats, "steps": args.steps, "step_ms": step_ms}, f, indent=1)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---- reference arm: the oracle on the host cores --------------------------------
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    w = workloads.standard(args.workload)
+    n = w.n
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.stable_argsort(w.bytes, w.offsets, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.stable_argsort(w.bytes, w.offsets, threads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = sum(times) / len(times) * 1e3
+    value = n / (ms / 1e3) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "bytes": int(w.bytes.size), "mode": "oracle",
+                   "index": "u32", "parallelism": "host threads"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"the full {args.workload} workload each step"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

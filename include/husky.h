@@ -1,0 +1,174 @@
+/*
+ * husky.h -- C ABI of the GB300 Huskysort string-argsort library (libhusky.so).
+ *
+ * The method (Hillyard, Liaozheng, K R, "Huskysort", arXiv 2012.00866):
+ *   Step 1  encode every element into a 64-bit order-preserving "husky code"
+ *           (Section 3.1 Step 1; Algorithm 4 stringToLong; Section 4.3
+ *           asciiToLong and its constants);
+ *   Step 2  sort the codes, moving the elements with them (Section 3.1
+ *           Step 2, the "object swap");
+ *   Step 3  if the coding was not perfect, fix the remaining inversions by
+ *           comparing the elements themselves (Section 3.1 Step 3,
+ *           Algorithm 1; skipped when perfect, Section 3.4).
+ * Here Step 2 is a stable LSD radix sort of (code, index) pairs and Step 3
+ * only touches runs of equal codes, the only places inversions can remain
+ * when the coder is order preserving (Section 3.2 with p restricted to ties).
+ *
+ * Data model (all entry points)
+ *   d_bytes    device pointer to the concatenated string bytes.
+ *   d_offsets  device pointer to n + 1 uint64 offsets, non-decreasing; string i
+ *              is d_bytes[d_offsets[i] .. d_offsets[i+1]).  Bytes compare as
+ *              unsigned; a proper prefix is smaller.
+ *   Every pointer argument named d_* is device memory owned by the caller;
+ *   the library never frees or retains it past the call.  h_* pointers are
+ *   host memory.
+ *   d_ws/ws_bytes  caller-owned device scratch of at least the size reported
+ *              by hs_workspace_size (or hs_batched_workspace_size); its
+ *              contents on entry are irrelevant and undefined on return.
+ *   stream     a cudaStream_t (passed as void*; NULL = legacy default stream).
+ *              All device work is enqueued on it.  The calls synchronise this
+ *              stream internally (to read small device-side counters) and
+ *              return only after all their work has finished, so the status
+ *              they return is final.
+ *
+ * Errors: every entry point returns an hs_status; HS_OK is 0, errors are
+ * negative.  hs_last_error() returns a message for the calling host thread's
+ * most recent failure.  Device-side waits are bounded: a wait that gives up
+ * reports HS_ERR_TIMEOUT; the library never traps or asserts on the device.
+ */
+#ifndef HUSKY_H
+#define HUSKY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HS_API __attribute__((visibility("default")))
+#else
+#define HS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_INVALID_ARG = -1,  /* bad pointer, size, enum, or offsets       */
+    HS_ERR_CODER_DOMAIN = -2, /* ASCII7 coder given a byte >= 0x80 in the
+                                 first 9 bytes of a string                  */
+    HS_ERR_OOM = -3,          /* host allocation failed                     */
+    HS_ERR_CUDA = -4,         /* a CUDA runtime call failed                 */
+    HS_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up         */
+    HS_ERR_INTERNAL = -6,     /* an internal consistency check failed       */
+    HS_ERR_WORKSPACE = -7     /* ws_bytes smaller than required             */
+} hs_status;
+
+/* Coders (Algorithm 4 parameters).
+ *   HS_CODER_ASCII7  bitWidth 7, maxLength 64/7 = 9, mask 0x7F (asciiToLong,
+ *                    Section 4.3).  Order preserving only on bytes < 0x80.
+ *   HS_CODER_BYTE8   bitWidth 8, maxLength 8, no mask: order preserving on
+ *                    all bytes (this library's coder for arbitrary bytes).
+ *   HS_CODER_AUTO    ASCII7, re-encoding with BYTE8 when any string has a
+ *                    byte >= 0x80 among its first 9 bytes. */
+typedef enum { HS_CODER_AUTO = 0, HS_CODER_ASCII7 = 1, HS_CODER_BYTE8 = 2 } hs_coder;
+
+/* Sort strategies for Step 2; both give the identical permutation.
+ *   HS_MODE_PLAIN    LSD radix sort of the 64-bit codes (8-bit digits,
+ *                    digits constant over all keys skipped).
+ *   HS_MODE_LEARNED  a learned CDF model (RMI: FP32 1->32->32->1 root,
+ *                    linear leaves) trained on a sample of the codes picks a
+ *                    monotone bucket per code; the pairs are partitioned by
+ *                    bucket and each bucket sorted by code.  Falls back to
+ *                    PLAIN internally when the buckets come out too uneven. */
+typedef enum { HS_MODE_PLAIN = 0, HS_MODE_LEARNED = 1 } hs_mode;
+
+/* Index type of the output permutation. */
+typedef enum { HS_U32 = 0, HS_U64 = 1 } hs_index_t;
+
+/* Largest n accepted by hs_argsort (the internal payload keeps one flag bit
+ * beside a 31-bit index). */
+#define HS_MAX_N ((uint64_t)0x7FFFFFFF)
+
+/* hs_encode -- Step 1 alone (Algorithms 2, 3 and 4).
+ *   d_codes      out, device, n uint64: code of string i.
+ *   h_all_exact  out, host, nullable: 1 if every string is exactly
+ *                represented (length <= maxLength and, when non-empty, last
+ *                byte != 0: "a" and "a\0" share a code), else 0 -- the
+ *                paper's "perfect" flag (Algorithm 3).
+ *   coder        hs_coder; with HS_CODER_AUTO the coder actually used is
+ *                written to *h_coder_used when that pointer is non-NULL.
+ * Returns HS_ERR_CODER_DOMAIN for HS_CODER_ASCII7 on bytes >= 0x80. */
+HS_API hs_status hs_encode(const uint8_t *d_bytes, const uint64_t *d_offsets,
+                    uint64_t n, int coder, uint64_t *d_codes,
+                    int *h_all_exact, int *h_coder_used, void *d_ws,
+                    size_t ws_bytes, void *stream);
+
+/* hs_argsort -- Steps 1-3: the stable argsort of n strings.
+ *   d_perm   out, device, n entries of uint32 (out_t = HS_U32) or uint64
+ *            (HS_U64): d_perm[k] is the index of the k-th smallest string;
+ *            equal strings appear in increasing index order.  This is the
+ *            unique stable ascending argsort under unsigned-byte
+ *            lexicographic order.
+ *   mode     hs_mode; coder hs_coder.
+ *   n        0 <= n <= HS_MAX_N; n = 0 is a no-op. */
+HS_API hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets,
+                     uint64_t n, int mode, int coder, int out_t, void *d_perm,
+                     void *d_ws, size_t ws_bytes, void *stream);
+
+/* hs_argsort_batched -- many independent sorts in one call.
+ *   d_seg_offsets  device, num_segs + 1 uint64 string-index boundaries:
+ *                  instance s owns strings seg_offsets[s] ..
+ *                  seg_offsets[s+1] - 1 (non-decreasing, last = n).
+ *   d_perm         out, device, n uint32: for instance s, entries
+ *                  d_perm[seg_offsets[s] .. seg_offsets[s+1]) hold the stable
+ *                  argsort of that instance as LOCAL indices (0-based within
+ *                  the instance).
+ *   Each instance must hold fewer than 2^31 strings; n may exceed 2^32. */
+HS_API hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets,
+                             const uint64_t *d_seg_offsets, uint64_t num_segs,
+                             uint64_t n, int coder, uint32_t *d_perm,
+                             void *d_ws, size_t ws_bytes, void *stream);
+
+/* Workspace needed by hs_encode / hs_argsort for n strings (mode, out_t as
+ * in hs_argsort).  total_bytes (the byte-buffer size) is accepted for
+ * forward compatibility and currently unused.  Writes *out; HS_OK. */
+HS_API hs_status hs_workspace_size(uint64_t n, uint64_t total_bytes, int mode,
+                            int out_t, size_t *out);
+
+/* Workspace needed by hs_argsort_batched for n strings in num_segs
+ * instances. */
+HS_API hs_status hs_batched_workspace_size(uint64_t n, uint64_t num_segs,
+                                    size_t *out);
+
+/* Per-kernel timing (no counterpart in the paper: measurement support).
+ * While enabled, every kernel the library launches is bracketed by CUDA
+ * events recorded on the caller's stream; after each call the elapsed times
+ * are added to a process-wide table, one row per kernel kind, with the
+ * launch count and the algorithmic bytes the launches had to move (inputs
+ * read once plus outputs written once).  Enabling resets the table. */
+typedef struct {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+    double algo_bytes;
+} hs_kernel_stat;
+
+HS_API hs_status hs_stats_enable(int on);
+
+/* Copies up to max rows into out (host) and writes the number of rows that
+ * exist to *count. */
+HS_API hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count);
+
+/* Message describing the calling thread's last failure ("" if none).  The
+ * pointer stays valid until the next library call on this thread. */
+HS_API const char *hs_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+HS_API int hs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUSKY_H */

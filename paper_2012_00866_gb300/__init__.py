@@ -1,0 +1,250 @@
+"""GB300 Huskysort: stable argsort of byte strings on one GPU.
+
+Thin ctypes binding over the C ABI in include/husky.h (libhusky.so, built
+in-tree by ``paper_2012_00866_gb300.build``).  This module only marshals
+arguments: every step of the sort runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+Strings are passed as a uint8 byte tensor plus an int64 (bit-identical to
+uint64) offsets tensor of n + 1 entries; string i is
+bytes[offsets[i]:offsets[i+1]].
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhusky.so")
+
+# hs_status
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CODER_DOMAIN = -2
+ERR_OOM = -3
+ERR_CUDA = -4
+ERR_TIMEOUT = -5
+ERR_INTERNAL = -6
+ERR_WORKSPACE = -7
+# hs_coder
+CODER_AUTO, CODER_ASCII7, CODER_BYTE8 = 0, 1, 2
+# hs_mode
+MODE_PLAIN, MODE_LEARNED = 0, 1
+# hs_index_t
+U32, U64 = 0, 1
+
+MAX_N = 0x7FFFFFFF
+
+# Every symbol include/husky.h declares (checked by the export test).
+EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
+           "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
+           "hs_last_error", "hs_version")
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
+
+_lib = None
+
+
+class HuskyError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"hs_status {status}: {message}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libhusky.so (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        from . import build as _build
+        _build.build()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libhusky.so not found at {p}")
+    lib = ctypes.CDLL(p)
+    vp, u64, ci, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t
+    lib.hs_encode.restype = ci
+    lib.hs_encode.argtypes = [vp, vp, u64, ci, vp, vp, vp, vp, sz, vp]
+    lib.hs_argsort.restype = ci
+    lib.hs_argsort.argtypes = [vp, vp, u64, ci, ci, ci, vp, vp, sz, vp]
+    lib.hs_argsort_batched.restype = ci
+    lib.hs_argsort_batched.argtypes = [vp, vp, vp, u64, u64, ci, vp, vp, sz, vp]
+    lib.hs_workspace_size.restype = ci
+    lib.hs_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
+    lib.hs_batched_workspace_size.restype = ci
+    lib.hs_batched_workspace_size.argtypes = [u64, u64, ctypes.POINTER(sz)]
+    lib.hs_stats_enable.restype = ci
+    lib.hs_stats_enable.argtypes = [ci]
+    lib.hs_stats_read.restype = ci
+    lib.hs_stats_read.argtypes = [ctypes.POINTER(KernelStat), ci, ctypes.POINTER(ci)]
+    lib.hs_last_error.restype = ctypes.c_char_p
+    lib.hs_last_error.argtypes = []
+    lib.hs_version.restype = ci
+    lib.hs_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        msg = load().hs_last_error().decode(errors="replace")
+        raise HuskyError(status, msg)
+
+
+def _stream_handle(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def workspace_size(n: int, mode: int = MODE_PLAIN, out_t: int = U32,
+                   total_bytes: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().hs_workspace_size(n, total_bytes, mode, out_t, ctypes.byref(out)))
+    return int(out.value)
+
+
+def batched_workspace_size(n: int, num_segs: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().hs_batched_workspace_size(n, num_segs, ctypes.byref(out)))
+    return int(out.value)
+
+
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """A cached device scratch buffer of at least nbytes (grown on demand)."""
+    dev = torch.device(device)
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        _ws_cache.pop(key, None)
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        _ws_cache[key] = buf
+    return buf
+
+
+def free_workspace():
+    _ws_cache.clear()
+
+
+def _as_device_inputs(data: torch.Tensor, offsets: torch.Tensor):
+    if data.dtype != torch.uint8:
+        raise TypeError("bytes must be a uint8 tensor")
+    if offsets.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("offsets must be an int64/uint64 tensor")
+    if not data.is_cuda or not offsets.is_cuda:
+        raise ValueError("device tensors expected")
+    if data.numel() == 0:  # the library wants a valid pointer even for no bytes
+        data = torch.zeros(16, dtype=torch.uint8, device=offsets.device)
+    return data.contiguous(), offsets.contiguous()
+
+
+def encode(data: torch.Tensor, offsets: torch.Tensor, coder: int = CODER_AUTO,
+           stream=None):
+    """Step 1: (codes int64 tensor holding the uint64 codes, all_exact bool,
+    coder used)."""
+    data, offsets = _as_device_inputs(data, offsets)
+    n = offsets.numel() - 1
+    codes = torch.empty(max(n, 0), dtype=torch.int64, device=offsets.device)
+    ws = workspace(workspace_size(0), offsets.device)
+    exact = ctypes.c_int(0)
+    used = ctypes.c_int(0)
+    _check(load().hs_encode(_ptr(data), _ptr(offsets), n, coder, _ptr(codes),
+                            ctypes.byref(exact), ctypes.byref(used), _ptr(ws),
+                            ws.numel(), _stream_handle(stream)))
+    return codes, bool(exact.value), int(used.value)
+
+
+def argsort_device(data: torch.Tensor, offsets: torch.Tensor,
+                   mode: int = MODE_PLAIN, coder: int = CODER_AUTO,
+                   index_u64: bool = False, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Stable argsort of device-resident strings; returns a device tensor
+    (int32 for uint32 indices, int64 for uint64)."""
+    data, offsets = _as_device_inputs(data, offsets)
+    n = offsets.numel() - 1
+    dt = torch.int64 if index_u64 else torch.int32
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=dt, device=offsets.device)
+    elif out.dtype != dt or out.numel() != n or not out.is_cuda:
+        raise ValueError("out has the wrong dtype, size or device")
+    out_t = U64 if index_u64 else U32
+    need = workspace_size(n, mode, out_t)
+    ws = workspace(need, offsets.device)
+    _check(load().hs_argsort(_ptr(data), _ptr(offsets), n, mode, coder, out_t,
+                             _ptr(out), _ptr(ws), ws.numel(),
+                             _stream_handle(stream)))
+    return out
+
+
+def argsort(data: torch.Tensor, offsets: torch.Tensor, mode: int = MODE_PLAIN,
+            coder: int = CODER_AUTO, index_u64: bool = False,
+            device="cuda", stream=None) -> torch.Tensor:
+    """Stable argsort of strings held in host or device tensors.
+
+    Host (CPU) inputs are copied to the device (non-blocking when pinned),
+    sorted there, and the permutation is copied back into host memory;
+    device inputs are sorted in place on the device."""
+    if data.is_cuda and offsets.is_cuda:
+        return argsort_device(data, offsets, mode, coder, index_u64, stream=stream)
+    d_data = data.to(device, non_blocking=True)
+    d_off = offsets.to(device, non_blocking=True)
+    perm = argsort_device(d_data, d_off, mode, coder, index_u64, stream=stream)
+    host = torch.empty(perm.shape, dtype=perm.dtype, pin_memory=True)
+    host.copy_(perm, non_blocking=True)
+    (stream or torch.cuda.current_stream()).synchronize()
+    return host
+
+
+def argsort_batched(data: torch.Tensor, offsets: torch.Tensor,
+                    seg_offsets: torch.Tensor, coder: int = CODER_AUTO,
+                    stream=None) -> torch.Tensor:
+    """Independent stable argsorts of the instances delimited by seg_offsets
+    (string-index boundaries); returns local indices (int32) laid out like
+    the strings."""
+    data, offsets = _as_device_inputs(data, offsets)
+    if seg_offsets.dtype not in (torch.int64, torch.uint64) or not seg_offsets.is_cuda:
+        raise TypeError("seg_offsets must be an int64 device tensor")
+    seg_offsets = seg_offsets.contiguous()
+    n = offsets.numel() - 1
+    num_segs = seg_offsets.numel() - 1
+    out = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+    ws = workspace(batched_workspace_size(n, num_segs), offsets.device)
+    _check(load().hs_argsort_batched(_ptr(data), _ptr(offsets), _ptr(seg_offsets),
+                                     num_segs, n, coder, _ptr(out), _ptr(ws),
+                                     ws.numel(), _stream_handle(stream)))
+    return out
+
+
+def stats_enable(on: bool = True):
+    """Start (and reset) or stop per-kernel event timing inside the library."""
+    _check(load().hs_stats_enable(1 if on else 0))
+
+
+def stats_read() -> dict:
+    """{kernel kind: {"launches", "total_ms", "algo_bytes"}} since enabling."""
+    rows = (KernelStat * 64)()
+    count = ctypes.c_int(0)
+    _check(load().hs_stats_read(rows, 64, ctypes.byref(count)))
+    out = {}
+    for r in rows[: min(count.value, 64)]:
+        out[r.name.decode()] = dict(launches=int(r.launches), total_ms=float(r.total_ms),
+                                    algo_bytes=float(r.algo_bytes))
+    return out
+
+
+def version() -> int:
+    return int(load().hs_version())

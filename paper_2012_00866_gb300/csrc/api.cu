@@ -1,0 +1,598 @@
+// C ABI entry points and host-side orchestration of the three steps.
+//
+// hs_argsort(PLAIN):
+//   encode (codes, non-exact bits, digit histograms)   -- Step 1
+//   plan   (bucket bases, which digits vary)            -- host reads flags
+//   onesweep passes over the varying digits             -- Step 2
+//   if not perfect: tie detection, then large-run
+//   refinement rounds, then CTA and warp run sorts       -- Step 3
+// The caller owns every device buffer; scratch is carved from d_ws.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "husky.h"
+#include "hs_internal.h"
+
+namespace hs {
+namespace {
+
+thread_local std::string g_last_error;
+
+hs_status fail(hs_status st, const char *msg) {
+    g_last_error = msg;
+    return st;
+}
+
+hs_status fail_cuda(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return HS_ERR_CUDA;
+}
+
+// ---- per-kernel timing (hs_stats_*) ----------------------------------------
+
+enum KernelKind {
+    kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
+    kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKNumKinds
+};
+const char *const kKindNames[kKNumKinds] = {
+    "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
+    "run_scan", "refine_keys", "push_constant_runs", "histogram"};
+
+struct StatsTable {
+    std::mutex mu;
+    bool enabled = false;
+    uint64_t launches[kKNumKinds] = {};
+    double ms[kKNumKinds] = {};
+    double bytes[kKNumKinds] = {};
+    std::vector<cudaEvent_t> pool;   // reused events
+};
+StatsTable g_stats;
+
+struct PendingStat {
+    int kind;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+cudaEvent_t pooled_event() {
+    std::lock_guard<std::mutex> g(g_stats.mu);
+    if (!g_stats.pool.empty()) {
+        cudaEvent_t e = g_stats.pool.back();
+        g_stats.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+constexpr size_t kAlign = 256;
+constexpr int kNumCounters = 4096;
+constexpr int kHistPasses = 12;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    }
+};
+
+// Workspace layout of hs_argsort / hs_encode for n strings.
+struct Layout {
+    size_t flags, hist, bucket, counters;  // control block (zeroed per call)
+    size_t control_end;
+    size_t codes_a, codes_b, vals_a, vals_b, segs_a, segs_b, bits;
+    size_t lb_a, lb_b, lb_tie;
+    size_t q_small, q_medium, q_large_a, q_large_b, run_base;
+    uint64_t cap_small, cap_medium, cap_large;
+    size_t total;
+};
+
+Layout make_layout(uint64_t n) {
+    Layout L{};
+    Carver c;
+    L.flags = c.take(sizeof(DevFlags));
+    L.hist = c.take(kHistPasses * kBins * sizeof(unsigned long long));
+    L.bucket = c.take(kHistPasses * kBins * sizeof(unsigned long long));
+    L.counters = c.take(kNumCounters * sizeof(unsigned int));
+    L.control_end = c.off;
+    L.codes_a = c.take(n * 8);
+    L.codes_b = c.take(n * 8);
+    L.vals_a = c.take(n * 4);
+    L.vals_b = c.take(n * 4);
+    L.segs_a = c.take(n * 4);
+    L.segs_b = c.take(n * 4);
+    L.bits = c.take(((n + 31) / 32) * 4);
+    const uint64_t tiles = sort_tiles(n);
+    L.lb_a = c.take(tiles * kBins * 8);
+    L.lb_b = c.take(tiles * kBins * 8);
+    L.lb_tie = c.take(tiles * 8);
+    L.cap_small = n / 2 + 1;
+    L.cap_medium = n / (kSmallMax + 1) + 1;
+    L.cap_large = n / (kMediumMax + 1) + 1;
+    L.q_small = c.take(L.cap_small * sizeof(RunEntry));
+    L.q_medium = c.take(L.cap_medium * sizeof(RunEntry));
+    L.q_large_a = c.take(L.cap_large * sizeof(RunEntry));
+    L.q_large_b = c.take(L.cap_large * sizeof(RunEntry));
+    L.run_base = c.take((L.cap_large + 1) * 8);
+    L.total = c.off;
+    return L;
+}
+
+int num_sms_cached() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms;
+}
+
+// Per-call execution context.
+struct Ctx {
+    cudaStream_t s;
+    char *ws;
+    Layout L;
+    int sms;
+    DevFlags *d_flags;
+    unsigned int *d_counters;
+    int next_counter = 0;
+    DevFlags h;  // last host copy of the flags
+
+    template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(ws + off); }
+
+    cudaError_t counter(unsigned int **out) {
+        if (next_counter >= kNumCounters) {
+            cudaError_t e = cudaMemsetAsync(d_counters, 0, kNumCounters * sizeof(unsigned int), s);
+            if (e != cudaSuccess) return e;
+            next_counter = 0;
+        }
+        *out = d_counters + next_counter++;
+        return cudaSuccess;
+    }
+
+    cudaError_t read_flags() {
+        cudaError_t e = cudaMemcpyAsync(&h, d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return e;
+        return cudaStreamSynchronize(s);
+    }
+
+    // Launch through f(), bracketed by events when timing is enabled.
+    std::vector<PendingStat> pending;
+    bool timing = false;
+    template <typename F> cudaError_t timed(int kind, double bytes, F f) {
+        if (!timing) return f();
+        PendingStat p{kind, bytes, pooled_event(), pooled_event()};
+        cudaEventRecord(p.a, s);
+        cudaError_t e = f();
+        cudaEventRecord(p.b, s);
+        pending.push_back(p);
+        return e;
+    }
+
+    // Called once the stream is idle: fold event times into the table.
+    void flush_stats() {
+        if (pending.empty()) return;
+        cudaStreamSynchronize(s);
+        std::lock_guard<std::mutex> g(g_stats.mu);
+        for (auto &p : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && g_stats.enabled) {
+                g_stats.launches[p.kind] += 1;
+                g_stats.ms[p.kind] += ms;
+                g_stats.bytes[p.kind] += p.bytes;
+            }
+            g_stats.pool.push_back(p.a);
+            g_stats.pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    ~Ctx() { flush_stats(); }
+};
+
+#define HS_TRY(expr, where)                               \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return fail_cuda(_e, where); \
+    } while (0)
+
+hs_status device_error_status(const DevFlags &h) {
+    if (h.error & kErrOffsets) return fail(HS_ERR_INVALID_ARG, "offsets are decreasing or exceed offsets[n]");
+    if (h.error & kErrTimeout) return fail(HS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (h.error) return fail(HS_ERR_INTERNAL, "device-side consistency check failed");
+    return HS_OK;
+}
+
+// Step 1 into ctx buffers; resolves HS_CODER_AUTO.  On return ctx.h holds the
+// flags and *used the coder actually used.
+hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int coder,
+                     uint64_t *codes, uint32_t *bits, bool hist, int *used) {
+    int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : HS_CODER_ASCII7;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
+        c.next_counter = 0;
+        const double enc_bytes = 8.0 * (n + 1) + 8.0 * n + (bits ? n / 8.0 : 0.0);
+        HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
+                   return launch_encode(u, bytes, offsets, n, codes, bits,
+                                        hist ? c.at<unsigned long long>(c.L.hist) : nullptr, c.d_flags, c.sms,
+                                        c.s);
+               }),
+               "encode");
+        if (hist)
+            HS_TRY(c.timed(kKPlan, 8.0 * kBins * 16, [&] {
+                       return launch_plan(c.at<unsigned long long>(c.L.hist), 8, n,
+                                          c.at<unsigned long long>(c.L.bucket), c.d_flags, c.s);
+                   }),
+                   "plan");
+        HS_TRY(c.read_flags(), "encode sync");
+        hs_status st = device_error_status(c.h);
+        if (st != HS_OK) return st;
+        if (u == HS_CODER_ASCII7 && c.h.domain) {
+            if (coder == HS_CODER_ASCII7)
+                return fail(HS_ERR_CODER_DOMAIN, "ASCII7 coder: a byte >= 0x80 among the first 9 bytes");
+            u = HS_CODER_BYTE8;  // AUTO: the byte coder is order preserving on all bytes
+            continue;
+        }
+        break;
+    }
+    *used = u;
+    return HS_OK;
+}
+
+// Runs the active radix passes over (keys, vals) pairs.  Returns the index
+// (0 or 1) of the buffers holding the result when the result is not written
+// to `final_out`.
+struct SortBufs {
+    uint64_t *keys[2];
+    uint32_t *vals[2];
+    uint32_t *segs[2];
+};
+
+hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passes, int npasses,
+                     bool segmented, const uint32_t *flag_bits, bool synth_first, void *final_out,
+                     OutMode final_mode, bool keep_keys) {
+    uint64_t *lb[2] = {c.at<uint64_t>(c.L.lb_a), c.at<uint64_t>(c.L.lb_b)};
+    HS_TRY(cudaMemsetAsync(lb[0], 0, sort_tiles(n) * kBins * 8, c.s), "memset lookback");
+    for (int i = 0; i < npasses; ++i) {
+        const int p = passes[i];
+        const bool first = i == 0, last = i == npasses - 1;
+        const bool digit_seg = p >= 8;
+        OnesweepArgs a{};
+        a.keys_in = b.keys[*cur];
+        a.keys_out = (last && !keep_keys) ? nullptr : b.keys[*cur ^ 1];
+        a.segs_in = segmented ? b.segs[*cur] : nullptr;
+        a.segs_out = segmented ? b.segs[*cur ^ 1] : nullptr;
+        a.vals_in = (first && synth_first) ? nullptr : b.vals[*cur];
+        const bool to_final = last && final_out != nullptr;
+        a.vals_out = to_final ? final_out : b.vals[*cur ^ 1];
+        a.flag_bits = flag_bits;
+        a.n = n;
+        a.shift = 8 * (p % 8);
+        a.bucket_base = c.at<unsigned long long>(c.L.bucket) + (size_t)p * kBins;
+        a.lookback = lb[i & 1];
+        a.lookback_next = last ? nullptr : lb[(i + 1) & 1];
+        HS_TRY(c.counter(&a.tile_counter), "counter");
+        a.flags = c.d_flags;
+        const OutMode om = to_final ? final_mode : kOutVals;
+        double ob = 8.0 * n;                                   // keys read
+        ob += (first && synth_first) ? (flag_bits ? n / 8.0 : 0.0) : 4.0 * n;  // vals read
+        ob += a.keys_out ? 8.0 * n : 0.0;                      // keys written
+        ob += om == kOutPerm64 ? 8.0 * n : 4.0 * n;            // vals written
+        ob += segmented ? 8.0 * n : 0.0;                       // segs read + written
+        HS_TRY(c.timed(kKOnesweep, ob, [&] {
+                   return launch_onesweep(a, segmented, digit_seg, first && synth_first, om, c.s);
+               }),
+               "onesweep");
+        *cur ^= 1;
+    }
+    return HS_OK;
+}
+
+struct Input {
+    const uint8_t *bytes;
+    const uint64_t *offsets;
+    uint64_t n;
+    int prefix_len;
+    void *perm;
+    int perm_u64;
+};
+
+hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
+    const uint64_t n = in.n;
+    RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
+    RunEntry *q_medium = c.at<RunEntry>(c.L.q_medium);
+    RunEntry *q_large[2] = {c.at<RunEntry>(c.L.q_large_a), c.at<RunEntry>(c.L.q_large_b)};
+    unsigned long long *run_base = c.at<unsigned long long>(c.L.run_base);
+    uint64_t *lb_tie = c.at<uint64_t>(c.L.lb_tie);
+
+    TieArgs t{};
+    t.keys = b.keys[cur];
+    t.vals = b.vals[cur];
+    t.n = n;
+    t.prefix_len = in.prefix_len;
+    t.perm = in.perm;
+    t.perm_u64 = in.perm_u64;
+    t.q_small = q_small;
+    t.q_medium = q_medium;
+    t.q_large = q_large[0];
+    t.cap_small = c.L.cap_small;
+    t.cap_medium = c.L.cap_medium;
+    t.cap_large = c.L.cap_large;
+    t.q_large_id = kQLargeA;
+    t.lookback = lb_tie;
+    t.flags = c.d_flags;
+    HS_TRY(cudaMemsetAsync(lb_tie, 0, ((n + kSortTile - 1) / kSortTile) * 8, c.s), "memset tie lookback");
+    HS_TRY(c.counter(&t.tile_counter), "counter");
+    HS_TRY(c.timed(kKTieDetect, 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n,
+                   [&] { return launch_tie_detect(t, false, c.s); }),
+           "tie detect");
+    HS_TRY(c.read_flags(), "tie sync");
+    hs_status st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+
+    // Large runs: refine 7 bytes per round until every run is constant-and-
+    // resolved or has been split into CTA / warp sized pieces.
+    int li = 0;
+    uint64_t large = c.h.qcount[kQLargeA];
+    int rounds = 0;
+    while (large > 0) {
+        if (++rounds > (1 << 26)) return fail(HS_ERR_INTERNAL, "refinement did not terminate");
+        if (large > c.L.cap_large) return fail(HS_ERR_INTERNAL, "large-run queue overflow");
+        const int next = li ^ 1;
+        const int next_id = next ? kQLargeB : kQLargeA;
+        const int cur_id = li ? kQLargeB : kQLargeA;
+        HS_TRY(cudaMemsetAsync(&c.d_flags->qcount[next_id], 0, sizeof(unsigned long long), c.s), "memset q");
+        HS_TRY(cudaMemsetAsync(&c.d_flags->nonconst, 0, sizeof(unsigned int), c.s), "memset nonconst");
+        HS_TRY(c.timed(kKRunScan, 24.0 * large, [&] { return launch_run_scan(q_large[li], large, run_base, c.s); }),
+               "run scan");
+        unsigned long long total = 0;
+        HS_TRY(cudaMemcpyAsync(&total, run_base + large, 8, cudaMemcpyDeviceToHost, c.s), "read total");
+        HS_TRY(cudaStreamSynchronize(c.s), "scan sync");
+        SortBufs r = b;
+        int rc = 0;
+        HS_TRY(c.timed(kKRefineKeys, 32.0 * total, [&] {
+                   return launch_refine_keys(in.bytes, in.offsets, in.perm, in.perm_u64, q_large[li], large,
+                                             run_base, total, in.prefix_len, r.keys[0], r.segs[0], r.vals[0],
+                                             c.d_flags, c.s);
+               }),
+               "refine keys");
+        HS_TRY(c.read_flags(), "refine sync");
+        st = device_error_status(c.h);
+        if (st != HS_OK) return st;
+        if (!c.h.nonconst) {
+            HS_TRY(c.timed(kKPushConstant, 32.0 * large, [&] {
+                       return launch_push_constant_runs(q_large[li], large, run_base, r.keys[0], in.prefix_len,
+                                                        q_small, q_medium, q_large[next], c.L.cap_small,
+                                                        c.L.cap_medium, c.L.cap_large, next_id, c.d_flags, c.s);
+                   }),
+                   "push constant runs");
+        } else {
+            unsigned long long *hist = c.at<unsigned long long>(c.L.hist);
+            HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
+            HS_TRY(c.timed(kKHistogram, 12.0 * total,
+                           [&] { return launch_histogram(r.keys[0], r.segs[0], total, hist, c.sms, c.s); }),
+                   "histogram");
+            HS_TRY(c.timed(kKPlan, 8.0 * kBins * 24, [&] {
+                       return launch_plan(hist, kHistPasses, total, c.at<unsigned long long>(c.L.bucket), c.d_flags,
+                                          c.s);
+                   }),
+                   "plan");
+            HS_TRY(c.read_flags(), "plan sync");
+            int passes[kHistPasses], np = 0;
+            for (int p = 0; p < kHistPasses; ++p)
+                if (c.h.active[p]) passes[np++] = p;
+            st = run_passes(c, r, &rc, total, passes, np, true, nullptr, false, nullptr, kOutVals, true);
+            if (st != HS_OK) return st;
+            TieArgs u = t;
+            u.keys = r.keys[rc];
+            u.segs = r.segs[rc];
+            u.vals = r.vals[rc];
+            u.n = total;
+            u.runs = q_large[li];
+            u.run_base = run_base;
+            u.q_large = q_large[next];
+            u.q_large_id = next_id;
+            HS_TRY(cudaMemsetAsync(lb_tie, 0, ((total + kSortTile - 1) / kSortTile) * 8, c.s), "memset lb");
+            HS_TRY(c.counter(&u.tile_counter), "counter");
+            HS_TRY(c.timed(kKTieDetect, 20.0 * total, [&] { return launch_tie_detect(u, true, c.s); }),
+                   "refine tie detect");
+        }
+        (void)cur_id;
+        HS_TRY(c.read_flags(), "round sync");
+        st = device_error_status(c.h);
+        if (st != HS_OK) return st;
+        large = c.h.qcount[next_id];
+        li = next;
+    }
+
+    const double isz = in.perm_u64 ? 8.0 : 4.0;
+    if (c.h.qcount[kQMedium])
+        HS_TRY(c.timed(kKMediumRuns, (double)c.h.qcount[kQMedium] * 16.0 * (2 * isz + 16.0), [&] {
+                   return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
+                                             &c.d_flags->qcount[kQMedium], c.L.cap_medium, in.prefix_len, c.sms,
+                                             c.s);
+               }),
+               "medium runs");
+    if (c.h.qcount[kQSmall])
+        HS_TRY(c.timed(kKSmallRuns, (double)c.h.qcount[kQSmall] * (16.0 + 2.0 * (2 * isz + 16.0)), [&] {
+                   return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
+                                            &c.d_flags->qcount[kQSmall], c.L.cap_small, in.prefix_len, c.sms,
+                                            c.s);
+               }),
+               "small runs");
+    return HS_OK;
+}
+
+hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
+    Input in = in0;
+    const uint64_t n = in.n;
+    SortBufs b{{c.at<uint64_t>(c.L.codes_a), c.at<uint64_t>(c.L.codes_b)},
+               {c.at<uint32_t>(c.L.vals_a), c.at<uint32_t>(c.L.vals_b)},
+               {c.at<uint32_t>(c.L.segs_a), c.at<uint32_t>(c.L.segs_b)}};
+    uint32_t *bits = c.at<uint32_t>(c.L.bits);
+    int used = 0;
+    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, &used);
+    if (st != HS_OK) return st;
+    in.prefix_len = used == HS_CODER_BYTE8 ? 8 : 9;
+    const bool perfect = c.h.nonexact == 0;
+    int passes[8], np = 0;
+    for (int p = 0; p < 8; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    const OutMode perm_mode = in.perm_u64 ? kOutPerm64 : kOutPerm32;
+    int cur = 0;
+    if (np == 0) {
+        HS_TRY(c.timed(kKIdentity, n / 8.0 + 4.0 * n, [&] {
+                   return launch_identity(bits, n, perfect ? in.perm : (void *)b.vals[0],
+                                          perfect ? perm_mode : kOutVals, c.s);
+               }),
+               "identity");
+    } else {
+        st = run_passes(c, b, &cur, n, passes, np, false, bits, true, perfect ? in.perm : nullptr, perm_mode,
+                        !perfect);
+        if (st != HS_OK) return st;
+    }
+    if (!perfect) {
+        st = run_fixup(c, in, b, cur);
+        if (st != HS_OK) return st;
+    }
+    HS_TRY(c.read_flags(), "final sync");
+    return device_error_status(c.h);
+}
+
+bool make_ctx(Ctx &c, void *ws, size_t ws_bytes, uint64_t n, void *stream, hs_status *st) {
+    c.L = make_layout(n);
+    if (ws == nullptr || ws_bytes < c.L.total) {
+        *st = fail(HS_ERR_WORKSPACE, "workspace missing or smaller than hs_workspace_size()");
+        return false;
+    }
+    if ((reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) {
+        *st = fail(HS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+        return false;
+    }
+    c.s = static_cast<cudaStream_t>(stream);
+    c.ws = static_cast<char *>(ws);
+    c.sms = num_sms_cached();
+    c.d_flags = c.at<DevFlags>(c.L.flags);
+    c.d_counters = c.at<unsigned int>(c.L.counters);
+    {
+        std::lock_guard<std::mutex> g(g_stats.mu);
+        c.timing = g_stats.enabled;
+    }
+    return true;
+}
+
+}  // namespace
+}  // namespace hs
+
+using namespace hs;
+
+extern "C" {
+
+hs_status hs_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_t, size_t *out) {
+    (void)total_bytes;
+    (void)out_t;
+    g_last_error.clear();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    *out = make_layout(n).total;
+    return HS_OK;
+}
+
+hs_status hs_encode(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int coder, uint64_t *d_codes,
+                    int *h_all_exact, int *h_coder_used, void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (!d_offsets || (n > 0 && !d_codes)) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, ws_bytes, 0, stream, &st)) return st;
+    if (n == 0) {
+        if (h_all_exact) *h_all_exact = 1;
+        if (h_coder_used) *h_coder_used = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : HS_CODER_ASCII7;
+        return HS_OK;
+    }
+    if (!d_bytes) return fail(HS_ERR_INVALID_ARG, "null bytes");
+    int used = 0;
+    st = run_encode(c, d_bytes, d_offsets, n, coder, d_codes, nullptr, false, &used);
+    if (st != HS_OK) return st;
+    if (h_all_exact) *h_all_exact = c.h.nonexact ? 0 : 1;
+    if (h_coder_used) *h_coder_used = used;
+    return HS_OK;
+}
+
+hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int mode, int coder, int out_t,
+                     void *d_perm, void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
+    if (n == 0) return HS_OK;
+    if (!d_bytes || !d_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st)) return st;
+    Input in{d_bytes, d_offsets, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
+    return argsort_plain(c, in, coder);
+}
+
+hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets, const uint64_t *d_seg_offsets,
+                             uint64_t num_segs, uint64_t n, int coder, uint32_t *d_perm, void *d_ws,
+                             size_t ws_bytes, void *stream) {
+    (void)d_bytes; (void)d_offsets; (void)d_seg_offsets; (void)num_segs; (void)n; (void)coder;
+    (void)d_perm; (void)d_ws; (void)ws_bytes; (void)stream;
+    g_last_error.clear();
+    return fail(HS_ERR_INTERNAL, "hs_argsort_batched: not built yet");
+}
+
+hs_status hs_batched_workspace_size(uint64_t n, uint64_t num_segs, size_t *out) {
+    (void)num_segs;
+    g_last_error.clear();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
+    *out = make_layout(n).total;
+    return HS_OK;
+}
+
+hs_status hs_stats_enable(int on) {
+    g_last_error.clear();
+    std::lock_guard<std::mutex> g(g_stats.mu);
+    g_stats.enabled = on != 0;
+    if (on) {
+        for (int k = 0; k < kKNumKinds; ++k) {
+            g_stats.launches[k] = 0;
+            g_stats.ms[k] = 0;
+            g_stats.bytes[k] = 0;
+        }
+    }
+    return HS_OK;
+}
+
+hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count) {
+    g_last_error.clear();
+    if (!count || (max > 0 && !out)) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    std::lock_guard<std::mutex> g(g_stats.mu);
+    for (int k = 0; k < kKNumKinds && k < max; ++k) {
+        std::memset(&out[k], 0, sizeof(hs_kernel_stat));
+        std::strncpy(out[k].name, kKindNames[k], sizeof(out[k].name) - 1);
+        out[k].launches = g_stats.launches[k];
+        out[k].total_ms = g_stats.ms[k];
+        out[k].algo_bytes = g_stats.bytes[k];
+    }
+    *count = kKNumKinds;
+    return HS_OK;
+}
+
+const char *hs_last_error(void) { return g_last_error.c_str(); }
+
+int hs_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,560 @@
+// Step 3: fix the inversions the code sort leaves (Section 3.1 Step 3,
+// Algorithm 1; skipped entirely when the coding is perfect, Section 3.4).
+//
+// With an order-preserving coder, code(a) < code(b) implies a < b (Section
+// 3.2 with p confined to ties), so after a stable sort by code only runs of
+// equal codes can be out of order, and only if some member was not exactly
+// represented.  The paper re-sorts the whole array with Timsort; here only
+// those runs are sorted, by size class:
+//   tie detection   one chained-scan pass finds each run of equal keys and
+//                   whether any member needs work (decoupled look-back);
+//   2..32           a warp per run ranks its members by full comparison;
+//   33..2048        a CTA per run sorts (window key, index) in shared memory,
+//                   refining 7 bytes at a time until every tie is resolved;
+//   larger          refined globally: window keys for all members, a
+//                   segmented radix sort by (run, key), and tie detection
+//                   again on the result (driven from the host).
+#include "hs_internal.h"
+
+namespace hs {
+namespace {
+
+// ---- tie detection ----------------------------------------------------------
+//
+// Scan state over positions: has_head, position of the last run head, OR of
+// the "needs work" flags since that head.  (a then b) = b if b has a head,
+// else (a.has, a.last, a.or | b.or).  Packed into 62 bits for look-back:
+// bit 61 has, bit 60 or, bits 0..59 last.
+
+struct RunState {
+    uint64_t last;
+    uint32_t has;
+    uint32_t orf;
+};
+
+__device__ __forceinline__ RunState combine(const RunState &a, const RunState &b) {
+    if (b.has) return b;
+    return RunState{a.last, a.has, a.orf | b.orf};
+}
+
+__device__ __forceinline__ uint64_t pack(const RunState &s) {
+    return ((uint64_t)s.has << 61) | ((uint64_t)s.orf << 60) | (s.last & ((1ull << 60) - 1));
+}
+
+__device__ __forceinline__ RunState unpack(uint64_t v) {
+    return RunState{v & ((1ull << 60) - 1), (uint32_t)((v >> 61) & 1), (uint32_t)((v >> 60) & 1)};
+}
+
+constexpr int kTieThreads = 256;
+constexpr int kTieItems = 16;
+constexpr int kTieTile = kTieThreads * kTieItems;
+
+__device__ __forceinline__ void push_run(const TieArgs &a, uint64_t start, uint64_t len, uint32_t depth) {
+    RunEntry e;
+    e.start = start;
+    e.len = (uint32_t)umin64(len, 0xFFFFFFFFull);
+    e.depth = depth;
+    if (len <= kSmallMax) {
+        const unsigned long long i = atomicAdd(&a.flags->qcount[kQSmall], 1ull);
+        if (i < a.cap_small) a.q_small[i] = e; else atomicOr(&a.flags->error, kErrInternal);
+    } else if (len <= kMediumMax) {
+        const unsigned long long i = atomicAdd(&a.flags->qcount[kQMedium], 1ull);
+        if (i < a.cap_medium) a.q_medium[i] = e; else atomicOr(&a.flags->error, kErrInternal);
+    } else {
+        const unsigned long long i = atomicAdd(&a.flags->qcount[a.q_large_id], 1ull);
+        if (i < a.cap_large && len < 0xFFFFFFFFull) a.q_large[i] = e;
+        else atomicOr(&a.flags->error, kErrInternal);
+    }
+}
+
+template <bool REFINE>
+__global__ void __launch_bounds__(kTieThreads)
+tie_detect_kernel(const TieArgs a) {
+    __shared__ uint64_t s_state[kTieThreads / 32];
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t n = a.n;
+    const uint64_t j0 = tile * kTieTile + (uint64_t)tid * kTieItems;
+    const uint32_t cont_tag = (uint32_t)a.prefix_len + 8;
+
+    // Thread-local pass: heads and flags of my items.
+    uint64_t key_prev = 0;
+    uint32_t seg_prev = 0;
+    if (j0 > 0 && j0 - 1 < n) {
+        key_prev = a.keys[j0 - 1];
+        if (REFINE) seg_prev = a.segs[j0 - 1];
+    }
+    uint32_t heads = 0, flagsb = 0;
+    RunState mine{0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < kTieItems; ++i) {
+        const uint64_t j = j0 + i;
+        if (j < n) {
+            const uint64_t k = a.keys[j];
+            const uint32_t sg = REFINE ? a.segs[j] : 0;
+            const bool head = (j == 0) || k != key_prev || (REFINE && sg != seg_prev);
+            const uint32_t v = a.vals[j];
+            const bool f = REFINE ? ((uint32_t)(k & 0xFF) == cont_tag) : ((v >> 31) != 0);
+            heads |= (uint32_t)head << i;
+            flagsb |= (uint32_t)f << i;
+            mine = combine(mine, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
+            key_prev = k;
+            seg_prev = sg;
+        }
+    }
+
+    // Exclusive scan of thread states across the block.
+    RunState x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        RunState y;
+        y.last = __shfl_up_sync(kFull, x.last, o);
+        y.has = __shfl_up_sync(kFull, x.has, o);
+        y.orf = __shfl_up_sync(kFull, x.orf, o);
+        if (lane >= o) x = combine(y, x);
+    }
+    if (lane == 31) s_state[warp] = pack(x);
+    __syncthreads();
+    RunState wpre{0, 0, 0};
+    for (int w = 0; w < warp; ++w) wpre = combine(wpre, unpack(s_state[w]));
+    RunState excl;
+    {
+        RunState xp;
+        xp.last = __shfl_up_sync(kFull, x.last, 1);
+        xp.has = __shfl_up_sync(kFull, x.has, 1);
+        xp.orf = __shfl_up_sync(kFull, x.orf, 1);
+        excl = lane == 0 ? wpre : combine(wpre, xp);
+    }
+
+    // Tile aggregate and look-back (thread 0).
+    if (tid == 0) {
+        RunState agg{0, 0, 0};
+        for (int w = 0; w < kTieThreads / 32; ++w) agg = combine(agg, unpack(s_state[w]));
+        uint64_t *lb = a.lookback + tile;
+        RunState prefix{0, 0, 0};
+        if (tile == 0) {
+            st_relaxed(lb, kLbInclusive | pack(agg));
+        } else {
+            st_relaxed(lb, kLbAggregate | pack(agg));
+            int64_t t = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (t >= 0) {
+                const uint64_t v = ld_relaxed(&a.lookback[t]);
+                const uint64_t st = v & ~kLbValueMask;
+                if (st == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(&a.flags->error, kErrTimeout);
+                        break;
+                    }
+                    if (spins > 8) __nanosleep(32);
+                    continue;
+                }
+                prefix = combine(unpack(v & kLbValueMask), prefix);
+                if (st == kLbInclusive) break;
+                --t;
+            }
+            st_relaxed(lb, kLbInclusive | pack(combine(prefix, agg)));
+        }
+        s_prefix = pack(prefix);
+    }
+    __syncthreads();
+    RunState st = combine(unpack(s_prefix), excl);
+
+    // Replay my items: write the permutation, emit runs at their tails.
+    uint64_t next_key = 0;
+    uint32_t next_seg = 0;
+    const uint64_t jn = j0 + kTieItems;
+    bool next_head = true;
+    if (jn < n) {
+        next_key = a.keys[jn];
+        if (REFINE) next_seg = a.segs[jn];
+    }
+#pragma unroll
+    for (int i = 0; i < kTieItems; ++i) {
+        const uint64_t j = j0 + i;
+        if (j >= n) break;
+        const bool head = (heads >> i) & 1u;
+        const bool f = (flagsb >> i) & 1u;
+        st = combine(st, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
+        const uint32_t v = a.vals[j];
+        uint64_t pos = j, run_start = st.last;
+        uint32_t depth = 0;
+        if (REFINE) {
+            const uint32_t sg = a.segs[j];
+            const RunEntry r = a.runs[sg];
+            pos = r.start + (j - a.run_base[sg]);
+            run_start = r.start + (st.last - a.run_base[sg]);
+            depth = r.depth + 1;
+        }
+        if (a.perm_u64)
+            static_cast<uint64_t *>(a.perm)[pos] = REFINE ? v : (v & kIdxMask);
+        else
+            static_cast<uint32_t *>(a.perm)[pos] = REFINE ? v : (v & kIdxMask);
+        bool tail;
+        if (i + 1 < kTieItems) {
+            tail = (j + 1 >= n) || ((heads >> (i + 1)) & 1u);
+        } else {
+            if (jn >= n) {
+                tail = true;
+            } else {
+                const uint64_t k = a.keys[j];
+                const uint32_t sg = REFINE ? a.segs[j] : 0;
+                tail = next_key != k || (REFINE && next_seg != sg);
+            }
+        }
+        (void)next_head;
+        if (tail) {
+            const uint64_t len = j - st.last + 1;
+            if (len >= 2 && st.orf) push_run(a, run_start, len, depth);
+        }
+    }
+}
+
+// ---- 2..32: warp per run ---------------------------------------------------
+
+template <typename IdxT>
+__global__ void __launch_bounds__(256)
+small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                  IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
+                  const unsigned long long *__restrict__ qcount, uint64_t cap, int prefix_len) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t count = umin64(*qcount, cap);
+    for (uint64_t r = warp_id; r < count; r += nwarps) {
+        const RunEntry e = q[r];
+        if (e.len > kSmallMax) continue;  // never queued here
+        const bool mine = (uint32_t)lane < e.len;
+        IdxT idx = 0;
+        uint64_t off = 0, len = 0;
+        if (mine) {
+            idx = perm[e.start + lane];
+            off = offsets[idx];
+            len = offsets[idx + 1] - off;
+        }
+        const uint64_t o = window_offset(prefix_len, e.depth);
+        uint32_t rank = 0;
+        for (uint32_t m = 0; m < e.len; ++m) {
+            const IdxT im = __shfl_sync(kFull, idx, m);
+            const uint64_t om = __shfl_sync(kFull, off, m);
+            const uint64_t lm = __shfl_sync(kFull, len, m);
+            if (mine && m != (uint32_t)lane) {
+                const uint64_t from = min(o, min(len, lm));
+                const int c = compare_from(bytes + off, len, bytes + om, lm, from);
+                if (c > 0 || (c == 0 && im < idx)) ++rank;
+            }
+        }
+        __syncwarp();
+        if (mine) perm[e.start + rank] = idx;
+        __syncwarp();
+    }
+}
+
+// ---- 33..2048: CTA per run ---------------------------------------------------
+
+constexpr int kMedThreads = 512;
+
+template <typename IdxT>
+__device__ __forceinline__ bool elem_greater(uint32_t sa, uint64_t ka, IdxT ia,
+                                             uint32_t sb, uint64_t kb, IdxT ib) {
+    if (sa != sb) return sa > sb;
+    if (ka != kb) return ka > kb;
+    return ia > ib;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kMedThreads)
+medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                   IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
+                   const unsigned long long *__restrict__ qcount, uint64_t cap, int prefix_len) {
+    constexpr int CAP = kMediumMax;
+    __shared__ uint64_t s_key[CAP];
+    __shared__ uint32_t s_seg[CAP];
+    __shared__ IdxT s_idx[CAP];
+    __shared__ uint8_t s_segact[CAP];
+    __shared__ uint8_t s_newact[CAP];
+    __shared__ uint32_t s_scan[kMedThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t count = umin64(*qcount, cap);
+    const uint32_t cont_tag = (uint32_t)prefix_len + 8;
+
+    for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
+        const RunEntry e = q[r];
+        if (e.len > (uint32_t)CAP) continue;  // never queued here
+        const int len = (int)e.len;
+        int P = 1;
+        while (P < len) P <<= 1;
+        __syncthreads();
+        for (int j = tid; j < P; j += kMedThreads) {
+            if (j < len) {
+                s_idx[j] = perm[e.start + j];
+                s_seg[j] = 0;
+            } else {
+                s_idx[j] = (IdxT)~(IdxT)0;
+                s_seg[j] = 0xFFFFFFFFu;
+                s_key[j] = ~0ull;
+            }
+            s_segact[j] = (j == 0);
+        }
+        uint32_t depth = e.depth;
+        for (;;) {
+            __syncthreads();
+            const uint64_t o = window_offset(prefix_len, depth);
+            for (int j = tid; j < len; j += kMedThreads) {
+                if (s_segact[s_seg[j]]) {
+                    const IdxT idx = s_idx[j];
+                    const uint64_t off = offsets[idx];
+                    s_key[j] = window_key(bytes + off, offsets[idx + 1] - off, o, prefix_len);
+                } else {
+                    s_key[j] = 0;
+                }
+            }
+            __syncthreads();
+            // Bitonic sort of P elements by (seg, key, idx).
+            for (int k = 2; k <= P; k <<= 1) {
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int i = tid; i < P; i += kMedThreads) {
+                        const int ixj = i ^ jj;
+                        if (ixj > i) {
+                            const bool up = (i & k) == 0;
+                            const bool gt = elem_greater<IdxT>(s_seg[i], s_key[i], s_idx[i],
+                                                               s_seg[ixj], s_key[ixj], s_idx[ixj]);
+                            if (gt == up) {
+                                uint32_t ts = s_seg[i]; s_seg[i] = s_seg[ixj]; s_seg[ixj] = ts;
+                                uint64_t tk = s_key[i]; s_key[i] = s_key[ixj]; s_key[ixj] = tk;
+                                IdxT ti = s_idx[i]; s_idx[i] = s_idx[ixj]; s_idx[ixj] = ti;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // New segments: heads where (seg, key) changes; a segment stays
+            // active iff its members continue past the window and it has at
+            // least two members.  Thread t owns items [t*4, t*4+4).
+            constexpr int PER = CAP / kMedThreads;
+            uint32_t hcount = 0;
+            bool head[PER], act[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int j = tid * PER + u;
+                head[u] = false;
+                act[u] = false;
+                if (j < len) {
+                    const bool same_prev = j > 0 && s_seg[j - 1] == s_seg[j] && s_key[j - 1] == s_key[j];
+                    const bool same_next = j + 1 < len && s_seg[j + 1] == s_seg[j] && s_key[j + 1] == s_key[j];
+                    const bool was_active = s_segact[s_seg[j]] != 0;
+                    head[u] = !same_prev;
+                    act[u] = was_active && (uint32_t)(s_key[j] & 0xFF) == cont_tag && (same_prev || same_next);
+                    hcount += head[u];
+                }
+            }
+            // exclusive scan of head counts
+            uint32_t xs = hcount;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                uint32_t y = __shfl_up_sync(kFull, xs, o2);
+                if (lane >= o2) xs += y;
+            }
+            if (lane == 31) s_scan[warp] = xs;
+            __syncthreads();
+            uint32_t base = 0;
+            for (int w = 0; w < warp; ++w) base += s_scan[w];
+            base += xs - hcount;
+            bool any = false;
+            uint32_t segid = base;  // id of the segment the next head opens
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int j = tid * PER + u;
+                if (j < len) {
+                    if (head[u]) {
+                        s_newact[segid] = act[u];
+                        ++segid;
+                    }
+                    any |= act[u];
+                }
+            }
+            __syncthreads();
+            // relabel (segid - 1 is the segment of the last head at or before j)
+            segid = base;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int j = tid * PER + u;
+                if (j < len) {
+                    if (head[u]) ++segid;
+                    s_seg[j] = segid - 1;
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < len; j += kMedThreads) s_segact[j] = s_newact[j];
+            if (!__syncthreads_or(any)) break;
+            ++depth;
+        }
+        for (int j = tid; j < len; j += kMedThreads) perm[e.start + j] = s_idx[j];
+    }
+}
+
+// ---- large-run helpers ---------------------------------------------------------
+
+// run_base[r] = sum of lengths of runs before r; run_base[count] = total.
+__global__ void run_scan_kernel(const RunEntry *__restrict__ runs, uint64_t count,
+                                unsigned long long *__restrict__ run_base) {
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (uint64_t b = 0; b < count; b += blockDim.x) {
+        const uint64_t r = b + tid;
+        const unsigned long long v = r < count ? runs[r].len : 0;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned long long wsum = 0;
+        for (int w = 0; w < warp; ++w) wsum += s_warp[w];
+        const unsigned long long carry = s_carry;
+        if (r < count) run_base[r] = carry + wsum + x - v;
+        __syncthreads();
+        if (tid == blockDim.x - 1) s_carry = carry + wsum + x;
+        __syncthreads();
+    }
+    if (tid == 0) run_base[count] = s_carry;
+}
+
+template <typename IdxT>
+__global__ void refine_keys_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                                   const IdxT *__restrict__ perm, const RunEntry *__restrict__ runs,
+                                   uint64_t count, const unsigned long long *__restrict__ run_base,
+                                   uint64_t total, int prefix_len, uint64_t *__restrict__ keys,
+                                   uint32_t *__restrict__ segs, uint32_t *__restrict__ vals,
+                                   DevFlags *flags) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool nonconst = false;
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {
+        // run containing a: last r with run_base[r] <= a
+        uint64_t lo = 0, hi = count;  // invariant run_base[lo] <= a < run_base[hi]
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (run_base[mid] <= a) lo = mid; else hi = mid;
+        }
+        const RunEntry r = runs[lo];
+        const uint64_t pos = r.start + (a - run_base[lo]);
+        const uint64_t o = window_offset(prefix_len, r.depth);
+        const IdxT idx = perm[pos];
+        const uint64_t off = offsets[idx];
+        const uint64_t k = window_key(bytes + off, offsets[idx + 1] - off, o, prefix_len);
+        const IdxT idx0 = perm[r.start];
+        const uint64_t off0 = offsets[idx0];
+        const uint64_t k0 = window_key(bytes + off0, offsets[idx0 + 1] - off0, o, prefix_len);
+        nonconst |= k != k0;
+        keys[a] = k;
+        segs[a] = (uint32_t)lo;
+        vals[a] = (uint32_t)idx;
+    }
+    if (__syncthreads_or(nonconst) && threadIdx.x == 0) atomicOr(&flags->nonconst, 1u);
+}
+
+__global__ void push_constant_runs_kernel(const RunEntry *__restrict__ runs, uint64_t count,
+                                          const unsigned long long *__restrict__ run_base,
+                                          const uint64_t *__restrict__ keys, TieArgs a) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint32_t cont_tag = (uint32_t)a.prefix_len + 8;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += stride) {
+        const RunEntry e = runs[r];
+        const uint64_t k = keys[run_base[r]];
+        if ((uint32_t)(k & 0xFF) == cont_tag) push_run(a, e.start, e.len, e.depth + 1);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tie_detect(const TieArgs &a, bool refine, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    const uint64_t tiles = (a.n + kTieTile - 1) / kTieTile;
+    if (refine)
+        tie_detect_kernel<true><<<(unsigned)tiles, kTieThreads, 0, s>>>(a);
+    else
+        tie_detect_kernel<false><<<(unsigned)tiles, kTieThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
+                              const RunEntry *q, const unsigned long long *qcount, uint64_t cap, int prefix_len,
+                              int num_sms, cudaStream_t s) {
+    const unsigned grid = (unsigned)num_sms * 8;
+    if (perm_u64)
+        small_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q,
+                                                         qcount, cap, prefix_len);
+    else
+        small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
+                                                         qcount, cap, prefix_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
+                               const RunEntry *q, const unsigned long long *qcount, uint64_t cap,
+                               int prefix_len, int num_sms, cudaStream_t s) {
+    const unsigned grid = (unsigned)num_sms * 2;
+    if (perm_u64)
+        medium_runs_kernel<uint64_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm),
+                                                                  q, qcount, cap, prefix_len);
+    else
+        medium_runs_kernel<uint32_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm),
+                                                                  q, qcount, cap, prefix_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count, unsigned long long *run_base,
+                            cudaStream_t s) {
+    run_scan_kernel<<<1, 1024, 0, s>>>(runs, count, run_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_keys(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                               const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
+                               uint64_t total, int prefix_len, uint64_t *keys, uint32_t *segs, uint32_t *vals,
+                               DevFlags *flags, cudaStream_t s) {
+    if (total == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
+    if (perm_u64)
+        refine_keys_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint64_t *>(perm),
+                                                          runs, count, run_base, total, prefix_len, keys,
+                                                          segs, vals, flags);
+    else
+        refine_keys_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint32_t *>(perm),
+                                                          runs, count, run_base, total, prefix_len, keys,
+                                                          segs, vals, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
+                                      const uint64_t *keys, int prefix_len, RunEntry *q_small,
+                                      RunEntry *q_medium, RunEntry *q_large, uint64_t cap_small,
+                                      uint64_t cap_medium, uint64_t cap_large, int q_large_id,
+                                      DevFlags *flags, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    TieArgs a{};
+    a.prefix_len = prefix_len;
+    a.q_small = q_small;
+    a.q_medium = q_medium;
+    a.q_large = q_large;
+    a.cap_small = cap_small;
+    a.cap_medium = cap_medium;
+    a.cap_large = cap_large;
+    a.q_large_id = q_large_id;
+    a.flags = flags;
+    const unsigned grid = (unsigned)umin64((count + 255) / 256, 1024);
+    push_constant_runs_kernel<<<grid, 256, 0, s>>>(runs, count, run_base, keys, a);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

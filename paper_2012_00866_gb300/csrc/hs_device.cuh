@@ -1,0 +1,120 @@
+// Device-side helpers shared by the library's kernels (internal header).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hs {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kBins = 256;             // 8-bit radix digits
+constexpr uint32_t kFlagBit = 0x80000000u;  // "not exactly encoded" payload bit
+constexpr uint32_t kIdxMask = 0x7FFFFFFFu;
+
+// Device error word bits (DevFlags::error).
+enum : uint32_t {
+    kErrTimeout = 1u,    // a bounded look-back / queue wait gave up
+    kErrOffsets = 2u,    // offsets decreasing
+    kErrInternal = 4u,   // index out of range, capacity exceeded
+};
+
+// Small device-resident control block, zeroed at the start of every call.
+struct DevFlags {
+    unsigned int error;
+    unsigned int nonexact;   // 1 if any string is not exactly represented
+    unsigned int domain;     // 1 if ASCII7 saw a byte >= 0x80
+    unsigned int nonconst;   // refinement: some large run is not constant
+    unsigned long long qcount[8];   // run-queue lengths (see RunQueue ids)
+    unsigned int active[16];        // plan: radix pass p is needed
+    unsigned int pad[4];
+};
+
+// Run queue entry: a run of equal keys at positions [start, start + len)
+// whose members agree on their first byte_offset(depth) bytes.
+struct RunEntry {
+    unsigned long long start;
+    unsigned int len;
+    unsigned int depth;
+};
+
+// Decoupled look-back words: 2-bit status in bits 62..63, 62-bit value.
+constexpr uint64_t kLbAggregate = 1ull << 62;
+constexpr uint64_t kLbInclusive = 2ull << 62;
+constexpr uint64_t kLbValueMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;   // polls before a wait gives up
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Lanes of the warp whose 8-bit digit equals this lane's, restricted to
+// `active` (8 ballots, one per digit bit).
+__device__ __forceinline__ unsigned match_digit(unsigned d, unsigned active) {
+    unsigned peers = active;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        unsigned bit = (d >> b) & 1u;
+        unsigned vote = __ballot_sync(kFull, bit);
+        peers &= bit ? vote : ~vote;
+    }
+    return peers;
+}
+
+// Byte offset at which refinement depth `depth` starts comparing: the first
+// `prefix_len` bytes are covered by the husky code, each later depth by a
+// 7-byte window.
+__device__ __forceinline__ uint64_t window_offset(int prefix_len, uint32_t depth) {
+    return (uint64_t)prefix_len + 7ull * depth;
+}
+
+// Refinement key of a string of length len at byte offset o: the 7 bytes
+// [o, o+7) big-endian (zero padded) in bits 8..63 and a tag in bits 0..7,
+//   tag = min(len + prefix_len - o, prefix_len + 8).
+// Among strings that agree on their first o bytes (or, at o = prefix_len,
+// share a husky code), unsigned key order is lexicographic order on the
+// window; equal keys with tag < prefix_len + 8 mean identical strings; tag ==
+// prefix_len + 8 means both continue past the window.
+__device__ __forceinline__ uint64_t window_key(const uint8_t *s, uint64_t len,
+                                               uint64_t o, int prefix_len) {
+    uint64_t key = 0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        uint64_t p = o + i;
+        uint64_t c = p < len ? s[p] : 0;
+        key = (key << 8) | c;
+    }
+    int64_t t = (int64_t)len + prefix_len - (int64_t)o;
+    int64_t cap = prefix_len + 8;
+    if (t > cap) t = cap;
+    if (t < 0) t = 0;
+    return (key << 8) | (uint64_t)t;
+}
+
+// Three-way unsigned-byte comparison of a and b starting at byte `from`
+// (both strings agree before it).
+__device__ __forceinline__ int compare_from(const uint8_t *a, uint64_t la,
+                                            const uint8_t *b, uint64_t lb,
+                                            uint64_t from) {
+    uint64_t m = la < lb ? la : lb;
+    for (uint64_t i = from; i < m; ++i) {
+        unsigned ca = a[i], cb = b[i];
+        if (ca != cb) return ca < cb ? -1 : 1;
+    }
+    return la < lb ? -1 : (la > lb ? 1 : 0);
+}
+
+}  // namespace hs

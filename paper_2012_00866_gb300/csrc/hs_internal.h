@@ -1,0 +1,125 @@
+// Host-side internal interface between the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hs_device.cuh"
+
+namespace hs {
+
+// ---- encode.cu -----------------------------------------------------------
+// Step 1 over n strings: codes[i], optional non-exact bitmask (bit i of word
+// i/32), optional 8 digit histograms (8 x 256 u64, accumulated), flags.
+cudaError_t launch_encode(int coder, const uint8_t *bytes,
+                          const uint64_t *offsets, uint64_t n, uint64_t *codes,
+                          uint32_t *nonexact_bits, unsigned long long *hist,
+                          DevFlags *flags, int num_sms, cudaStream_t s);
+
+// ---- sort.cu -------------------------------------------------------------
+constexpr int kSortTile = 4096;  // elements per onesweep tile
+inline uint64_t sort_tiles(uint64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+enum OutMode { kOutVals = 0, kOutPerm32 = 1, kOutPerm64 = 2 };
+
+struct OnesweepArgs {
+    const uint64_t *keys_in;
+    uint64_t *keys_out;          // nullable: keys not needed downstream
+    const uint32_t *segs_in;     // segmented sorts only
+    uint32_t *segs_out;
+    const uint32_t *vals_in;     // nullable when vals are synthesised
+    void *vals_out;
+    const uint32_t *flag_bits;   // synthesised vals: bit 31 source (nullable)
+    uint64_t n;
+    int shift;                   // digit = (source >> shift) & 255
+    const unsigned long long *bucket_base;  // 256 entries for this pass
+    uint64_t *lookback;          // sort_tiles(n) * 256 words, zeroed
+    uint64_t *lookback_next;     // zeroed by this pass for the next one
+    unsigned int *tile_counter;  // zeroed
+    DevFlags *flags;
+};
+
+// One stable LSD pass.  has_seg: elements carry a u32 segment id; digit_seg:
+// the digit comes from the segment id instead of the key; synth: vals are
+// generated as i | flag_bit(i) << 31; out: what vals_out receives.
+cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg,
+                            bool digit_seg, bool synth, OutMode out,
+                            cudaStream_t s);
+
+// Digit histograms of keys (8 digits) and optionally segs (4 digits):
+// hist[(p) * 256 + d], p < 8 for keys, 8..11 for segs; accumulated.
+cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs,
+                             uint64_t n, unsigned long long *hist,
+                             int num_sms, cudaStream_t s);
+
+// Exclusive scans of npass histograms into bucket_base, and
+// flags->active[p] = (no single digit holds all n elements).
+cudaError_t launch_plan(const unsigned long long *hist, int npass, uint64_t n,
+                        unsigned long long *bucket_base, DevFlags *flags,
+                        cudaStream_t s);
+
+// vals[i] = i | flag_bit(i) << 31 (or perm output), used when no pass runs.
+cudaError_t launch_identity(const uint32_t *flag_bits, uint64_t n,
+                            void *out, OutMode mode, cudaStream_t s);
+
+// ---- fixup.cu ------------------------------------------------------------
+enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3 };
+constexpr uint32_t kSmallMax = 32;     // warp per run
+constexpr uint32_t kMediumMax = 2048;  // block per run
+
+struct TieArgs {
+    const uint64_t *keys;
+    const uint32_t *segs;           // refinement only
+    const uint32_t *vals;
+    uint64_t n;
+    int prefix_len;                 // bytes covered by the husky code
+    void *perm;                     // output permutation
+    int perm_u64;
+    const RunEntry *runs;           // refinement: runs being refined
+    const unsigned long long *run_base;  // refinement: compacted starts
+    RunEntry *q_small, *q_medium, *q_large;
+    uint64_t cap_small, cap_medium, cap_large;
+    int q_large_id;                 // which DevFlags::qcount slot q_large uses
+    uint64_t *lookback;             // sort_tiles(n) words, zeroed
+    unsigned int *tile_counter;     // zeroed
+    DevFlags *flags;
+};
+
+// Equal-key runs of a sorted sequence that still need work, pushed to the
+// size-class queues; also writes the permutation (plain: vals stripped of
+// the flag bit at position j; refinement: vals written back to positions).
+cudaError_t launch_tie_detect(const TieArgs &a, bool refine, cudaStream_t s);
+
+cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets,
+                              void *perm, int perm_u64, const RunEntry *q,
+                              const unsigned long long *qcount, uint64_t cap,
+                              int prefix_len, int num_sms, cudaStream_t s);
+
+cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
+                               void *perm, int perm_u64, const RunEntry *q,
+                               const unsigned long long *qcount, uint64_t cap,
+                               int prefix_len, int num_sms, cudaStream_t s);
+
+// Large-run refinement helpers.
+cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count,
+                            unsigned long long *run_base, cudaStream_t s);
+
+cudaError_t launch_refine_keys(const uint8_t *bytes, const uint64_t *offsets,
+                               const void *perm, int perm_u64,
+                               const RunEntry *runs, uint64_t count,
+                               const unsigned long long *run_base,
+                               uint64_t total, int prefix_len, uint64_t *keys,
+                               uint32_t *segs, uint32_t *vals,
+                               DevFlags *flags, cudaStream_t s);
+
+cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count,
+                                      const unsigned long long *run_base,
+                                      const uint64_t *keys, int prefix_len,
+                                      RunEntry *q_small, RunEntry *q_medium,
+                                      RunEntry *q_large, uint64_t cap_small,
+                                      uint64_t cap_medium, uint64_t cap_large,
+                                      int q_large_id, DevFlags *flags,
+                                      cudaStream_t s);
+
+}  // namespace hs

@@ -1,0 +1,318 @@
+// Step 2: stable LSD radix sort of (code, index) pairs -- the GPU replacement
+// for the paper's introsort with "object swap" (Section 3.1 Step 2, Algorithm
+// 1): moving the index with its code is the object swap; stability makes the
+// result unique.
+//
+// Each pass is a single "onesweep" kernel (Adinets and Merrill, 2022): the
+// global digit offsets come from histograms computed up front (fused into the
+// encoder), each CTA ranks a tile of 4096 keys with warp-private digit
+// counters (8-ballot match), publishes its per-digit counts and resolves its
+// global prefix by decoupled look-back over earlier tiles, then scatters the
+// tile through shared memory so that runs of equal digits leave as coalesced
+// stores.  Tile ids come from an atomic counter, so every tile a CTA waits on
+// is already running; each wait is bounded and reports kErrTimeout.
+#include "hs_internal.h"
+
+namespace hs {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = kSortTile / kThreads;  // 16
+
+// Exclusive scan of one u32 per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t wsum = 0;
+    for (int w = 0; w < warp; ++w) wsum += s_warp[w];
+    __syncthreads();
+    return wsum + x - v;
+}
+
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT>
+__global__ void __launch_bounds__(kThreads, 2)
+onesweep_kernel(const OnesweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
+    uint32_t *s_segs = s_vals + kSortTile;
+    uint32_t *s_whist = s_segs + (HAS_SEG ? kSortTile : 0);
+    uint32_t *s_dstart = s_whist + kWarps * kBins;
+    unsigned long long *s_gbase = reinterpret_cast<unsigned long long *>(s_dstart + kBins);
+    __shared__ uint32_t s_scan[kWarps];
+    __shared__ uint32_t s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    for (int i = tid; i < kWarps * kBins; i += kThreads) s_whist[i] = 0;
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t n = a.n;
+    const uint64_t tile_base = tile * kSortTile;
+    if (a.lookback_next) a.lookback_next[tile * kBins + tid] = 0;
+
+    // Warp-striped load: warp w owns elements [w*512, w*512+512) of the tile,
+    // item k of lane l is element w*512 + k*32 + l, so processing items in k
+    // order visits the warp's elements in input order (stability).
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+    uint32_t seg[kItems];
+    uint32_t rank[kItems];
+    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * kItems;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint64_t e = wbase + k * 32 + lane;
+        const bool valid = e < n;
+        key[k] = valid ? a.keys_in[e] : 0;
+        if (SYNTH) {
+            uint32_t bit = 0;
+            if (valid && a.flag_bits) bit = (a.flag_bits[e >> 5] >> lane) & 1u;
+            val[k] = (uint32_t)e | (bit << 31);
+        } else {
+            val[k] = valid ? a.vals_in[e] : 0;
+        }
+        seg[k] = (HAS_SEG && valid) ? a.segs_in[e] : 0;
+    }
+
+    uint32_t *my_hist = s_whist + warp * kBins;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint64_t e = wbase + k * 32 + lane;
+        const bool valid = e < n;
+        const unsigned active = __ballot_sync(kFull, valid);
+        const unsigned d = DIGIT_SEG ? ((seg[k] >> a.shift) & 0xFFu)
+                                     : (unsigned)((key[k] >> a.shift) & 0xFFu);
+        const unsigned peers = match_digit(d, active);
+        const int leader = valid ? __ffs(peers) - 1 : lane;
+        uint32_t before = 0;
+        if (valid && lane == leader) {
+            before = my_hist[d];
+            my_hist[d] = before + __popc(peers);
+        }
+        before = __shfl_sync(kFull, before, leader);
+        rank[k] = before + __popc(peers & lanemask_lt());
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Thread d: tile count of digit d, and exclusive per-warp offsets.
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_whist[w * kBins + tid];
+        s_whist[w * kBins + tid] = total;
+        total += c;
+    }
+    uint64_t *lb = a.lookback + tile * kBins;
+    uint64_t prefix = 0;
+    if (tile == 0) {
+        st_relaxed(&lb[tid], kLbInclusive | total);
+    } else {
+        st_relaxed(&lb[tid], kLbAggregate | total);
+        int64_t t = (int64_t)tile - 1;
+        uint32_t spins = 0;
+        while (t >= 0) {
+            const uint64_t v = ld_relaxed(&a.lookback[(uint64_t)t * kBins + tid]);
+            const uint64_t st = v & ~kLbValueMask;
+            if (st == 0) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(&a.flags->error, kErrTimeout);
+                    break;
+                }
+                if (spins > 8) __nanosleep(32);
+                continue;
+            }
+            prefix += v & kLbValueMask;
+            if (st == kLbInclusive) break;
+            --t;
+        }
+        st_relaxed(&lb[tid], kLbInclusive | (prefix + total));
+    }
+
+    const uint32_t dstart = block_exclusive_scan(total, s_scan);
+    s_dstart[tid] = dstart;
+    s_gbase[tid] = a.bucket_base[tid] + prefix - dstart;
+    __syncthreads();
+
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint64_t e = wbase + k * 32 + lane;
+        if (e < n) {
+            const unsigned d = DIGIT_SEG ? ((seg[k] >> a.shift) & 0xFFu)
+                                         : (unsigned)((key[k] >> a.shift) & 0xFFu);
+            const uint32_t p = s_dstart[d] + s_whist[warp * kBins + d] + rank[k];
+            s_keys[p] = key[k];
+            s_vals[p] = val[k];
+            if (HAS_SEG) s_segs[p] = seg[k];
+        }
+    }
+    __syncthreads();
+
+    const int cnt = (int)umin64(kSortTile, n - tile_base);
+    for (int i = tid; i < cnt; i += kThreads) {
+        const uint64_t k = s_keys[i];
+        const uint32_t sg = HAS_SEG ? s_segs[i] : 0;
+        const unsigned d = DIGIT_SEG ? ((sg >> a.shift) & 0xFFu) : (unsigned)((k >> a.shift) & 0xFFu);
+        const uint64_t pos = s_gbase[d] + (uint64_t)i;
+        if (pos >= n) {
+            atomicOr(&a.flags->error, kErrInternal);
+            continue;
+        }
+        if (a.keys_out) a.keys_out[pos] = k;
+        if (HAS_SEG) a.segs_out[pos] = sg;
+        const uint32_t v = s_vals[i];
+        if (OUT == kOutVals)
+            static_cast<uint32_t *>(a.vals_out)[pos] = v;
+        else if (OUT == kOutPerm32)
+            static_cast<uint32_t *>(a.vals_out)[pos] = v & kIdxMask;
+        else
+            static_cast<uint64_t *>(a.vals_out)[pos] = (uint64_t)(v & kIdxMask);
+    }
+}
+
+size_t onesweep_smem(bool has_seg) {
+    return (size_t)kSortTile * 8 + (size_t)kSortTile * 4 + (has_seg ? (size_t)kSortTile * 4 : 0) +
+           (size_t)kWarps * kBins * 4 + (size_t)kBins * 4 + (size_t)kBins * 8;
+}
+
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT>
+cudaError_t launch_os(const OnesweepArgs &a, cudaStream_t s) {
+    auto kern = onesweep_kernel<HAS_SEG, DIGIT_SEG, SYNTH, OUT>;
+    const size_t smem = onesweep_smem(HAS_SEG);
+    static bool configured = false;  // attribute is per function, idempotent
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const uint64_t tiles = sort_tiles(a.n);
+    kern<<<(unsigned)tiles, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- up-front histograms -------------------------------------------------
+
+constexpr int kHistThreads = 512;
+
+template <bool HAS_SEG>
+__global__ void __launch_bounds__(kHistThreads)
+histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ segs,
+                 uint64_t n, unsigned long long *__restrict__ hist) {
+    constexpr int P = HAS_SEG ? 12 : 8;
+    __shared__ uint32_t s_hist[P * kBins];
+    for (int i = threadIdx.x; i < P * kBins; i += kHistThreads) s_hist[i] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
+    for (uint64_t i = (uint64_t)blockIdx.x * kHistThreads + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) atomicAdd(&s_hist[p * kBins + (unsigned)((k >> (8 * p)) & 0xFF)], 1u);
+        if (HAS_SEG) {
+            const uint32_t sg = segs[i];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[(8 + p) * kBins + ((sg >> (8 * p)) & 0xFF)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < P * kBins; i += kHistThreads)
+        if (s_hist[i]) atomicAdd(&hist[i], (unsigned long long)s_hist[i]);
+}
+
+// ---- pass plan -------------------------------------------------------------
+
+__global__ void plan_kernel(const unsigned long long *__restrict__ hist, int npass, uint64_t n,
+                            unsigned long long *__restrict__ bucket_base, DevFlags *flags) {
+    __shared__ unsigned long long s_warp[kBins / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int p = 0; p < npass; ++p) {
+        const unsigned long long c = hist[p * kBins + tid];
+        unsigned long long x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned long long wsum = 0;
+        for (int w = 0; w < warp; ++w) wsum += s_warp[w];
+        bucket_base[p * kBins + tid] = wsum + x - c;
+        const int all_in_one = __syncthreads_or(c == n);
+        if (tid == 0) flags->active[p] = (n > 1 && !all_in_one) ? 1u : 0u;
+        __syncthreads();
+    }
+}
+
+__global__ void identity_kernel(const uint32_t *__restrict__ flag_bits, uint64_t n, void *out, int mode) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t bit = flag_bits ? ((flag_bits[i >> 5] >> (i & 31)) & 1u) : 0u;
+        if (mode == kOutVals)
+            static_cast<uint32_t *>(out)[i] = (uint32_t)i | (bit << 31);
+        else if (mode == kOutPerm32)
+            static_cast<uint32_t *>(out)[i] = (uint32_t)i;
+        else
+            static_cast<uint64_t *>(out)[i] = i;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg, bool digit_seg, bool synth,
+                            OutMode out, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (has_seg) {
+        if (synth || out != kOutVals) return cudaErrorInvalidValue;
+        return digit_seg ? launch_os<true, true, false, kOutVals>(a, s)
+                         : launch_os<true, false, false, kOutVals>(a, s);
+    }
+    if (digit_seg) return cudaErrorInvalidValue;
+    if (synth) {
+        switch (out) {
+            case kOutVals: return launch_os<false, false, true, kOutVals>(a, s);
+            case kOutPerm32: return launch_os<false, false, true, kOutPerm32>(a, s);
+            default: return launch_os<false, false, true, kOutPerm64>(a, s);
+        }
+    }
+    switch (out) {
+        case kOutVals: return launch_os<false, false, false, kOutVals>(a, s);
+        case kOutPerm32: return launch_os<false, false, false, kOutPerm32>(a, s);
+        default: return launch_os<false, false, false, kOutPerm64>(a, s);
+    }
+}
+
+cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs, uint64_t n,
+                             unsigned long long *hist, int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + kHistThreads * 16 - 1) / (kHistThreads * 16);
+    const unsigned grid = (unsigned)umin64(blocks, (uint64_t)num_sms * 4);
+    if (segs)
+        histogram_kernel<true><<<grid, kHistThreads, 0, s>>>(keys, segs, n, hist);
+    else
+        histogram_kernel<false><<<grid, kHistThreads, 0, s>>>(keys, nullptr, n, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const unsigned long long *hist, int npass, uint64_t n,
+                        unsigned long long *bucket_base, DevFlags *flags, cudaStream_t s) {
+    plan_kernel<<<1, kBins, 0, s>>>(hist, npass, n, bucket_base, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_identity(const uint32_t *flag_bits, uint64_t n, void *out, OutMode mode,
+                            cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((n + 255) / 256, 4096);
+    identity_kernel<<<grid, 256, 0, s>>>(flag_bits, n, out, (int)mode);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

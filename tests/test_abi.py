@@ -1,0 +1,84 @@
+"""The C-ABI library loads and exports every symbol its headers declare, and
+host-side argument validation works without a GPU (no compute calls)."""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"HS_API\s+[\w\s\*]+?\b(hs_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2012_00866_gb300 as hs
+    return hs.load()
+
+
+def test_headers_declare_the_boundary():
+    names = _declared_functions()
+    for required in ("hs_encode", "hs_argsort", "hs_argsort_batched",
+                     "hs_workspace_size", "hs_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_names_match_headers():
+    import paper_2012_00866_gb300 as hs
+    assert set(hs.EXPORTS) >= set(n for n in _declared_functions()
+                                  if not n.startswith("hs_noalloc"))
+
+
+def test_workspace_size_host_only():
+    import paper_2012_00866_gb300 as hs
+    sizes = [hs.workspace_size(n) for n in (0, 1, 1000, 10**6, 10**7)]
+    assert all(b >= a for a, b in zip(sizes, sizes[1:]))
+    assert sizes[-1] >= 10**7 * 24   # two key and two payload buffers at least
+    with pytest.raises(hs.HuskyError) as e:
+        hs.workspace_size(10, mode=7)
+    assert e.value.status == hs.ERR_INVALID_ARG
+
+
+def test_argument_validation_without_gpu(lib):
+    import paper_2012_00866_gb300 as hs
+    vp = ctypes.c_void_p
+    # n = 0 is a no-op and touches nothing
+    assert lib.hs_argsort(None, None, 0, 0, 0, 0, None, None, 0, None) == hs.OK
+    # bad enums, n too large, NULL pointers: rejected before any CUDA call
+    assert lib.hs_argsort(vp(16), vp(16), 5, 9, 0, 0, vp(16), vp(256), 1 << 20, None) == hs.ERR_INVALID_ARG
+    assert lib.hs_argsort(vp(16), vp(16), 5, 0, 9, 0, vp(16), vp(256), 1 << 20, None) == hs.ERR_INVALID_ARG
+    assert lib.hs_argsort(vp(16), vp(16), 5, 0, 0, 9, vp(16), vp(256), 1 << 20, None) == hs.ERR_INVALID_ARG
+    assert lib.hs_argsort(vp(16), vp(16), hs.MAX_N + 1, 0, 0, 0, vp(16), vp(256), 1 << 20, None) == hs.ERR_INVALID_ARG
+    assert lib.hs_argsort(None, vp(16), 5, 0, 0, 0, vp(16), vp(256), 1 << 20, None) == hs.ERR_INVALID_ARG
+    assert b"null" in lib.hs_last_error()
+    # workspace too small is reported before any device work
+    assert lib.hs_argsort(vp(16), vp(16), 5, 0, 0, 0, vp(16), vp(256), 16, None) == hs.ERR_WORKSPACE
+    assert lib.hs_last_error() != b""
+
+
+def test_no_cpu_fallback_without_gpu():
+    """The product path must fail loudly (not fall back) without a GPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    import paper_2012_00866_gb300 as hs
+    data = torch.zeros(4, dtype=torch.uint8)
+    off = torch.zeros(3, dtype=torch.int64)
+    with pytest.raises(Exception):
+        hs.argsort(data, off)

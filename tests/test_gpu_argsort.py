@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Integer work, so the bar is bit-exact: codes equal the oracle's Algorithm 4
+codes, permutations equal the oracle's stable argsort element by element (or,
+at sizes the oracle cannot re-sort quickly, satisfy the property check that
+characterises the stable argsort uniquely)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from conftest import literal, read_golden
+from gpu_util import assert_oracle_equal, assert_stable_sorted, perm_numpy, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+# ---- Step 1 ------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("coder", [1, 2])
+def test_encode_matches_oracle(cuda_lib, kind, coder):
+    hs = cuda_lib
+    w = workloads.generate(kind, 300_001, 11 + kind)
+    data, off = to_device(w)
+    codes, exact, used = hs.encode(data, off, coder=coder)
+    want, want_exact, perfect = oracle.encode(w.bytes, w.offsets, coder)
+    assert used == coder
+    assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
+    assert exact == perfect
+
+
+def test_encode_edge_strings(cuda_lib):
+    hs = cuda_lib
+    strs = [b"", b"a", b"a\x00", b"\x00", b"abcdefghi", b"abcdefghij", b"\x7f" * 9,
+            b"z" * 40, b"ab"]
+    w = workloads.from_strings(strs)
+    data, off = to_device(w)
+    for coder in (1, 2):
+        codes, exact, _ = hs.encode(data, off, coder=coder)
+        want, _, perfect = oracle.encode(w.bytes, w.offsets, coder)
+        assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
+        assert exact == perfect
+
+
+def test_encode_golden(cuda_lib):
+    hs = cuda_lib
+    rows = read_golden("husky_codes.txt")
+    for coder_name, coder in (("ASCII7", 1), ("BYTE8", 2)):
+        sel = [r for r in rows if r[0] == coder_name and (coder == 2 or
+               all(b < 0x80 for b in literal(r[1])))]
+        w = workloads.from_strings([literal(r[1]) for r in sel])
+        data, off = to_device(w)
+        codes, _, _ = hs.encode(data, off, coder=coder)
+        got = codes.cpu().numpy().view(np.uint64)
+        assert [int(x) for x in got] == [int(r[2], 16) for r in sel]
+
+
+def test_ascii7_domain_error_and_auto(cuda_lib):
+    hs = cuda_lib
+    w = workloads.from_strings([b"abc", b"\xc3\xa9t\xc3\xa9", b"ab\x80", b"zz"])
+    data, off = to_device(w)
+    with pytest.raises(hs.HuskyError) as e:
+        hs.encode(data, off, coder=hs.CODER_ASCII7)
+    assert e.value.status == hs.ERR_CODER_DOMAIN
+    codes, _, used = hs.encode(data, off, coder=hs.CODER_AUTO)
+    assert used == hs.CODER_BYTE8
+    want, _, _ = oracle.encode(w.bytes, w.offsets, oracle.CODER_BYTE8)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
+    perm = hs.argsort_device(data, off)
+    assert_oracle_equal(w, perm)
+
+
+def test_decreasing_offsets_rejected(cuda_lib):
+    hs = cuda_lib
+    import torch
+    data = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    off = torch.tensor([0, 5, 3, 9], dtype=torch.int64, device="cuda")
+    with pytest.raises(hs.HuskyError) as e:
+        hs.argsort_device(data, off)
+    assert e.value.status == hs.ERR_INVALID_ARG
+    off = torch.tensor([0, 5, 9, 65], dtype=torch.int64, device="cuda")
+    with pytest.raises(hs.HuskyError):
+        hs.argsort_device(data[:64], off)
+
+
+def test_workspace_too_small(cuda_lib):
+    hs = cuda_lib
+    import ctypes
+    import torch
+    w = workloads.generate(1, 1000, 0)
+    data, off = to_device(w)
+    perm = torch.empty(1000, dtype=torch.int32, device="cuda")
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    st = hs.load().hs_argsort(data.data_ptr(), off.data_ptr(), 1000, 0, 0, 0,
+                              perm.data_ptr(), ws.data_ptr(), 1024,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == hs.ERR_WORKSPACE
+
+
+# ---- Steps 1-3 ----------------------------------------------------------------
+
+def test_worked_example(cuda_lib):
+    hs = cuda_lib
+    rows = dict((r[0], r[1]) for r in read_golden("tiny_sort.txt"))
+    w = workloads.from_strings(literal(rows["strings"]))
+    data, off = to_device(w)
+    perm = hs.argsort_device(data, off)
+    assert list(perm_numpy(perm)) == literal(rows["perm"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 4095, 4096, 4097, 8193, 100_003])
+@pytest.mark.parametrize("kind", [1, 2, 5])
+def test_sizes_and_ragged_tails(cuda_lib, kind, n):
+    hs = cuda_lib
+    w = workloads.generate(kind, n, 100 + n)
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("index_u64", [False, True])
+def test_workloads_scaled(cuda_lib, kind, index_u64):
+    hs = cuda_lib
+    w = workloads.generate(kind, 1_000_003, 7 * kind)
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off, index_u64=index_u64))
+
+
+@pytest.mark.parametrize("run", [2, 31, 32, 33, 2047, 2048, 2049, 5000, 70_000])
+@pytest.mark.parametrize("shape", ["identical", "suffix", "deep"])
+def test_run_size_classes(cuda_lib, run, shape):
+    """Runs of equal husky codes at every size-class boundary: identical long
+    strings, distinct suffixes after a shared 9-char prefix, and ties that
+    need several 7-byte refinement windows."""
+    hs = cuda_lib
+    rng = np.random.default_rng(run)
+    strs = []
+    for i in range(run):
+        if shape == "identical":
+            s = b"abcdefghijklmnop"
+        elif shape == "suffix":
+            s = b"abcdefghi" + bytes(rng.integers(97, 100, size=rng.integers(0, 6)).astype(np.uint8))
+        else:
+            s = b"x" * 30 + bytes(rng.integers(97, 99, size=rng.integers(0, 12)).astype(np.uint8))
+        strs.append(s)
+    strs += [b"short", b"abcdefgh", b"abcdefghi", b"zzzz"] * 3
+    order = rng.permutation(len(strs))
+    w = workloads.from_strings([strs[i] for i in order])
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
+@pytest.mark.parametrize("case", ["equal_long", "equal_short", "empty", "sorted",
+                                  "reverse", "nul", "binary", "long_strings"])
+def test_adversarial(cuda_lib, case):
+    hs = cuda_lib
+    n = 20_000
+    rng = np.random.default_rng(3)
+    if case == "equal_long":
+        strs = [b"the-same-string-longer-than-nine"] * n
+    elif case == "equal_short":
+        strs = [b"same"] * n
+    elif case == "empty":
+        strs = [b""] * n
+    elif case == "sorted":
+        strs = [b"%012d" % i for i in range(n)]
+    elif case == "reverse":
+        strs = [b"%012d" % (n - i) for i in range(n)]
+    elif case == "nul":
+        strs = [b"a" + b"\x00" * (i % 13) + (b"b" if i % 3 == 0 else b"") for i in range(n)]
+    elif case == "binary":
+        strs = [bytes(rng.integers(0, 256, size=rng.integers(0, 20)).astype(np.uint8)) for _ in range(n)]
+    else:
+        strs = [b"q" * int(rng.integers(0, 3000)) + bytes([97 + i % 3]) for i in range(2000)]
+    w = workloads.from_strings(strs)
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
+def test_empty_input(cuda_lib):
+    hs = cuda_lib
+    w = workloads.from_strings([])
+    data, off = to_device(w)
+    assert hs.argsort_device(data, off).numel() == 0
+
+
+def test_host_inputs_roundtrip(cuda_lib):
+    hs = cuda_lib
+    import torch
+    w = workloads.generate(2, 200_000, 5)
+    data = torch.from_numpy(w.bytes).pin_memory()
+    off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+    perm = hs.argsort(data, off)
+    assert not perm.is_cuda
+    assert_oracle_equal(w, perm)
+
+
+def test_repeated_calls_reuse_workspace(cuda_lib):
+    hs = cuda_lib
+    for seed in range(3):
+        w = workloads.generate(5, 50_000 + seed, seed)
+        data, off = to_device(w)
+        assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
+# ---- full-size workloads (the bench's launch configuration) -------------------
+
+@pytest.mark.slow
+def test_full_zipf_words_1e7(cuda_lib):
+    hs = cuda_lib
+    w = workloads.standard("zipf_words_1e7")
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
+@pytest.mark.slow
+def test_full_shared_prefix_1e8(cuda_lib):
+    hs = cuda_lib
+    w = workloads.standard("shared_prefix_1e8")
+    data, off = to_device(w)
+    perm = hs.argsort_device(data, off)
+    del data, off
+    assert_stable_sorted(w, perm)
+
+
+@pytest.mark.slow
+def test_random_lower_1e5(cuda_lib):
+    hs = cuda_lib
+    w = workloads.standard("random_lower_1e5")
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
