@@ -90,13 +90,12 @@ __device__ __forceinline__ uint64_t window_offset(int prefix_len, uint32_t depth
 // prefix_len + 8 means both continue past the window.
 __device__ __forceinline__ uint64_t window_key(const uint8_t *s, uint64_t len,
                                                uint64_t o, int prefix_len) {
+    // Only the bytes that exist are loaded (a runtime-bounded loop); the rest
+    // of the window stays zero.
+    const uint64_t avail = len > o ? len - o : 0;
+    const uint32_t m = avail < 7 ? (uint32_t)avail : 7u;
     uint64_t key = 0;
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        uint64_t p = o + i;
-        uint64_t c = p < len ? s[p] : 0;
-        key = (key << 8) | c;
-    }
+    for (uint32_t i = 0; i < m; ++i) key |= (uint64_t)s[o + i] << (8 * (6 - i));
     int64_t t = (int64_t)len + prefix_len - (int64_t)o;
     int64_t cap = prefix_len + 8;
     if (t > cap) t = cap;
