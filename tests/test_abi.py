@@ -41,8 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_binding_names_match_headers():
     import paper_2012_00866_gb300 as hs
-    assert set(hs.EXPORTS) >= set(n for n in _declared_functions()
-                                  if not n.startswith("hs_noalloc"))
+    assert set(hs.EXPORTS) >= set(_declared_functions())
 
 
 def test_workspace_size_host_only():
