@@ -130,6 +130,41 @@ HS_API hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_of
                              uint64_t n, int coder, uint32_t *d_perm,
                              void *d_ws, size_t ws_bytes, void *stream);
 
+/* hs_argsort_noalloc -- hs_argsort for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a deployment convenience.
+ *
+ * Who needs it: code that runs inside a host application which owns the
+ * GPU's memory through its own pool and forbids side allocations (an engine
+ * plug-in or user-defined function, for instance), code on a latency-critical
+ * path where cudaMalloc's implicit device-wide synchronisation would stall
+ * other streams, and code whose memory budget is fixed when it is loaded.
+ * Such a caller can still pass its own inputs and output, but not a
+ * workspace.
+ *
+ * Scratch comes from one static device array of HS_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) inside the library; every GPU on which the library is loaded holds
+ * it until the process exits.  No cudaMalloc, cudaFree or other allocating
+ * routine is called.  The first call on each device looks up the array's
+ * device address with cudaGetSymbolAddress while that device is current;
+ * make that first call before any stream capture begins on the device.
+ *
+ * All calls share the one array and it keeps the previous call's contents
+ * (the call clears what must start at zero itself).  Calls whose GPU work
+ * overlaps -- on different streams or host threads -- race on the array and
+ * must be serialised by the caller.
+ *
+ * Arguments are those of hs_argsort with mode HS_MODE_PLAIN and no
+ * workspace; n must not exceed HS_NOALLOC_MAX_N (HS_ERR_INVALID_ARG
+ * otherwise, before any device work).  The permutation is identical to
+ * hs_argsort's. */
+#define HS_NOALLOC_MAX_N ((uint64_t)262144)
+#define HS_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+HS_API hs_status hs_argsort_noalloc(const uint8_t *d_bytes,
+                                    const uint64_t *d_offsets, uint64_t n,
+                                    int coder, int out_t, void *d_perm,
+                                    void *stream);
+
 /* Workspace needed by hs_encode / hs_argsort for n strings (mode, out_t as
  * in hs_argsort).  total_bytes (the byte-buffer size) is accepted for
  * forward compatibility and currently unused.  Writes *out; HS_OK. */

@@ -42,7 +42,9 @@ MAX_N = 0x7FFFFFFF
 # Every symbol include/husky.h declares (checked by the export test).
 EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
-           "hs_last_error", "hs_version")
+           "hs_argsort_noalloc", "hs_last_error", "hs_version")
+
+NOALLOC_MAX_N = 262144
 
 
 class KernelStat(ctypes.Structure):
@@ -81,6 +83,8 @@ def load(path: str | None = None):
     lib.hs_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
     lib.hs_batched_workspace_size.restype = ci
     lib.hs_batched_workspace_size.argtypes = [u64, u64, ctypes.POINTER(sz)]
+    lib.hs_argsort_noalloc.restype = ci
+    lib.hs_argsort_noalloc.argtypes = [vp, vp, u64, ci, ci, vp, vp]
     lib.hs_stats_enable.restype = ci
     lib.hs_stats_enable.argtypes = [ci]
     lib.hs_stats_read.restype = ci

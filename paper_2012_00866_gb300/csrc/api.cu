@@ -596,3 +596,63 @@ const char *hs_last_error(void) { return g_last_error.c_str(); }
 int hs_version(void) { return 100; }
 
 }  // extern "C"
+
+// ---- allocation-free variant (hs_argsort_noalloc) -----------------------------
+//
+// The scratch of hs_argsort, carved from one static device array instead of
+// a caller-supplied workspace.  Host code must not use the array's name as a
+// device address: its device address is looked up once per device with
+// cudaGetSymbolAddress while that device is current, and that pointer is what
+// the kernels receive.
+
+static __device__ __align__(256) unsigned char hs_noalloc_scratch[HS_NOALLOC_SCRATCH_BYTES];
+
+namespace hs {
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the static scratch on the current device (set-up on the
+// first call per device).
+hs_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(e, "hs_argsort_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HS_ERR_INVALID_ARG, "hs_argsort_noalloc: device id too large");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, hs_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return fail_cuda(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "hs_argsort_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HS_OK;
+}
+
+}  // namespace
+}  // namespace hs
+
+extern "C" hs_status hs_argsort_noalloc(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int coder,
+                                        int out_t, void *d_perm, void *stream) {
+    g_last_error.clear();
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    if (n > HS_NOALLOC_MAX_N)
+        return fail(HS_ERR_INVALID_ARG, "hs_argsort_noalloc: n exceeds HS_NOALLOC_MAX_N (262144 strings)");
+    if (n == 0) return HS_OK;
+    if (!d_bytes || !d_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    if (make_layout(n).total > HS_NOALLOC_SCRATCH_BYTES)
+        return fail(HS_ERR_INTERNAL, "hs_argsort_noalloc: scratch layout exceeds the static array");
+    void *ws = nullptr;
+    hs_status st = noalloc_scratch(&ws);
+    if (st != HS_OK) return st;
+    Ctx c;
+    if (!make_ctx(c, ws, HS_NOALLOC_SCRATCH_BYTES, n, stream, &st)) return st;
+    c.timing = false;  // no event objects on this path
+    Input in{d_bytes, d_offsets, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
+    return argsort_plain(c, in, coder);
+}
