@@ -71,7 +71,6 @@ cudaEvent_t pooled_event() {
 
 constexpr size_t kAlign = 256;
 constexpr int kNumCounters = 4096;
-constexpr int kHistPasses = 12;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -89,7 +88,7 @@ struct Layout {
     size_t flags, hist, bucket, counters;  // control block (zeroed per call)
     size_t control_end;
     size_t codes_a, codes_b, vals_a, vals_b, segs_a, segs_b, bits;
-    size_t lb_a, lb_b, lb_tie;
+    size_t lb;
     size_t q_small, q_medium, q_large_a, q_large_b, run_base;
     uint64_t cap_small, cap_medium, cap_large;
     size_t total;
@@ -110,10 +109,7 @@ Layout make_layout(uint64_t n) {
     L.segs_a = c.take(n * 4);
     L.segs_b = c.take(n * 4);
     L.bits = c.take(((n + 31) / 32) * 4);
-    const uint64_t tiles = sort_tiles(n);
-    L.lb_a = c.take(tiles * kBins * 8);
-    L.lb_b = c.take(tiles * kBins * 8);
-    L.lb_tie = c.take(tiles * 8);
+    L.lb = c.take(sort_tiles(n) * kBins * 8);
     L.cap_small = n / 2 + 1;
     L.cap_medium = n / (kSmallMax + 1) + 1;
     L.cap_large = n / (kMediumMax + 1) + 1;
@@ -157,6 +153,20 @@ struct Ctx {
             next_counter = 0;
         }
         *out = d_counters + next_counter++;
+        return cudaSuccess;
+    }
+
+    // Look-back epochs: each look-back launch gets its own; the array is
+    // cleared when they run out.
+    uint32_t epoch = kLbEpochs;  // forces a clear before the first use
+    uint64_t lb_words = 0;       // words to clear (sort_tiles(n) * kBins)
+    cudaError_t next_epoch(uint32_t *out) {
+        if (epoch >= kLbEpochs) {
+            cudaError_t e = cudaMemsetAsync(ws + L.lb, 0, lb_words * 8, s);
+            if (e != cudaSuccess) return e;
+            epoch = 0;
+        }
+        *out = ++epoch;
         return cudaSuccess;
     }
 
@@ -215,21 +225,22 @@ hs_status device_error_status(const DevFlags &h) {
 // Step 1 into ctx buffers; resolves HS_CODER_AUTO.  On return ctx.h holds the
 // flags and *used the coder actually used.
 hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int coder,
-                     uint64_t *codes, uint32_t *bits, bool hist, int *used) {
+                     uint64_t *codes, uint32_t *bits, bool hist, bool sort_key, int *used) {
     int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : HS_CODER_ASCII7;
     for (int attempt = 0; attempt < 2; ++attempt) {
         HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
         c.next_counter = 0;
         const double enc_bytes = 8.0 * (n + 1) + 8.0 * n + (bits ? n / 8.0 : 0.0);
         HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
-                   return launch_encode(u, bytes, offsets, n, codes, bits,
+                   return launch_encode(u, sort_key && u == HS_CODER_ASCII7, bytes, offsets, n, codes,
+                                        u == HS_CODER_ASCII7 && sort_key ? nullptr : bits,
                                         hist ? c.at<unsigned long long>(c.L.hist) : nullptr, c.d_flags, c.sms,
                                         c.s);
                }),
                "encode");
         if (hist)
             HS_TRY(c.timed(kKPlan, 8.0 * kBins * 16, [&] {
-                       return launch_plan(c.at<unsigned long long>(c.L.hist), 8, n,
+                       return launch_plan(c.at<unsigned long long>(c.L.hist), kKeyPasses, n,
                                           c.at<unsigned long long>(c.L.bucket), c.d_flags, c.s);
                    }),
                    "plan");
@@ -260,12 +271,11 @@ struct SortBufs {
 hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passes, int npasses,
                      bool segmented, const uint32_t *flag_bits, bool synth_first, void *final_out,
                      OutMode final_mode, bool keep_keys) {
-    uint64_t *lb[2] = {c.at<uint64_t>(c.L.lb_a), c.at<uint64_t>(c.L.lb_b)};
-    HS_TRY(cudaMemsetAsync(lb[0], 0, sort_tiles(n) * kBins * 8, c.s), "memset lookback");
+    uint64_t *lb = c.at<uint64_t>(c.L.lb);
     for (int i = 0; i < npasses; ++i) {
         const int p = passes[i];
         const bool first = i == 0, last = i == npasses - 1;
-        const bool digit_seg = p >= 8;
+        const bool digit_seg = p >= kKeyPasses;
         OnesweepArgs a{};
         a.keys_in = b.keys[*cur];
         a.keys_out = (last && !keep_keys) ? nullptr : b.keys[*cur ^ 1];
@@ -276,10 +286,11 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
         a.vals_out = to_final ? final_out : b.vals[*cur ^ 1];
         a.flag_bits = flag_bits;
         a.n = n;
-        a.shift = 8 * (p % 8);
+        a.shift = digit_shift(p);
+        a.mask = digit_mask(p);
         a.bucket_base = c.at<unsigned long long>(c.L.bucket) + (size_t)p * kBins;
-        a.lookback = lb[i & 1];
-        a.lookback_next = last ? nullptr : lb[(i + 1) & 1];
+        a.lookback = lb;
+        HS_TRY(c.next_epoch(&a.epoch), "epoch");
         HS_TRY(c.counter(&a.tile_counter), "counter");
         a.flags = c.d_flags;
         const OutMode om = to_final ? final_mode : kOutVals;
@@ -306,13 +317,13 @@ struct Input {
     int perm_u64;
 };
 
-hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
+hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode) {
     const uint64_t n = in.n;
     RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
     RunEntry *q_medium = c.at<RunEntry>(c.L.q_medium);
     RunEntry *q_large[2] = {c.at<RunEntry>(c.L.q_large_a), c.at<RunEntry>(c.L.q_large_b)};
     unsigned long long *run_base = c.at<unsigned long long>(c.L.run_base);
-    uint64_t *lb_tie = c.at<uint64_t>(c.L.lb_tie);
+    uint64_t *lb = c.at<uint64_t>(c.L.lb);
 
     TieArgs t{};
     t.keys = b.keys[cur];
@@ -321,6 +332,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
     t.prefix_len = in.prefix_len;
     t.perm = in.perm;
     t.perm_u64 = in.perm_u64;
+    t.perm_n = n;
     t.q_small = q_small;
     t.q_medium = q_medium;
     t.q_large = q_large[0];
@@ -328,13 +340,12 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
     t.cap_medium = c.L.cap_medium;
     t.cap_large = c.L.cap_large;
     t.q_large_id = kQLargeA;
-    t.lookback = lb_tie;
+    t.lookback = lb;
     t.flags = c.d_flags;
-    HS_TRY(cudaMemsetAsync(lb_tie, 0, ((n + kSortTile - 1) / kSortTile) * 8, c.s), "memset tie lookback");
+    HS_TRY(c.next_epoch(&t.epoch), "epoch");
     HS_TRY(c.counter(&t.tile_counter), "counter");
-    HS_TRY(c.timed(kKTieDetect, 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n,
-                   [&] { return launch_tie_detect(t, false, c.s); }),
-           "tie detect");
+    const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
+    HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
     HS_TRY(c.read_flags(), "tie sync");
     hs_status st = device_error_status(c.h);
     if (st != HS_OK) return st;
@@ -357,6 +368,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
         unsigned long long total = 0;
         HS_TRY(cudaMemcpyAsync(&total, run_base + large, 8, cudaMemcpyDeviceToHost, c.s), "read total");
         HS_TRY(cudaStreamSynchronize(c.s), "scan sync");
+        if (total > n) return fail(HS_ERR_INTERNAL, "large runs overlap (run descriptors inconsistent)");
         SortBufs r = b;
         int rc = 0;
         HS_TRY(c.timed(kKRefineKeys, 32.0 * total, [&] {
@@ -372,7 +384,8 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
             HS_TRY(c.timed(kKPushConstant, 32.0 * large, [&] {
                        return launch_push_constant_runs(q_large[li], large, run_base, r.keys[0], in.prefix_len,
                                                         q_small, q_medium, q_large[next], c.L.cap_small,
-                                                        c.L.cap_medium, c.L.cap_large, next_id, c.d_flags, c.s);
+                                                        c.L.cap_medium, c.L.cap_large, next_id, n, c.d_flags,
+                                                        c.s);
                    }),
                    "push constant runs");
         } else {
@@ -401,9 +414,9 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
             u.run_base = run_base;
             u.q_large = q_large[next];
             u.q_large_id = next_id;
-            HS_TRY(cudaMemsetAsync(lb_tie, 0, ((total + kSortTile - 1) / kSortTile) * 8, c.s), "memset lb");
+            HS_TRY(c.next_epoch(&u.epoch), "epoch");
             HS_TRY(c.counter(&u.tile_counter), "counter");
-            HS_TRY(c.timed(kKTieDetect, 20.0 * total, [&] { return launch_tie_detect(u, true, c.s); }),
+            HS_TRY(c.timed(kKTieDetect, 20.0 * total, [&] { return launch_tie_detect(u, kTieRefine, c.s); }),
                    "refine tie detect");
         }
         (void)cur_id;
@@ -418,15 +431,15 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur) {
     if (c.h.qcount[kQMedium])
         HS_TRY(c.timed(kKMediumRuns, (double)c.h.qcount[kQMedium] * 16.0 * (2 * isz + 16.0), [&] {
                    return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
-                                             &c.d_flags->qcount[kQMedium], c.L.cap_medium, in.prefix_len, c.sms,
-                                             c.s);
+                                             &c.d_flags->qcount[kQMedium], c.L.cap_medium, n, in.prefix_len,
+                                             c.sms, c.s);
                }),
                "medium runs");
     if (c.h.qcount[kQSmall])
         HS_TRY(c.timed(kKSmallRuns, (double)c.h.qcount[kQSmall] * (16.0 + 2.0 * (2 * isz + 16.0)), [&] {
                    return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
-                                            &c.d_flags->qcount[kQSmall], c.L.cap_small, in.prefix_len, c.sms,
-                                            c.s);
+                                            &c.d_flags->qcount[kQSmall], c.L.cap_small, n, in.prefix_len,
+                                            c.sms, c.s);
                }),
                "small runs");
     return HS_OK;
@@ -439,29 +452,37 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
                {c.at<uint32_t>(c.L.vals_a), c.at<uint32_t>(c.L.vals_b)},
                {c.at<uint32_t>(c.L.segs_a), c.at<uint32_t>(c.L.segs_b)}};
     uint32_t *bits = c.at<uint32_t>(c.L.bits);
+    c.lb_words = sort_tiles(n) * kBins;
     int used = 0;
-    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, &used);
+    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used);
     if (st != HS_OK) return st;
     in.prefix_len = used == HS_CODER_BYTE8 ? 8 : 9;
+    // ASCII7: the sort key carries the not-exact bit, so the permutation is
+    // final after the last pass and runs needing work are read off the keys.
+    // BYTE8: the bit rides in the payload and tie detection writes the
+    // permutation.
+    const bool key_flag = used == HS_CODER_ASCII7;
     const bool perfect = c.h.nonexact == 0;
-    int passes[8], np = 0;
-    for (int p = 0; p < 8; ++p)
+    int passes[kKeyPasses], np = 0;
+    for (int p = 0; p < kKeyPasses; ++p)
         if (c.h.active[p]) passes[np++] = p;
     const OutMode perm_mode = in.perm_u64 ? kOutPerm64 : kOutPerm32;
+    const bool final_is_perm = key_flag || perfect;
+    const uint32_t *flag_bits = key_flag ? nullptr : bits;
     int cur = 0;
     if (np == 0) {
         HS_TRY(c.timed(kKIdentity, n / 8.0 + 4.0 * n, [&] {
-                   return launch_identity(bits, n, perfect ? in.perm : (void *)b.vals[0],
-                                          perfect ? perm_mode : kOutVals, c.s);
+                   return launch_identity(flag_bits, n, final_is_perm ? in.perm : (void *)b.vals[0],
+                                          final_is_perm ? perm_mode : kOutVals, c.s);
                }),
                "identity");
     } else {
-        st = run_passes(c, b, &cur, n, passes, np, false, bits, true, perfect ? in.perm : nullptr, perm_mode,
-                        !perfect);
+        st = run_passes(c, b, &cur, n, passes, np, false, flag_bits, true, final_is_perm ? in.perm : nullptr,
+                        perm_mode, !perfect);
         if (st != HS_OK) return st;
     }
     if (!perfect) {
-        st = run_fixup(c, in, b, cur);
+        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag);
         if (st != HS_OK) return st;
     }
     HS_TRY(c.read_flags(), "final sync");
@@ -522,7 +543,7 @@ hs_status hs_encode(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t 
     }
     if (!d_bytes) return fail(HS_ERR_INVALID_ARG, "null bytes");
     int used = 0;
-    st = run_encode(c, d_bytes, d_offsets, n, coder, d_codes, nullptr, false, &used);
+    st = run_encode(c, d_bytes, d_offsets, n, coder, d_codes, nullptr, false, false, &used);
     if (st != HS_OK) return st;
     if (h_all_exact) *h_all_exact = c.h.nonexact ? 0 : 1;
     if (h_coder_used) *h_coder_used = used;

@@ -2,9 +2,18 @@
 // array with the per-element perfection test; Section 4.3 asciiToLong and
 // constants: 7 bits x 64/7 = 9 chars, mask 0x7F).
 //
-// One pass over offsets and bytes produces, per string i, the code, the
-// "not exactly represented" bit, and -- fused so the codes are not read back
-// -- the eight 8-bit digit histograms the radix sort needs up front.
+// One pass over offsets and bytes produces, per string i, the code (or the
+// sort key (code << 1) | not_exact, see below), the "not exactly represented"
+// bit, and -- fused so the keys are not read back -- the digit histograms the
+// radix sort needs up front.
+//
+// Sort key.  Under ASCII7 the code uses 63 bits.  Appending the not-exact bit
+// below it keeps the order of distinct codes and, among equal codes, puts the
+// exactly represented string first -- its true place, since an exact member
+// of a run of equal codes is a prefix of every other member (they agree on
+// the first 9 chars, and the exact one ends there or earlier).  Runs of equal
+// sort keys then either consist of identical strings (bit 0 clear: already in
+// index order after a stable sort) or need the fix-up (bit 0 set).
 //
 // Layout: a CTA takes a tile of 1024 consecutive strings.  Their offsets are
 // loaded coalesced into shared memory; their bytes, which are contiguous,
@@ -21,6 +30,10 @@ constexpr int kEncThreads = 256;
 constexpr int kEncTile = 1024;
 constexpr int kEncItems = kEncTile / kEncThreads;
 constexpr int kEncStage = 28672;   // staged bytes per tile
+constexpr int kEncHistPasses = kKeyPasses;
+constexpr size_t kEncOffBytes = (((size_t)kEncTile + 1) * 8 + 15) & ~(size_t)15;  // keeps s_bytes 16-B aligned
+constexpr size_t kEncSmem = kEncOffBytes + kEncStage + (size_t)kEncHistPasses * kBins * 4;
+static_assert(kEncStage % 16 == 0, "staging buffer must keep 16-byte alignment");
 
 template <int CODER> struct CoderTraits;
 template <> struct CoderTraits<1> {   // ASCII7
@@ -32,23 +45,24 @@ template <> struct CoderTraits<2> {   // BYTE8
     static constexpr unsigned MASK = 0xFF;
 };
 
-template <int CODER>
+template <int CODER, bool KEYFLAG>
 __global__ void __launch_bounds__(kEncThreads)
 encode_kernel(const uint8_t *__restrict__ bytes,
               const uint64_t *__restrict__ offsets, uint64_t n,
               uint64_t *__restrict__ codes, uint32_t *__restrict__ nonexact_bits,
               unsigned long long *__restrict__ hist, DevFlags *flags) {
     using C = CoderTraits<CODER>;
-    __shared__ uint64_t s_off[kEncTile + 1];
-    __shared__ __align__(16) uint8_t s_bytes[kEncStage];
-    __shared__ uint32_t s_hist[8 * kBins];
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_off = reinterpret_cast<uint64_t *>(smem);
+    uint8_t *s_bytes = smem + kEncOffBytes;
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_bytes + kEncStage);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total = offsets[n];
     const uintptr_t base = reinterpret_cast<uintptr_t>(bytes);
 
     if (hist)
-        for (int i = tid; i < 8 * kBins; i += kEncThreads) s_hist[i] = 0;
+        for (int i = tid; i < kEncHistPasses * kBins; i += kEncThreads) s_hist[i] = 0;
 
     bool any_nonexact = false, any_domain = false;
     const uint64_t num_tiles = (n + kEncTile - 1) / kEncTile;
@@ -110,11 +124,12 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                 const int shift = C::W * (C::K - m);
                 code = shift >= 64 ? 0 : (code << shift);
                 exact = len <= (uint64_t)C::K && (len == 0 || last != 0);
+                if (KEYFLAG) code = (code << 1) | (exact ? 0u : 1u);
                 codes[t0 + j] = code;
                 if (hist) {
 #pragma unroll
-                    for (int p = 0; p < 8; ++p)
-                        atomicAdd(&s_hist[p * kBins + (unsigned)((code >> (8 * p)) & 0xFF)], 1u);
+                    for (int p = 0; p < kEncHistPasses; ++p)
+                        atomicAdd(&s_hist[p * kBins + (unsigned)((code >> digit_shift(p)) & digit_mask(p))], 1u);
                 }
             }
             const unsigned ne = __ballot_sync(kFull, valid && !exact);
@@ -125,7 +140,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     }
     __syncthreads();
     if (hist)
-        for (int i = tid; i < 8 * kBins; i += kEncThreads)
+        for (int i = tid; i < kEncHistPasses * kBins; i += kEncThreads)
             if (s_hist[i]) atomicAdd(&hist[i], (unsigned long long)s_hist[i]);
     any_nonexact = __syncthreads_or(any_nonexact);
     any_domain = __syncthreads_or(any_domain);
@@ -135,22 +150,36 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     }
 }
 
+template <int CODER, bool KEYFLAG>
+cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t *codes,
+                       uint32_t *nonexact_bits, unsigned long long *hist, DevFlags *flags, unsigned grid,
+                       cudaStream_t s) {
+    auto kern = encode_kernel<CODER, KEYFLAG>;
+    static bool configured = false;  // attribute is per function, idempotent
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEncSmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<grid, kEncThreads, kEncSmem, s>>>(bytes, offsets, n, codes, nonexact_bits, hist, flags);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_encode(int coder, const uint8_t *bytes,
+cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
                           DevFlags *flags, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint64_t tiles = (n + kEncTile - 1) / kEncTile;
-    const unsigned grid = (unsigned)umin64(tiles, (uint64_t)num_sms * 5);
-    if (coder == 2)
-        encode_kernel<2><<<grid, kEncThreads, 0, s>>>(bytes, offsets, n, codes,
-                                                     nonexact_bits, hist, flags);
-    else
-        encode_kernel<1><<<grid, kEncThreads, 0, s>>>(bytes, offsets, n, codes,
-                                                     nonexact_bits, hist, flags);
-    return cudaGetLastError();
+    const unsigned grid = (unsigned)umin64(tiles, (uint64_t)num_sms * 4);
+    if (coder == 2) {
+        if (key_flag) return cudaErrorInvalidValue;  // BYTE8 codes use all 64 bits
+        return launch_enc<2, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, s);
+    }
+    if (key_flag) return launch_enc<1, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, s);
+    return launch_enc<1, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, s);
 }
 
 }  // namespace hs

@@ -23,8 +23,8 @@ namespace {
 //
 // Scan state over positions: has_head, position of the last run head, OR of
 // the "needs work" flags since that head.  (a then b) = b if b has a head,
-// else (a.has, a.last, a.or | b.or).  Packed into 62 bits for look-back:
-// bit 61 has, bit 60 or, bits 0..59 last.
+// else (a.has, a.last, a.or | b.or).  Packed into the 56-bit look-back value:
+// bit 55 has, bit 54 or, bits 0..53 last.
 
 struct RunState {
     uint64_t last;
@@ -37,12 +37,16 @@ __device__ __forceinline__ RunState combine(const RunState &a, const RunState &b
     return RunState{a.last, a.has, a.orf | b.orf};
 }
 
+constexpr uint64_t kRunLastMask = (1ull << 54) - 1;
+static_assert(((1ull << 55) | (1ull << 54) | kRunLastMask) <= kLbValueMask,
+              "packed run state must fit the look-back value");
+
 __device__ __forceinline__ uint64_t pack(const RunState &s) {
-    return ((uint64_t)s.has << 61) | ((uint64_t)s.orf << 60) | (s.last & ((1ull << 60) - 1));
+    return ((uint64_t)s.has << 55) | ((uint64_t)s.orf << 54) | (s.last & kRunLastMask);
 }
 
 __device__ __forceinline__ RunState unpack(uint64_t v) {
-    return RunState{v & ((1ull << 60) - 1), (uint32_t)((v >> 61) & 1), (uint32_t)((v >> 60) & 1)};
+    return RunState{v & kRunLastMask, (uint32_t)((v >> 55) & 1), (uint32_t)((v >> 54) & 1)};
 }
 
 constexpr int kTieThreads = 256;
@@ -50,6 +54,10 @@ constexpr int kTieItems = 16;
 constexpr int kTieTile = kTieThreads * kTieItems;
 
 __device__ __forceinline__ void push_run(const TieArgs &a, uint64_t start, uint64_t len, uint32_t depth) {
+    if (start >= a.perm_n || len > a.perm_n - start) {  // a run must lie inside perm
+        atomicOr(&a.flags->error, kErrInternal);
+        return;
+    }
     RunEntry e;
     e.start = start;
     e.len = (uint32_t)umin64(len, 0xFFFFFFFFull);
@@ -67,9 +75,17 @@ __device__ __forceinline__ void push_run(const TieArgs &a, uint64_t start, uint6
     }
 }
 
-template <bool REFINE>
+// Keys of the tile (plus one neighbour on each side) are staged through
+// shared memory with coalesced loads; each thread then scans 16 consecutive
+// positions.
+constexpr size_t kTieSmem = (size_t)(kTieTile + 2) * 8;
+
+template <int MODE>
 __global__ void __launch_bounds__(kTieThreads)
 tie_detect_kernel(const TieArgs a) {
+    constexpr bool REFINE = MODE == kTieRefine;
+    extern __shared__ __align__(16) unsigned char tie_smem[];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(tie_smem);  // s_key[i + 1] = keys[t0 + i]
     __shared__ uint64_t s_state[kTieThreads / 32];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_prefix;
@@ -78,31 +94,35 @@ tie_detect_kernel(const TieArgs a) {
     __syncthreads();
     const uint64_t tile = s_tile;
     const uint64_t n = a.n;
-    const uint64_t j0 = tile * kTieTile + (uint64_t)tid * kTieItems;
+    const uint64_t t0 = tile * kTieTile;
     const uint32_t cont_tag = (uint32_t)a.prefix_len + 8;
 
-    // Thread-local pass: heads and flags of my items.
-    uint64_t key_prev = 0;
-    uint32_t seg_prev = 0;
-    if (j0 > 0 && j0 - 1 < n) {
-        key_prev = a.keys[j0 - 1];
-        if (REFINE) seg_prev = a.segs[j0 - 1];
+    for (int i = tid; i < kTieTile + 2; i += kTieThreads) {
+        const uint64_t j = t0 + i;  // position t0 + i - 1
+        s_key[i] = (j >= 1 && j - 1 < n) ? a.keys[j - 1] : 0;
     }
+    __syncthreads();
+
+    const int i0 = tid * kTieItems;
+    const uint64_t j0 = t0 + i0;
+    uint32_t seg_prev = 0;
+    if (REFINE && j0 > 0 && j0 - 1 < n) seg_prev = a.segs[j0 - 1];
     uint32_t heads = 0, flagsb = 0;
     RunState mine{0, 0, 0};
 #pragma unroll
     for (int i = 0; i < kTieItems; ++i) {
         const uint64_t j = j0 + i;
         if (j < n) {
-            const uint64_t k = a.keys[j];
+            const uint64_t k = s_key[i0 + i + 1];
             const uint32_t sg = REFINE ? a.segs[j] : 0;
-            const bool head = (j == 0) || k != key_prev || (REFINE && sg != seg_prev);
-            const uint32_t v = a.vals[j];
-            const bool f = REFINE ? ((uint32_t)(k & 0xFF) == cont_tag) : ((v >> 31) != 0);
+            const bool head = (j == 0) || k != s_key[i0 + i] || (REFINE && sg != seg_prev);
+            bool f;
+            if (MODE == kTieKeyFlag) f = (k & 1u) != 0;
+            else if (MODE == kTieValFlag) f = (a.vals[j] >> 31) != 0;
+            else f = window_tag(k) == cont_tag;
             heads |= (uint32_t)head << i;
             flagsb |= (uint32_t)f << i;
             mine = combine(mine, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
-            key_prev = k;
             seg_prev = sg;
         }
     }
@@ -135,17 +155,17 @@ tie_detect_kernel(const TieArgs a) {
         RunState agg{0, 0, 0};
         for (int w = 0; w < kTieThreads / 32; ++w) agg = combine(agg, unpack(s_state[w]));
         uint64_t *lb = a.lookback + tile;
+        const uint32_t epoch = a.epoch;
         RunState prefix{0, 0, 0};
         if (tile == 0) {
-            st_relaxed(lb, kLbInclusive | pack(agg));
+            st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(agg)));
         } else {
-            st_relaxed(lb, kLbAggregate | pack(agg));
+            st_relaxed(lb, lb_word(epoch, kLbAggregate, pack(agg)));
             int64_t t = (int64_t)tile - 1;
             uint32_t spins = 0;
             while (t >= 0) {
                 const uint64_t v = ld_relaxed(&a.lookback[t]);
-                const uint64_t st = v & ~kLbValueMask;
-                if (st == 0) {
+                if ((uint32_t)(v >> 58) != epoch) {
                     if (++spins > kSpinLimit) {
                         atomicOr(&a.flags->error, kErrTimeout);
                         break;
@@ -154,10 +174,10 @@ tie_detect_kernel(const TieArgs a) {
                     continue;
                 }
                 prefix = combine(unpack(v & kLbValueMask), prefix);
-                if (st == kLbInclusive) break;
+                if ((v & (3ull << 56)) == kLbInclusive) break;
                 --t;
             }
-            st_relaxed(lb, kLbInclusive | pack(combine(prefix, agg)));
+            st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(combine(prefix, agg))));
         }
         s_prefix = pack(prefix);
     }
@@ -165,14 +185,9 @@ tie_detect_kernel(const TieArgs a) {
     RunState st = combine(unpack(s_prefix), excl);
 
     // Replay my items: write the permutation, emit runs at their tails.
-    uint64_t next_key = 0;
     uint32_t next_seg = 0;
     const uint64_t jn = j0 + kTieItems;
-    bool next_head = true;
-    if (jn < n) {
-        next_key = a.keys[jn];
-        if (REFINE) next_seg = a.segs[jn];
-    }
+    if (REFINE && jn < n) next_seg = a.segs[jn];
 #pragma unroll
     for (int i = 0; i < kTieItems; ++i) {
         const uint64_t j = j0 + i;
@@ -180,7 +195,6 @@ tie_detect_kernel(const TieArgs a) {
         const bool head = (heads >> i) & 1u;
         const bool f = (flagsb >> i) & 1u;
         st = combine(st, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
-        const uint32_t v = a.vals[j];
         uint64_t pos = j, run_start = st.last;
         uint32_t depth = 0;
         if (REFINE) {
@@ -190,23 +204,22 @@ tie_detect_kernel(const TieArgs a) {
             run_start = r.start + (st.last - a.run_base[sg]);
             depth = r.depth + 1;
         }
-        if (a.perm_u64)
-            static_cast<uint64_t *>(a.perm)[pos] = REFINE ? v : (v & kIdxMask);
-        else
-            static_cast<uint32_t *>(a.perm)[pos] = REFINE ? v : (v & kIdxMask);
+        if (MODE != kTieKeyFlag) {
+            const uint32_t v = a.vals[j];
+            const uint32_t out = REFINE ? v : (v & kIdxMask);
+            if (a.perm_u64)
+                static_cast<uint64_t *>(a.perm)[pos] = out;
+            else
+                static_cast<uint32_t *>(a.perm)[pos] = out;
+        }
         bool tail;
         if (i + 1 < kTieItems) {
             tail = (j + 1 >= n) || ((heads >> (i + 1)) & 1u);
+        } else if (jn >= n) {
+            tail = true;
         } else {
-            if (jn >= n) {
-                tail = true;
-            } else {
-                const uint64_t k = a.keys[j];
-                const uint32_t sg = REFINE ? a.segs[j] : 0;
-                tail = next_key != k || (REFINE && next_seg != sg);
-            }
+            tail = s_key[i0 + i + 2] != s_key[i0 + i + 1] || (REFINE && next_seg != a.segs[j]);
         }
-        (void)next_head;
         if (tail) {
             const uint64_t len = j - st.last + 1;
             if (len >= 2 && st.orf) push_run(a, run_start, len, depth);
@@ -220,14 +233,15 @@ template <typename IdxT>
 __global__ void __launch_bounds__(256)
 small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                   IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
-                  const unsigned long long *__restrict__ qcount, uint64_t cap, int prefix_len) {
+                  const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
+                  int prefix_len) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t count = umin64(*qcount, cap);
     for (uint64_t r = warp_id; r < count; r += nwarps) {
         const RunEntry e = q[r];
-        if (e.len > kSmallMax) continue;  // never queued here
+        if (e.len > kSmallMax || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
         const bool mine = (uint32_t)lane < e.len;
         IdxT idx = 0;
         uint64_t off = 0, len = 0;
@@ -270,7 +284,8 @@ template <typename IdxT>
 __global__ void __launch_bounds__(kMedThreads)
 medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
-                   const unsigned long long *__restrict__ qcount, uint64_t cap, int prefix_len) {
+                   const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
+                   int prefix_len) {
     constexpr int CAP = kMediumMax;
     __shared__ uint64_t s_key[CAP];
     __shared__ uint32_t s_seg[CAP];
@@ -284,7 +299,7 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
 
     for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
         const RunEntry e = q[r];
-        if (e.len > (uint32_t)CAP) continue;  // never queued here
+        if (e.len > (uint32_t)CAP || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
         const int len = (int)e.len;
         int P = 1;
         while (P < len) P <<= 1;
@@ -314,8 +329,13 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
                 }
             }
             __syncthreads();
-            // Bitonic sort of P elements by (seg, key, idx).
-            for (int k = 2; k <= P; k <<= 1) {
+            // Bitonic sort of P elements by (seg, key, idx), skipped when the
+            // run is already in that order (e.g. copies of one string).
+            bool unsorted = false;
+            for (int j = tid; j + 1 < len; j += kMedThreads)
+                unsorted |= elem_greater<IdxT>(s_seg[j], s_key[j], s_idx[j], s_seg[j + 1], s_key[j + 1], s_idx[j + 1]);
+            const bool do_sort = __syncthreads_or(unsorted);
+            for (int k = 2; do_sort && k <= P; k <<= 1) {
                 for (int jj = k >> 1; jj > 0; jj >>= 1) {
                     for (int i = tid; i < P; i += kMedThreads) {
                         const int ixj = i ^ jj;
@@ -349,7 +369,7 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
                     const bool same_next = j + 1 < len && s_seg[j + 1] == s_seg[j] && s_key[j + 1] == s_key[j];
                     const bool was_active = s_segact[s_seg[j]] != 0;
                     head[u] = !same_prev;
-                    act[u] = was_active && (uint32_t)(s_key[j] & 0xFF) == cont_tag && (same_prev || same_next);
+                    act[u] = was_active && window_tag(s_key[j]) == cont_tag && (same_prev || same_next);
                     hcount += head[u];
                 }
             }
@@ -471,45 +491,46 @@ __global__ void push_constant_runs_kernel(const RunEntry *__restrict__ runs, uin
     for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += stride) {
         const RunEntry e = runs[r];
         const uint64_t k = keys[run_base[r]];
-        if ((uint32_t)(k & 0xFF) == cont_tag) push_run(a, e.start, e.len, e.depth + 1);
+        if (window_tag(k) == cont_tag) push_run(a, e.start, e.len, e.depth + 1);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_tie_detect(const TieArgs &a, bool refine, cudaStream_t s) {
+cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    const uint64_t tiles = (a.n + kTieTile - 1) / kTieTile;
-    if (refine)
-        tie_detect_kernel<true><<<(unsigned)tiles, kTieThreads, 0, s>>>(a);
-    else
-        tie_detect_kernel<false><<<(unsigned)tiles, kTieThreads, 0, s>>>(a);
+    const unsigned tiles = (unsigned)((a.n + kTieTile - 1) / kTieTile);
+    switch (mode) {
+        case kTieKeyFlag: tie_detect_kernel<kTieKeyFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
+        case kTieValFlag: tie_detect_kernel<kTieValFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
+        default: tie_detect_kernel<kTieRefine><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
-                              const RunEntry *q, const unsigned long long *qcount, uint64_t cap, int prefix_len,
-                              int num_sms, cudaStream_t s) {
+                              const RunEntry *q, const unsigned long long *qcount, uint64_t cap, uint64_t perm_n,
+                              int prefix_len, int num_sms, cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 8;
     if (perm_u64)
         small_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q,
-                                                         qcount, cap, prefix_len);
+                                                         qcount, cap, perm_n, prefix_len);
     else
         small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
-                                                         qcount, cap, prefix_len);
+                                                         qcount, cap, perm_n, prefix_len);
     return cudaGetLastError();
 }
 
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
                                const RunEntry *q, const unsigned long long *qcount, uint64_t cap,
-                               int prefix_len, int num_sms, cudaStream_t s) {
+                               uint64_t perm_n, int prefix_len, int num_sms, cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 2;
     if (perm_u64)
         medium_runs_kernel<uint64_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm),
-                                                                  q, qcount, cap, prefix_len);
+                                                                  q, qcount, cap, perm_n, prefix_len);
     else
         medium_runs_kernel<uint32_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm),
-                                                                  q, qcount, cap, prefix_len);
+                                                                  q, qcount, cap, perm_n, prefix_len);
     return cudaGetLastError();
 }
 
@@ -540,7 +561,7 @@ cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count, cons
                                       const uint64_t *keys, int prefix_len, RunEntry *q_small,
                                       RunEntry *q_medium, RunEntry *q_large, uint64_t cap_small,
                                       uint64_t cap_medium, uint64_t cap_large, int q_large_id,
-                                      DevFlags *flags, cudaStream_t s) {
+                                      uint64_t perm_n, DevFlags *flags, cudaStream_t s) {
     if (count == 0) return cudaSuccess;
     TieArgs a{};
     a.prefix_len = prefix_len;
@@ -551,6 +572,7 @@ cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count, cons
     a.cap_medium = cap_medium;
     a.cap_large = cap_large;
     a.q_large_id = q_large_id;
+    a.perm_n = perm_n;
     a.flags = flags;
     const unsigned grid = (unsigned)umin64((count + 255) / 256, 1024);
     push_constant_runs_kernel<<<grid, 256, 0, s>>>(runs, count, run_base, keys, a);

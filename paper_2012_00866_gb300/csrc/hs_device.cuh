@@ -7,7 +7,8 @@
 namespace hs {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kBins = 256;             // 8-bit radix digits
+constexpr int kRadixBits = 9;          // radix digit width
+constexpr int kBins = 1 << kRadixBits; // 512 digit values
 constexpr uint32_t kFlagBit = 0x80000000u;  // "not exactly encoded" payload bit
 constexpr uint32_t kIdxMask = 0x7FFFFFFFu;
 
@@ -37,11 +38,20 @@ struct RunEntry {
     unsigned int depth;
 };
 
-// Decoupled look-back words: 2-bit status in bits 62..63, 62-bit value.
-constexpr uint64_t kLbAggregate = 1ull << 62;
-constexpr uint64_t kLbInclusive = 2ull << 62;
-constexpr uint64_t kLbValueMask = (1ull << 62) - 1;
+// Decoupled look-back words: a 6-bit epoch in bits 58..63 (which launch
+// wrote the word; 0 = never written), a 2-bit status in bits 56..57
+// (aggregate of this tile only / inclusive prefix), a 56-bit value.  Words
+// from earlier launches carry another epoch and read as "not ready", so the
+// array is cleared once per call rather than once per pass.
+constexpr uint64_t kLbAggregate = 1ull << 56;
+constexpr uint64_t kLbInclusive = 2ull << 56;
+constexpr uint64_t kLbValueMask = (1ull << 56) - 1;
+constexpr uint32_t kLbEpochs = 63;          // usable epochs 1..63
 constexpr uint32_t kSpinLimit = 1u << 22;   // polls before a wait gives up
+
+__host__ __device__ __forceinline__ uint64_t lb_word(uint32_t epoch, uint64_t status, uint64_t value) {
+    return ((uint64_t)epoch << 58) | status | (value & kLbValueMask);
+}
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
@@ -61,12 +71,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Lanes of the warp whose 8-bit digit equals this lane's, restricted to
-// `active` (8 ballots, one per digit bit).
+// Lanes of the warp whose radix digit equals this lane's, restricted to
+// `active` (one ballot per digit bit).
 __device__ __forceinline__ unsigned match_digit(unsigned d, unsigned active) {
     unsigned peers = active;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
+    for (int b = 0; b < kRadixBits; ++b) {
         unsigned bit = (d >> b) & 1u;
         unsigned vote = __ballot_sync(kFull, bit);
         peers &= bit ? vote : ~vote;
@@ -82,12 +92,16 @@ __device__ __forceinline__ uint64_t window_offset(int prefix_len, uint32_t depth
 }
 
 // Refinement key of a string of length len at byte offset o: the 7 bytes
-// [o, o+7) big-endian (zero padded) in bits 8..63 and a tag in bits 0..7,
-//   tag = min(len + prefix_len - o, prefix_len + 8).
+// [o, o+7) big-endian (zero padded) in bits 5..60 and a tag in bits 0..4,
+//   tag = min(len + prefix_len - o, prefix_len + 8)   (at most 17 < 32).
 // Among strings that agree on their first o bytes (or, at o = prefix_len,
 // share a husky code), unsigned key order is lexicographic order on the
 // window; equal keys with tag < prefix_len + 8 mean identical strings; tag ==
-// prefix_len + 8 means both continue past the window.
+// prefix_len + 8 means both continue past the window.  The key fits in 61
+// bits, so it sorts in seven 9-bit digits.
+constexpr int kTagBits = 5;
+__device__ __forceinline__ uint32_t window_tag(uint64_t key) { return (uint32_t)(key & ((1u << kTagBits) - 1)); }
+
 __device__ __forceinline__ uint64_t window_key(const uint8_t *s, uint64_t len,
                                                uint64_t o, int prefix_len) {
     // Only the bytes that exist are loaded (a runtime-bounded loop); the rest
@@ -100,7 +114,7 @@ __device__ __forceinline__ uint64_t window_key(const uint8_t *s, uint64_t len,
     int64_t cap = prefix_len + 8;
     if (t > cap) t = cap;
     if (t < 0) t = 0;
-    return (key << 8) | (uint64_t)t;
+    return (key << kTagBits) | (uint64_t)t;
 }
 
 // Three-way unsigned-byte comparison of a and b starting at byte `from`

@@ -10,9 +10,11 @@
 namespace hs {
 
 // ---- encode.cu -----------------------------------------------------------
-// Step 1 over n strings: codes[i], optional non-exact bitmask (bit i of word
-// i/32), optional 8 digit histograms (8 x 256 u64, accumulated), flags.
-cudaError_t launch_encode(int coder, const uint8_t *bytes,
+// Step 1 over n strings.  Writes per string either the husky code or, with
+// key_flag (ASCII7 only), the sort key (code << 1) | not_exact; optionally
+// the non-exact bitmask (bit i of word i/32) and the 8 digit histograms of
+// what it wrote (8 x kBins u64, accumulated); sets flags.
+cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
                           DevFlags *flags, int num_sms, cudaStream_t s);
@@ -20,6 +22,17 @@ cudaError_t launch_encode(int coder, const uint8_t *bytes,
 // ---- sort.cu -------------------------------------------------------------
 constexpr int kSortTile = 4096;  // elements per onesweep tile
 inline uint64_t sort_tiles(uint64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+// Digit plan.  A 64-bit key has 8 digits: seven of 9 bits (bits 0..62) and
+// the top bit alone; a 32-bit segment id has 4 digits of 9 bits.  Histogram
+// index p: 0..7 key digits, 8..11 segment digits.
+constexpr int kKeyPasses = 8;
+constexpr int kSegPasses = 4;
+constexpr int kHistPasses = kKeyPasses + kSegPasses;
+__host__ __device__ inline int digit_shift(int p) {
+    return p < 7 ? kRadixBits * p : (p == 7 ? 63 : kRadixBits * (p - 8));
+}
+__host__ __device__ inline unsigned digit_mask(int p) { return p == 7 ? 1u : (unsigned)(kBins - 1); }
 
 enum OutMode { kOutVals = 0, kOutPerm32 = 1, kOutPerm64 = 2 };
 
@@ -32,10 +45,11 @@ struct OnesweepArgs {
     void *vals_out;
     const uint32_t *flag_bits;   // synthesised vals: bit 31 source (nullable)
     uint64_t n;
-    int shift;                   // digit = (source >> shift) & 255
-    const unsigned long long *bucket_base;  // 256 entries for this pass
-    uint64_t *lookback;          // sort_tiles(n) * 256 words, zeroed
-    uint64_t *lookback_next;     // zeroed by this pass for the next one
+    int shift;                   // digit = (source >> shift) & mask
+    unsigned mask;
+    const unsigned long long *bucket_base;  // kBins entries for this pass
+    uint64_t *lookback;          // sort_tiles(n) * kBins words
+    uint32_t epoch;              // look-back epoch of this launch (1..63)
     unsigned int *tile_counter;  // zeroed
     DevFlags *flags;
 };
@@ -48,7 +62,7 @@ cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg,
                             cudaStream_t s);
 
 // Digit histograms of keys (8 digits) and optionally segs (4 digits):
-// hist[(p) * 256 + d], p < 8 for keys, 8..11 for segs; accumulated.
+// hist[p * kBins + d], p < 8 for keys, 8..11 for segs; accumulated.
 cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs,
                              uint64_t n, unsigned long long *hist,
                              int num_sms, cudaStream_t s);
@@ -68,6 +82,14 @@ enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3 };
 constexpr uint32_t kSmallMax = 32;     // warp per run
 constexpr uint32_t kMediumMax = 2048;  // block per run
 
+// Tie-detection modes: where the "needs work" flag of an element lives and
+// what is written to the permutation.
+enum TieMode {
+    kTieKeyFlag = 0,   // flag = key bit 0 (ASCII7 sort key); perm already written
+    kTieValFlag = 1,   // flag = payload bit 31; perm[j] = payload & kIdxMask
+    kTieRefine = 2     // flag = window tag "continues"; perm[pos(j)] = payload
+};
+
 struct TieArgs {
     const uint64_t *keys;
     const uint32_t *segs;           // refinement only
@@ -76,30 +98,33 @@ struct TieArgs {
     int prefix_len;                 // bytes covered by the husky code
     void *perm;                     // output permutation
     int perm_u64;
+    uint64_t perm_n;                // length of perm (every run must fit)
     const RunEntry *runs;           // refinement: runs being refined
     const unsigned long long *run_base;  // refinement: compacted starts
     RunEntry *q_small, *q_medium, *q_large;
     uint64_t cap_small, cap_medium, cap_large;
     int q_large_id;                 // which DevFlags::qcount slot q_large uses
-    uint64_t *lookback;             // sort_tiles(n) words, zeroed
+    uint64_t *lookback;             // sort_tiles(n) words
+    uint32_t epoch;                 // look-back epoch (1..63)
     unsigned int *tile_counter;     // zeroed
     DevFlags *flags;
 };
 
 // Equal-key runs of a sorted sequence that still need work, pushed to the
-// size-class queues; also writes the permutation (plain: vals stripped of
-// the flag bit at position j; refinement: vals written back to positions).
-cudaError_t launch_tie_detect(const TieArgs &a, bool refine, cudaStream_t s);
+// size-class queues; writes the permutation as the mode says.
+cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s);
 
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets,
                               void *perm, int perm_u64, const RunEntry *q,
                               const unsigned long long *qcount, uint64_t cap,
-                              int prefix_len, int num_sms, cudaStream_t s);
+                              uint64_t perm_n, int prefix_len, int num_sms,
+                              cudaStream_t s);
 
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
                                void *perm, int perm_u64, const RunEntry *q,
                                const unsigned long long *qcount, uint64_t cap,
-                               int prefix_len, int num_sms, cudaStream_t s);
+                               uint64_t perm_n, int prefix_len, int num_sms,
+                               cudaStream_t s);
 
 // Large-run refinement helpers.
 cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count,
@@ -119,7 +144,7 @@ cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count,
                                       RunEntry *q_small, RunEntry *q_medium,
                                       RunEntry *q_large, uint64_t cap_small,
                                       uint64_t cap_medium, uint64_t cap_large,
-                                      int q_large_id, DevFlags *flags,
-                                      cudaStream_t s);
+                                      int q_large_id, uint64_t perm_n,
+                                      DevFlags *flags, cudaStream_t s);
 
 }  // namespace hs

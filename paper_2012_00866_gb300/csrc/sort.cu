@@ -6,21 +6,24 @@
 // Each pass is a single "onesweep" kernel (Adinets and Merrill, 2022): the
 // global digit offsets come from histograms computed up front (fused into the
 // encoder), each CTA ranks a tile of 4096 keys with warp-private digit
-// counters (8-ballot match), publishes its per-digit counts and resolves its
-// global prefix by decoupled look-back over earlier tiles, then scatters the
-// tile through shared memory so that runs of equal digits leave as coalesced
-// stores.  Tile ids come from an atomic counter, so every tile a CTA waits on
-// is already running; each wait is bounded and reports kErrTimeout.
+// counters (one ballot per digit bit), publishes its per-digit counts and
+// resolves its global prefix by decoupled look-back over earlier tiles, then
+// scatters the tile through shared memory so that runs of equal digits leave
+// as coalesced stores.  Digits are 9 bits wide (512 bins, one per thread in
+// the per-digit phase); 512 threads x 8 keys per CTA at <= 64 registers keep
+// two CTAs (32 warps) resident per SM.  Tile ids come from an atomic counter,
+// so every tile a CTA waits on is already running; each wait is bounded and
+// reports kErrTimeout.
 #include "hs_internal.h"
 
 namespace hs {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = kSortTile / kThreads;  // 16
+constexpr int kItems = kSortTile / kThreads;  // 8
 
-// Exclusive scan of one u32 per thread over a 256-thread block.
+// Exclusive scan of one u32 per thread over a 512-thread block.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -32,7 +35,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     if (lane == 31) s_warp[warp] = x;
     __syncthreads();
     uint32_t wsum = 0;
-    for (int w = 0; w < warp; ++w) wsum += s_warp[w];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wsum += w < warp ? s_warp[w] : 0u;
     __syncthreads();
     return wsum + x - v;
 }
@@ -45,8 +49,7 @@ onesweep_kernel(const OnesweepArgs a) {
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
     uint32_t *s_segs = s_vals + kSortTile;
     uint32_t *s_whist = s_segs + (HAS_SEG ? kSortTile : 0);
-    uint32_t *s_dstart = s_whist + kWarps * kBins;
-    unsigned long long *s_gbase = reinterpret_cast<unsigned long long *>(s_dstart + kBins);
+    unsigned long long *s_gbase = reinterpret_cast<unsigned long long *>(s_whist + kWarps * kBins);
     __shared__ uint32_t s_scan[kWarps];
     __shared__ uint32_t s_tile;
 
@@ -57,10 +60,11 @@ onesweep_kernel(const OnesweepArgs a) {
     const uint64_t tile = s_tile;
     const uint64_t n = a.n;
     const uint64_t tile_base = tile * kSortTile;
-    if (a.lookback_next) a.lookback_next[tile * kBins + tid] = 0;
+    const int shift = a.shift;
+    const unsigned mask = a.mask;
 
-    // Warp-striped load: warp w owns elements [w*512, w*512+512) of the tile,
-    // item k of lane l is element w*512 + k*32 + l, so processing items in k
+    // Warp-striped load: warp w owns elements [w*256, w*256+256) of the tile,
+    // item k of lane l is element w*256 + k*32 + l, so processing items in k
     // order visits the warp's elements in input order (stability).
     uint64_t key[kItems];
     uint32_t val[kItems];
@@ -88,8 +92,7 @@ onesweep_kernel(const OnesweepArgs a) {
         const uint64_t e = wbase + k * 32 + lane;
         const bool valid = e < n;
         const unsigned active = __ballot_sync(kFull, valid);
-        const unsigned d = DIGIT_SEG ? ((seg[k] >> a.shift) & 0xFFu)
-                                     : (unsigned)((key[k] >> a.shift) & 0xFFu);
+        const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
         const unsigned peers = match_digit(d, active);
         const int leader = valid ? __ffs(peers) - 1 : lane;
         uint32_t before = 0;
@@ -112,17 +115,17 @@ onesweep_kernel(const OnesweepArgs a) {
         total += c;
     }
     uint64_t *lb = a.lookback + tile * kBins;
+    const uint32_t epoch = a.epoch;
     uint64_t prefix = 0;
     if (tile == 0) {
-        st_relaxed(&lb[tid], kLbInclusive | total);
+        st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, total));
     } else {
-        st_relaxed(&lb[tid], kLbAggregate | total);
+        st_relaxed(&lb[tid], lb_word(epoch, kLbAggregate, total));
         int64_t t = (int64_t)tile - 1;
         uint32_t spins = 0;
         while (t >= 0) {
             const uint64_t v = ld_relaxed(&a.lookback[(uint64_t)t * kBins + tid]);
-            const uint64_t st = v & ~kLbValueMask;
-            if (st == 0) {
+            if ((uint32_t)(v >> 58) != epoch) {
                 if (++spins > kSpinLimit) {
                     atomicOr(&a.flags->error, kErrTimeout);
                     break;
@@ -131,24 +134,24 @@ onesweep_kernel(const OnesweepArgs a) {
                 continue;
             }
             prefix += v & kLbValueMask;
-            if (st == kLbInclusive) break;
+            if ((v & (3ull << 56)) == kLbInclusive) break;
             --t;
         }
-        st_relaxed(&lb[tid], kLbInclusive | (prefix + total));
+        st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, prefix + total));
     }
 
     const uint32_t dstart = block_exclusive_scan(total, s_scan);
-    s_dstart[tid] = dstart;
     s_gbase[tid] = a.bucket_base[tid] + prefix - dstart;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s_whist[w * kBins + tid] += dstart;
     __syncthreads();
 
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const uint64_t e = wbase + k * 32 + lane;
         if (e < n) {
-            const unsigned d = DIGIT_SEG ? ((seg[k] >> a.shift) & 0xFFu)
-                                         : (unsigned)((key[k] >> a.shift) & 0xFFu);
-            const uint32_t p = s_dstart[d] + s_whist[warp * kBins + d] + rank[k];
+            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
+            const uint32_t p = my_hist[d] + rank[k];
             s_keys[p] = key[k];
             s_vals[p] = val[k];
             if (HAS_SEG) s_segs[p] = seg[k];
@@ -160,7 +163,7 @@ onesweep_kernel(const OnesweepArgs a) {
     for (int i = tid; i < cnt; i += kThreads) {
         const uint64_t k = s_keys[i];
         const uint32_t sg = HAS_SEG ? s_segs[i] : 0;
-        const unsigned d = DIGIT_SEG ? ((sg >> a.shift) & 0xFFu) : (unsigned)((k >> a.shift) & 0xFFu);
+        const unsigned d = DIGIT_SEG ? ((sg >> shift) & mask) : (unsigned)((k >> shift) & mask);
         const uint64_t pos = s_gbase[d] + (uint64_t)i;
         if (pos >= n) {
             atomicOr(&a.flags->error, kErrInternal);
@@ -180,7 +183,7 @@ onesweep_kernel(const OnesweepArgs a) {
 
 size_t onesweep_smem(bool has_seg) {
     return (size_t)kSortTile * 8 + (size_t)kSortTile * 4 + (has_seg ? (size_t)kSortTile * 4 : 0) +
-           (size_t)kWarps * kBins * 4 + (size_t)kBins * 4 + (size_t)kBins * 8;
+           (size_t)kWarps * kBins * 4 + (size_t)kBins * 8;
 }
 
 template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT>
@@ -206,19 +209,21 @@ template <bool HAS_SEG>
 __global__ void __launch_bounds__(kHistThreads)
 histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ segs,
                  uint64_t n, unsigned long long *__restrict__ hist) {
-    constexpr int P = HAS_SEG ? 12 : 8;
-    __shared__ uint32_t s_hist[P * kBins];
+    constexpr int P = HAS_SEG ? kHistPasses : kKeyPasses;
+    extern __shared__ uint32_t s_hist[];
     for (int i = threadIdx.x; i < P * kBins; i += kHistThreads) s_hist[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
     for (uint64_t i = (uint64_t)blockIdx.x * kHistThreads + threadIdx.x; i < n; i += stride) {
         const uint64_t k = keys[i];
 #pragma unroll
-        for (int p = 0; p < 8; ++p) atomicAdd(&s_hist[p * kBins + (unsigned)((k >> (8 * p)) & 0xFF)], 1u);
+        for (int p = 0; p < kKeyPasses; ++p)
+            atomicAdd(&s_hist[p * kBins + (unsigned)((k >> digit_shift(p)) & digit_mask(p))], 1u);
         if (HAS_SEG) {
             const uint32_t sg = segs[i];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[(8 + p) * kBins + ((sg >> (8 * p)) & 0xFF)], 1u);
+            for (int p = kKeyPasses; p < kHistPasses; ++p)
+                atomicAdd(&s_hist[p * kBins + ((sg >> digit_shift(p)) & digit_mask(p))], 1u);
         }
     }
     __syncthreads();
@@ -228,8 +233,9 @@ histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__
 
 // ---- pass plan -------------------------------------------------------------
 
-__global__ void plan_kernel(const unsigned long long *__restrict__ hist, int npass, uint64_t n,
-                            unsigned long long *__restrict__ bucket_base, DevFlags *flags) {
+__global__ void __launch_bounds__(kBins)
+plan_kernel(const unsigned long long *__restrict__ hist, int npass, uint64_t n,
+            unsigned long long *__restrict__ bucket_base, DevFlags *flags) {
     __shared__ unsigned long long s_warp[kBins / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int p = 0; p < npass; ++p) {
@@ -293,11 +299,21 @@ cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs, uint64_
                              unsigned long long *hist, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const uint64_t blocks = (n + kHistThreads * 16 - 1) / (kHistThreads * 16);
-    const unsigned grid = (unsigned)umin64(blocks, (uint64_t)num_sms * 4);
-    if (segs)
-        histogram_kernel<true><<<grid, kHistThreads, 0, s>>>(keys, segs, n, hist);
-    else
-        histogram_kernel<false><<<grid, kHistThreads, 0, s>>>(keys, nullptr, n, hist);
+    const unsigned grid = (unsigned)umin64(blocks, (uint64_t)num_sms * 2);
+    if (segs) {
+        const size_t smem = (size_t)kHistPasses * kBins * 4;
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(histogram_kernel<true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        histogram_kernel<true><<<grid, kHistThreads, smem, s>>>(keys, segs, n, hist);
+    } else {
+        const size_t smem = (size_t)kKeyPasses * kBins * 4;
+        histogram_kernel<false><<<grid, kHistThreads, smem, s>>>(keys, nullptr, n, hist);
+    }
     return cudaGetLastError();
 }
 
