@@ -150,36 +150,65 @@ tie_detect_kernel(const TieArgs a) {
         excl = lane == 0 ? wpre : combine(wpre, xp);
     }
 
-    // Tile aggregate and look-back (thread 0).
-    if (tid == 0) {
+    // Tile aggregate and look-back (warp 0).  Lane i reads the word of tile
+    // t - i, 32 predecessors per round trip; the ready words before the first
+    // inclusive one (or before the first unwritten one) are folded in
+    // position order by a shuffle reduction.
+    if (warp == 0) {
         RunState agg{0, 0, 0};
         for (int w = 0; w < kTieThreads / 32; ++w) agg = combine(agg, unpack(s_state[w]));
         uint64_t *lb = a.lookback + tile;
         const uint32_t epoch = a.epoch;
         RunState prefix{0, 0, 0};
         if (tile == 0) {
-            st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(agg)));
+            if (lane == 0) st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(agg)));
         } else {
-            st_relaxed(lb, lb_word(epoch, kLbAggregate, pack(agg)));
+            if (lane == 0) st_relaxed(lb, lb_word(epoch, kLbAggregate, pack(agg)));
             int64_t t = (int64_t)tile - 1;
             uint32_t spins = 0;
             while (t >= 0) {
-                const uint64_t v = ld_relaxed(&a.lookback[t]);
-                if ((uint32_t)(v >> 58) != epoch) {
+                const int64_t tt = t - lane;
+                const uint64_t v = tt >= 0 ? ld_relaxed(&a.lookback[tt]) : 0;
+                const bool ready = tt >= 0 && (uint32_t)(v >> 58) == epoch;
+                const bool incl = ready && (v & (3ull << 56)) == kLbInclusive;
+                const unsigned not_ready = __ballot_sync(kFull, !ready && tt >= 0);
+                const unsigned inclusive = __ballot_sync(kFull, incl);
+                const int first_nr = not_ready ? __ffs(not_ready) - 1 : 32;
+                const int first_in = inclusive ? __ffs(inclusive) - 1 : 32;
+                const int stop = first_in < first_nr ? first_in : first_nr - 1;  // last lane to fold
+                const int avail = t + 1 < 32 ? (int)(t + 1) : 32;               // lanes with tt >= 0
+                const int last = stop < avail - 1 ? stop : avail - 1;
+                if (last >= 0) {
+                    // fold lanes 0..last; lane i holds the word of an earlier tile than lane i-1
+                    RunState x = lane <= last ? unpack(v & kLbValueMask) : RunState{0, 0, 0};
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        RunState y;
+                        y.last = __shfl_down_sync(kFull, x.last, o);
+                        y.has = __shfl_down_sync(kFull, x.has, o);
+                        y.orf = __shfl_down_sync(kFull, x.orf, o);
+                        if (lane + o < 32) x = combine(y, x);
+                    }
+                    RunState folded;
+                    folded.last = __shfl_sync(kFull, x.last, 0);
+                    folded.has = __shfl_sync(kFull, x.has, 0);
+                    folded.orf = __shfl_sync(kFull, x.orf, 0);
+                    prefix = combine(folded, prefix);
+                }
+                if (first_in < first_nr) break;  // folded through an inclusive prefix
+                if (last >= 0) {
+                    t -= last + 1;
+                } else {
                     if (++spins > kSpinLimit) {
-                        atomicOr(&a.flags->error, kErrTimeout);
+                        if (lane == 0) atomicOr(&a.flags->error, kErrTimeout);
                         break;
                     }
                     if (spins > 8) __nanosleep(32);
-                    continue;
                 }
-                prefix = combine(unpack(v & kLbValueMask), prefix);
-                if ((v & (3ull << 56)) == kLbInclusive) break;
-                --t;
             }
-            st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(combine(prefix, agg))));
+            if (lane == 0) st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(combine(prefix, agg))));
         }
-        s_prefix = pack(prefix);
+        if (lane == 0) s_prefix = pack(prefix);
     }
     __syncthreads();
     RunState st = combine(unpack(s_prefix), excl);

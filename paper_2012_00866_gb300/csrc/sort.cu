@@ -22,6 +22,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = kSortTile / kThreads;  // 8
+constexpr int kLbBatch = 4;                   // look-back words loaded per round trip
 
 // Exclusive scan of one u32 per thread over a 512-thread block.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
@@ -69,7 +70,9 @@ onesweep_kernel(const OnesweepArgs a) {
     uint64_t key[kItems];
     uint32_t val[kItems];
     uint32_t seg[kItems];
-    uint32_t rank[kItems];
+    // Rank of item k among the warp's earlier items with the same digit:
+    // below 256 (a warp holds 256 items), so four ranks share a register.
+    uint32_t rank4[kItems / 4] = {};
     const uint64_t wbase = tile_base + (uint64_t)warp * 32 * kItems;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -86,6 +89,8 @@ onesweep_kernel(const OnesweepArgs a) {
         seg[k] = (HAS_SEG && valid) ? a.segs_in[e] : 0;
     }
 
+    // Ranking: lanes with equal digits find each other with one ballot per
+    // digit bit; the lowest such lane (leader) advances the warp's count.
     uint32_t *my_hist = s_whist + warp * kBins;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -101,7 +106,7 @@ onesweep_kernel(const OnesweepArgs a) {
             my_hist[d] = before + __popc(peers);
         }
         before = __shfl_sync(kFull, before, leader);
-        rank[k] = before + __popc(peers & lanemask_lt());
+        rank4[k >> 2] |= (before + __popc(peers & lanemask_lt())) << (8 * (k & 3));
         __syncwarp();
     }
     __syncthreads();
@@ -121,21 +126,38 @@ onesweep_kernel(const OnesweepArgs a) {
         st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, total));
     } else {
         st_relaxed(&lb[tid], lb_word(epoch, kLbAggregate, total));
+        // Walk back over earlier tiles' words for digit tid, kLbBatch per
+        // round trip: add aggregates until an inclusive prefix; stop at the
+        // first word not yet written and poll it again.
         int64_t t = (int64_t)tile - 1;
         uint32_t spins = 0;
         while (t >= 0) {
-            const uint64_t v = ld_relaxed(&a.lookback[(uint64_t)t * kBins + tid]);
-            if ((uint32_t)(v >> 58) != epoch) {
+            uint64_t v[kLbBatch];
+#pragma unroll
+            for (int i = 0; i < kLbBatch; ++i)
+                v[i] = (t - i >= 0) ? ld_relaxed(&a.lookback[(uint64_t)(t - i) * kBins + tid]) : 0;
+            bool done = false, stalled = false;
+            int used = 0;
+#pragma unroll
+            for (int i = 0; i < kLbBatch; ++i) {
+                if (done || stalled || t - i < 0) continue;
+                if ((uint32_t)(v[i] >> 58) != epoch) {
+                    stalled = true;
+                    continue;
+                }
+                prefix += v[i] & kLbValueMask;
+                used = i + 1;
+                done = (v[i] & (3ull << 56)) == kLbInclusive;
+            }
+            if (done) break;
+            t -= used;
+            if (used == 0) {
                 if (++spins > kSpinLimit) {
                     atomicOr(&a.flags->error, kErrTimeout);
                     break;
                 }
                 if (spins > 8) __nanosleep(32);
-                continue;
             }
-            prefix += v & kLbValueMask;
-            if ((v & (3ull << 56)) == kLbInclusive) break;
-            --t;
         }
         st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, prefix + total));
     }
@@ -151,7 +173,7 @@ onesweep_kernel(const OnesweepArgs a) {
         const uint64_t e = wbase + k * 32 + lane;
         if (e < n) {
             const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-            const uint32_t p = my_hist[d] + rank[k];
+            const uint32_t p = my_hist[d] + ((rank4[k >> 2] >> (8 * (k & 3))) & 0xFFu);
             s_keys[p] = key[k];
             s_vals[p] = val[k];
             if (HAS_SEG) s_segs[p] = seg[k];
