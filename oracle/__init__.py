@@ -55,6 +55,10 @@ def _load():
         lib.oracle_stable_argsort.argtypes = [vp, vp, u64, vp, ci, ci]
         lib.oracle_check_sorted.restype = ctypes.c_int64
         lib.oracle_check_sorted.argtypes = [vp, vp, u64, vp, ci, ci]
+        lib.oracle_stable_argsort_batched.restype = ci
+        lib.oracle_stable_argsort_batched.argtypes = [vp, vp, vp, u64, vp, ci]
+        lib.oracle_check_sorted_batched.restype = ctypes.c_int64
+        lib.oracle_check_sorted_batched.argtypes = [vp, vp, vp, u64, vp, ci]
         _lib = lib
     return _lib
 
@@ -126,6 +130,33 @@ def check_sorted(data: np.ndarray, offsets: np.ndarray, perm: np.ndarray,
                                            _ptr(perm),
                                            1 if perm.dtype == np.uint64 else 0,
                                            _threads(threads)))
+
+
+def stable_argsort_batched(data: np.ndarray, offsets: np.ndarray, seg_offsets: np.ndarray,
+                           threads: int | None = None) -> np.ndarray:
+    """Per-instance stable argsort as local uint32 indices, laid out like the
+    strings (instance s at positions seg_offsets[s] .. seg_offsets[s+1]-1)."""
+    n = offsets.shape[0] - 1
+    perm = np.empty(n, dtype=np.uint32)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    seg = np.ascontiguousarray(seg_offsets, dtype=np.uint64)
+    rc = _load().oracle_stable_argsort_batched(_ptr(data), _ptr(offsets), _ptr(seg),
+                                               seg.shape[0] - 1, _ptr(perm), _threads(threads))
+    if rc != 0:
+        raise MemoryError("oracle_stable_argsort_batched: out of memory")
+    return perm
+
+
+def check_sorted_batched(data: np.ndarray, offsets: np.ndarray, seg_offsets: np.ndarray,
+                         perm: np.ndarray, threads: int | None = None) -> int:
+    """-1 if every instance holds its stable argsort (local indices)."""
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    seg = np.ascontiguousarray(seg_offsets, dtype=np.uint64)
+    return int(_load().oracle_check_sorted_batched(_ptr(data), _ptr(offsets), _ptr(seg),
+                                                   seg.shape[0] - 1, _ptr(perm), _threads(threads)))
 
 
 def string_compare(data: np.ndarray, offsets: np.ndarray, i: int, j: int) -> int:

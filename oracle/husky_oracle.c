@@ -356,3 +356,127 @@ int64_t oracle_check_sorted(const uint8_t *bytes, const uint64_t *offsets,
     }
     return bad;
 }
+
+/* ---- batched instances ------------------------------------------------------
+ *
+ * Instance s owns strings seg_offsets[s] .. seg_offsets[s+1]-1; its result is
+ * the stable argsort of those strings alone, as local indices (0-based within
+ * the instance), stored at positions seg_offsets[s] .. seg_offsets[s+1]-1.
+ * Threads take instances in turn; each instance is sorted exactly as
+ * oracle_stable_argsort sorts a whole input. */
+
+typedef struct {
+    const uint8_t *bytes;
+    const uint64_t *offsets;
+    const uint64_t *seg;
+    uint64_t num_segs;
+    uint32_t *perm;
+    const uint32_t *cperm;
+    int tid, threads;
+    int64_t bad;
+    int oom;
+} batch_job;
+
+static void *batch_sort_run(void *p)
+{
+    batch_job *j = (batch_job *)p;
+    for (uint64_t s = (uint64_t)j->tid; s < j->num_segs; s += (uint64_t)j->threads) {
+        uint64_t lo = j->seg[s], hi = j->seg[s + 1];
+        uint64_t m = hi - lo;
+        if (m == 0)
+            continue;
+        uint64_t *a = (uint64_t *)malloc((size_t)m * sizeof(uint64_t));
+        uint64_t *tmp = (uint64_t *)malloc((size_t)m * sizeof(uint64_t));
+        if (!a || !tmp) {
+            free(a);
+            free(tmp);
+            j->oom = 1;
+            return NULL;
+        }
+        for (uint64_t i = 0; i < m; i++)
+            a[i] = lo + i;
+        str_ctx c = {j->bytes, j->offsets};
+        merge_sort(&c, a, tmp, 0, m);
+        for (uint64_t i = 0; i < m; i++)
+            j->perm[lo + i] = (uint32_t)(a[i] - lo);
+        free(a);
+        free(tmp);
+    }
+    return NULL;
+}
+
+int oracle_stable_argsort_batched(const uint8_t *bytes, const uint64_t *offsets,
+                                  const uint64_t *seg_offsets, uint64_t num_segs,
+                                  uint32_t *perm, int threads)
+{
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    pthread_t tid[256];
+    batch_job jobs[256];
+    for (int t = 0; t < threads; t++) {
+        jobs[t] = (batch_job){bytes, offsets, seg_offsets, num_segs, perm, NULL, t, threads, -1, 0};
+        pthread_create(&tid[t], NULL, batch_sort_run, &jobs[t]);
+    }
+    int oom = 0;
+    for (int t = 0; t < threads; t++) {
+        pthread_join(tid[t], NULL);
+        oom |= jobs[t].oom;
+    }
+    return oom ? -1 : 0;
+}
+
+/* Property check per instance (see oracle_check_sorted): returns -1 if every
+ * instance holds its stable argsort, else the first failing global
+ * position found. */
+static void *batch_check_run(void *p)
+{
+    batch_job *j = (batch_job *)p;
+    j->bad = -1;
+    for (uint64_t s = (uint64_t)j->tid; s < j->num_segs; s += (uint64_t)j->threads) {
+        uint64_t lo = j->seg[s], hi = j->seg[s + 1];
+        uint64_t m = hi - lo;
+        for (uint64_t k = 0; k < m; k++) {
+            uint64_t q = j->cperm[lo + k];
+            if (q >= m) {
+                if (j->bad < 0 || (int64_t)(lo + k) < j->bad)
+                    j->bad = (int64_t)(lo + k);
+                break;
+            }
+            if (k == 0)
+                continue;
+            uint64_t p0 = j->cperm[lo + k - 1];
+            int c = string_compare(j->bytes, j->offsets, lo + p0, lo + q);
+            if (c > 0 || (c == 0 && !(p0 < q))) {
+                if (j->bad < 0 || (int64_t)(lo + k) < j->bad)
+                    j->bad = (int64_t)(lo + k);
+                break;
+            }
+        }
+    }
+    return NULL;
+}
+
+int64_t oracle_check_sorted_batched(const uint8_t *bytes, const uint64_t *offsets,
+                                    const uint64_t *seg_offsets, uint64_t num_segs,
+                                    const uint32_t *perm, int threads)
+{
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    pthread_t tid[256];
+    batch_job jobs[256];
+    for (int t = 0; t < threads; t++) {
+        jobs[t] = (batch_job){bytes, offsets, seg_offsets, num_segs, NULL, perm, t, threads, -1, 0};
+        pthread_create(&tid[t], NULL, batch_check_run, &jobs[t]);
+    }
+    int64_t bad = -1;
+    for (int t = 0; t < threads; t++) {
+        pthread_join(tid[t], NULL);
+        if (jobs[t].bad >= 0 && (bad < 0 || jobs[t].bad < bad))
+            bad = jobs[t].bad;
+    }
+    return bad;
+}

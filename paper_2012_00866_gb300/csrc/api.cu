@@ -35,11 +35,11 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
-    kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKNumKinds
+    kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
-    "run_scan", "refine_keys", "push_constant_runs", "histogram"};
+    "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill"};
 
 struct StatsTable {
     std::mutex mu;
@@ -317,7 +317,7 @@ struct Input {
     int perm_u64;
 };
 
-hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode) {
+hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst) {
     const uint64_t n = in.n;
     RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
     RunEntry *q_medium = c.at<RunEntry>(c.L.q_medium);
@@ -327,6 +327,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode)
 
     TieArgs t{};
     t.keys = b.keys[cur];
+    t.segs = inst.seg_offsets ? b.segs[cur] : nullptr;  // batched: runs end at instance boundaries
     t.vals = b.vals[cur];
     t.n = n;
     t.prefix_len = in.prefix_len;
@@ -373,8 +374,8 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode)
         int rc = 0;
         HS_TRY(c.timed(kKRefineKeys, 32.0 * total, [&] {
                    return launch_refine_keys(in.bytes, in.offsets, in.perm, in.perm_u64, q_large[li], large,
-                                             run_base, total, in.prefix_len, r.keys[0], r.segs[0], r.vals[0],
-                                             c.d_flags, c.s);
+                                             run_base, total, inst, in.prefix_len, r.keys[0], r.segs[0],
+                                             r.vals[0], c.d_flags, c.s);
                }),
                "refine keys");
         HS_TRY(c.read_flags(), "refine sync");
@@ -431,15 +432,15 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode)
     if (c.h.qcount[kQMedium])
         HS_TRY(c.timed(kKMediumRuns, (double)c.h.qcount[kQMedium] * 16.0 * (2 * isz + 16.0), [&] {
                    return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
-                                             &c.d_flags->qcount[kQMedium], c.L.cap_medium, n, in.prefix_len,
-                                             c.sms, c.s);
+                                             &c.d_flags->qcount[kQMedium], c.L.cap_medium, n, inst,
+                                             in.prefix_len, c.sms, c.s);
                }),
                "medium runs");
     if (c.h.qcount[kQSmall])
         HS_TRY(c.timed(kKSmallRuns, (double)c.h.qcount[kQSmall] * (16.0 + 2.0 * (2 * isz + 16.0)), [&] {
                    return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
-                                            &c.d_flags->qcount[kQSmall], c.L.cap_small, n, in.prefix_len,
-                                            c.sms, c.s);
+                                            &c.d_flags->qcount[kQSmall], c.L.cap_small, n, inst,
+                                            in.prefix_len, c.sms, c.s);
                }),
                "small runs");
     return HS_OK;
@@ -482,7 +483,54 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
         if (st != HS_OK) return st;
     }
     if (!perfect) {
-        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag);
+        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag, Instances{nullptr, 0});
+        if (st != HS_OK) return st;
+    }
+    HS_TRY(c.read_flags(), "final sync");
+    return device_error_status(c.h);
+}
+
+// Batched: one segmented sort by (instance, sort key) over all strings; the
+// payload is the local index, so the last pass writes the local permutation.
+hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets, uint64_t num_segs, int coder) {
+    Input in = in0;
+    const uint64_t n = in.n;
+    SortBufs b{{c.at<uint64_t>(c.L.codes_a), c.at<uint64_t>(c.L.codes_b)},
+               {c.at<uint32_t>(c.L.vals_a), c.at<uint32_t>(c.L.vals_b)},
+               {c.at<uint32_t>(c.L.segs_a), c.at<uint32_t>(c.L.segs_b)}};
+    uint32_t *bits = c.at<uint32_t>(c.L.bits);
+    c.lb_words = sort_tiles(n) * kBins;
+    HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
+    HS_TRY(launch_validate_segments(seg_offsets, num_segs, n, c.d_flags, c.s), "validate segments");
+    HS_TRY(c.read_flags(), "validate sync");
+    if (c.h.error & kErrOffsets) return fail(HS_ERR_INVALID_ARG, "seg_offsets must start at 0, not decrease, and end at n");
+    int used = 0;
+    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used);
+    if (st != HS_OK) return st;
+    in.prefix_len = used == HS_CODER_BYTE8 ? 8 : 9;
+    const bool key_flag = used == HS_CODER_ASCII7;
+    const bool perfect = c.h.nonexact == 0;
+    unsigned long long *hist = c.at<unsigned long long>(c.L.hist);
+    HS_TRY(c.timed(kKSegFill, 8.0 * n + 8.0 * n, [&] {
+               return launch_seg_fill(seg_offsets, num_segs, n, key_flag ? nullptr : bits, b.segs[0], b.vals[0],
+                                      hist, c.d_flags, c.sms, c.s);
+           }),
+           "seg fill");
+    HS_TRY(launch_plan(hist, kHistPasses, n, c.at<unsigned long long>(c.L.bucket), c.d_flags, c.s), "plan");
+    HS_TRY(c.read_flags(), "plan sync");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    int passes[kHistPasses], np = 0;
+    for (int p = 0; p < kHistPasses; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    if (np == 0) passes[np++] = 0;  // a no-op pass still writes the permutation
+    const bool final_is_perm = key_flag || perfect;
+    int cur = 0;
+    st = run_passes(c, b, &cur, n, passes, np, true, nullptr, false, final_is_perm ? in.perm : nullptr, kOutPerm32,
+                    !perfect);
+    if (st != HS_OK) return st;
+    if (!perfect) {
+        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag, Instances{seg_offsets, num_segs});
         if (st != HS_OK) return st;
     }
     HS_TRY(c.read_flags(), "final sync");
@@ -569,10 +617,17 @@ hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t
 hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets, const uint64_t *d_seg_offsets,
                              uint64_t num_segs, uint64_t n, int coder, uint32_t *d_perm, void *d_ws,
                              size_t ws_bytes, void *stream) {
-    (void)d_bytes; (void)d_offsets; (void)d_seg_offsets; (void)num_segs; (void)n; (void)coder;
-    (void)d_perm; (void)d_ws; (void)ws_bytes; (void)stream;
     g_last_error.clear();
-    return fail(HS_ERR_INTERNAL, "hs_argsort_batched: not built yet");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (num_segs > 0xFFFFFFFFull) return fail(HS_ERR_INVALID_ARG, "num_segs must fit 32 bits");
+    if (n == 0) return HS_OK;
+    if (num_segs == 0) return fail(HS_ERR_INVALID_ARG, "n > 0 strings but no instances");
+    if (!d_bytes || !d_offsets || !d_seg_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st)) return st;
+    Input in{d_bytes, d_offsets, n, 9, d_perm, 0};
+    return argsort_batched(c, in, d_seg_offsets, num_segs, coder);
 }
 
 hs_status hs_batched_workspace_size(uint64_t n, uint64_t num_segs, size_t *out) {

@@ -105,8 +105,9 @@ tie_detect_kernel(const TieArgs a) {
 
     const int i0 = tid * kTieItems;
     const uint64_t j0 = t0 + i0;
+    const bool SEGS = REFINE || a.segs != nullptr;  // runs also break where the segment changes
     uint32_t seg_prev = 0;
-    if (REFINE && j0 > 0 && j0 - 1 < n) seg_prev = a.segs[j0 - 1];
+    if (SEGS && j0 > 0 && j0 - 1 < n) seg_prev = a.segs[j0 - 1];
     uint32_t heads = 0, flagsb = 0;
     RunState mine{0, 0, 0};
 #pragma unroll
@@ -114,8 +115,8 @@ tie_detect_kernel(const TieArgs a) {
         const uint64_t j = j0 + i;
         if (j < n) {
             const uint64_t k = s_key[i0 + i + 1];
-            const uint32_t sg = REFINE ? a.segs[j] : 0;
-            const bool head = (j == 0) || k != s_key[i0 + i] || (REFINE && sg != seg_prev);
+            const uint32_t sg = SEGS ? a.segs[j] : 0;
+            const bool head = (j == 0) || k != s_key[i0 + i] || (SEGS && sg != seg_prev);
             bool f;
             if (MODE == kTieKeyFlag) f = (k & 1u) != 0;
             else if (MODE == kTieValFlag) f = (a.vals[j] >> 31) != 0;
@@ -216,7 +217,7 @@ tie_detect_kernel(const TieArgs a) {
     // Replay my items: write the permutation, emit runs at their tails.
     uint32_t next_seg = 0;
     const uint64_t jn = j0 + kTieItems;
-    if (REFINE && jn < n) next_seg = a.segs[jn];
+    if (SEGS && jn < n) next_seg = a.segs[jn];
 #pragma unroll
     for (int i = 0; i < kTieItems; ++i) {
         const uint64_t j = j0 + i;
@@ -247,7 +248,7 @@ tie_detect_kernel(const TieArgs a) {
         } else if (jn >= n) {
             tail = true;
         } else {
-            tail = s_key[i0 + i + 2] != s_key[i0 + i + 1] || (REFINE && next_seg != a.segs[j]);
+            tail = s_key[i0 + i + 2] != s_key[i0 + i + 1] || (SEGS && next_seg != a.segs[j]);
         }
         if (tail) {
             const uint64_t len = j - st.last + 1;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256)
 small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                   IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
                   const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
-                  int prefix_len) {
+                  Instances inst, int prefix_len) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -272,12 +273,13 @@ small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict_
         const RunEntry e = q[r];
         if (e.len > kSmallMax || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
         const bool mine = (uint32_t)lane < e.len;
+        const uint64_t base = instance_base(inst, e.start);  // string index of local index 0
         IdxT idx = 0;
         uint64_t off = 0, len = 0;
         if (mine) {
             idx = perm[e.start + lane];
-            off = offsets[idx];
-            len = offsets[idx + 1] - off;
+            off = offsets[base + idx];
+            len = offsets[base + idx + 1] - off;
         }
         const uint64_t o = window_offset(prefix_len, e.depth);
         uint32_t rank = 0;
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(kMedThreads)
 medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
                    const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
-                   int prefix_len) {
+                   Instances inst, int prefix_len) {
     constexpr int CAP = kMediumMax;
     __shared__ uint64_t s_key[CAP];
     __shared__ uint32_t s_seg[CAP];
@@ -330,6 +332,7 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
         const RunEntry e = q[r];
         if (e.len > (uint32_t)CAP || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
         const int len = (int)e.len;
+        const uint64_t base = instance_base(inst, e.start);
         int P = 1;
         while (P < len) P <<= 1;
         __syncthreads();
@@ -350,9 +353,9 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
             const uint64_t o = window_offset(prefix_len, depth);
             for (int j = tid; j < len; j += kMedThreads) {
                 if (s_segact[s_seg[j]]) {
-                    const IdxT idx = s_idx[j];
-                    const uint64_t off = offsets[idx];
-                    s_key[j] = window_key(bytes + off, offsets[idx + 1] - off, o, prefix_len);
+                    const uint64_t g = base + s_idx[j];
+                    const uint64_t off = offsets[g];
+                    s_key[j] = window_key(bytes + off, offsets[g + 1] - off, o, prefix_len);
                 } else {
                     s_key[j] = 0;
                 }
@@ -483,7 +486,7 @@ template <typename IdxT>
 __global__ void refine_keys_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                                    const IdxT *__restrict__ perm, const RunEntry *__restrict__ runs,
                                    uint64_t count, const unsigned long long *__restrict__ run_base,
-                                   uint64_t total, int prefix_len, uint64_t *__restrict__ keys,
+                                   uint64_t total, Instances inst, int prefix_len, uint64_t *__restrict__ keys,
                                    uint32_t *__restrict__ segs, uint32_t *__restrict__ vals,
                                    DevFlags *flags) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -498,12 +501,13 @@ __global__ void refine_keys_kernel(const uint8_t *__restrict__ bytes, const uint
         const RunEntry r = runs[lo];
         const uint64_t pos = r.start + (a - run_base[lo]);
         const uint64_t o = window_offset(prefix_len, r.depth);
+        const uint64_t base = instance_base(inst, r.start);
         const IdxT idx = perm[pos];
-        const uint64_t off = offsets[idx];
-        const uint64_t k = window_key(bytes + off, offsets[idx + 1] - off, o, prefix_len);
-        const IdxT idx0 = perm[r.start];
-        const uint64_t off0 = offsets[idx0];
-        const uint64_t k0 = window_key(bytes + off0, offsets[idx0 + 1] - off0, o, prefix_len);
+        const uint64_t off = offsets[base + idx];
+        const uint64_t k = window_key(bytes + off, offsets[base + idx + 1] - off, o, prefix_len);
+        const uint64_t g0 = base + perm[r.start];
+        const uint64_t off0 = offsets[g0];
+        const uint64_t k0 = window_key(bytes + off0, offsets[g0 + 1] - off0, o, prefix_len);
         nonconst |= k != k0;
         keys[a] = k;
         segs[a] = (uint32_t)lo;
@@ -539,27 +543,27 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
 
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
                               const RunEntry *q, const unsigned long long *qcount, uint64_t cap, uint64_t perm_n,
-                              int prefix_len, int num_sms, cudaStream_t s) {
+                              Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 8;
     if (perm_u64)
         small_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q,
-                                                         qcount, cap, perm_n, prefix_len);
+                                                         qcount, cap, perm_n, inst, prefix_len);
     else
         small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
-                                                         qcount, cap, perm_n, prefix_len);
+                                                         qcount, cap, perm_n, inst, prefix_len);
     return cudaGetLastError();
 }
 
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
                                const RunEntry *q, const unsigned long long *qcount, uint64_t cap,
-                               uint64_t perm_n, int prefix_len, int num_sms, cudaStream_t s) {
+                               uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 2;
     if (perm_u64)
         medium_runs_kernel<uint64_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm),
-                                                                  q, qcount, cap, perm_n, prefix_len);
+                                                                  q, qcount, cap, perm_n, inst, prefix_len);
     else
         medium_runs_kernel<uint32_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm),
-                                                                  q, qcount, cap, perm_n, prefix_len);
+                                                                  q, qcount, cap, perm_n, inst, prefix_len);
     return cudaGetLastError();
 }
 
@@ -571,17 +575,17 @@ cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count, unsigned long 
 
 cudaError_t launch_refine_keys(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
                                const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
-                               uint64_t total, int prefix_len, uint64_t *keys, uint32_t *segs, uint32_t *vals,
-                               DevFlags *flags, cudaStream_t s) {
+                               uint64_t total, Instances inst, int prefix_len, uint64_t *keys, uint32_t *segs,
+                               uint32_t *vals, DevFlags *flags, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
     if (perm_u64)
         refine_keys_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint64_t *>(perm),
-                                                          runs, count, run_base, total, prefix_len, keys,
+                                                          runs, count, run_base, total, inst, prefix_len, keys,
                                                           segs, vals, flags);
     else
         refine_keys_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint32_t *>(perm),
-                                                          runs, count, run_base, total, prefix_len, keys,
+                                                          runs, count, run_base, total, inst, prefix_len, keys,
                                                           segs, vals, flags);
     return cudaGetLastError();
 }

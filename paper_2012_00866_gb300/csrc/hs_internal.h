@@ -77,6 +77,39 @@ cudaError_t launch_plan(const unsigned long long *hist, int npass, uint64_t n,
 cudaError_t launch_identity(const uint32_t *flag_bits, uint64_t n,
                             void *out, OutMode mode, cudaStream_t s);
 
+// Batched sorts: segs[i] = instance of string i (seg_offsets holds the
+// num_segs + 1 string-index boundaries), vals[i] = local index of i
+// (| flag_bit(i) << 31 when flag_bits is given), and the instance-id digit
+// histograms (hist rows kKeyPasses..kHistPasses-1, accumulated).
+cudaError_t launch_seg_fill(const uint64_t *seg_offsets, uint64_t num_segs,
+                            uint64_t n, const uint32_t *flag_bits,
+                            uint32_t *segs, uint32_t *vals,
+                            unsigned long long *hist, DevFlags *flags,
+                            int num_sms, cudaStream_t s);
+
+// flags->error |= kErrOffsets unless seg_offsets[0] == 0, seg_offsets is
+// non-decreasing and seg_offsets[num_segs] == n.
+cudaError_t launch_validate_segments(const uint64_t *seg_offsets, uint64_t num_segs,
+                                     uint64_t n, DevFlags *flags, cudaStream_t s);
+
+// Instance boundaries used by the fix-up kernels of a batched sort: a run at
+// permutation position p belongs to instance s with seg_offsets[s] <= p <
+// seg_offsets[s+1], and its entries are local indices of that instance.
+struct Instances {
+    const uint64_t *seg_offsets;  // NULL for a single sort
+    uint64_t num_segs;
+};
+
+__device__ __forceinline__ uint64_t instance_base(const Instances &in, uint64_t pos) {
+    if (in.seg_offsets == nullptr) return 0;
+    uint64_t lo = 0, hi = in.num_segs;  // seg_offsets[lo] <= pos < seg_offsets[hi]
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (in.seg_offsets[mid] <= pos) lo = mid; else hi = mid;
+    }
+    return in.seg_offsets[lo];
+}
+
 // ---- fixup.cu ------------------------------------------------------------
 enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3 };
 constexpr uint32_t kSmallMax = 32;     // warp per run
@@ -92,7 +125,7 @@ enum TieMode {
 
 struct TieArgs {
     const uint64_t *keys;
-    const uint32_t *segs;           // refinement only
+    const uint32_t *segs;           // refinement run ids, or instance ids (batched); NULL otherwise
     const uint32_t *vals;
     uint64_t n;
     int prefix_len;                 // bytes covered by the husky code
@@ -117,14 +150,14 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s);
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets,
                               void *perm, int perm_u64, const RunEntry *q,
                               const unsigned long long *qcount, uint64_t cap,
-                              uint64_t perm_n, int prefix_len, int num_sms,
-                              cudaStream_t s);
+                              uint64_t perm_n, Instances inst, int prefix_len,
+                              int num_sms, cudaStream_t s);
 
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
                                void *perm, int perm_u64, const RunEntry *q,
                                const unsigned long long *qcount, uint64_t cap,
-                               uint64_t perm_n, int prefix_len, int num_sms,
-                               cudaStream_t s);
+                               uint64_t perm_n, Instances inst, int prefix_len,
+                               int num_sms, cudaStream_t s);
 
 // Large-run refinement helpers.
 cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count,
@@ -134,8 +167,8 @@ cudaError_t launch_refine_keys(const uint8_t *bytes, const uint64_t *offsets,
                                const void *perm, int perm_u64,
                                const RunEntry *runs, uint64_t count,
                                const unsigned long long *run_base,
-                               uint64_t total, int prefix_len, uint64_t *keys,
-                               uint32_t *segs, uint32_t *vals,
+                               uint64_t total, Instances inst, int prefix_len,
+                               uint64_t *keys, uint32_t *segs, uint32_t *vals,
                                DevFlags *flags, cudaStream_t s);
 
 cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count,

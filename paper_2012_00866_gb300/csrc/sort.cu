@@ -279,6 +279,38 @@ plan_kernel(const unsigned long long *__restrict__ hist, int npass, uint64_t n,
     }
 }
 
+constexpr int kSegThreads = 512;
+
+__global__ void __launch_bounds__(kSegThreads)
+seg_fill_kernel(const uint64_t *__restrict__ seg_offsets, uint64_t num_segs, uint64_t n,
+                const uint32_t *__restrict__ flag_bits, uint32_t *__restrict__ segs,
+                uint32_t *__restrict__ vals, unsigned long long *__restrict__ hist, DevFlags *flags) {
+    __shared__ uint32_t s_hist[kSegPasses * kBins];
+    for (int i = threadIdx.x; i < kSegPasses * kBins; i += kSegThreads) s_hist[i] = 0;
+    __syncthreads();
+    bool bad = false;
+    const uint64_t stride = (uint64_t)gridDim.x * kSegThreads;
+    for (uint64_t i = (uint64_t)blockIdx.x * kSegThreads + threadIdx.x; i < n; i += stride) {
+        uint64_t lo = 0, hi = num_segs;  // seg_offsets[lo] <= i < seg_offsets[hi]
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (seg_offsets[mid] <= i) lo = mid; else hi = mid;
+        }
+        const uint64_t local = i - seg_offsets[lo];
+        bad |= local > kIdxMask;
+        const uint32_t bit = flag_bits ? ((flag_bits[i >> 5] >> (i & 31)) & 1u) : 0u;
+        segs[i] = (uint32_t)lo;
+        vals[i] = ((uint32_t)local & kIdxMask) | (bit << 31);
+#pragma unroll
+        for (int p = 0; p < kSegPasses; ++p)
+            atomicAdd(&s_hist[p * kBins + ((uint32_t)(lo >> digit_shift(kKeyPasses + p)) & (kBins - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSegPasses * kBins; i += kSegThreads)
+        if (s_hist[i]) atomicAdd(&hist[kKeyPasses * kBins + i], (unsigned long long)s_hist[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags->error, kErrInternal);
+}
+
 __global__ void identity_kernel(const uint32_t *__restrict__ flag_bits, uint64_t n, void *out, int mode) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -298,7 +330,10 @@ cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg, bool digit_seg,
                             OutMode out, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (has_seg) {
-        if (synth || out != kOutVals) return cudaErrorInvalidValue;
+        if (synth || out == kOutPerm64) return cudaErrorInvalidValue;
+        if (out == kOutPerm32)
+            return digit_seg ? launch_os<true, true, false, kOutPerm32>(a, s)
+                             : launch_os<true, false, false, kOutPerm32>(a, s);
         return digit_seg ? launch_os<true, true, false, kOutVals>(a, s)
                          : launch_os<true, false, false, kOutVals>(a, s);
     }
@@ -342,6 +377,36 @@ cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs, uint64_
 cudaError_t launch_plan(const unsigned long long *hist, int npass, uint64_t n,
                         unsigned long long *bucket_base, DevFlags *flags, cudaStream_t s) {
     plan_kernel<<<1, kBins, 0, s>>>(hist, npass, n, bucket_base, flags);
+    return cudaGetLastError();
+}
+
+__global__ void validate_segments_kernel(const uint64_t *__restrict__ seg_offsets, uint64_t num_segs, uint64_t n,
+                                         DevFlags *flags) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < num_segs; i += stride) {
+        bad |= seg_offsets[i] > seg_offsets[i + 1];
+        if (i == 0) bad |= seg_offsets[0] != 0;
+        if (i == num_segs - 1) bad |= seg_offsets[num_segs] != n;
+    }
+    if (bad) atomicOr(&flags->error, kErrOffsets);
+}
+
+cudaError_t launch_validate_segments(const uint64_t *seg_offsets, uint64_t num_segs, uint64_t n, DevFlags *flags,
+                                     cudaStream_t s) {
+    if (num_segs == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((num_segs + 255) / 256, 4096);
+    validate_segments_kernel<<<grid, 256, 0, s>>>(seg_offsets, num_segs, n, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_fill(const uint64_t *seg_offsets, uint64_t num_segs, uint64_t n,
+                            const uint32_t *flag_bits, uint32_t *segs, uint32_t *vals,
+                            unsigned long long *hist, DevFlags *flags, int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + kSegThreads * 8 - 1) / (kSegThreads * 8);
+    const unsigned grid = (unsigned)umin64(blocks, (uint64_t)num_sms * 4);
+    seg_fill_kernel<<<grid, kSegThreads, 0, s>>>(seg_offsets, num_segs, n, flag_bits, segs, vals, hist, flags);
     return cudaGetLastError();
 }
 

@@ -111,3 +111,31 @@ def test_checker_threads_agree():
     bad[[j, j + 1]] = bad[[j + 1, j]]
     for t in (1, 7):
         assert oracle.check_sorted(w.bytes, w.offsets, bad, threads=t) == j + 1
+
+
+def test_batched_oracle_matches_per_instance():
+    """The batched oracle equals the single-input oracle run on each instance
+    (and Python's sorted), including empty and single-string instances."""
+    w = workloads.generate_batched(40, 3, lo=1, hi=3000)
+    seg = w.seg_offsets.copy()
+    seg[5] = seg[4]   # an empty instance
+    got = oracle.stable_argsort_batched(w.bytes, w.offsets, seg, threads=3)
+    for s in range(seg.shape[0] - 1):
+        lo, hi = int(seg[s]), int(seg[s + 1])
+        sub = workloads.from_strings([w.string(i) for i in range(lo, hi)])
+        want = np.array(sorted(range(hi - lo), key=sub.string), dtype=np.uint32)
+        assert np.array_equal(got[lo:hi], want), s
+    assert oracle.check_sorted_batched(w.bytes, w.offsets, seg, got) == -1
+
+
+def test_batched_checker_catches_planted_mistakes():
+    w = workloads.from_strings([b"b", b"a", b"a", b"c", b"z", b"y"])
+    seg = np.array([0, 4, 6], dtype=np.uint64)
+    good = np.array([1, 2, 0, 3, 1, 0], dtype=np.uint32)
+    assert oracle.check_sorted_batched(w.bytes, w.offsets, seg, good) == -1
+    unstable = good.copy(); unstable[[0, 1]] = unstable[[1, 0]]
+    assert oracle.check_sorted_batched(w.bytes, w.offsets, seg, unstable) == 1
+    global_idx = good.copy(); global_idx[4] = 5          # not a local index
+    assert oracle.check_sorted_batched(w.bytes, w.offsets, seg, global_idx) == 4
+    wrong_order = good.copy(); wrong_order[[4, 5]] = wrong_order[[5, 4]]
+    assert oracle.check_sorted_batched(w.bytes, w.offsets, seg, wrong_order) == 5
