@@ -11,9 +11,14 @@ construction, in FP64 here and in FP32 on the device:
 
   feature    x(code) = ((code - cmin) >> shift) * 2**-24, shift chosen so the
              shifted range fits in 24 bits (exact in FP32 and FP64);
-  root       y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, 1 -> 32 -> 32 -> 1,
-             with W1, W2, w3 >= 0 (projected after every SGD step), so y is
-             non-decreasing in x;
+  root       y = w3 . h(W2 h(W1 x + b1) + b2) + b3, 1 -> 32 -> 32 -> 1, with
+             the ramp h(z) = min(max(z, 0), 1) and W1, W2, w3 >= 0 (projected
+             after every SGD step), so y is non-decreasing in x.  (With relu
+             and non-negative weights the root could only be convex; sums of
+             ramps can follow any monotone, e.g. concave, CDF.);
+  init       first-layer ramp j rises over [q_j, q_{j+1}] between consecutive
+             1/32-quantiles of the sample, second layer identity, w3 = 1/32:
+             the untrained root already interpolates the empirical CDF;
   training   full-batch gradient descent on mean squared error against the
              empirical CDF targets t_j = j / m of the sorted sample;
   leaves     leaf(x) = clamp(floor(y(x) * L), 0, L - 1), L linear leaves;
@@ -23,8 +28,12 @@ construction, in FP64 here and in FP32 on the device:
              to leaves below l;
   bucket     bucket(x) = min(B - 1, floor(pos(x) * B)).
 
-Nothing here is shared with the CUDA library.  The derivative of relu at 0 is
-taken as 0.
+  leaf table leaf(X) = number of thresholds <= X, thresholds T_l = the least
+             integer feature X with floor(root(X 2^-24) L) >= l, l = 1..L-1
+             (the exact step function of the monotone root, as a table).
+
+Nothing here is shared with the CUDA library.  The derivative of the ramp is
+taken as 1 strictly inside (0, 1) and 0 elsewhere.
 """
 
 import numpy as np
@@ -46,32 +55,61 @@ def feature(codes: np.ndarray, cmin: int, shift: int) -> np.ndarray:
     return q.astype(np.float64) * (2.0 ** -FEATURE_BITS)
 
 
+MAX_SLOPE = float(1 << 20)
+
+
+def ramp(z):
+    return np.minimum(np.maximum(z, 0.0), 1.0)
+
+
+def ramp_grad(z):
+    return ((z > 0.0) & (z < 1.0)).astype(np.float64)
+
+
 def init_params(seed: int = 0) -> dict:
-    """A monotone starting point: unit first-layer slopes with breakpoints
-    spread over [0, 1), small positive second layer, positive readout."""
+    """A monotone starting point: ramps spread evenly over [0, 1), identity
+    second layer, readout 1/32 -- the root is then y = x."""
     rng = np.random.default_rng(seed)
-    W1 = np.ones(HIDDEN)
-    b1 = -np.arange(HIDDEN) / HIDDEN
-    W2 = rng.uniform(0.0, 2.0 / HIDDEN, size=(HIDDEN, HIDDEN))
+    W1 = np.full(HIDDEN, float(HIDDEN))
+    b1 = -np.arange(HIDDEN, dtype=np.float64)
+    W2 = np.eye(HIDDEN) + rng.uniform(0.0, 1e-3, size=(HIDDEN, HIDDEN))
     b2 = np.zeros(HIDDEN)
     w3 = np.full(HIDDEN, 1.0 / HIDDEN)
     b3 = 0.0
     return dict(W1=W1, b1=b1, W2=W2, b2=b2, w3=w3, b3=np.float64(b3))
 
 
+def quantile_init(x_sorted: np.ndarray) -> dict:
+    """Ramp j rises over [q_j, q_{j+1}], q_j = x at rank floor(j m / 32) of
+    the sorted sample (q_32 = the last x); slopes capped at 2^20; identity
+    second layer; w3 = 1/32.  root(x) is then the piecewise-linear
+    interpolation of the empirical CDF through the 33 quantile knots."""
+    m = x_sorted.shape[0]
+    q = np.array([x_sorted[min(m - 1, (j * m) // HIDDEN)] for j in range(HIDDEN)] +
+                 [x_sorted[m - 1]], dtype=np.float64)
+    W1 = np.empty(HIDDEN)
+    b1 = np.empty(HIDDEN)
+    for j in range(HIDDEN):
+        width = q[j + 1] - q[j]
+        W1[j] = MAX_SLOPE if width * MAX_SLOPE <= 1.0 else 1.0 / width
+        b1[j] = -q[j] * W1[j]
+    return dict(W1=W1, b1=b1, W2=np.eye(HIDDEN), b2=np.zeros(HIDDEN),
+                w3=np.full(HIDDEN, 1.0 / HIDDEN), b3=np.float64(0.0))
+
+
 def forward(p: dict, x: np.ndarray):
     """Root network output y for every x, plus the activations."""
     z1 = np.outer(x, p["W1"]) + p["b1"]          # (m, 32)
-    h1 = np.maximum(z1, 0.0)
+    h1 = ramp(z1)
     z2 = h1 @ p["W2"].T + p["b2"]                # (m, 32)
-    h2 = np.maximum(z2, 0.0)
+    h2 = ramp(z2)
     y = h2 @ p["w3"] + p["b3"]                   # (m,)
     return y, (z1, h1, z2, h2)
 
 
 def loss_and_grad(p: dict, x: np.ndarray, t: np.ndarray):
     """Mean squared error (1/m) sum (y - t)^2 and its exact gradient by the
-    chain rule through both relu layers."""
+    chain rule through both ramp layers."""
     m = x.shape[0]
     y, (z1, h1, z2, h2) = forward(p, x)
     r = y - t
@@ -80,10 +118,10 @@ def loss_and_grad(p: dict, x: np.ndarray, t: np.ndarray):
     g = {}
     g["w3"] = h2.T @ dy
     g["b3"] = np.float64(dy.sum())
-    dz2 = np.outer(dy, p["w3"]) * (z2 > 0.0)     # dL/dz2
+    dz2 = np.outer(dy, p["w3"]) * ramp_grad(z2)  # dL/dz2
     g["W2"] = dz2.T @ h1
     g["b2"] = dz2.sum(axis=0)
-    dz1 = (dz2 @ p["W2"]) * (z1 > 0.0)           # dL/dz1
+    dz1 = (dz2 @ p["W2"]) * ramp_grad(z1)        # dL/dz1
     g["W1"] = dz1.T @ x
     g["b1"] = dz1.sum(axis=0)
     return loss, g
@@ -154,3 +192,49 @@ def bucket_of(pos: np.ndarray, buckets: int) -> np.ndarray:
     """bucket = min(B - 1, floor(pos * B)), pos in [0, 1]."""
     b = np.floor(pos * buckets).astype(np.int64)
     return np.clip(b, 0, buckets - 1)
+
+
+def thresholds(p: dict, leaves: int) -> np.ndarray:
+    """T_l (l = 1..L-1) = least integer X in [0, 2^24) with
+    floor(root(X 2^-24) L) >= l, else 2^24; by bisection on the monotone root."""
+    out = np.empty(leaves - 1, dtype=np.int64)
+    top = 1 << FEATURE_BITS
+    for l in range(1, leaves):
+        lo, hi = 0, top
+        while lo < hi:
+            mid = (lo + hi) // 2
+            y, _ = forward(p, np.array([mid * 2.0 ** -FEATURE_BITS]))
+            if leaf_of(y, leaves)[0] >= l:
+                hi = mid
+            else:
+                lo = mid + 1
+        out[l - 1] = lo
+    return out
+
+
+def leaf_by_table(thresh: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Number of thresholds <= X (thresholds sorted)."""
+    return np.searchsorted(thresh, X, side="right")
+
+
+def mix64(z: int) -> int:
+    """SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014)."""
+    M = (1 << 64) - 1
+    z &= M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def sample_indices(n: int, seed: int, stride: int = 100) -> np.ndarray:
+    """One index per block of `stride` consecutive elements, at offset
+    splitmix64(seed ^ k) mod stride within block k (SplitMix64 finaliser:
+    Steele, Lea and Flood, OOPSLA 2014)."""
+    m = n // stride
+    k = np.arange(m, dtype=np.uint64)
+    z = k ^ np.uint64(seed)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (k * np.uint64(stride) + z % np.uint64(stride)).astype(np.int64)

@@ -42,7 +42,8 @@ MAX_N = 0x7FFFFFFF
 # Every symbol include/husky.h declares (checked by the export test).
 EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
-           "hs_argsort_noalloc", "hs_last_error", "hs_version")
+           "hs_argsort_noalloc", "hs_last_error", "hs_version",
+           "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile")
 
 NOALLOC_MAX_N = 262144
 
@@ -83,6 +84,14 @@ def load(path: str | None = None):
     lib.hs_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
     lib.hs_batched_workspace_size.restype = ci
     lib.hs_batched_workspace_size.argtypes = [u64, u64, ctypes.POINTER(sz)]
+    lib.hs_rmi_grad.restype = ci
+    lib.hs_rmi_grad.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp, vp]
+    lib.hs_rmi_leaf_fit.restype = ci
+    lib.hs_rmi_leaf_fit.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp, vp, vp]
+    lib.hs_rmi_sample_indices.restype = ci
+    lib.hs_rmi_sample_indices.argtypes = [u64, u64, vp, vp]
+    lib.hs_learned_profile.restype = ci
+    lib.hs_learned_profile.argtypes = [vp, vp, u64, ci, vp, vp, vp, vp, sz, vp]
     lib.hs_argsort_noalloc.restype = ci
     lib.hs_argsort_noalloc.argtypes = [vp, vp, u64, ci, ci, vp, vp]
     lib.hs_stats_enable.restype = ci
@@ -248,6 +257,43 @@ def stats_read() -> dict:
         out[r.name.decode()] = dict(launches=int(r.launches), total_ms=float(r.total_ms),
                                     algo_bytes=float(r.algo_bytes))
     return out
+
+
+def rmi_grad(params: torch.Tensor, x: torch.Tensor, t: torch.Tensor, stream=None):
+    """(loss, grad) of the learned root network on device float32 tensors."""
+    grad = torch.empty(1153, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(load().hs_rmi_grad(_ptr(params), _ptr(x), _ptr(t), x.numel(), _ptr(grad), _ptr(loss),
+                              _stream_handle(stream)))
+    return float(loss.item()), grad
+
+
+def rmi_leaf_fit(x: torch.Tensor, t: torch.Tensor, leaf_start: torch.Tensor, stream=None):
+    """Per-leaf (slope, intercept, band lo, band hi) float32 device tensors."""
+    leaves = leaf_start.numel() - 1
+    outs = [torch.empty(leaves, dtype=torch.float32, device=x.device) for _ in range(4)]
+    _check(load().hs_rmi_leaf_fit(_ptr(x), _ptr(t), _ptr(leaf_start), x.numel(), leaves,
+                                  *[_ptr(o) for o in outs], _stream_handle(stream)))
+    return outs
+
+
+def rmi_sample_indices(n: int, seed: int, device="cuda", stream=None) -> torch.Tensor:
+    out = torch.empty(max(n // 100, 1), dtype=torch.int64, device=device)
+    _check(load().hs_rmi_sample_indices(n, seed, _ptr(out), _stream_handle(stream)))
+    return out[: n // 100]
+
+
+def learned_profile(data: torch.Tensor, offsets: torch.Tensor, linear: bool = False, stream=None):
+    """(sort keys int64, buckets int32, info dict) from the learned path's model."""
+    data, offsets = _as_device_inputs(data, offsets)
+    n = offsets.numel() - 1
+    keys = torch.empty(n, dtype=torch.int64, device=offsets.device)
+    buckets = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    info = (ctypes.c_double * 4)()
+    ws = workspace(workspace_size(n, MODE_LEARNED), offsets.device)
+    _check(load().hs_learned_profile(_ptr(data), _ptr(offsets), n, 1 if linear else 0, _ptr(keys),
+                                     _ptr(buckets), info, _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return keys, buckets, dict(bits=int(info[0]), sample=int(info[1]), loss0=info[2], loss1=info[3])
 
 
 def version() -> int:

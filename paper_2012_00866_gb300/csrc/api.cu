@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "husky.h"
+#include "husky_learned.h"
 #include "hs_internal.h"
 
 namespace hs {
@@ -35,11 +36,13 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
-    kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKNumKinds
+    kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
+    kKBucketBounds, kKBucketSort, kKOverflow, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
-    "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill"};
+    "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_fit",
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow"};
 
 struct StatsTable {
     std::mutex mu;
@@ -91,10 +94,25 @@ struct Layout {
     size_t lb;
     size_t q_small, q_medium, q_large_a, q_large_b, run_base;
     uint64_t cap_small, cap_medium, cap_large;
+    // learned mode only
+    bool learned;
+    int bucket_bits;
+    uint32_t m;  // sample size
+    size_t model, samp_keys_a, samp_keys_b, samp_vals_a, samp_vals_b, samp_X, samp_x, samp_t;
+    size_t b_first, b_last, q_over, over_base, keys_extra;
+    uint64_t cap_over;
     size_t total;
 };
 
-Layout make_layout(uint64_t n) {
+constexpr uint64_t kLearnedMinN = 1ull << 16;  // below this the plain path is used
+
+int learned_bits(uint64_t n) {
+    int b = 1;
+    while (b < 27 && (1ull << b) * 256 < n) ++b;
+    return b;
+}
+
+Layout make_layout(uint64_t n, bool learned = false) {
     Layout L{};
     Carver c;
     L.flags = c.take(sizeof(DevFlags));
@@ -118,6 +136,26 @@ Layout make_layout(uint64_t n) {
     L.q_large_a = c.take(L.cap_large * sizeof(RunEntry));
     L.q_large_b = c.take(L.cap_large * sizeof(RunEntry));
     L.run_base = c.take((L.cap_large + 1) * 8);
+    L.learned = learned && n >= kLearnedMinN;
+    if (L.learned) {
+        L.bucket_bits = learned_bits(n);
+        L.m = (uint32_t)(n / kRmiStride);
+        L.model = c.take(sizeof(RmiModel));
+        L.samp_keys_a = c.take((size_t)L.m * 8);
+        L.samp_keys_b = c.take((size_t)L.m * 8);
+        L.samp_vals_a = c.take((size_t)L.m * 4);
+        L.samp_vals_b = c.take((size_t)L.m * 4);
+        L.samp_X = c.take((size_t)L.m * 4);
+        L.samp_x = c.take((size_t)L.m * 4);
+        L.samp_t = c.take((size_t)L.m * 4);
+        const uint64_t B = 1ull << L.bucket_bits;
+        L.b_first = c.take(B * 8);
+        L.b_last = c.take(B * 8);
+        L.cap_over = n / (kBucketCap + 1) + 1;
+        L.q_over = c.take(L.cap_over * sizeof(RunEntry));
+        L.over_base = c.take((L.cap_over + 1) * 8);
+        L.keys_extra = c.take(n * 8);
+    }
     L.total = c.off;
     return L;
 }
@@ -229,6 +267,7 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
     int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : HS_CODER_ASCII7;
     for (int attempt = 0; attempt < 2; ++attempt) {
         HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
+        HS_TRY(cudaMemsetAsync(&c.d_flags->kmin, 0xFF, sizeof(unsigned long long), c.s), "memset kmin");
         c.next_counter = 0;
         const double enc_bytes = 8.0 * (n + 1) + 8.0 * n + (bits ? n / 8.0 : 0.0);
         HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
@@ -490,6 +529,161 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
     return device_error_status(c.h);
 }
 
+// Learned: a monotone model maps sort keys to buckets; a stable partition by
+// bucket (two or three 9-bit passes) plus a sort inside each bucket gives the
+// sort by key.  Oversize buckets are copied when constant, sorted by a
+// segmented radix sort otherwise.  Returns HS_OK with *fallback = true when
+// the plain path must be used instead (BYTE8 coder).
+struct LearnedProfile {
+    uint64_t *keys;      // out: sort keys
+    uint32_t *buckets;   // out: bucket per string
+    int linear;          // untrained linear map instead of the model
+    double info[4];
+};
+
+hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, LearnedProfile *prof = nullptr) {
+    Input in = in0;
+    const uint64_t n = in.n;
+    const Layout &L = c.L;
+    SortBufs b{{c.at<uint64_t>(L.codes_a), c.at<uint64_t>(L.codes_b)},
+               {c.at<uint32_t>(L.vals_a), c.at<uint32_t>(L.vals_b)},
+               {c.at<uint32_t>(L.segs_a), c.at<uint32_t>(L.segs_b)}};
+    c.lb_words = sort_tiles(n) * kBins;
+    int used = 0;
+    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], c.at<uint32_t>(L.bits), false, true,
+                              &used);
+    if (st != HS_OK) return st;
+    if (used != HS_CODER_ASCII7) {
+        *fallback = true;
+        return HS_OK;
+    }
+    in.prefix_len = 9;
+    const bool perfect = c.h.nonexact == 0;
+    const uint64_t kmin = c.h.kmin, kmax = c.h.kmax;
+    int shift = 0;
+    while (((kmax - kmin) >> shift) >= (1ull << kRmiFeatureBits)) ++shift;
+    RmiModel *model = c.at<RmiModel>(L.model);
+    unsigned long long *hist = c.at<unsigned long long>(L.hist);
+    unsigned long long *bucket = c.at<unsigned long long>(L.bucket);
+
+    // 1% sample, sorted with the plain radix sort
+    const uint32_t m = L.m;
+    SortBufs sb{{c.at<uint64_t>(L.samp_keys_a), c.at<uint64_t>(L.samp_keys_b)},
+                {c.at<uint32_t>(L.samp_vals_a), c.at<uint32_t>(L.samp_vals_b)},
+                {nullptr, nullptr}};
+    HS_TRY(c.timed(kKRmiSample, 16.0 * m, [&] { return launch_rmi_sample(b.keys[0], n, kRmiSeed, sb.keys[0], m, c.s); }),
+           "rmi sample");
+    HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
+    HS_TRY(launch_histogram(sb.keys[0], nullptr, m, hist, c.sms, c.s), "sample histogram");
+    HS_TRY(launch_plan(hist, kKeyPasses, m, bucket, c.d_flags, c.s), "sample plan");
+    HS_TRY(c.read_flags(), "sample plan sync");
+    int passes[kHistPasses], np = 0;
+    for (int p = 0; p < kKeyPasses; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    int sc = 0;
+    st = run_passes(c, sb, &sc, m, passes, np, false, nullptr, true, nullptr, kOutVals, true);
+    if (st != HS_OK) return st;
+
+    // model: quantile init, gradient steps, leaf table, leaf fits
+    {
+        const unsigned long long km = kmin;
+        const int sh = shift;
+        HS_TRY(cudaMemcpyAsync(&model->kmin, &km, sizeof(km), cudaMemcpyHostToDevice, c.s), "model kmin");
+        HS_TRY(cudaMemcpyAsync(&model->shift, &sh, sizeof(sh), cudaMemcpyHostToDevice, c.s), "model shift");
+    }
+    HS_TRY(c.timed(kKRmiFit, 24.0 * m, [&] {
+               return launch_rmi_fit(sb.keys[sc], m, model, kmin, shift, c.at<uint32_t>(L.samp_X),
+                                     c.at<float>(L.samp_x), c.at<float>(L.samp_t), kRmiSteps, kRmiLr, c.s);
+           }),
+           "rmi fit");
+
+    // buckets, then the stable partition by bucket digits
+    const int bits = L.bucket_bits;
+    const uint64_t B = 1ull << bits;
+    if (prof) {
+        HS_TRY(launch_rmi_bucket(b.keys[0], n, model, bits, prof->linear, prof->buckets, nullptr, nullptr, c.sms, c.s),
+               "profile buckets");
+        HS_TRY(cudaMemcpyAsync(prof->keys, b.keys[0], n * 8, cudaMemcpyDeviceToDevice, c.s), "profile keys");
+        float losses[2] = {0.f, 0.f};
+        HS_TRY(cudaMemcpyAsync(losses, &model->loss0, sizeof(losses), cudaMemcpyDeviceToHost, c.s), "profile loss");
+        HS_TRY(cudaStreamSynchronize(c.s), "profile sync");
+        prof->info[0] = bits;
+        prof->info[1] = m;
+        prof->info[2] = losses[0];
+        prof->info[3] = losses[1];
+        return HS_OK;
+    }
+    HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
+    HS_TRY(c.timed(kKRmiBucket, 16.0 * n, [&] {
+               return launch_rmi_bucket(b.keys[0], n, model, bits, 0, b.segs[0], b.vals[0], hist, c.sms, c.s);
+           }),
+           "rmi bucket");
+    HS_TRY(launch_plan(hist, kHistPasses, n, bucket, c.d_flags, c.s), "bucket plan");
+    HS_TRY(c.read_flags(), "bucket plan sync");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    np = 0;
+    for (int p = kKeyPasses; p < kKeyPasses + (bits + kRadixBits - 1) / kRadixBits; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    int cur = 0;
+    st = run_passes(c, b, &cur, n, passes, np, true, nullptr, false, nullptr, kOutVals, true);
+    if (st != HS_OK) return st;
+
+    // per-bucket sorts
+    unsigned long long *first = c.at<unsigned long long>(L.b_first), *last = c.at<unsigned long long>(L.b_last);
+    HS_TRY(cudaMemsetAsync(first, 0xFF, B * 8, c.s), "memset bucket bounds");
+    HS_TRY(c.timed(kKBucketBounds, 4.0 * n, [&] { return launch_bucket_bounds(b.segs[cur], n, first, last, c.sms, c.s); }),
+           "bucket bounds");
+    RunEntry *q_over = c.at<RunEntry>(L.q_over);
+    HS_TRY(c.timed(kKBucketSort, 12.0 * n + (in.perm_u64 ? 16.0 : 12.0) * n, [&] {
+               return launch_bucket_sort(first, last, B, b.keys[cur], b.vals[cur], in.perm, in.perm_u64, q_over,
+                                         L.cap_over, c.d_flags, c.sms, c.s);
+           }),
+           "bucket sort");
+    HS_TRY(c.read_flags(), "bucket sort sync");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+
+    const uint64_t over = c.h.qcount[kQOverflow];
+    if (over > 0) {
+        unsigned long long *ob = c.at<unsigned long long>(L.over_base);
+        HS_TRY(launch_run_scan(q_over, over, ob, c.s), "overflow scan");
+        unsigned long long total = 0;
+        HS_TRY(cudaMemcpyAsync(&total, ob + over, 8, cudaMemcpyDeviceToHost, c.s), "overflow total");
+        HS_TRY(cudaStreamSynchronize(c.s), "overflow sync");
+        if (total > n) return fail(HS_ERR_INTERNAL, "overflow buckets overlap");
+        SortBufs ov{{c.at<uint64_t>(L.keys_extra), b.keys[cur ^ 1]},
+                    {b.segs[cur ^ 1], b.segs[cur]},
+                    {b.vals[cur ^ 1], b.vals[cur]}};
+        HS_TRY(c.timed(kKOverflow, 28.0 * total, [&] {
+                   return launch_overflow_gather(q_over, over, ob, total, b.keys[cur], b.vals[cur], ov.keys[0],
+                                                 ov.segs[0], ov.vals[0], c.s);
+               }),
+               "overflow gather");
+        HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
+        HS_TRY(launch_histogram(ov.keys[0], ov.segs[0], total, hist, c.sms, c.s), "overflow histogram");
+        HS_TRY(launch_plan(hist, kHistPasses, total, bucket, c.d_flags, c.s), "overflow plan");
+        HS_TRY(c.read_flags(), "overflow plan sync");
+        np = 0;
+        for (int p = 0; p < kHistPasses; ++p)
+            if (c.h.active[p]) passes[np++] = p;
+        int oc = 0;
+        st = run_passes(c, ov, &oc, total, passes, np, true, nullptr, false, nullptr, kOutVals, true);
+        if (st != HS_OK) return st;
+        HS_TRY(c.timed(kKOverflow, 28.0 * total, [&] {
+                   return launch_overflow_scatter(q_over, ob, total, ov.keys[oc], ov.segs[oc], ov.vals[oc],
+                                                  b.keys[cur], in.perm, in.perm_u64, c.s);
+               }),
+               "overflow scatter");
+    }
+    if (!perfect) {
+        st = run_fixup(c, in, b, cur, kTieKeyFlag, Instances{nullptr, 0});
+        if (st != HS_OK) return st;
+    }
+    HS_TRY(c.read_flags(), "final sync");
+    return device_error_status(c.h);
+}
+
 // Batched: one segmented sort by (instance, sort key) over all strings; the
 // payload is the local index, so the last pass writes the local permutation.
 hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets, uint64_t num_segs, int coder) {
@@ -537,8 +731,8 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
     return device_error_status(c.h);
 }
 
-bool make_ctx(Ctx &c, void *ws, size_t ws_bytes, uint64_t n, void *stream, hs_status *st) {
-    c.L = make_layout(n);
+bool make_ctx(Ctx &c, void *ws, size_t ws_bytes, uint64_t n, void *stream, hs_status *st, bool learned = false) {
+    c.L = make_layout(n, learned);
     if (ws == nullptr || ws_bytes < c.L.total) {
         *st = fail(HS_ERR_WORKSPACE, "workspace missing or smaller than hs_workspace_size()");
         return false;
@@ -572,7 +766,7 @@ hs_status hs_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_
     g_last_error.clear();
     if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
     if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
-    *out = make_layout(n).total;
+    *out = make_layout(n, mode == HS_MODE_LEARNED).total;
     return HS_OK;
 }
 
@@ -609,8 +803,13 @@ hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t
     if (!d_bytes || !d_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
     Ctx c;
     hs_status st;
-    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st)) return st;
+    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st, mode == HS_MODE_LEARNED)) return st;
     Input in{d_bytes, d_offsets, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
+    if (c.L.learned) {
+        bool fallback = false;
+        st = argsort_learned(c, in, coder, &fallback);
+        if (st != HS_OK || !fallback) return st;
+    }
     return argsort_plain(c, in, coder);
 }
 
@@ -664,6 +863,61 @@ hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count) {
         out[k].algo_bytes = g_stats.bytes[k];
     }
     *count = kKNumKinds;
+    return HS_OK;
+}
+
+hs_status hs_rmi_grad(const float *d_params, const float *d_x, const float *d_t, uint32_t T, float *d_grad,
+                      float *d_loss, void *stream) {
+    g_last_error.clear();
+    if (T < 1 || T > HS_RMI_MAX_POINTS) return fail(HS_ERR_INVALID_ARG, "T must be 1..HS_RMI_MAX_POINTS");
+    if (!d_params || !d_x || !d_t || !d_grad || !d_loss) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HS_TRY(launch_rmi_grad(d_params, d_x, d_t, (int)T, d_grad, d_loss, s), "rmi grad");
+    HS_TRY(cudaStreamSynchronize(s), "rmi grad sync");
+    return HS_OK;
+}
+
+hs_status hs_rmi_leaf_fit(const float *d_x, const float *d_t, const uint32_t *d_leaf_start, uint32_t m,
+                          uint32_t leaves, float *d_slope, float *d_icept, float *d_lo, float *d_hi, void *stream) {
+    g_last_error.clear();
+    if (leaves == 0) return HS_OK;
+    if (!d_x || !d_t || !d_leaf_start || !d_slope || !d_icept || !d_lo || !d_hi)
+        return fail(HS_ERR_INVALID_ARG, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HS_TRY(launch_leaf_fit(d_x, d_t, d_leaf_start, m, (int)leaves, d_slope, d_icept, d_lo, d_hi, s), "leaf fit");
+    HS_TRY(cudaStreamSynchronize(s), "leaf fit sync");
+    return HS_OK;
+}
+
+hs_status hs_rmi_sample_indices(uint64_t n, uint64_t seed, uint64_t *d_out, void *stream) {
+    g_last_error.clear();
+    const uint64_t m = n / kRmiStride;
+    if (m == 0) return HS_OK;
+    if (!d_out) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    if (m > 0xFFFFFFFFull) return fail(HS_ERR_INVALID_ARG, "n too large");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HS_TRY(launch_sample_indices(n, seed, d_out, (uint32_t)m, s), "sample indices");
+    HS_TRY(cudaStreamSynchronize(s), "sample sync");
+    return HS_OK;
+}
+
+hs_status hs_learned_profile(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int linear,
+                             uint64_t *d_keys, uint32_t *d_buckets, double *h_info, void *d_ws, size_t ws_bytes,
+                             void *stream) {
+    g_last_error.clear();
+    if (n < kLearnedMinN || n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n must be 65536..HS_MAX_N");
+    if (!d_bytes || !d_offsets || !d_keys || !d_buckets) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st, true)) return st;
+    Input in{d_bytes, d_offsets, n, 9, nullptr, 0};
+    LearnedProfile prof{d_keys, d_buckets, linear, {0, 0, 0, 0}};
+    bool fallback = false;
+    st = argsort_learned(c, in, HS_CODER_ASCII7, &fallback, &prof);
+    if (st != HS_OK) return st;
+    if (fallback) return fail(HS_ERR_CODER_DOMAIN, "learned profile needs ASCII7 input");
+    if (h_info)
+        for (int i = 0; i < 4; ++i) h_info[i] = prof.info[i];
     return HS_OK;
 }
 

@@ -65,6 +65,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         for (int i = tid; i < kEncHistPasses * kBins; i += kEncThreads) s_hist[i] = 0;
 
     bool any_nonexact = false, any_domain = false;
+    uint64_t kmin = ~0ull, kmax = 0;
     const uint64_t num_tiles = (n + kEncTile - 1) / kEncTile;
     for (uint64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
         const uint64_t t0 = tile * kEncTile;
@@ -126,6 +127,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                 exact = len <= (uint64_t)C::K && (len == 0 || last != 0);
                 if (KEYFLAG) code = (code << 1) | (exact ? 0u : 1u);
                 codes[t0 + j] = code;
+                kmin = code < kmin ? code : kmin;
+                kmax = code > kmax ? code : kmax;
                 if (hist) {
 #pragma unroll
                     for (int p = 0; p < kEncHistPasses; ++p)
@@ -147,6 +150,16 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     if (tid == 0) {
         if (any_nonexact) atomicOr(&flags->nonexact, 1u);
         if (any_domain) atomicOr(&flags->domain, 1u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t a = __shfl_xor_sync(kFull, kmin, o), b = __shfl_xor_sync(kFull, kmax, o);
+        kmin = a < kmin ? a : kmin;
+        kmax = b > kmax ? b : kmax;
+    }
+    if (lane == 0 && kmin <= kmax) {
+        atomicMin(&flags->kmin, (unsigned long long)kmin);
+        atomicMax(&flags->kmax, (unsigned long long)kmax);
     }
 }
 

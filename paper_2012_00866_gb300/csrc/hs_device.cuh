@@ -25,7 +25,8 @@ struct DevFlags {
     unsigned int nonexact;   // 1 if any string is not exactly represented
     unsigned int domain;     // 1 if ASCII7 saw a byte >= 0x80
     unsigned int nonconst;   // refinement: some large run is not constant
-    unsigned long long qcount[8];   // run-queue lengths (see RunQueue ids)
+    unsigned long long qcount[8];   // run-queue lengths (see QueueId)
+    unsigned long long kmin, kmax;  // range of the keys the encoder wrote (kmin preset to ~0)
     unsigned int active[16];        // plan: radix pass p is needed
     unsigned int pad[4];
 };

@@ -111,7 +111,7 @@ __device__ __forceinline__ uint64_t instance_base(const Instances &in, uint64_t 
 }
 
 // ---- fixup.cu ------------------------------------------------------------
-enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3 };
+enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3, kQOverflow = 4 };
 constexpr uint32_t kSmallMax = 32;     // warp per run
 constexpr uint32_t kMediumMax = 2048;  // block per run
 
@@ -179,5 +179,73 @@ cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count,
                                       uint64_t cap_medium, uint64_t cap_large,
                                       int q_large_id, uint64_t perm_n,
                                       DevFlags *flags, cudaStream_t s);
+
+// ---- rmi.cu (learned bucketing) --------------------------------------------
+constexpr int kRmiHidden = 32;
+constexpr int kRmiParams = 32 + 32 + 32 * 32 + 32 + 32 + 1;  // W1 b1 W2 b2 w3 b3
+constexpr int kRmiLeaves = 4096;
+constexpr int kRmiTrain = 2048;       // training points taken from the sample
+constexpr int kRmiSteps = 16;         // projected gradient steps after the quantile init
+constexpr float kRmiLr = 0.02f;
+constexpr int kRmiFeatureBits = 24;
+constexpr uint64_t kRmiStride = 100;  // one sample per 100 keys (a 1% sample)
+constexpr uint64_t kRmiSeed = 0x5DEECE66Dull;
+constexpr int kBucketCap = 4096;      // largest bucket sorted inside one CTA
+
+// Model state (device, in the workspace).  thresh[l-1] = least feature X
+// routed to leaf >= l (l = 1..L-1); thresh[L-1] = 2^24.
+struct RmiModel {
+    float p[kRmiParams];
+    float pad0[3];
+    uint32_t thresh[kRmiLeaves];
+    uint32_t leaf_start[kRmiLeaves + 4];
+    float slope[kRmiLeaves], icept[kRmiLeaves], lo[kRmiLeaves], hi[kRmiLeaves];
+    unsigned long long kmin;
+    int shift;
+    int pad1;
+    float loss0, loss1;  // training loss before / after the gradient steps
+};
+
+cudaError_t launch_rmi_sample(const uint64_t *keys, uint64_t n, uint64_t seed,
+                              uint64_t *out, uint32_t m, cudaStream_t s);
+cudaError_t launch_sample_indices(uint64_t n, uint64_t seed, uint64_t *out,
+                                  uint32_t m, cudaStream_t s);
+// Features of the sorted sample, training, leaf table, leaf fits.
+cudaError_t launch_rmi_fit(const uint64_t *sorted_sample, uint32_t m,
+                           RmiModel *model, uint64_t kmin, int shift,
+                           uint32_t *Xi, float *xf, float *tf, int steps,
+                           float lr, cudaStream_t s);
+cudaError_t launch_rmi_grad(const float *params, const float *x, const float *t,
+                            int T, float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_leaf_fit(const float *x, const float *t,
+                            const uint32_t *leaf_start, uint32_t m, int leaves,
+                            float *slope, float *icept, float *lo, float *hi,
+                            cudaStream_t s);
+cudaError_t launch_rmi_bucket(const uint64_t *keys, uint64_t n,
+                              const RmiModel *model, int bits, int linear,
+                              uint32_t *buckets, uint32_t *vals,
+                              unsigned long long *hist, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_bucket_bounds(const uint32_t *bk, uint64_t n,
+                                 unsigned long long *first,
+                                 unsigned long long *last, int num_sms,
+                                 cudaStream_t s);
+cudaError_t launch_bucket_sort(const unsigned long long *first,
+                               const unsigned long long *last,
+                               uint64_t num_buckets, uint64_t *keys,
+                               const uint32_t *vals, void *perm, int perm_u64,
+                               RunEntry *overflow, uint64_t cap_overflow,
+                               DevFlags *flags, int num_sms, cudaStream_t s);
+cudaError_t launch_overflow_gather(const RunEntry *runs, uint64_t count,
+                                   const unsigned long long *run_base,
+                                   uint64_t total, const uint64_t *keys,
+                                   const uint32_t *vals, uint64_t *ck,
+                                   uint32_t *cs, uint32_t *cv, cudaStream_t s);
+cudaError_t launch_overflow_scatter(const RunEntry *runs,
+                                    const unsigned long long *run_base,
+                                    uint64_t total, const uint64_t *ck,
+                                    const uint32_t *cs, const uint32_t *cv,
+                                    uint64_t *keys, void *perm, int perm_u64,
+                                    cudaStream_t s);
 
 }  // namespace hs

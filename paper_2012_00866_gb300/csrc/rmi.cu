@@ -1,0 +1,682 @@
+// Learned bucketing for Step 2 (a recursive-model index over the sort keys).
+//
+// Huskysort's first pass only needs a key order that agrees with the codes
+// (Section 3.1 Step 2; Section 3.2: x > y must never map below y).  Here a
+// small learned CDF model maps each 63-bit sort key to one of B = 2^k
+// buckets by a function that is monotone non-decreasing in the key, so a
+// stable partition by bucket followed by a sort inside each bucket is the
+// full sort by key -- two or three partition passes instead of seven radix
+// passes.  The model never decides the order, only the speed.
+//
+//   feature   X = min((key - kmin) >> shift, 2^24 - 1), x = X 2^-24 (exact);
+//   root      y = w3 . h(W2 h(W1 x + b1) + b2) + b3, h(z) = min(max(z,0),1),
+//             1 -> 32 -> 32 -> 1, W1, W2, w3 >= 0: monotone in x (every FP32
+//             operation used is monotone in its varying operand);
+//   init      first-layer ramps between consecutive 1/32-quantiles of a 1%
+//             sample, identity second layer: the root starts as the
+//             piecewise-linear empirical CDF; then projected gradient steps
+//             on the mean squared error (forward and backward in this file);
+//   leaves    4096 leaves; leaf(X) = number of table thresholds <= X, the
+//             table being the exact step function of the root (bisection);
+//             leaf l fitted by least squares (FP64 sums), slope >= 0, output
+//             clamped to the band [c_l, c_{l+1}] of sample fractions;
+//   bucket    min(B - 1, floor(clamp(a_l x + b_l, c_l, c_{l+1}) B)).
+#include "hs_internal.h"
+
+namespace hs {
+namespace {
+
+constexpr int kP_W1 = 0, kP_B1 = 32, kP_W2 = 64, kP_B2 = 64 + 1024, kP_W3 = kP_B2 + 32, kP_B3 = kP_W3 + 32;
+static_assert(kP_B3 + 1 == kRmiParams, "parameter layout");
+constexpr int kTrainThreads = 1024;
+constexpr int kChunk = 128;           // training points per forward/backward chunk
+constexpr int kRow = 33;              // padded activation row
+constexpr float kMaxSlope = 1048576.0f;
+
+__device__ __forceinline__ float ramp(float z) { return fminf(fmaxf(z, 0.0f), 1.0f); }
+__device__ __forceinline__ float ramp_grad(float z) { return (z > 0.0f && z < 1.0f) ? 1.0f : 0.0f; }
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Root network, sequential order of operations (used for the leaf table).
+__device__ float rmi_root(const float *__restrict__ P, float x) {
+    float h1[kRmiHidden];
+#pragma unroll
+    for (int j = 0; j < kRmiHidden; ++j) h1[j] = ramp(fmaf(P[kP_W1 + j], x, P[kP_B1 + j]));
+    float y = P[kP_B3];
+#pragma unroll 4
+    for (int i = 0; i < kRmiHidden; ++i) {
+        float z = P[kP_B2 + i];
+#pragma unroll
+        for (int j = 0; j < kRmiHidden; ++j) z = fmaf(P[kP_W2 + i * kRmiHidden + j], h1[j], z);
+        y = fmaf(P[kP_W3 + i], ramp(z), y);
+    }
+    return y;
+}
+
+__device__ __forceinline__ uint32_t root_leaf(const float *P, uint32_t X) {
+    const float y = rmi_root(P, (float)X * 5.9604644775390625e-8f);  // X * 2^-24, exact
+    const float v = fminf(fmaxf(y * (float)kRmiLeaves, 0.0f), (float)(kRmiLeaves - 1));
+    return (uint32_t)v;
+}
+
+__device__ __forceinline__ uint32_t table_leaf(const uint32_t *__restrict__ thresh, uint32_t X) {
+    // number of thresholds <= X among kRmiLeaves - 1 sorted entries
+    uint32_t lo = 0, hi = kRmiLeaves - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (thresh[mid] <= X) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t feature_of(uint64_t key, uint64_t kmin, int shift) {
+    const uint64_t d = key >= kmin ? (key - kmin) >> shift : 0;
+    return d < (1u << kRmiFeatureBits) ? (uint32_t)d : (1u << kRmiFeatureBits) - 1;
+}
+
+// ---- loss and gradient over T points, one 1024-thread block --------------------
+//
+// Points are processed in chunks of 128, eight threads per point (each owns
+// four of the 32 second-layer units); activations go to shared memory and
+// then each thread accumulates the gradient of its own parameters over the
+// chunk in point order, so the sums are deterministic.
+
+struct GradSmem {
+    float H1[kChunk][kRow], Z1[kChunk][kRow], DZ2[kChunk][kRow], H2[kChunk][kRow];
+    float DY[kChunk], XC[kChunk], R2[kChunk];
+};
+
+__device__ void loss_grad_block(const float *__restrict__ P, const float *__restrict__ X,
+                                const float *__restrict__ Tt, int T, GradSmem &s, float *__restrict__ G,
+                                float *loss_out) {
+    const int tid = threadIdx.x, pt = tid >> 3, g = tid & 7;
+    float acc_w2 = 0.f, acc_small = 0.f, acc_loss = 0.f;
+    const float invT = 1.0f / (float)T;
+    for (int c0 = 0; c0 < T; c0 += kChunk) {
+        const int i = c0 + pt;
+        const bool valid = i < T;
+        const float x = valid ? X[i] : 0.f, t = valid ? Tt[i] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = g * 4 + u;
+            const float z1 = fmaf(P[kP_W1 + j], x, P[kP_B1 + j]);
+            s.Z1[pt][j] = z1;
+            s.H1[pt][j] = ramp(z1);
+        }
+        __syncwarp();
+        float z2[4], yp = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = g * 4 + u;
+            float z = P[kP_B2 + r];
+#pragma unroll 8
+            for (int j = 0; j < kRmiHidden; ++j) z = fmaf(P[kP_W2 + r * kRmiHidden + j], s.H1[pt][j], z);
+            z2[u] = z;
+            yp = fmaf(P[kP_W3 + r], ramp(z), yp);
+        }
+        yp += __shfl_xor_sync(kFull, yp, 1);
+        yp += __shfl_xor_sync(kFull, yp, 2);
+        yp += __shfl_xor_sync(kFull, yp, 4);
+        const float y = yp + P[kP_B3];
+        const float res = valid ? y - t : 0.f;
+        const float dy = 2.0f * res * invT;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = g * 4 + u;
+            s.DZ2[pt][r] = dy * P[kP_W3 + r] * ramp_grad(z2[u]);
+            s.H2[pt][r] = ramp(z2[u]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // dz1_j = (sum_r W2[r][j] dz2_r) h'(z1_j), stored over Z1
+            const int j = g * 4 + u;
+            float dh = 0.f;
+#pragma unroll 8
+            for (int r = 0; r < kRmiHidden; ++r) dh = fmaf(P[kP_W2 + r * kRmiHidden + j], s.DZ2[pt][r], dh);
+            s.Z1[pt][j] = dh * ramp_grad(s.Z1[pt][j]);
+        }
+        if (g == 0) {
+            s.DY[pt] = dy;
+            s.XC[pt] = x;
+            s.R2[pt] = res * res;
+        }
+        __syncthreads();
+        {   // W2[r][j]: thread tid = r * 32 + j
+            const int r = tid >> 5, j = tid & 31;
+            for (int q = 0; q < kChunk; ++q) acc_w2 = fmaf(s.DZ2[q][r], s.H1[q][j], acc_w2);
+        }
+        if (tid < 32) {
+            for (int q = 0; q < kChunk; ++q) acc_small = fmaf(s.Z1[q][tid], s.XC[q], acc_small);       // W1
+        } else if (tid < 64) {
+            for (int q = 0; q < kChunk; ++q) acc_small += s.Z1[q][tid - 32];                            // b1
+        } else if (tid < 96) {
+            for (int q = 0; q < kChunk; ++q) acc_small += s.DZ2[q][tid - 64];                           // b2
+        } else if (tid < 128) {
+            for (int q = 0; q < kChunk; ++q) acc_small = fmaf(s.DY[q], s.H2[q][tid - 96], acc_small);  // w3
+        } else if (tid == 128) {
+            for (int q = 0; q < kChunk; ++q) acc_small += s.DY[q];                                      // b3
+        } else if (tid == 129) {
+            for (int q = 0; q < kChunk; ++q) acc_loss += s.R2[q];
+        }
+        __syncthreads();
+    }
+    G[kP_W2 + tid] = acc_w2;
+    if (tid < 32) G[kP_W1 + tid] = acc_small;
+    else if (tid < 64) G[kP_B1 + tid - 32] = acc_small;
+    else if (tid < 96) G[kP_B2 + tid - 64] = acc_small;
+    else if (tid < 128) G[kP_W3 + tid - 96] = acc_small;
+    else if (tid == 128) G[kP_B3] = acc_small;
+    else if (tid == 129) *loss_out = acc_loss * invT;
+    __syncthreads();
+}
+
+struct TrainSmem {
+    float P[kRmiParams + 3];
+    float G[kRmiParams + 3];
+    float X[kRmiTrain], T[kRmiTrain];
+    float red[32];
+    float loss;
+    GradSmem g;
+};
+
+// hs_rmi_grad test hook: one loss/gradient evaluation.
+__global__ void __launch_bounds__(kTrainThreads)
+rmi_grad_kernel(const float *__restrict__ params, const float *__restrict__ x, const float *__restrict__ t, int T,
+                float *__restrict__ grad, float *__restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char train_smem[];
+    TrainSmem &s = *reinterpret_cast<TrainSmem *>(train_smem);
+    for (int k = threadIdx.x; k < kRmiParams; k += kTrainThreads) s.P[k] = params[k];
+    __syncthreads();
+    loss_grad_block(s.P, x, t, T, s.g, s.G, &s.loss);
+    for (int k = threadIdx.x; k < kRmiParams; k += kTrainThreads) grad[k] = s.G[k];
+    if (threadIdx.x == 0) *loss = s.loss;
+}
+
+// Features and targets of the sorted sample; T training points spread evenly.
+__global__ void rmi_features_kernel(const uint64_t *__restrict__ S, uint32_t m, uint64_t kmin, int shift,
+                                    uint32_t *__restrict__ Xi, float *__restrict__ xf, float *__restrict__ tf) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint32_t X = feature_of(S[j], kmin, shift);
+        Xi[j] = X;
+        xf[j] = (float)X * 5.9604644775390625e-8f;
+        tf[j] = (float)(((double)j + 0.5) / (double)m);
+    }
+}
+
+__global__ void __launch_bounds__(kTrainThreads)
+rmi_train_kernel(const float *__restrict__ xf, uint32_t m, RmiModel *model, int steps, float lr) {
+    extern __shared__ __align__(16) unsigned char train_smem[];
+    TrainSmem &s = *reinterpret_cast<TrainSmem *>(train_smem);
+    const int tid = threadIdx.x;
+    const int T = (int)umin64(m, kRmiTrain);
+    for (int i = tid; i < T; i += kTrainThreads) {
+        const uint32_t j = (uint32_t)(((uint64_t)i * m) / (uint64_t)T);
+        s.X[i] = xf[j];
+        s.T[i] = (float)(((double)j + 0.5) / (double)m);
+    }
+    // quantile init
+    if (tid < kRmiHidden) {
+        const float q0 = xf[umin64(m - 1, ((uint64_t)tid * m) / kRmiHidden)];
+        const float q1 = tid + 1 < kRmiHidden ? xf[umin64(m - 1, ((uint64_t)(tid + 1) * m) / kRmiHidden)] : xf[m - 1];
+        const float width = q1 - q0;
+        const float w = (width * kMaxSlope <= 1.0f) ? kMaxSlope : 1.0f / width;
+        s.P[kP_W1 + tid] = w;
+        s.P[kP_B1 + tid] = -q0 * w;
+        s.P[kP_B2 + tid] = 0.f;
+        s.P[kP_W3 + tid] = 1.0f / kRmiHidden;
+    }
+    s.P[kP_W2 + tid] = ((tid >> 5) == (tid & 31)) ? 1.0f : 0.0f;
+    if (tid == 0) s.P[kP_B3] = 0.f;
+    __syncthreads();
+    for (int step = 0; step <= steps; ++step) {
+        loss_grad_block(s.P, s.X, s.T, T, s.g, s.G, &s.loss);
+        if (step == 0 && tid == 0) model->loss0 = s.loss;
+        if (step == steps) break;
+        // global gradient norm (fixed-order reduction), clip to 1
+        float sq = 0.f;
+        for (int k = tid; k < kRmiParams; k += kTrainThreads) sq = fmaf(s.G[k], s.G[k], sq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+        if ((tid & 31) == 0) s.red[tid >> 5] = sq;
+        __syncthreads();
+        float tot = 0.f;
+        for (int w = 0; w < kTrainThreads / 32; ++w) tot += s.red[w];
+        const float scale = tot > 1.0f ? lr * rsqrtf(tot) : lr;
+        for (int k = tid; k < kRmiParams; k += kTrainThreads) {
+            float v = s.P[k] - scale * s.G[k];
+            const bool weight = (k < kP_B1) || (k >= kP_W2 && k < kP_B2) || (k >= kP_W3 && k < kP_B3);
+            if (weight) v = fmaxf(v, 0.f);  // projection keeps the root monotone
+            s.P[k] = v;
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < kRmiParams; k += kTrainThreads) model->p[k] = s.P[k];
+    if (tid == 0) model->loss1 = s.loss;
+}
+
+// thresh[l-1] = least X with root_leaf(X) >= l (bisection), l = 1..L-1.
+__global__ void rmi_thresholds_kernel(RmiModel *model) {
+    __shared__ float P[kRmiParams];
+    for (int k = threadIdx.x; k < kRmiParams; k += blockDim.x) P[k] = model->p[k];
+    __syncthreads();
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (l >= (uint32_t)kRmiLeaves) return;
+    uint32_t lo = 0, hi = 1u << kRmiFeatureBits;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (root_leaf(P, mid) >= l) hi = mid; else lo = mid + 1;
+    }
+    model->thresh[l - 1] = lo;
+}
+
+// Make the table non-decreasing (prefix maximum), so table_leaf is monotone
+// whatever the rounding of the root evaluation did.
+constexpr int kFixThreads = 1024;
+constexpr int kFixPer = kRmiLeaves / kFixThreads;  // 4
+
+__global__ void __launch_bounds__(kFixThreads) rmi_table_fix_kernel(RmiModel *model) {
+    __shared__ uint32_t s_warp[kFixThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t v[kFixPer];
+    uint32_t run = 0;
+#pragma unroll
+    for (int u = 0; u < kFixPer; ++u) {
+        const int i = tid * kFixPer + u;
+        v[u] = i < kRmiLeaves - 1 ? model->thresh[i] : (1u << kRmiFeatureBits);
+        run = max(run, v[u]);
+    }
+    uint32_t x = run;  // inclusive max-scan of thread maxima
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x = max(x, y);
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre = max(pre, s_warp[w]);
+    const uint32_t xp = __shfl_up_sync(kFull, x, 1);
+    run = max(pre, lane ? xp : 0u);  // maximum over earlier threads
+#pragma unroll
+    for (int u = 0; u < kFixPer; ++u) {
+        const int i = tid * kFixPer + u;
+        run = max(run, v[u]);
+        if (i < kRmiLeaves) model->thresh[i] = i < kRmiLeaves - 1 ? run : (1u << kRmiFeatureBits);
+    }
+}
+
+// leaf_start[l] = first sample index routed to a leaf >= l (the sample is
+// sorted and routing is monotone); leaf_start[L] = m.
+__global__ void rmi_leaf_start_kernel(const uint32_t *__restrict__ Xi, uint32_t m, RmiModel *model) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= m; j += stride) {
+        const uint32_t lj = j < m ? table_leaf(model->thresh, Xi[j]) : (uint32_t)kRmiLeaves;
+        const uint32_t lp = j > 0 ? table_leaf(model->thresh, Xi[j - 1]) : 0u;
+        const uint32_t from = j > 0 ? lp + 1 : 0u;
+        for (uint32_t l = from; l <= lj; ++l) model->leaf_start[l] = j;
+    }
+}
+
+// Least squares per leaf over its contiguous sample range, FP64 sums in a
+// fixed order (lane-strided, then a fixed shuffle tree); one warp per leaf.
+__global__ void rmi_leaf_fit_kernel(const float *__restrict__ xf, const float *__restrict__ tf,
+                                    const uint32_t *__restrict__ leaf_start, uint32_t m, int leaves,
+                                    float *__restrict__ slope, float *__restrict__ icept, float *__restrict__ lo_out,
+                                    float *__restrict__ hi_out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t l = warp_id; l < (uint32_t)leaves; l += nwarps) {
+        const uint32_t a = leaf_start[l], b = leaf_start[l + 1];
+        double Sx = 0, Sy = 0, Sxx = 0, Sxy = 0;
+        for (uint32_t j = a + lane; j < b; j += 32) {
+            const double x = xf[j], y = tf[j];
+            Sx += x;
+            Sy += y;
+            Sxx += x * x;
+            Sxy += x * y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Sx += __shfl_xor_sync(kFull, Sx, o);
+            Sy += __shfl_xor_sync(kFull, Sy, o);
+            Sxx += __shfl_xor_sync(kFull, Sxx, o);
+            Sxy += __shfl_xor_sync(kFull, Sxy, o);
+        }
+        if (lane == 0) {
+            const double S = (double)(b - a);
+            const double lo = m ? (double)a / m : 0.0, hi = m ? (double)b / m : 0.0;
+            double k = 0.0, c = lo;
+            if (b > a) {
+                const double den = S * Sxx - Sx * Sx;
+                if (b - a >= 2 && den > 0.0) k = (S * Sxy - Sx * Sy) / den;
+                if (k < 0.0) k = 0.0;
+                c = (Sy - k * Sx) / S;
+            }
+            slope[l] = (float)k;
+            icept[l] = (float)c;
+            lo_out[l] = (float)lo;
+            hi_out[l] = (float)hi;
+        }
+    }
+}
+
+// ---- bucketing ---------------------------------------------------------------
+
+constexpr int kBucketThreads = 512;
+
+__device__ __forceinline__ uint32_t bucket_of(const RmiModel &M, const uint32_t *s_thresh, uint64_t key,
+                                              uint64_t kmin, int shift, int bits, bool linear) {
+    const uint32_t X = feature_of(key, kmin, shift);
+    const float x = (float)X * 5.9604644775390625e-8f;
+    float pos;
+    if (linear) {
+        pos = x;
+    } else {
+        const uint32_t l = table_leaf(s_thresh, X);
+        pos = fminf(fmaxf(fmaf(__ldg(&M.slope[l]), x, __ldg(&M.icept[l])), __ldg(&M.lo[l])), __ldg(&M.hi[l]));
+    }
+    const float B = (float)(1u << bits);
+    const float v = fminf(fmaxf(pos * B, 0.0f), B - 1.0f);
+    return (uint32_t)v;
+}
+
+__global__ void __launch_bounds__(kBucketThreads)
+rmi_bucket_kernel(const uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__restrict__ model, int bits,
+                  int linear, uint32_t *__restrict__ buckets, uint32_t *__restrict__ vals,
+                  unsigned long long *__restrict__ hist) {
+    __shared__ uint32_t s_thresh[kRmiLeaves];
+    __shared__ uint32_t s_hist[kSegPasses * kBins];
+    for (int i = threadIdx.x; i < kRmiLeaves; i += kBucketThreads) s_thresh[i] = model->thresh[i];
+    for (int i = threadIdx.x; i < kSegPasses * kBins; i += kBucketThreads) s_hist[i] = 0;
+    __syncthreads();
+    const uint64_t kmin = model->kmin;
+    const int shift = model->shift;
+    const uint64_t stride = (uint64_t)gridDim.x * kBucketThreads;
+    for (uint64_t i = (uint64_t)blockIdx.x * kBucketThreads + threadIdx.x; i < n; i += stride) {
+        const uint32_t b = bucket_of(*model, s_thresh, keys[i], kmin, shift, bits, linear != 0);
+        buckets[i] = b;
+        if (vals) vals[i] = (uint32_t)i;
+        if (hist) {
+#pragma unroll
+            for (int p = 0; p < kSegPasses; ++p)
+                atomicAdd(&s_hist[p * kBins + ((b >> (kRadixBits * p)) & (kBins - 1))], 1u);
+        }
+    }
+    __syncthreads();
+    if (hist)
+        for (int i = threadIdx.x; i < kSegPasses * kBins; i += kBucketThreads)
+            if (s_hist[i]) atomicAdd(&hist[kKeyPasses * kBins + i], (unsigned long long)s_hist[i]);
+}
+
+// first[b] / last[b]: positions of bucket b's first and last element after the
+// stable partition (buckets are contiguous and in increasing order).
+__global__ void bucket_bounds_kernel(const uint32_t *__restrict__ bk, uint64_t n, unsigned long long *__restrict__ first,
+                                     unsigned long long *__restrict__ last) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const uint32_t b = bk[j];
+        if (j == 0 || bk[j - 1] != b) first[b] = j;
+        if (j + 1 == n || bk[j + 1] != b) last[b] = j;
+    }
+}
+
+// Sort inside each bucket by key (stable: ties keep partition order, which is
+// input order).  Buckets up to kBucketCap: bitonic in shared memory on (key,
+// position).  Larger buckets: copied as they are when all keys are equal,
+// otherwise queued for the segmented overflow sort.  Writes keys back in
+// place and the payload to the permutation.
+constexpr int kBsThreads = 256;
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kBsThreads)
+bucket_sort_kernel(const unsigned long long *__restrict__ first, const unsigned long long *__restrict__ last,
+                   uint64_t num_buckets, uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                   IdxT *__restrict__ perm, RunEntry *__restrict__ overflow, uint64_t cap_overflow,
+                   DevFlags *flags) {
+    extern __shared__ __align__(16) unsigned char bs_smem[];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(bs_smem);
+    uint32_t *s_pos = reinterpret_cast<uint32_t *>(s_key + kBucketCap);
+    const int tid = threadIdx.x;
+    for (uint64_t b = blockIdx.x; b < num_buckets; b += gridDim.x) {
+        const unsigned long long f = first[b];
+        if (f == ~0ull) continue;  // empty
+        const uint64_t len = last[b] - f + 1;
+        if (len > (uint64_t)kBucketCap) {
+            const uint64_t k0 = keys[f];
+            bool diff = false;
+            for (uint64_t j = tid; j < len; j += kBsThreads) {
+                diff |= keys[f + j] != k0;
+                perm[f + j] = (IdxT)vals[f + j];
+            }
+            if (__syncthreads_or(diff) && tid == 0) {
+                const unsigned long long q = atomicAdd(&flags->qcount[kQOverflow], 1ull);
+                if (q < cap_overflow && len < 0xFFFFFFFFull) overflow[q] = RunEntry{f, (uint32_t)len, 0u};
+                else atomicOr(&flags->error, kErrInternal);
+            }
+            __syncthreads();
+            continue;
+        }
+        const int n_b = (int)len;
+        int P = 1;
+        while (P < n_b) P <<= 1;
+        __syncthreads();
+        bool unsorted = false;
+        for (int j = tid; j < P; j += kBsThreads) {
+            if (j < n_b) {
+                s_key[j] = keys[f + j];
+                s_pos[j] = (uint32_t)j;
+            } else {
+                s_key[j] = ~0ull;
+                s_pos[j] = 0xFFFFFFFFu;
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j + 1 < n_b; j += kBsThreads) unsorted |= s_key[j] > s_key[j + 1];
+        if (__syncthreads_or(unsorted)) {
+            for (int k = 2; k <= P; k <<= 1) {
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int i = tid; i < P; i += kBsThreads) {
+                        const int ixj = i ^ jj;
+                        if (ixj > i) {
+                            const bool up = (i & k) == 0;
+                            const bool gt = s_key[i] != s_key[ixj] ? s_key[i] > s_key[ixj] : s_pos[i] > s_pos[ixj];
+                            if (gt == up) {
+                                const uint64_t tk = s_key[i]; s_key[i] = s_key[ixj]; s_key[ixj] = tk;
+                                const uint32_t tp = s_pos[i]; s_pos[i] = s_pos[ixj]; s_pos[ixj] = tp;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int j = tid; j < n_b; j += kBsThreads) {
+                keys[f + j] = s_key[j];
+                perm[f + j] = (IdxT)vals[f + s_pos[j]];
+            }
+        } else {
+            for (int j = tid; j < n_b; j += kBsThreads) perm[f + j] = (IdxT)vals[f + j];
+        }
+    }
+}
+
+// Overflow buckets: gather (key, bucket run id, payload) into compacted
+// arrays, and scatter the sorted result back.
+__global__ void overflow_gather_kernel(const RunEntry *__restrict__ runs, uint64_t count,
+                                       const unsigned long long *__restrict__ run_base, uint64_t total,
+                                       const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                       uint64_t *__restrict__ ck, uint32_t *__restrict__ cs, uint32_t *__restrict__ cv) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {
+        uint64_t lo = 0, hi = count;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (run_base[mid] <= a) lo = mid; else hi = mid;
+        }
+        const uint64_t pos = runs[lo].start + (a - run_base[lo]);
+        ck[a] = keys[pos];
+        cs[a] = (uint32_t)lo;
+        cv[a] = vals[pos];
+    }
+}
+
+template <typename IdxT>
+__global__ void overflow_scatter_kernel(const RunEntry *__restrict__ runs, const unsigned long long *__restrict__ run_base,
+                                        uint64_t total, const uint64_t *__restrict__ ck, const uint32_t *__restrict__ cs,
+                                        const uint32_t *__restrict__ cv, uint64_t *__restrict__ keys,
+                                        IdxT *__restrict__ perm) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {
+        const uint32_t r = cs[a];
+        const uint64_t pos = runs[r].start + (a - run_base[r]);
+        keys[pos] = ck[a];
+        perm[pos] = (IdxT)cv[a];
+    }
+}
+
+__global__ void rmi_sample_kernel(const uint64_t *__restrict__ keys, uint64_t n, uint64_t seed,
+                                  uint64_t *__restrict__ out, uint32_t m) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+        const uint64_t i = (uint64_t)k * kRmiStride + splitmix64((uint64_t)k ^ seed) % kRmiStride;
+        out[k] = i < n ? keys[i] : keys[n - 1];
+    }
+}
+
+__global__ void sample_index_kernel(uint64_t n, uint64_t seed, uint64_t *__restrict__ out, uint32_t m) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride)
+        out[k] = (uint64_t)k * kRmiStride + splitmix64((uint64_t)k ^ seed) % kRmiStride;
+}
+
+size_t train_smem_bytes() { return sizeof(TrainSmem); }
+
+cudaError_t set_train_attr() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rmi_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rmi_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)train_smem_bytes());
+    if (e != cudaSuccess) return e;
+    done = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_rmi_sample(const uint64_t *keys, uint64_t n, uint64_t seed, uint64_t *out, uint32_t m,
+                              cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    rmi_sample_kernel<<<(m + 255) / 256, 256, 0, s>>>(keys, n, seed, out, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_indices(uint64_t n, uint64_t seed, uint64_t *out, uint32_t m, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    sample_index_kernel<<<(m + 255) / 256, 256, 0, s>>>(n, seed, out, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmi_fit(const uint64_t *sorted_sample, uint32_t m, RmiModel *model, uint64_t kmin, int shift,
+                           uint32_t *Xi, float *xf, float *tf, int steps, float lr, cudaStream_t s) {
+    cudaError_t e = set_train_attr();
+    if (e != cudaSuccess) return e;
+    rmi_features_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, m, kmin, shift, Xi, xf, tf);
+    rmi_train_kernel<<<1, kTrainThreads, train_smem_bytes(), s>>>(xf, m, model, steps, lr);
+    rmi_thresholds_kernel<<<(kRmiLeaves + 127) / 128, 128, 0, s>>>(model);
+    rmi_table_fix_kernel<<<1, kFixThreads, 0, s>>>(model);
+    rmi_leaf_start_kernel<<<(m + 256) / 256, 256, 0, s>>>(Xi, m, model);
+    rmi_leaf_fit_kernel<<<kRmiLeaves / 8, 256, 0, s>>>(xf, tf, model->leaf_start, m, kRmiLeaves, model->slope,
+                                                        model->icept, model->lo, model->hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmi_grad(const float *params, const float *x, const float *t, int T, float *grad, float *loss,
+                            cudaStream_t s) {
+    cudaError_t e = set_train_attr();
+    if (e != cudaSuccess) return e;
+    rmi_grad_kernel<<<1, kTrainThreads, train_smem_bytes(), s>>>(params, x, t, T, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_fit(const float *x, const float *t, const uint32_t *leaf_start, uint32_t m, int leaves,
+                            float *slope, float *icept, float *lo, float *hi, cudaStream_t s) {
+    const unsigned grid = (unsigned)((leaves + 7) / 8);
+    rmi_leaf_fit_kernel<<<grid, 256, 0, s>>>(x, t, leaf_start, m, leaves, slope, icept, lo, hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmi_bucket(const uint64_t *keys, uint64_t n, const RmiModel *model, int bits, int linear,
+                              uint32_t *buckets, uint32_t *vals, unsigned long long *hist, int num_sms,
+                              cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + kBucketThreads * 8 - 1) / (kBucketThreads * 8);
+    const unsigned grid = (unsigned)umin64(blocks, (uint64_t)num_sms * 4);
+    rmi_bucket_kernel<<<grid, kBucketThreads, 0, s>>>(keys, n, model, bits, linear, buckets, vals, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_bounds(const uint32_t *bk, uint64_t n, unsigned long long *first, unsigned long long *last,
+                                 int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((n + 255) / 256, (uint64_t)num_sms * 16);
+    bucket_bounds_kernel<<<grid, 256, 0, s>>>(bk, n, first, last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_sort(const unsigned long long *first, const unsigned long long *last, uint64_t num_buckets,
+                               uint64_t *keys, const uint32_t *vals, void *perm, int perm_u64, RunEntry *overflow,
+                               uint64_t cap_overflow, DevFlags *flags, int num_sms, cudaStream_t s) {
+    const unsigned grid = (unsigned)umin64(num_buckets, (uint64_t)num_sms * 8);
+    const size_t smem = (size_t)kBucketCap * 12;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(bucket_sort_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bucket_sort_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (perm_u64)
+        bucket_sort_kernel<uint64_t><<<grid, kBsThreads, smem, s>>>(first, last, num_buckets, keys, vals,
+                                                                    static_cast<uint64_t *>(perm), overflow,
+                                                                    cap_overflow, flags);
+    else
+        bucket_sort_kernel<uint32_t><<<grid, kBsThreads, smem, s>>>(first, last, num_buckets, keys, vals,
+                                                                    static_cast<uint32_t *>(perm), overflow,
+                                                                    cap_overflow, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overflow_gather(const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
+                                   uint64_t total, const uint64_t *keys, const uint32_t *vals, uint64_t *ck,
+                                   uint32_t *cs, uint32_t *cv, cudaStream_t s) {
+    if (total == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
+    overflow_gather_kernel<<<grid, 256, 0, s>>>(runs, count, run_base, total, keys, vals, ck, cs, cv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overflow_scatter(const RunEntry *runs, const unsigned long long *run_base, uint64_t total,
+                                    const uint64_t *ck, const uint32_t *cs, const uint32_t *cv, uint64_t *keys,
+                                    void *perm, int perm_u64, cudaStream_t s) {
+    if (total == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
+    if (perm_u64)
+        overflow_scatter_kernel<uint64_t><<<grid, 256, 0, s>>>(runs, run_base, total, ck, cs, cv, keys,
+                                                               static_cast<uint64_t *>(perm));
+    else
+        overflow_scatter_kernel<uint32_t><<<grid, 256, 0, s>>>(runs, run_base, total, ck, cs, cv, keys,
+                                                               static_cast<uint32_t *>(perm));
+    return cudaGetLastError();
+}
+
+}  // namespace hs

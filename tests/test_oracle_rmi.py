@@ -52,7 +52,7 @@ def test_gradient_matches_finite_differences(seed):
 
 
 def test_forward_known_function():
-    """W1 = e0, W2 = e0 e0^T, w3 = e0, zero biases: y = relu(relu(x)) = x."""
+    """W1 = e0, W2 = e0 e0^T, w3 = e0, zero biases: y = h(h(x)) = x on [0, 1]."""
     H = R.HIDDEN
     e0 = np.zeros(H); e0[0] = 1.0
     p = dict(W1=e0.copy(), b1=np.zeros(H), W2=np.outer(e0, e0), b2=np.zeros(H),
@@ -126,3 +126,53 @@ def test_training_reduces_loss():
     assert l1 < 0.5 * l0
     for k in ("W1", "W2", "w3"):
         assert np.all(p[k] >= 0)
+
+
+def test_root_can_be_concave():
+    """With ramps (unlike relu) a non-negative-weight root follows a concave
+    CDF: the quantile init interpolates the empirical CDF of a skewed sample
+    within a small error, far better than the identity."""
+    rng = np.random.default_rng(3)
+    x = np.sort(rng.beta(0.3, 3.0, 20000))           # mass piled near 0: concave CDF
+    t = (np.arange(x.size) + 0.5) / x.size
+    p = R.quantile_init(x)
+    y, _ = R.forward(p, x)
+    assert np.max(np.abs(y - t)) < 0.04
+    assert np.max(np.abs(x - t)) > 0.4                # the linear map is far off
+    assert np.all(np.diff(y) >= 0)
+
+
+def test_thresholds_reproduce_the_root_step_function():
+    """leaf(X) from the table equals floor(root(X 2^-24) L) at every X probed,
+    including each threshold and its predecessor."""
+    rng = np.random.default_rng(4)
+    x = np.sort(rng.uniform(0, 1, 5000) ** 3)
+    p = R.quantile_init(x)
+    L = 64
+    T = R.thresholds(p, L)
+    assert np.all(np.diff(T) >= 0)
+    probe = np.unique(np.concatenate([T, np.maximum(T - 1, 0),
+                                      rng.integers(0, 1 << 24, 2000)]))
+    probe = probe[probe < (1 << 24)]
+    y, _ = R.forward(p, probe * 2.0 ** -24)
+    assert np.array_equal(R.leaf_by_table(T, probe), R.leaf_of(y, L))
+
+
+def test_sample_indices_one_per_block():
+    idx = R.sample_indices(1_000_050, seed=7)
+    assert idx.shape[0] == 10_000
+    assert np.all(idx // 100 == np.arange(10_000))
+    assert np.all(np.diff(idx) > 0)
+    # the finaliser on 0 is 0, so block 0 of seed 0 is sampled at offset 0
+    assert R.sample_indices(100, seed=0)[0] == 0
+    # published SplitMix64 stream for seed 1234567: 6457827717110365317,
+    # 3203168211198807973 (state advanced by 0x9E3779B97F4A7C15 before mixing)
+    g = 0x9E3779B97F4A7C15
+    M = (1 << 64) - 1
+    assert R.mix64((1234567 + g) & M) == 6457827717110365317
+    assert R.mix64((1234567 + 2 * g) & M) == 3203168211198807973
+    seed = (1234567 + g) & M   # block k = 0 mixes k ^ seed = seed
+    assert R.sample_indices(100, seed=seed)[0] == 6457827717110365317 % 100
+    ks = np.arange(5, dtype=np.int64)
+    idx = R.sample_indices(500, seed=99)
+    assert [int(i) for i in idx] == [int(k) * 100 + R.mix64(int(k) ^ 99) % 100 for k in ks]
