@@ -33,6 +33,7 @@ METRIC = "strings sorted/sec (M keys/s) and % of HBM roofline, learned/batched v
 UNIT = "M keys/s"
 DEFAULT_WORKLOAD = "zipf_words_1e7"
 L2_FLUSH_BYTES = 256 << 20
+CPU_SAMPLE_MAX = 10_000_000   # strings the CPU baseline sorts at most
 
 
 def parse_args():
@@ -41,8 +42,13 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
-    p.add_argument("--mode", default="plain", choices=["plain", "learned"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                   help="one of workloads.STANDARD (batched_* use hs_argsort_batched)")
+    p.add_argument("--scale", type=float, default=1.0, help="scale the workload's size")
+    p.add_argument("--mode", default="plain", choices=["plain", "learned", "loop"],
+                   help="loop: a batched workload sorted one instance at a time with hs_argsort")
+    p.add_argument("--index", default=None, choices=["u32", "u64"],
+                   help="permutation index type (default: u64 above 2^31 strings or for skewed_1e9, else u32)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--stats", default=None, help="write per-kernel stats JSON here")
     return p.parse_args()
@@ -169,6 +175,15 @@ def profile_traffic(kernel_source: str, key: str):
 
 # ---- our arm --------------------------------------------------------------------
 
+def _sample(w, limit):
+    """The first `limit` strings of a workload (same distribution)."""
+    import workloads
+    if w.n <= limit:
+        return w
+    off = w.offsets[: limit + 1]
+    return workloads.Workload(w.bytes[: int(off[-1])], off.copy())
+
+
 def run_ours(args, rank, world, local):
     import torch
     import workloads
@@ -180,16 +195,38 @@ def run_ours(args, rank, world, local):
     hs.load()
     mode = hs.MODE_LEARNED if args.mode == "learned" else hs.MODE_PLAIN
 
-    w = workloads.standard(args.workload)
+    w = workloads.standard(args.workload, scale=args.scale)
     n = w.n
+    batched = w.seg_offsets is not None
+    index = args.index or ("u64" if (args.workload.startswith("skewed") and not batched) else "u32")
+    index_u64 = index == "u64" and not batched
     data = torch.from_numpy(w.bytes).to(device)
     off = torch.from_numpy(w.offsets.view(np.int64)).to(device)
-    perm = torch.empty(n, dtype=torch.int32, device=device)
+    seg = torch.from_numpy(w.seg_offsets.view(np.int64)).to(device) if batched else None
+    perm = torch.empty(n, dtype=torch.int64 if index_u64 else torch.int32, device=device)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream(device)
 
+    loop = args.mode == "loop" and batched
+    if loop:  # per-instance views: string offsets rebased to the instance's first byte
+        views = []
+        for k in range(len(w.seg_offsets) - 1):
+            lo, hi = int(w.seg_offsets[k]), int(w.seg_offsets[k + 1])
+            if hi > lo:
+                views.append((data[int(w.offsets[lo]):int(w.offsets[hi])],
+                              off[lo:hi + 1] - int(w.offsets[lo]), perm[lo:hi]))
+
+    def step():
+        if loop:
+            for d, o, p in views:
+                hs.argsort_device(d, o, out=p)
+            return perm
+        if batched:
+            return hs.argsort_batched(data, off, seg)
+        return hs.argsort_device(data, off, mode=mode, index_u64=index_u64, out=perm)
+
     for _ in range(args.warmup):
-        hs.argsort_device(data, off, mode=mode, out=perm)
+        step()
     torch.cuda.synchronize(device)
 
     uuid = None
@@ -210,7 +247,7 @@ def run_ours(args, rank, world, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        hs.argsort_device(data, off, mode=mode, out=perm)
+        step()
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -225,39 +262,44 @@ def run_ours(args, rank, world, local):
     value = n * world / (ms / 1e3) / 1e6
 
     # end to end through the public API: pinned host inputs in, host perm out
-    h_data = torch.from_numpy(w.bytes).pin_memory()
-    h_off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
-    for _ in range(max(1, args.warmup)):
-        hs.argsort(h_data, h_off, mode=mode)
-    torch.cuda.synchronize(device)
-    barrier(world)
-    e2e_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
+    e2e = None
+    if not batched:
+        h_data = torch.from_numpy(w.bytes).pin_memory()
+        h_off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            hs.argsort(h_data, h_off, mode=mode, index_u64=index_u64)
         torch.cuda.synchronize(device)
-        t0 = time.perf_counter()
-        host_perm = hs.argsort(h_data, h_off, mode=mode)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    barrier(world)
-    e2e = sum(e2e_ms) / len(e2e_ms)
-    e2e = max_over_ranks(e2e, world, device)
-    e2e_value = n * world / (e2e / 1e3) / 1e6
-    del host_perm
+        barrier(world)
+        e2e_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            host_perm = hs.argsort(h_data, h_off, mode=mode, index_u64=index_u64)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        barrier(world)
+        e2e_t = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, device)
+        e2e = {"value": round(n * world / (e2e_t / 1e3) / 1e6, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(w.bytes.nbytes + w.offsets.nbytes),
+               "d2h_bytes_per_step": int(n * (8 if index_u64 else 4)), "ms_per_step": round(e2e_t, 3)}
+        del host_perm, h_data, h_off
 
     peaks, peak_src = measured_peaks()
-    os_stat = kstats.get("onesweep", {})
     launches = sum(v["launches"] for v in kstats.values())
     roofline = None
-    if os_stat.get("launches"):
-        achieved = os_stat["algo_bytes"] / (os_stat["total_ms"] / 1e3) / 1e9
-        per_launch = os_stat["algo_bytes"] / os_stat["launches"]
-        roofline = {"kernel": "onesweep_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+    timed = {k: v for k, v in kstats.items() if v["launches"] and v["total_ms"] > 0}
+    if timed:
+        top = max(timed, key=lambda k: timed[k]["total_ms"])
+        st = timed[top]
+        achieved = st["algo_bytes"] / (st["total_ms"] / 1e3) / 1e9
+        roofline = {"kernel": top + "_kernel", "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": round(achieved / peaks["hbm_gbs"], 4),
-                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                    "algo_bytes_per_launch": per_launch,
-                    "launch_ms": round(os_stat["total_ms"] / os_stat["launches"], 5),
-                    "traffic": profile_traffic("paper_2012_00866_gb300/csrc/sort.cu", f"onesweep/{args.workload}")}
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                    "algo_bytes_per_launch": st["algo_bytes"] / st["launches"],
+                    "launch_ms": round(st["total_ms"] / st["launches"], 5),
+                    "share_of_step": round(st["total_ms"] / args.steps / ms, 3),
+                    "traffic": profile_traffic("paper_2012_00866_gb300/csrc/sort.cu", f"{top}/{args.workload}")}
 
     stages = {k: {"launches_per_step": v["launches"] / args.steps,
                   "ms_per_step": round(v["total_ms"] / args.steps, 4),
@@ -268,12 +310,25 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         threads = os.cpu_count() or 1
-        t0 = time.perf_counter()
-        oracle.stable_argsort(w.bytes, w.offsets, threads=threads)
-        dt = time.perf_counter() - t0
-        cpu = {"value": round(n / dt / 1e6, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"the full {args.workload} workload ({n} strings), one run, "
-                         f"stable merge sort on {threads} threads"}
+        if batched:
+            k = 1
+            while k < len(w.seg_offsets) - 1 and int(w.seg_offsets[k + 1]) <= CPU_SAMPLE_MAX:
+                k += 1
+            cut = int(w.seg_offsets[k])
+            t0 = time.perf_counter()
+            oracle.stable_argsort_batched(w.bytes, w.offsets[: cut + 1], w.seg_offsets[: k + 1], threads=threads)
+            dt = time.perf_counter() - t0
+            what = f"the first {k} instances ({cut} strings)"
+            ns = cut
+        else:
+            sw = _sample(w, CPU_SAMPLE_MAX)
+            t0 = time.perf_counter()
+            oracle.stable_argsort(sw.bytes, sw.offsets, threads=threads)
+            dt = time.perf_counter() - t0
+            ns = sw.n
+            what = "the full workload" if sw.n == n else f"the first {sw.n} strings"
+        cpu = {"value": round(ns / dt / 1e6, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{what} of {args.workload}, one run, stable merge sort on {threads} threads"}
 
     if rank == 0:
         line = {
@@ -281,13 +336,15 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "bytes": int(w.bytes.size),
-                       "mode": args.mode, "index": "u32", "coder": "auto(ascii7)",
+            "config": {"workload": args.workload + (f"@{args.scale:g}" if args.scale != 1.0 else ""),
+                       "n": n, "bytes": int(w.bytes.size),
+                       "instances": int(len(w.seg_offsets) - 1) if batched else 1,
+                       "mode": ("loop" if loop else "batched") if batched else args.mode,
+                       "index": "u32" if not index_u64 else "u64",
+                       "coder": "auto(ascii7)",
                        "l2": "flushed by a 256 MiB write before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(w.bytes.nbytes + w.offsets.nbytes),
-                    "d2h_bytes_per_step": int(n * 4), "ms_per_step": round(e2e, 3)},
+            "e2e": e2e,
             "gpu_launches": int(launches),
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -310,15 +367,27 @@ def run_reference(args, rank, world, local):
         return
     import oracle
     import workloads
-    w = workloads.standard(args.workload)
-    n = w.n
+    w = workloads.standard(args.workload, scale=args.scale)
+    full_n = w.n
+    if w.seg_offsets is not None:   # batched: the leading instances up to the sample bound
+        k = 1
+        while k < len(w.seg_offsets) - 1 and int(w.seg_offsets[k + 1]) <= CPU_SAMPLE_MAX:
+            k += 1
+        cut = int(w.seg_offsets[k])
+        sort = lambda: oracle.stable_argsort_batched(w.bytes, w.offsets[: cut + 1], w.seg_offsets[: k + 1],
+                                                     threads=threads)
+        n = cut
+    else:
+        sw = _sample(w, CPU_SAMPLE_MAX)
+        sort = lambda: oracle.stable_argsort(sw.bytes, sw.offsets, threads=threads)
+        n = sw.n
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.stable_argsort(w.bytes, w.offsets, threads=threads)
+        sort()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.stable_argsort(w.bytes, w.offsets, threads=threads)
+        sort()
         times.append(time.perf_counter() - t0)
     ms = sum(times) / len(times) * 1e3
     value = n / (ms / 1e3) / 1e6
@@ -327,10 +396,12 @@ def run_reference(args, rank, world, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "bytes": int(w.bytes.size), "mode": "oracle",
+        "config": {"workload": args.workload + (f"@{args.scale:g}" if args.scale != 1.0 else ""),
+                   "n": full_n, "bytes": int(w.bytes.size), "mode": "oracle",
                    "index": "u32", "parallelism": "host threads"},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"the full {args.workload} workload each step"},
+                         "sample": (f"the full {args.workload} workload each step" if n == full_n else
+                                    f"the first {n} strings of {args.workload} each step")},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

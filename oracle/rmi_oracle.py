@@ -28,6 +28,14 @@ construction, in FP64 here and in FP32 on the device:
              to leaves below l;
   bucket     bucket(x) = min(B - 1, floor(pos(x) * B)).
 
+  leaf-relative inputs: the 24-bit feature only routes keys to leaves; each
+             leaf's line is evaluated on the key's full offset from the
+             leaf's base key, kb_l = cmin + (T_l << shift) (T_0 = 0), scaled
+             by s_l = 2^-e_l, e_l the bit length of the leaf's key range, so
+             keys sharing a 24-bit feature are still told apart.  The offset
+             is >= 0 for every key routed to the leaf, and converting it to
+             floating point and scaling are monotone, so pos stays monotone.
+
   leaf table leaf(X) = number of thresholds <= X, thresholds T_l = the least
              integer feature X with floor(root(X 2^-24) L) >= l, l = 1..L-1
              (the exact step function of the monotone root, as a table).
@@ -238,3 +246,24 @@ def sample_indices(n: int, seed: int, stride: int = 100) -> np.ndarray:
         z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
         z = z ^ (z >> np.uint64(31))
     return (k * np.uint64(stride) + z % np.uint64(stride)).astype(np.int64)
+
+
+def leaf_bases(thresh: np.ndarray, cmin: int, shift: int, leaves: int):
+    """(kb_l, s_l) per leaf: base key cmin + (T_l << shift) with T_0 = 0 and
+    T_l = thresh[l-1]; s_l = 2^-e_l, e_l = bit length of
+    (T_{l+1} - T_l) << shift (T_L = 2^24); s_l = 1 for an empty range."""
+    T = np.concatenate([[0], np.asarray(thresh, dtype=np.int64), [1 << FEATURE_BITS]])
+    kb = [int(cmin) + (int(T[l]) << shift) for l in range(leaves)]
+    sc = []
+    for l in range(leaves):
+        rng = (int(T[l + 1]) - int(T[l])) << shift
+        sc.append(2.0 ** -rng.bit_length() if rng > 0 else 1.0)
+    return kb, np.array(sc)
+
+
+def leaf_offsets(keys: np.ndarray, leaf: np.ndarray, kb, sc) -> np.ndarray:
+    """Scaled offset (key - kb_l) * s_l of every key within its leaf."""
+    out = np.empty(keys.shape[0])
+    for i, (k, l) in enumerate(zip(keys, leaf)):
+        out[i] = float(int(k) - kb[int(l)]) * sc[int(l)]
+    return out

@@ -37,12 +37,12 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
-    "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_fit",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow"};
+    "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves"};
 
 struct StatsTable {
     std::mutex mu;
@@ -99,17 +99,19 @@ struct Layout {
     int bucket_bits;
     uint32_t m;  // sample size
     size_t model, samp_keys_a, samp_keys_b, samp_vals_a, samp_vals_b, samp_X, samp_x, samp_t;
-    size_t b_first, b_last, q_over, over_base, keys_extra;
+    size_t b_first, b_last, q_over, over_base, keys_extra, big_mixed, q_mixed, mixed_base;
     uint64_t cap_over;
     size_t total;
 };
 
 constexpr uint64_t kLearnedMinN = 1ull << 16;  // below this the plain path is used
 
+// Bucket-id bits: about n/256 buckets, rounded to whole 9-bit partition
+// passes -- 18 bits (two passes) up to ~2.7e8 keys, 24 bits (three) above.
 int learned_bits(uint64_t n) {
-    int b = 1;
-    while (b < 27 && (1ull << b) * 256 < n) ++b;
-    return b;
+    int want = 1;
+    while (want < 30 && (1ull << want) * 256 < n) ++want;
+    return want <= 20 ? 18 : (want + 2 < 24 ? want + 2 : 24);
 }
 
 Layout make_layout(uint64_t n, bool learned = false) {
@@ -154,6 +156,9 @@ Layout make_layout(uint64_t n, bool learned = false) {
         L.cap_over = n / (kBucketCap + 1) + 1;
         L.q_over = c.take(L.cap_over * sizeof(RunEntry));
         L.over_base = c.take((L.cap_over + 1) * 8);
+        L.big_mixed = c.take(L.cap_over * 4);
+        L.q_mixed = c.take(L.cap_over * sizeof(RunEntry));
+        L.mixed_base = c.take((L.cap_over + 1) * 8);
         L.keys_extra = c.take(n * 8);
     }
     L.total = c.off;
@@ -591,11 +596,17 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
         HS_TRY(cudaMemcpyAsync(&model->kmin, &km, sizeof(km), cudaMemcpyHostToDevice, c.s), "model kmin");
         HS_TRY(cudaMemcpyAsync(&model->shift, &sh, sizeof(sh), cudaMemcpyHostToDevice, c.s), "model shift");
     }
-    HS_TRY(c.timed(kKRmiFit, 24.0 * m, [&] {
-               return launch_rmi_fit(sb.keys[sc], m, model, kmin, shift, c.at<uint32_t>(L.samp_X),
-                                     c.at<float>(L.samp_x), c.at<float>(L.samp_t), kRmiSteps, kRmiLr, c.s);
+    HS_TRY(c.timed(kKRmiFit, 20.0 * m, [&] {
+               return launch_rmi_train(sb.keys[sc], m, model, kmin, shift, c.at<uint32_t>(L.samp_X),
+                                       c.at<float>(L.samp_x), c.at<float>(L.samp_t), kRmiSteps, kRmiLr, c.s);
            }),
-           "rmi fit");
+           "rmi train");
+    HS_TRY(c.timed(kKRmiTable, 0.0, [&] { return launch_rmi_table(model, c.s); }), "rmi table");
+    HS_TRY(c.timed(kKRmiLeaves, 12.0 * m, [&] {
+               return launch_rmi_leaves(sb.keys[sc], c.at<uint32_t>(L.samp_X), c.at<float>(L.samp_x),
+                                        c.at<float>(L.samp_t), m, model, c.s);
+           }),
+           "rmi leaves");
 
     // buckets, then the stable partition by bucket digits
     const int bits = L.bucket_bits;
@@ -644,9 +655,34 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     st = device_error_status(c.h);
     if (st != HS_OK) return st;
 
-    const uint64_t over = c.h.qcount[kQOverflow];
+    // Oversize buckets: payload copied grid-wide; only the ones holding
+    // different keys (mixed) need the segmented sort.
+    const uint64_t big = c.h.qcount[kQOverflow];
+    uint64_t over = 0;
+    RunEntry *q_mixed = c.at<RunEntry>(L.q_mixed);
+    if (big > 0) {
+        unsigned long long *bb = c.at<unsigned long long>(L.over_base);
+        HS_TRY(launch_run_scan(q_over, big, bb, c.s), "big scan");
+        unsigned long long big_total = 0;
+        HS_TRY(cudaMemcpyAsync(&big_total, bb + big, 8, cudaMemcpyDeviceToHost, c.s), "big total");
+        HS_TRY(cudaStreamSynchronize(c.s), "big sync");
+        if (big_total > n) return fail(HS_ERR_INTERNAL, "oversize buckets overlap");
+        uint32_t *mixed = c.at<uint32_t>(L.big_mixed);
+        HS_TRY(cudaMemsetAsync(mixed, 0, big * 4, c.s), "memset mixed");
+        HS_TRY(c.timed(kKBucketSort, 20.0 * big_total, [&] {
+                   return launch_big_buckets(q_over, big, bb, big_total, b.keys[cur], b.vals[cur], in.perm,
+                                             in.perm_u64, mixed, c.s);
+               }),
+               "big buckets");
+        HS_TRY(launch_collect_mixed(q_over, big, mixed, q_mixed, L.cap_over, c.d_flags, c.s), "collect mixed");
+        HS_TRY(c.read_flags(), "mixed sync");
+        st = device_error_status(c.h);
+        if (st != HS_OK) return st;
+        over = c.h.qcount[kQMixed];
+    }
     if (over > 0) {
-        unsigned long long *ob = c.at<unsigned long long>(L.over_base);
+        q_over = q_mixed;
+        unsigned long long *ob = c.at<unsigned long long>(L.mixed_base);
         HS_TRY(launch_run_scan(q_over, over, ob, c.s), "overflow scan");
         unsigned long long total = 0;
         HS_TRY(cudaMemcpyAsync(&total, ob + over, 8, cudaMemcpyDeviceToHost, c.s), "overflow total");

@@ -129,11 +129,11 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                 codes[t0 + j] = code;
                 kmin = code < kmin ? code : kmin;
                 kmax = code > kmax ? code : kmax;
-                if (hist) {
+            }
+            if (hist) {  // whole warp converged here
 #pragma unroll
-                    for (int p = 0; p < kEncHistPasses; ++p)
-                        atomicAdd(&s_hist[p * kBins + (unsigned)((code >> digit_shift(p)) & digit_mask(p))], 1u);
-                }
+                for (int p = 0; p < kEncHistPasses; ++p)
+                    hist_add(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)), valid);
             }
             const unsigned ne = __ballot_sync(kFull, valid && !exact);
             any_nonexact |= valid && !exact;

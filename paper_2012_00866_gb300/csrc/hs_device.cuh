@@ -85,6 +85,23 @@ __device__ __forceinline__ unsigned match_digit(unsigned d, unsigned active) {
     return peers;
 }
 
+// Shared-memory histogram increment of digit d: when the whole warp holds
+// the same digit (constant or low-entropy digits), one add of the lane count
+// replaces 32 contending atomics.  Call with the full warp converged; lanes
+// with valid == false contribute nothing.
+__device__ __forceinline__ void hist_add(uint32_t *hist, unsigned d, bool valid) {
+    const unsigned active = __ballot_sync(kFull, valid);
+    if (active == 0) return;
+    const int src = __ffs(active) - 1;
+    const unsigned d0 = __shfl_sync(kFull, d, src);
+    const bool same = __all_sync(kFull, !valid || d == d0);
+    if (same) {
+        if ((threadIdx.x & 31) == (unsigned)src) atomicAdd(&hist[d0], (uint32_t)__popc(active));
+    } else if (valid) {
+        atomicAdd(&hist[d], 1u);
+    }
+}
+
 // Byte offset at which refinement depth `depth` starts comparing: the first
 // `prefix_len` bytes are covered by the husky code, each later depth by a
 // 7-byte window.

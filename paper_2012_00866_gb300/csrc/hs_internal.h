@@ -111,7 +111,7 @@ __device__ __forceinline__ uint64_t instance_base(const Instances &in, uint64_t 
 }
 
 // ---- fixup.cu ------------------------------------------------------------
-enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3, kQOverflow = 4 };
+enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3, kQOverflow = 4, kQMixed = 5 };
 constexpr uint32_t kSmallMax = 32;     // warp per run
 constexpr uint32_t kMediumMax = 2048;  // block per run
 
@@ -184,8 +184,9 @@ cudaError_t launch_push_constant_runs(const RunEntry *runs, uint64_t count,
 constexpr int kRmiHidden = 32;
 constexpr int kRmiParams = 32 + 32 + 32 * 32 + 32 + 32 + 1;  // W1 b1 W2 b2 w3 b3
 constexpr int kRmiLeaves = 4096;
-constexpr int kRmiTrain = 2048;       // training points taken from the sample
-constexpr int kRmiSteps = 16;         // projected gradient steps after the quantile init
+constexpr int kRmiTrain = 2048;       // training-point capacity (hs_rmi_grad)
+constexpr int kRmiTrainPoints = 512;  // points the learned path trains on
+constexpr int kRmiSteps = 8;          // projected gradient steps after the quantile init
 constexpr float kRmiLr = 0.02f;
 constexpr int kRmiFeatureBits = 24;
 constexpr uint64_t kRmiStride = 100;  // one sample per 100 keys (a 1% sample)
@@ -200,6 +201,9 @@ struct RmiModel {
     uint32_t thresh[kRmiLeaves];
     uint32_t leaf_start[kRmiLeaves + 4];
     float slope[kRmiLeaves], icept[kRmiLeaves], lo[kRmiLeaves], hi[kRmiLeaves];
+    // leaf l evaluates its line on (key - kbase[l]) * kscale[l]
+    unsigned long long kbase[kRmiLeaves];
+    float kscale[kRmiLeaves];
     unsigned long long kmin;
     int shift;
     int pad1;
@@ -210,11 +214,29 @@ cudaError_t launch_rmi_sample(const uint64_t *keys, uint64_t n, uint64_t seed,
                               uint64_t *out, uint32_t m, cudaStream_t s);
 cudaError_t launch_sample_indices(uint64_t n, uint64_t seed, uint64_t *out,
                                   uint32_t m, cudaStream_t s);
-// Features of the sorted sample, training, leaf table, leaf fits.
-cudaError_t launch_rmi_fit(const uint64_t *sorted_sample, uint32_t m,
-                           RmiModel *model, uint64_t kmin, int shift,
-                           uint32_t *Xi, float *xf, float *tf, int steps,
-                           float lr, cudaStream_t s);
+// Features of the sorted sample and training (quantile init + steps).
+cudaError_t launch_rmi_train(const uint64_t *sorted_sample, uint32_t m,
+                             RmiModel *model, uint64_t kmin, int shift,
+                             uint32_t *Xi, float *xf, float *tf, int steps,
+                             float lr, cudaStream_t s);
+// Leaf table (bisection of the root) made non-decreasing.
+cudaError_t launch_rmi_table(RmiModel *model, cudaStream_t s);
+// Leaf ranges of the sorted sample, leaf bases, leaf-relative sample
+// inputs (written over xf), least-squares leaves.
+cudaError_t launch_rmi_leaves(const uint64_t *sorted_sample, const uint32_t *Xi,
+                              float *xf, const float *tf, uint32_t m,
+                              RmiModel *model, cudaStream_t s);
+// Oversize buckets (from the bucket sort's queue): copy payload to perm and
+// flag buckets whose keys are not all equal (mixed[r] = 1, zeroed by caller).
+cudaError_t launch_big_buckets(const RunEntry *big, uint64_t count,
+                               const unsigned long long *base, uint64_t total,
+                               const uint64_t *keys, const uint32_t *vals,
+                               void *perm, int perm_u64, uint32_t *mixed,
+                               cudaStream_t s);
+// Push the mixed ones to q_mixed (DevFlags::qcount[kQMixed]).
+cudaError_t launch_collect_mixed(const RunEntry *big, uint64_t count,
+                                 const uint32_t *mixed, RunEntry *q_mixed,
+                                 uint64_t cap, DevFlags *flags, cudaStream_t s);
 cudaError_t launch_rmi_grad(const float *params, const float *x, const float *t,
                             int T, float *grad, float *loss, cudaStream_t s);
 cudaError_t launch_leaf_fit(const float *x, const float *t,

@@ -2,7 +2,7 @@
 //
 // Huskysort's first pass only needs a key order that agrees with the codes
 // (Section 3.1 Step 2; Section 3.2: x > y must never map below y).  Here a
-// small learned CDF model maps each 63-bit sort key to one of B = 2^k
+// small learned CDF model maps each 64-bit sort key to one of B = 2^k
 // buckets by a function that is monotone non-decreasing in the key, so a
 // stable partition by bucket followed by a sort inside each bucket is the
 // full sort by key -- two or three partition passes instead of seven radix
@@ -91,9 +91,11 @@ struct GradSmem {
     float DY[kChunk], XC[kChunk], R2[kChunk];
 };
 
-__device__ void loss_grad_block(const float *__restrict__ P, const float *__restrict__ X,
-                                const float *__restrict__ Tt, int T, GradSmem &s, float *__restrict__ G,
-                                float *loss_out) {
+// W2p: the second-layer weights again with a padded row stride of 33, so the
+// eight threads of a point (eight different rows) read different banks.
+__device__ void loss_grad_block(const float *__restrict__ P, const float (*__restrict__ W2p)[kRow],
+                                const float *__restrict__ X, const float *__restrict__ Tt, int T, GradSmem &s,
+                                float *__restrict__ G, float *loss_out) {
     const int tid = threadIdx.x, pt = tid >> 3, g = tid & 7;
     float acc_w2 = 0.f, acc_small = 0.f, acc_loss = 0.f;
     const float invT = 1.0f / (float)T;
@@ -115,7 +117,7 @@ __device__ void loss_grad_block(const float *__restrict__ P, const float *__rest
             const int r = g * 4 + u;
             float z = P[kP_B2 + r];
 #pragma unroll 8
-            for (int j = 0; j < kRmiHidden; ++j) z = fmaf(P[kP_W2 + r * kRmiHidden + j], s.H1[pt][j], z);
+            for (int j = 0; j < kRmiHidden; ++j) z = fmaf(W2p[r][j], s.H1[pt][j], z);
             z2[u] = z;
             yp = fmaf(P[kP_W3 + r], ramp(z), yp);
         }
@@ -137,7 +139,7 @@ __device__ void loss_grad_block(const float *__restrict__ P, const float *__rest
             const int j = g * 4 + u;
             float dh = 0.f;
 #pragma unroll 8
-            for (int r = 0; r < kRmiHidden; ++r) dh = fmaf(P[kP_W2 + r * kRmiHidden + j], s.DZ2[pt][r], dh);
+            for (int r = 0; r < kRmiHidden; ++r) dh = fmaf(W2p[r][j], s.DZ2[pt][r], dh);
             s.Z1[pt][j] = dh * ramp_grad(s.Z1[pt][j]);
         }
         if (g == 0) {
@@ -177,6 +179,7 @@ __device__ void loss_grad_block(const float *__restrict__ P, const float *__rest
 
 struct TrainSmem {
     float P[kRmiParams + 3];
+    float W2p[kRmiHidden][kRow];
     float G[kRmiParams + 3];
     float X[kRmiTrain], T[kRmiTrain];
     float red[32];
@@ -192,7 +195,9 @@ rmi_grad_kernel(const float *__restrict__ params, const float *__restrict__ x, c
     TrainSmem &s = *reinterpret_cast<TrainSmem *>(train_smem);
     for (int k = threadIdx.x; k < kRmiParams; k += kTrainThreads) s.P[k] = params[k];
     __syncthreads();
-    loss_grad_block(s.P, x, t, T, s.g, s.G, &s.loss);
+    s.W2p[threadIdx.x >> 5][threadIdx.x & 31] = s.P[kP_W2 + threadIdx.x];
+    __syncthreads();
+    loss_grad_block(s.P, s.W2p, x, t, T, s.g, s.G, &s.loss);
     for (int k = threadIdx.x; k < kRmiParams; k += kTrainThreads) grad[k] = s.G[k];
     if (threadIdx.x == 0) *loss = s.loss;
 }
@@ -214,7 +219,7 @@ rmi_train_kernel(const float *__restrict__ xf, uint32_t m, RmiModel *model, int 
     extern __shared__ __align__(16) unsigned char train_smem[];
     TrainSmem &s = *reinterpret_cast<TrainSmem *>(train_smem);
     const int tid = threadIdx.x;
-    const int T = (int)umin64(m, kRmiTrain);
+    const int T = (int)umin64(m, kRmiTrainPoints);
     for (int i = tid; i < T; i += kTrainThreads) {
         const uint32_t j = (uint32_t)(((uint64_t)i * m) / (uint64_t)T);
         s.X[i] = xf[j];
@@ -235,7 +240,9 @@ rmi_train_kernel(const float *__restrict__ xf, uint32_t m, RmiModel *model, int 
     if (tid == 0) s.P[kP_B3] = 0.f;
     __syncthreads();
     for (int step = 0; step <= steps; ++step) {
-        loss_grad_block(s.P, s.X, s.T, T, s.g, s.G, &s.loss);
+        s.W2p[tid >> 5][tid & 31] = s.P[kP_W2 + tid];
+        __syncthreads();
+        loss_grad_block(s.P, s.W2p, s.X, s.T, T, s.g, s.G, &s.loss);
         if (step == 0 && tid == 0) model->loss0 = s.loss;
         if (step == steps) break;
         // global gradient norm (fixed-order reduction), clip to 1
@@ -367,6 +374,31 @@ __global__ void rmi_leaf_fit_kernel(const float *__restrict__ xf, const float *_
     }
 }
 
+// kbase[l] = kmin + (T_l << shift), T_0 = 0, T_l = thresh[l-1]; kscale[l] =
+// 2^-e, e = bit length of the leaf's key range (T_{l+1} - T_l) << shift.
+__global__ void rmi_leaf_base_kernel(RmiModel *model) {
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= (uint32_t)kRmiLeaves) return;
+    const uint64_t t0 = l == 0 ? 0u : model->thresh[l - 1];
+    const uint64_t t1 = l + 1 < (uint32_t)kRmiLeaves ? model->thresh[l] : (1ull << kRmiFeatureBits);
+    const int shift = model->shift;
+    model->kbase[l] = model->kmin + (t0 << shift);
+    const uint64_t range = t1 > t0 ? (t1 - t0) << shift : 0ull;
+    const int e = range ? 64 - __clzll((long long)range) : 0;
+    model->kscale[l] = range ? ldexpf(1.0f, -e) : 1.0f;
+}
+
+// Leaf-relative inputs of the sorted sample (the least-squares x).
+__global__ void rmi_leaf_input_kernel(const uint64_t *__restrict__ S, const uint32_t *__restrict__ Xi, uint32_t m,
+                                      const RmiModel *__restrict__ model, float *__restrict__ xf) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const uint32_t l = table_leaf(model->thresh, Xi[j]);
+        const uint64_t kb = model->kbase[l];
+        xf[j] = (float)(S[j] >= kb ? S[j] - kb : 0ull) * model->kscale[l];
+    }
+}
+
 // ---- bucketing ---------------------------------------------------------------
 
 constexpr int kBucketThreads = 512;
@@ -380,7 +412,9 @@ __device__ __forceinline__ uint32_t bucket_of(const RmiModel &M, const uint32_t 
         pos = x;
     } else {
         const uint32_t l = table_leaf(s_thresh, X);
-        pos = fminf(fmaxf(fmaf(__ldg(&M.slope[l]), x, __ldg(&M.icept[l])), __ldg(&M.lo[l])), __ldg(&M.hi[l]));
+        const uint64_t kb = __ldg(&M.kbase[l]);
+        const float xl = (float)(key >= kb ? key - kb : 0ull) * __ldg(&M.kscale[l]);
+        pos = fminf(fmaxf(fmaf(__ldg(&M.slope[l]), xl, __ldg(&M.icept[l])), __ldg(&M.lo[l])), __ldg(&M.hi[l]));
     }
     const float B = (float)(1u << bits);
     const float v = fminf(fmaxf(pos * B, 0.0f), B - 1.0f);
@@ -399,14 +433,19 @@ rmi_bucket_kernel(const uint64_t *__restrict__ keys, uint64_t n, const RmiModel 
     const uint64_t kmin = model->kmin;
     const int shift = model->shift;
     const uint64_t stride = (uint64_t)gridDim.x * kBucketThreads;
-    for (uint64_t i = (uint64_t)blockIdx.x * kBucketThreads + threadIdx.x; i < n; i += stride) {
-        const uint32_t b = bucket_of(*model, s_thresh, keys[i], kmin, shift, bits, linear != 0);
-        buckets[i] = b;
-        if (vals) vals[i] = (uint32_t)i;
+    const uint64_t n_round = (n + 31) & ~31ull;  // whole warps iterate together
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    for (uint64_t i = (uint64_t)blockIdx.x * kBucketThreads + threadIdx.x; i < n_round; i += stride) {
+        const bool valid = i < n;
+        uint32_t b = 0;
+        if (valid) {
+            b = bucket_of(*model, s_thresh, keys[i], kmin, shift, bits, linear != 0);
+            buckets[i] = b;
+            if (vals) vals[i] = (uint32_t)i;
+        }
         if (hist) {
-#pragma unroll
-            for (int p = 0; p < kSegPasses; ++p)
-                atomicAdd(&s_hist[p * kBins + ((b >> (kRadixBits * p)) & (kBins - 1))], 1u);
+            for (int p = 0; p < passes; ++p)
+                hist_add(s_hist + p * kBins, (b >> (kRadixBits * p)) & (kBins - 1), valid);
         }
     }
     __syncthreads();
@@ -428,11 +467,14 @@ __global__ void bucket_bounds_kernel(const uint32_t *__restrict__ bk, uint64_t n
 }
 
 // Sort inside each bucket by key (stable: ties keep partition order, which is
-// input order).  Buckets up to kBucketCap: bitonic in shared memory on (key,
-// position).  Larger buckets: copied as they are when all keys are equal,
-// otherwise queued for the segmented overflow sort.  Writes keys back in
-// place and the payload to the permutation.
+// input order).  Buckets up to kBsRankMax keys: each key's rank counted
+// against the others; up to kBucketCap: bitonic in shared memory on (key,
+// position).  Larger buckets are queued: a grid-wide pass copies their
+// payload and flags the ones holding different keys for the segmented
+// overflow sort.  Writes keys back in place and the payload to the
+// permutation.
 constexpr int kBsThreads = 256;
+constexpr int kBsRankMax = 256;  // rank counting (n^2 / 2 compares) up to here, bitonic above
 
 template <typename IdxT>
 __global__ void __launch_bounds__(kBsThreads)
@@ -448,25 +490,32 @@ bucket_sort_kernel(const unsigned long long *__restrict__ first, const unsigned 
         const unsigned long long f = first[b];
         if (f == ~0ull) continue;  // empty
         const uint64_t len = last[b] - f + 1;
-        if (len > (uint64_t)kBucketCap) {
-            const uint64_t k0 = keys[f];
-            bool diff = false;
-            for (uint64_t j = tid; j < len; j += kBsThreads) {
-                diff |= keys[f + j] != k0;
-                perm[f + j] = (IdxT)vals[f + j];
-            }
-            if (__syncthreads_or(diff) && tid == 0) {
+        if (len > (uint64_t)kBucketCap) {  // handled grid-wide afterwards
+            if (tid == 0) {
                 const unsigned long long q = atomicAdd(&flags->qcount[kQOverflow], 1ull);
                 if (q < cap_overflow && len < 0xFFFFFFFFull) overflow[q] = RunEntry{f, (uint32_t)len, 0u};
                 else atomicOr(&flags->error, kErrInternal);
             }
-            __syncthreads();
             continue;
         }
         const int n_b = (int)len;
+        __syncthreads();
+        if (n_b <= kBsRankMax) {
+            // rank of element i = number of elements before it in (key, position) order
+            for (int j = tid; j < n_b; j += kBsThreads) s_key[j] = keys[f + j];
+            __syncthreads();
+            for (int i = tid; i < n_b; i += kBsThreads) {
+                const uint64_t ki = s_key[i];
+                int r = 0;
+                for (int j = 0; j < i; ++j) r += s_key[j] <= ki;      // earlier: equal keys count
+                for (int j = i + 1; j < n_b; ++j) r += s_key[j] < ki;  // later: only smaller keys
+                keys[f + r] = ki;
+                perm[f + r] = (IdxT)vals[f + i];
+            }
+            continue;
+        }
         int P = 1;
         while (P < n_b) P <<= 1;
-        __syncthreads();
         bool unsorted = false;
         for (int j = tid; j < P; j += kBsThreads) {
             if (j < n_b) {
@@ -504,6 +553,35 @@ bucket_sort_kernel(const unsigned long long *__restrict__ first, const unsigned 
             for (int j = tid; j < n_b; j += kBsThreads) perm[f + j] = (IdxT)vals[f + j];
         }
     }
+}
+
+// Oversize buckets, flattened over their elements: payload -> perm, and a
+// flag for every bucket holding two different keys.
+template <typename IdxT>
+__global__ void big_bucket_kernel(const RunEntry *__restrict__ big, uint64_t count,
+                                  const unsigned long long *__restrict__ base, uint64_t total,
+                                  const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                  IdxT *__restrict__ perm, uint32_t *__restrict__ mixed) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {
+        uint64_t lo = 0, hi = count;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (base[mid] <= a) lo = mid; else hi = mid;
+        }
+        const uint64_t start = big[lo].start;
+        const uint64_t pos = start + (a - base[lo]);
+        perm[pos] = (IdxT)vals[pos];
+        if (keys[pos] != keys[start] && mixed[lo] == 0u) mixed[lo] = 1u;
+    }
+}
+
+__global__ void collect_mixed_kernel(const RunEntry *__restrict__ big, uint64_t count, const uint32_t *__restrict__ mixed,
+                                     RunEntry *__restrict__ q_mixed, uint64_t cap, DevFlags *flags) {
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count || !mixed[r]) return;
+    const unsigned long long q = atomicAdd(&flags->qcount[kQMixed], 1ull);
+    if (q < cap) q_mixed[q] = big[r]; else atomicOr(&flags->error, kErrInternal);
 }
 
 // Overflow buckets: gather (key, bucket run id, payload) into compacted
@@ -583,17 +661,49 @@ cudaError_t launch_sample_indices(uint64_t n, uint64_t seed, uint64_t *out, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_rmi_fit(const uint64_t *sorted_sample, uint32_t m, RmiModel *model, uint64_t kmin, int shift,
-                           uint32_t *Xi, float *xf, float *tf, int steps, float lr, cudaStream_t s) {
+cudaError_t launch_rmi_train(const uint64_t *sorted_sample, uint32_t m, RmiModel *model, uint64_t kmin, int shift,
+                             uint32_t *Xi, float *xf, float *tf, int steps, float lr, cudaStream_t s) {
     cudaError_t e = set_train_attr();
     if (e != cudaSuccess) return e;
     rmi_features_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, m, kmin, shift, Xi, xf, tf);
     rmi_train_kernel<<<1, kTrainThreads, train_smem_bytes(), s>>>(xf, m, model, steps, lr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmi_table(RmiModel *model, cudaStream_t s) {
     rmi_thresholds_kernel<<<(kRmiLeaves + 127) / 128, 128, 0, s>>>(model);
     rmi_table_fix_kernel<<<1, kFixThreads, 0, s>>>(model);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmi_leaves(const uint64_t *sorted_sample, const uint32_t *Xi, float *xf, const float *tf,
+                              uint32_t m, RmiModel *model, cudaStream_t s) {
     rmi_leaf_start_kernel<<<(m + 256) / 256, 256, 0, s>>>(Xi, m, model);
+    rmi_leaf_base_kernel<<<kRmiLeaves / 256, 256, 0, s>>>(model);
+    rmi_leaf_input_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, Xi, m, model, xf);
     rmi_leaf_fit_kernel<<<kRmiLeaves / 8, 256, 0, s>>>(xf, tf, model->leaf_start, m, kRmiLeaves, model->slope,
                                                         model->icept, model->lo, model->hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_big_buckets(const RunEntry *big, uint64_t count, const unsigned long long *base, uint64_t total,
+                               const uint64_t *keys, const uint32_t *vals, void *perm, int perm_u64, uint32_t *mixed,
+                               cudaStream_t s) {
+    if (total == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
+    if (perm_u64)
+        big_bucket_kernel<uint64_t><<<grid, 256, 0, s>>>(big, count, base, total, keys, vals,
+                                                         static_cast<uint64_t *>(perm), mixed);
+    else
+        big_bucket_kernel<uint32_t><<<grid, 256, 0, s>>>(big, count, base, total, keys, vals,
+                                                         static_cast<uint32_t *>(perm), mixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collect_mixed(const RunEntry *big, uint64_t count, const uint32_t *mixed, RunEntry *q_mixed,
+                                 uint64_t cap, DevFlags *flags, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    collect_mixed_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(big, count, mixed, q_mixed, cap, flags);
     return cudaGetLastError();
 }
 

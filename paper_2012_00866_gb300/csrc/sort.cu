@@ -236,16 +236,18 @@ histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__
     for (int i = threadIdx.x; i < P * kBins; i += kHistThreads) s_hist[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
-    for (uint64_t i = (uint64_t)blockIdx.x * kHistThreads + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = keys[i];
+    const uint64_t n_round = (n + 31) & ~31ull;  // whole warps iterate together
+    for (uint64_t i = (uint64_t)blockIdx.x * kHistThreads + threadIdx.x; i < n_round; i += stride) {
+        const bool valid = i < n;
+        const uint64_t k = valid ? keys[i] : 0;
 #pragma unroll
         for (int p = 0; p < kKeyPasses; ++p)
-            atomicAdd(&s_hist[p * kBins + (unsigned)((k >> digit_shift(p)) & digit_mask(p))], 1u);
+            hist_add(s_hist + p * kBins, (unsigned)((k >> digit_shift(p)) & digit_mask(p)), valid);
         if (HAS_SEG) {
-            const uint32_t sg = segs[i];
+            const uint32_t sg = valid ? segs[i] : 0;
 #pragma unroll
             for (int p = kKeyPasses; p < kHistPasses; ++p)
-                atomicAdd(&s_hist[p * kBins + ((sg >> digit_shift(p)) & digit_mask(p))], 1u);
+                hist_add(s_hist + p * kBins, (sg >> digit_shift(p)) & digit_mask(p), valid);
         }
     }
     __syncthreads();
@@ -290,20 +292,25 @@ seg_fill_kernel(const uint64_t *__restrict__ seg_offsets, uint64_t num_segs, uin
     __syncthreads();
     bool bad = false;
     const uint64_t stride = (uint64_t)gridDim.x * kSegThreads;
-    for (uint64_t i = (uint64_t)blockIdx.x * kSegThreads + threadIdx.x; i < n; i += stride) {
-        uint64_t lo = 0, hi = num_segs;  // seg_offsets[lo] <= i < seg_offsets[hi]
-        while (hi - lo > 1) {
-            const uint64_t mid = (lo + hi) >> 1;
-            if (seg_offsets[mid] <= i) lo = mid; else hi = mid;
+    const uint64_t n_round = (n + 31) & ~31ull;  // whole warps iterate together
+    for (uint64_t i = (uint64_t)blockIdx.x * kSegThreads + threadIdx.x; i < n_round; i += stride) {
+        const bool valid = i < n;
+        uint64_t lo = 0;
+        if (valid) {
+            uint64_t hi = num_segs;  // seg_offsets[lo] <= i < seg_offsets[hi]
+            while (hi - lo > 1) {
+                const uint64_t mid = (lo + hi) >> 1;
+                if (seg_offsets[mid] <= i) lo = mid; else hi = mid;
+            }
+            const uint64_t local = i - seg_offsets[lo];
+            bad |= local > kIdxMask;
+            const uint32_t bit = flag_bits ? ((flag_bits[i >> 5] >> (i & 31)) & 1u) : 0u;
+            segs[i] = (uint32_t)lo;
+            vals[i] = ((uint32_t)local & kIdxMask) | (bit << 31);
         }
-        const uint64_t local = i - seg_offsets[lo];
-        bad |= local > kIdxMask;
-        const uint32_t bit = flag_bits ? ((flag_bits[i >> 5] >> (i & 31)) & 1u) : 0u;
-        segs[i] = (uint32_t)lo;
-        vals[i] = ((uint32_t)local & kIdxMask) | (bit << 31);
 #pragma unroll
         for (int p = 0; p < kSegPasses; ++p)
-            atomicAdd(&s_hist[p * kBins + ((uint32_t)(lo >> digit_shift(kKeyPasses + p)) & (kBins - 1))], 1u);
+            hist_add(s_hist + p * kBins, (uint32_t)(lo >> digit_shift(kKeyPasses + p)) & (kBins - 1), valid);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kSegPasses * kBins; i += kSegThreads)

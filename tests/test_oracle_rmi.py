@@ -176,3 +176,32 @@ def test_sample_indices_one_per_block():
     ks = np.arange(5, dtype=np.int64)
     idx = R.sample_indices(500, seed=99)
     assert [int(i) for i in idx] == [int(k) * 100 + R.mix64(int(k) ^ 99) % 100 for k in ks]
+
+
+def test_leaf_relative_positions_monotone_and_finer():
+    """Keys that share a 24-bit feature get distinct positions once each leaf
+    works on the key's offset from its base; positions stay monotone."""
+    rng = np.random.default_rng(11)
+    # 40 clusters of 2,000 keys inside 2^30-wide windows, and one far key that
+    # makes the range ~2^62 (shift 38): each cluster shares one 24-bit feature
+    base = (np.arange(40, dtype=np.uint64) + np.uint64(1)) << np.uint64(55)
+    low = rng.integers(0, 1 << 30, size=(40, 2000)).astype(np.uint64)
+    keys = np.sort(np.concatenate([(base[:, None] + low).ravel(), [np.uint64((1 << 62) - 1)]]))
+    cmin, cmax = int(keys[0]), int(keys[-1])
+    shift = R.feature_shift(cmin, cmax)
+    X = ((keys - np.uint64(cmin)) >> np.uint64(shift)).astype(np.int64)
+    assert np.unique(X).size < 100
+    t = (np.arange(keys.size) + 0.5) / keys.size
+    p = R.quantile_init(X * 2.0 ** -24)
+    L = 256                      # more leaves than clusters, as in use (4096)
+    T = R.thresholds(p, L)
+    leaf = R.leaf_by_table(T, X)
+    kb, sc = R.leaf_bases(T, cmin, shift, L)
+    xl = R.leaf_offsets(keys, leaf, kb, sc)
+    assert np.all(xl >= 0) and np.all(xl <= 1.0)
+    starts = np.searchsorted(leaf, np.arange(L + 1))
+    slope, icept, lo, hi_ = R.leaf_fit(xl, t, starts)
+    pos = np.clip(slope[leaf] * xl + icept[leaf], lo[leaf], hi_[leaf])
+    assert np.all(np.diff(pos) >= 0)
+    b = R.bucket_of(pos, 1 << 12)
+    assert np.unique(b).size > 20 * np.unique(X).size   # far finer than the feature
