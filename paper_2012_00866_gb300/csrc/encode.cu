@@ -32,7 +32,8 @@ constexpr int kEncItems = kEncTile / kEncThreads;
 constexpr int kEncStage = 28672;   // staged bytes per tile
 constexpr int kEncHistPasses = kKeyPasses;
 constexpr size_t kEncOffBytes = (((size_t)kEncTile + 1) * 8 + 15) & ~(size_t)15;  // keeps s_bytes 16-B aligned
-constexpr size_t kEncSmem = kEncOffBytes + kEncStage + (size_t)kEncHistPasses * kBins * 4;
+constexpr int kEncPad = 16;        // word reads of the last staged string may run 15 bytes past the stage
+constexpr size_t kEncSmem = kEncOffBytes + kEncStage + kEncPad + (size_t)kEncHistPasses * kBins * 4;
 static_assert(kEncStage % 16 == 0, "staging buffer must keep 16-byte alignment");
 
 template <int CODER> struct CoderTraits;
@@ -45,6 +46,63 @@ template <> struct CoderTraits<2> {   // BYTE8
     static constexpr unsigned MASK = 0xFF;
 };
 
+// Bytes b[0..7] of a little-endian word in the code's order (b[0] most
+// significant), each cut to its low 7 bits and packed into 56 bits: the
+// stringToLong loop of Algorithm 4 for eight ASCII7 chars at once.
+__device__ __forceinline__ uint64_t pack7x8(uint64_t x) {
+    uint64_t t = __byte_perm((uint32_t)(x >> 32), 0, 0x0123) |
+                 ((uint64_t)__byte_perm((uint32_t)x, 0, 0x0123) << 32);   // byte swap
+    t &= 0x7F7F7F7F7F7F7F7Full;
+    t = (t & 0x007F007F007F007Full) | ((t & 0x7F007F007F007F00ull) >> 1);  // 14-bit pairs
+    t = (t & 0x00003FFF00003FFFull) | ((t & 0x3FFF00003FFF0000ull) >> 2);  // 28-bit quads
+    t = (t & 0x000000000FFFFFFFull) | ((t & 0x0FFFFFFF00000000ull) >> 4);  // 56 bits
+    return t;
+}
+
+// Code, exactness and (ASCII7) domain bit of a string whose first bytes are
+// the little-endian words w0 (bytes 0..7) and b8 (byte 8), length len.
+template <int CODER>
+__device__ __forceinline__ uint64_t code_from_words(uint64_t w0, unsigned b8, uint64_t len, bool &exact,
+                                                    bool &domain) {
+    using C = CoderTraits<CODER>;
+    const int m = (int)umin64(len, C::K);
+    if (m == 0) {
+        exact = true;
+        domain = false;
+        return 0;
+    }
+    const uint64_t low = m >= 8 ? ~0ull : ((1ull << (8 * m)) - 1);   // the first min(m, 8) bytes
+    const unsigned last = m == 9 ? b8 : (unsigned)(w0 >> (8 * (m - 1))) & 0xFFu;
+    exact = len <= (uint64_t)C::K && last != 0;
+    uint64_t code;
+    if (CODER == 1) {
+        domain = ((w0 & low) & 0x8080808080808080ull) != 0 || (m == 9 && (b8 & 0x80u));
+        code = (pack7x8(w0) << 7) | (b8 & 0x7Fu);          // nine chars, 63 bits
+        const int sh = 7 * (9 - m);
+        code = (code >> sh) << sh;                         // chars past m are padding zeros
+    } else {
+        domain = false;
+        code = (uint64_t)__byte_perm((uint32_t)(w0 >> 32), 0, 0x0123) |
+               ((uint64_t)__byte_perm((uint32_t)w0, 0, 0x0123) << 32);
+        const int sh = 8 * (8 - m);
+        code = sh >= 64 ? 0 : ((code >> sh) << sh);
+    }
+    return code;
+}
+
+// Histogram add of digit d for a full warp (every lane valid): one match
+// finds whether all lanes hold the same digit, in which case one add of 32
+// replaces 32 contending atomics.
+__device__ __forceinline__ void hist_add_full(uint32_t *hist, unsigned d) {
+    int same;
+    __match_all_sync(kFull, d, &same);
+    if (same) {
+        if ((threadIdx.x & 31) == 0) atomicAdd(&hist[d], 32u);
+    } else {
+        atomicAdd(&hist[d], 1u);
+    }
+}
+
 template <int CODER, bool KEYFLAG>
 __global__ void __launch_bounds__(kEncThreads)
 encode_kernel(const uint8_t *__restrict__ bytes,
@@ -55,7 +113,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_off = reinterpret_cast<uint64_t *>(smem);
     uint8_t *s_bytes = smem + kEncOffBytes;
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_bytes + kEncStage);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_bytes + kEncStage + kEncPad);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total = offsets[n];
@@ -113,27 +171,46 @@ encode_kernel(const uint8_t *__restrict__ bytes,
             if (valid) {
                 const uint64_t off = s_off[j];
                 const uint64_t len = s_off[j + 1] - off;
-                const int m = (int)umin64(len, C::K);
-                const uint8_t *src = staged ? s_bytes + (base + off - a0) : bytes + off;
-                unsigned last = 0;
-                for (int i = 0; i < m; ++i) {
-                    const unsigned c = src[i];
-                    if (CODER == 1) any_domain |= c >= 0x80u;
-                    code = (code << C::W) | (uint64_t)(c & C::MASK);
-                    last = c;
+                if (staged) {
+                    // the two aligned words holding bytes q .. q+15 of the stage
+                    const uint32_t q = (uint32_t)(base + off - a0);
+                    const uint64_t *wp = reinterpret_cast<const uint64_t *>(s_bytes + (q & ~7u));
+                    const uint64_t lo = wp[0], hi = wp[1];
+                    const int r = 8 * (int)(q & 7u);
+                    const uint64_t w0 = r ? (lo >> r) | (hi << (64 - r)) : lo;
+                    const unsigned b8 = (unsigned)(hi >> r) & 0xFFu;
+                    bool dom;
+                    code = code_from_words<CODER>(w0, b8, len, exact, dom);
+                    any_domain |= dom;
+                } else {
+                    const int m = (int)umin64(len, C::K);
+                    const uint8_t *src = bytes + off;
+                    unsigned last = 0;
+                    for (int i = 0; i < m; ++i) {
+                        const unsigned c = src[i];
+                        if (CODER == 1) any_domain |= c >= 0x80u;
+                        code = (code << C::W) | (uint64_t)(c & C::MASK);
+                        last = c;
+                    }
+                    const int shift = C::W * (C::K - m);
+                    code = shift >= 64 ? 0 : (code << shift);
+                    exact = len <= (uint64_t)C::K && (len == 0 || last != 0);
                 }
-                const int shift = C::W * (C::K - m);
-                code = shift >= 64 ? 0 : (code << shift);
-                exact = len <= (uint64_t)C::K && (len == 0 || last != 0);
                 if (KEYFLAG) code = (code << 1) | (exact ? 0u : 1u);
                 codes[t0 + j] = code;
                 kmin = code < kmin ? code : kmin;
                 kmax = code > kmax ? code : kmax;
             }
             if (hist) {  // whole warp converged here
+                if (k * kEncThreads + warp * 32 + 32 <= cnt) {
 #pragma unroll
-                for (int p = 0; p < kEncHistPasses; ++p)
-                    hist_add(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)), valid);
+                    for (int p = 0; p < kEncHistPasses; ++p)
+                        hist_add_full(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)));
+                } else {
+#pragma unroll
+                    for (int p = 0; p < kEncHistPasses; ++p)
+                        hist_add(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)), valid);
+                }
             }
             const unsigned ne = __ballot_sync(kFull, valid && !exact);
             any_nonexact |= valid && !exact;

@@ -77,15 +77,19 @@ __device__ __forceinline__ void push_run(const TieArgs &a, uint64_t start, uint6
 
 // Keys of the tile (plus one neighbour on each side) are staged through
 // shared memory with coalesced loads; each thread then scans 16 consecutive
-// positions.
-constexpr size_t kTieSmem = (size_t)(kTieTile + 2) * 8;
+// positions.  Staging slot x lives at tie_slot(x) = x + x / 16: the 16
+// threads of a half-warp read words 17 apart, in distinct bank pairs (without
+// the gap all sixteen would hit the same pair).
+constexpr int kTieSlots = kTieTile + 2;
+__device__ __forceinline__ int tie_slot(int x) { return x + (x >> 4); }
+constexpr size_t kTieSmem = (size_t)(kTieSlots + kTieSlots / 16 + 1) * 8;
 
 template <int MODE>
 __global__ void __launch_bounds__(kTieThreads)
 tie_detect_kernel(const TieArgs a) {
     constexpr bool REFINE = MODE == kTieRefine;
     extern __shared__ __align__(16) unsigned char tie_smem[];
-    uint64_t *s_key = reinterpret_cast<uint64_t *>(tie_smem);  // s_key[i + 1] = keys[t0 + i]
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(tie_smem);  // s_key[tie_slot(i + 1)] = keys[t0 + i]
     __shared__ uint64_t s_state[kTieThreads / 32];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_prefix;
@@ -97,9 +101,9 @@ tie_detect_kernel(const TieArgs a) {
     const uint64_t t0 = tile * kTieTile;
     const uint32_t cont_tag = (uint32_t)a.prefix_len + 8;
 
-    for (int i = tid; i < kTieTile + 2; i += kTieThreads) {
+    for (int i = tid; i < kTieSlots; i += kTieThreads) {
         const uint64_t j = t0 + i;  // position t0 + i - 1
-        s_key[i] = (j >= 1 && j - 1 < n) ? a.keys[j - 1] : 0;
+        s_key[tie_slot(i)] = (j >= 1 && j - 1 < n) ? a.keys[j - 1] : 0;
     }
     __syncthreads();
 
@@ -110,13 +114,15 @@ tie_detect_kernel(const TieArgs a) {
     if (SEGS && j0 > 0 && j0 - 1 < n) seg_prev = a.segs[j0 - 1];
     uint32_t heads = 0, flagsb = 0;
     RunState mine{0, 0, 0};
+    uint64_t k_prev = s_key[tie_slot(i0)];
 #pragma unroll
     for (int i = 0; i < kTieItems; ++i) {
         const uint64_t j = j0 + i;
         if (j < n) {
-            const uint64_t k = s_key[i0 + i + 1];
+            const uint64_t k = s_key[tie_slot(i0 + i + 1)];
             const uint32_t sg = SEGS ? a.segs[j] : 0;
-            const bool head = (j == 0) || k != s_key[i0 + i] || (SEGS && sg != seg_prev);
+            const bool head = (j == 0) || k != k_prev || (SEGS && sg != seg_prev);
+            k_prev = k;
             bool f;
             if (MODE == kTieKeyFlag) f = (k & 1u) != 0;
             else if (MODE == kTieValFlag) f = (a.vals[j] >> 31) != 0;
@@ -248,7 +254,7 @@ tie_detect_kernel(const TieArgs a) {
         } else if (jn >= n) {
             tail = true;
         } else {
-            tail = s_key[i0 + i + 2] != s_key[i0 + i + 1] || (SEGS && next_seg != a.segs[j]);
+            tail = s_key[tie_slot(i0 + i + 2)] != s_key[tie_slot(i0 + i + 1)] || (SEGS && next_seg != a.segs[j]);
         }
         if (tail) {
             const uint64_t len = j - st.last + 1;

@@ -73,16 +73,11 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Lanes of the warp whose radix digit equals this lane's, restricted to
-// `active` (one ballot per digit bit).
+// `active`.  Call with the full warp converged (lanes outside `active` pass
+// any digit).  The hardware match instruction measured faster here than one
+// ballot per digit bit.
 __device__ __forceinline__ unsigned match_digit(unsigned d, unsigned active) {
-    unsigned peers = active;
-#pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
-        unsigned bit = (d >> b) & 1u;
-        unsigned vote = __ballot_sync(kFull, bit);
-        peers &= bit ? vote : ~vote;
-    }
-    return peers;
+    return __match_any_sync(kFull, d) & active;
 }
 
 // Shared-memory histogram increment of digit d: when the whole warp holds

@@ -6,10 +6,11 @@
 // Each pass is a single "onesweep" kernel (Adinets and Merrill, 2022): the
 // global digit offsets come from histograms computed up front (fused into the
 // encoder), each CTA ranks a tile of 4096 keys with warp-private digit
-// counters (one ballot per digit bit), publishes its per-digit counts and
-// resolves its global prefix by decoupled look-back over earlier tiles, then
-// scatters the tile through shared memory so that runs of equal digits leave
-// as coalesced stores.  Digits are 9 bits wide (512 bins, one per thread in
+// counters (lanes with equal digits found by a warp match), publishes its
+// per-digit counts, scatters the tile into shared memory in digit order,
+// resolves its global prefix by decoupled look-back over earlier tiles, and
+// writes the tile out so that runs of equal digits leave as coalesced
+// stores.  Digits are 9 bits wide (512 bins, one per thread in
 // the per-digit phase); 512 threads x 8 keys per CTA at <= 64 registers keep
 // two CTAs (32 warps) resident per SM.  Tile ids come from an atomic counter,
 // so every tile a CTA waits on is already running; each wait is bounded and
@@ -53,6 +54,7 @@ onesweep_kernel(const OnesweepArgs a) {
     unsigned long long *s_gbase = reinterpret_cast<unsigned long long *>(s_whist + kWarps * kBins);
     __shared__ uint32_t s_scan[kWarps];
     __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_dstart[kBins];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
@@ -89,25 +91,40 @@ onesweep_kernel(const OnesweepArgs a) {
         seg[k] = (HAS_SEG && valid) ? a.segs_in[e] : 0;
     }
 
-    // Ranking: lanes with equal digits find each other with one ballot per
-    // digit bit; the lowest such lane (leader) advances the warp's count.
+    // Ranking, four items at a time: the warp matches of the four are
+    // independent and issue back to back; then for each item the lowest lane
+    // of every equal-digit group (leader) advances the warp's count by the
+    // group size with one shared atomic (the __syncwarp orders the groups of
+    // consecutive items on the same counter), and the counts before the
+    // adds are broadcast to the groups last.
     uint32_t *my_hist = s_whist + warp * kBins;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const uint64_t e = wbase + k * 32 + lane;
-        const bool valid = e < n;
-        const unsigned active = __ballot_sync(kFull, valid);
-        const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-        const unsigned peers = match_digit(d, active);
-        const int leader = valid ? __ffs(peers) - 1 : lane;
-        uint32_t before = 0;
-        if (valid && lane == leader) {
-            before = my_hist[d];
-            my_hist[d] = before + __popc(peers);
+    for (int g = 0; g < kItems; g += 4) {
+        unsigned peers[4], before[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = g + q;
+            const bool valid = wbase + k * 32 + lane < n;
+            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
+            peers[q] = match_digit(d, __ballot_sync(kFull, valid));
         }
-        before = __shfl_sync(kFull, before, leader);
-        rank4[k >> 2] |= (before + __popc(peers & lanemask_lt())) << (8 * (k & 3));
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = g + q;
+            const bool valid = wbase + k * 32 + lane < n;
+            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
+            before[q] = 0;
+            if (valid && lane == __ffs(peers[q]) - 1) before[q] = atomicAdd(&my_hist[d], (unsigned)__popc(peers[q]));
+            __syncwarp();
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = g + q;
+            const bool valid = wbase + k * 32 + lane < n;
+            const int leader = valid ? __ffs(peers[q]) - 1 : lane;
+            const unsigned b = __shfl_sync(kFull, before[q], leader);
+            rank4[k >> 2] |= (b + __popc(peers[q] & lanemask_lt())) << (8 * (k & 3));
+        }
     }
     __syncthreads();
 
@@ -121,11 +138,30 @@ onesweep_kernel(const OnesweepArgs a) {
     }
     uint64_t *lb = a.lookback + tile * kBins;
     const uint32_t epoch = a.epoch;
+    // Publish this tile's count as early as possible: later tiles can sum
+    // past it before its global prefix is known.
+    st_relaxed(&lb[tid], lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, total));
+
+    // Tile-local digit starts and the shared-memory scatter need no global
+    // prefix, so they run before the look-back, which then overlaps with
+    // nothing but its own loads.
+    const uint32_t dstart = block_exclusive_scan(total, s_scan);
+    s_dstart[tid] = dstart;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const uint64_t e = wbase + k * 32 + lane;
+        if (e < n) {
+            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
+            const uint32_t p = my_hist[d] + s_dstart[d] + ((rank4[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+            s_keys[p] = key[k];
+            s_vals[p] = val[k];
+            if (HAS_SEG) s_segs[p] = seg[k];
+        }
+    }
+
     uint64_t prefix = 0;
-    if (tile == 0) {
-        st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, total));
-    } else {
-        st_relaxed(&lb[tid], lb_word(epoch, kLbAggregate, total));
+    if (tile > 0) {
         // Walk back over earlier tiles' words for digit tid, kLbBatch per
         // round trip: add aggregates until an inclusive prefix; stop at the
         // first word not yet written and poll it again.
@@ -161,24 +197,7 @@ onesweep_kernel(const OnesweepArgs a) {
         }
         st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, prefix + total));
     }
-
-    const uint32_t dstart = block_exclusive_scan(total, s_scan);
     s_gbase[tid] = a.bucket_base[tid] + prefix - dstart;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) s_whist[w * kBins + tid] += dstart;
-    __syncthreads();
-
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        const uint64_t e = wbase + k * 32 + lane;
-        if (e < n) {
-            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-            const uint32_t p = my_hist[d] + ((rank4[k >> 2] >> (8 * (k & 3))) & 0xFFu);
-            s_keys[p] = key[k];
-            s_vals[p] = val[k];
-            if (HAS_SEG) s_segs[p] = seg[k];
-        }
-    }
     __syncthreads();
 
     const int cnt = (int)umin64(kSortTile, n - tile_base);
