@@ -156,21 +156,32 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def profile_traffic(kernel_source: str, key: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_SOURCES = ["paper_2012_00866_gb300/csrc/sort.cu", "paper_2012_00866_gb300/csrc/hs_device.cuh",
+                   "paper_2012_00866_gb300/csrc/hs_internal.h"]
+
+
+def sources_digest(paths=TRAFFIC_SOURCES):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_traffic(key: str):
+    """DRAM bytes per launch (read + write, averaged over the step's launches
+    of the kernel) from the committed ncu summary profiles/traffic.json, if
+    the kernel's sources are unchanged since the capture (else None)."""
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             data = json.load(f)
-        with open(os.path.join(ROOT, kernel_source), "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+        digest = sources_digest()
     except OSError:
         return None
     entry = data.get(key)
-    if not entry or entry.get("source_sha256") != digest:
+    if not entry or entry.get("sources_sha256") != digest:
         return None
-    return entry.get("dram_bytes_per_launch_full")
+    return entry.get("dram_bytes_per_launch")
 
 
 # ---- our arm --------------------------------------------------------------------
@@ -299,7 +310,7 @@ def run_ours(args, rank, world, local):
                     "algo_bytes_per_launch": st["algo_bytes"] / st["launches"],
                     "launch_ms": round(st["total_ms"] / st["launches"], 5),
                     "share_of_step": round(st["total_ms"] / args.steps / ms, 3),
-                    "traffic": profile_traffic("paper_2012_00866_gb300/csrc/sort.cu", f"{top}/{args.workload}")}
+                    "traffic": profile_traffic(f"{top}/{args.workload}")}
 
     stages = {k: {"launches_per_step": v["launches"] / args.steps,
                   "ms_per_step": round(v["total_ms"] / args.steps, 4),

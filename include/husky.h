@@ -74,13 +74,15 @@ typedef enum {
 typedef enum { HS_CODER_AUTO = 0, HS_CODER_ASCII7 = 1, HS_CODER_BYTE8 = 2 } hs_coder;
 
 /* Sort strategies for Step 2; both give the identical permutation.
- *   HS_MODE_PLAIN    LSD radix sort of the 64-bit codes (8-bit digits,
+ *   HS_MODE_PLAIN    LSD radix sort of the 64-bit sort keys (9-bit digits,
  *                    digits constant over all keys skipped).
  *   HS_MODE_LEARNED  a learned CDF model (RMI: FP32 1->32->32->1 root,
- *                    linear leaves) trained on a sample of the codes picks a
- *                    monotone bucket per code; the pairs are partitioned by
- *                    bucket and each bucket sorted by code.  Falls back to
- *                    PLAIN internally when the buckets come out too uneven. */
+ *                    4096 linear leaves) trained on a 1% sample of the codes
+ *                    picks a monotone bucket per code; the pairs are
+ *                    partitioned by bucket and each bucket sorted by code;
+ *                    buckets over 4096 keys that hold different codes go
+ *                    through a segmented radix sort.  Runs as PLAIN when
+ *                    n < 65536 or when the strings need the BYTE8 coder. */
 typedef enum { HS_MODE_PLAIN = 0, HS_MODE_LEARNED = 1 } hs_mode;
 
 /* Index type of the output permutation. */

@@ -16,11 +16,13 @@
 // index order after a stable sort) or need the fix-up (bit 0 set).
 //
 // Layout: a CTA takes a tile of 1024 consecutive strings.  Their offsets are
-// loaded coalesced into shared memory; their bytes, which are contiguous,
-// are staged into shared memory with 16-byte vector loads when the tile's
-// byte range fits (the common case for words); otherwise each thread reads
-// its own string's first maxLength bytes from global memory.  The grid is a
-// multiple of the SM count and loops over tiles.
+// copied into shared memory and their bytes, which are contiguous, staged
+// there in aligned 16-byte pieces when the tile's byte range fits (the
+// common case for words), all with asynchronous copies that are in flight
+// together; otherwise each thread reads its own string's first maxLength
+// bytes from global memory.  A staged string's code is built from two
+// aligned words of the stage.  The grid is a multiple of the SM count and
+// loops over tiles.
 #include "hs_internal.h"
 
 namespace hs {
@@ -129,7 +131,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         const uint64_t t0 = tile * kEncTile;
         const int cnt = (int)umin64(kEncTile, n - t0);
         __syncthreads();
-        for (int i = tid; i <= cnt; i += kEncThreads) s_off[i] = offsets[t0 + i];
+        for (int i = tid; i <= cnt; i += kEncThreads) cp_async8(&s_off[i], offsets + t0 + i);
+        cp_async_wait_all();
         __syncthreads();
         // Offsets must be non-decreasing and end inside the byte buffer;
         // a tile that fails reads no bytes.
@@ -149,8 +152,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
             for (int c = tid; c < chunks; c += kEncThreads) {
                 const uintptr_t a = a0 + 16 * (uintptr_t)c;
                 if (a >= base && a + 16 <= base + total) {
-                    *reinterpret_cast<uint4 *>(s_bytes + 16 * c) =
-                        __ldg(reinterpret_cast<const uint4 *>(a));
+                    cp_async16(s_bytes + 16 * c, reinterpret_cast<const void *>(a));
                 } else {  // chunk straddles the buffer ends: bytewise
                     for (int b = 0; b < 16; ++b) {
                         const uintptr_t q = a + b;
@@ -160,6 +162,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                 }
             }
         }
+        cp_async_wait_all();
         __syncthreads();
 
 #pragma unroll

@@ -103,8 +103,10 @@ tie_detect_kernel(const TieArgs a) {
 
     for (int i = tid; i < kTieSlots; i += kTieThreads) {
         const uint64_t j = t0 + i;  // position t0 + i - 1
-        s_key[tie_slot(i)] = (j >= 1 && j - 1 < n) ? a.keys[j - 1] : 0;
+        const bool in = j >= 1 && j - 1 < n;
+        cp_async8(&s_key[tie_slot(i)], in ? a.keys + (j - 1) : a.keys, in ? 8u : 0u);
     }
+    cp_async_wait_all();
     __syncthreads();
 
     const int i0 = tid * kTieItems;
