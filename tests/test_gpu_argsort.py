@@ -44,6 +44,36 @@ def test_encode_edge_strings(cuda_lib):
         assert exact == perfect
 
 
+@pytest.mark.parametrize("coder", [1, 2])
+def test_encode_staged_and_unstaged_tiles(cuda_lib, coder):
+    """Tiles of 1024 strings whose bytes fit the shared stage build each code
+    from two aligned shared words; tiles of long strings read each string
+    from global memory.  Alternate the two kinds tile by tile, with lengths
+    0..12 around the 8- and 9-char limits, NUL bytes, high bytes (BYTE8) and
+    a ragged last tile; codes, the all-exact flag and the argsort must equal
+    the oracle's."""
+    hs = cuda_lib
+    rng = np.random.default_rng(5 + coder)
+    top = 256 if coder == 2 else 128
+    strs = []
+    for t in range(12):
+        for _ in range(1024):
+            n_bytes = int(rng.integers(20, 70)) if t % 3 == 1 else int(rng.integers(0, 13))
+            b = rng.integers(0, top, size=n_bytes).astype(np.uint8)
+            if rng.random() < 0.3:
+                b = (97 + b % 26).astype(np.uint8)
+            strs.append(bytes(b))
+    strs += [b"x" * 9, b"y" * 8 + b"\x00", b""]
+    w = workloads.from_strings(strs)
+    data, off = to_device(w)
+    codes, exact, used = hs.encode(data, off, coder=coder)
+    want, _, perfect = oracle.encode(w.bytes, w.offsets, coder)
+    assert used == coder
+    assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
+    assert exact == perfect
+    assert_oracle_equal(w, hs.argsort_device(data, off, coder=coder))
+
+
 def test_encode_golden(cuda_lib):
     hs = cuda_lib
     rows = read_golden("husky_codes.txt")
