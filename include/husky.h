@@ -132,6 +132,32 @@ HS_API hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_of
                              uint64_t n, int coder, uint32_t *d_perm,
                              void *d_ws, size_t ws_bytes, void *stream);
 
+/* hs_argsort_host -- hs_argsort on strings and a permutation in HOST memory
+ * (the paper's setting: an array in the host's memory, sorted and returned
+ * there).  The paper has no GPU transfer step; this entry point owns it.
+ *   h_bytes, h_offsets  host (pinned for full speed; pageable works but the
+ *              copies then block the calling thread): the data model above,
+ *              with h_offsets[n] = total byte count.
+ *   h_perm     out, host, n entries of uint32 / uint64 as in hs_argsort.
+ *   d_ws       device workspace of hs_host_workspace_size(n, h_offsets[n],
+ *              mode, out_t) bytes: the hs_argsort workspace followed by
+ *              device copies of the bytes, the offsets and the permutation.
+ * The offsets and bytes are copied in chunks of whole 1024-string tiles on a
+ * second stream owned by the library; each chunk is encoded (Step 1) as soon
+ * as it has arrived, so the encoder runs under the transfer.  Steps 2-3 run
+ * on the device copies and the permutation is copied back into h_perm before
+ * the call returns.  Chunk boundaries with decreasing offsets are rejected
+ * (HS_ERR_INVALID_ARG) before any copy; the rest of the offsets are checked
+ * on the device as in hs_argsort.  h_bytes, h_offsets and h_perm must not be
+ * device memory (HS_ERR_INVALID_ARG). */
+HS_API hs_status hs_argsort_host(const uint8_t *h_bytes, const uint64_t *h_offsets,
+                                 uint64_t n, int mode, int coder, int out_t,
+                                 void *h_perm, void *d_ws, size_t ws_bytes,
+                                 void *stream);
+/* Workspace needed by hs_argsort_host for n strings of total_bytes bytes. */
+HS_API hs_status hs_host_workspace_size(uint64_t n, uint64_t total_bytes,
+                                        int mode, int out_t, size_t *out);
+
 /* hs_argsort_noalloc -- hs_argsort for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a deployment convenience.
  *

@@ -42,7 +42,8 @@ MAX_N = 0x7FFFFFFF
 # Every symbol include/husky.h declares (checked by the export test).
 EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
-           "hs_argsort_noalloc", "hs_last_error", "hs_version",
+           "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size",
+           "hs_last_error", "hs_version",
            "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile")
 
 NOALLOC_MAX_N = 262144
@@ -92,6 +93,10 @@ def load(path: str | None = None):
     lib.hs_rmi_sample_indices.argtypes = [u64, u64, vp, vp]
     lib.hs_learned_profile.restype = ci
     lib.hs_learned_profile.argtypes = [vp, vp, u64, ci, vp, vp, vp, vp, sz, vp]
+    lib.hs_argsort_host.restype = ci
+    lib.hs_argsort_host.argtypes = [vp, vp, u64, ci, ci, ci, vp, vp, sz, vp]
+    lib.hs_host_workspace_size.restype = ci
+    lib.hs_host_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
     lib.hs_argsort_noalloc.restype = ci
     lib.hs_argsort_noalloc.argtypes = [vp, vp, u64, ci, ci, vp, vp]
     lib.hs_stats_enable.restype = ci
@@ -125,6 +130,12 @@ def workspace_size(n: int, mode: int = MODE_PLAIN, out_t: int = U32,
                    total_bytes: int = 0) -> int:
     out = ctypes.c_size_t(0)
     _check(load().hs_workspace_size(n, total_bytes, mode, out_t, ctypes.byref(out)))
+    return int(out.value)
+
+
+def host_workspace_size(n: int, total_bytes: int, mode: int = MODE_PLAIN, out_t: int = U32) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().hs_host_workspace_size(n, total_bytes, mode, out_t, ctypes.byref(out)))
     return int(out.value)
 
 
@@ -208,18 +219,38 @@ def argsort(data: torch.Tensor, offsets: torch.Tensor, mode: int = MODE_PLAIN,
             device="cuda", stream=None) -> torch.Tensor:
     """Stable argsort of strings held in host or device tensors.
 
-    Host (CPU) inputs are copied to the device (non-blocking when pinned),
-    sorted there, and the permutation is copied back into host memory;
-    device inputs are sorted in place on the device."""
+    Device inputs are sorted on the device (hs_argsort) and the permutation
+    stays there.  Host inputs go through hs_argsort_host: the library copies
+    them in chunks (overlapped with the encoder), sorts on the device and
+    copies the permutation back into a pinned host tensor, which is
+    returned.  Pinned inputs give the full transfer speed."""
     if data.is_cuda and offsets.is_cuda:
         return argsort_device(data, offsets, mode, coder, index_u64, stream=stream)
-    d_data = data.to(device, non_blocking=True)
-    d_off = offsets.to(device, non_blocking=True)
-    perm = argsort_device(d_data, d_off, mode, coder, index_u64, stream=stream)
-    host = torch.empty(perm.shape, dtype=perm.dtype, pin_memory=True)
-    host.copy_(perm, non_blocking=True)
-    (stream or torch.cuda.current_stream()).synchronize()
-    return host
+    if data.is_cuda or offsets.is_cuda:
+        raise ValueError("bytes and offsets must both be on the host or both on the device")
+    if data.dtype != torch.uint8:
+        raise TypeError("bytes must be a uint8 tensor")
+    if offsets.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("offsets must be an int64/uint64 tensor")
+    data = data.contiguous()
+    offsets = offsets.contiguous()
+    n = offsets.numel() - 1
+    dt = torch.int64 if index_u64 else torch.int32
+    out = torch.empty(max(n, 0), dtype=dt, pin_memory=True)
+    if n <= 0:
+        return out
+    lib = load()
+    out_t = U64 if index_u64 else U32
+    total = int(offsets[-1])
+    if total > data.numel():
+        raise ValueError("offsets[n] exceeds the byte buffer")
+    dev = torch.device(device)
+    with torch.cuda.device(dev):
+        nbytes = host_workspace_size(n, total, mode, out_t)
+        ws = workspace(nbytes, dev)
+        _check(lib.hs_argsort_host(_ptr(data), _ptr(offsets), n, mode, coder, out_t, _ptr(out),
+                                   _ptr(ws), nbytes, _stream_handle(stream)))
+    return out
 
 
 def argsort_batched(data: torch.Tensor, offsets: torch.Tensor,

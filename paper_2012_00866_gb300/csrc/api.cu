@@ -101,6 +101,8 @@ struct Layout {
     size_t model, samp_keys_a, samp_keys_b, samp_vals_a, samp_vals_b, samp_X, samp_x, samp_t;
     size_t b_first, b_last, q_over, over_base, keys_extra, big_mixed, q_mixed, mixed_base;
     uint64_t cap_over;
+    // hs_argsort_host only: device copies of the host inputs and output
+    size_t dev_bytes, dev_offsets, dev_perm;
     size_t total;
 };
 
@@ -165,6 +167,73 @@ Layout make_layout(uint64_t n, bool learned = false) {
     return L;
 }
 
+// hs_argsort_host: the hs_argsort layout followed by device copies of the
+// bytes (plus 16 bytes of slack), the offsets and the permutation.
+Layout make_host_layout(uint64_t n, uint64_t total_bytes, bool learned, size_t isz) {
+    Layout L = make_layout(n, learned);
+    Carver c{L.total};
+    L.dev_bytes = c.take(total_bytes + 16);
+    L.dev_offsets = c.take((n + 1) * 8);
+    L.dev_perm = c.take(n * isz);
+    L.total = c.off;
+    return L;
+}
+
+// Library-owned copy stream per device (non-blocking, created once) and a
+// pool of timing-free events for the chunk hand-offs.
+constexpr int kMaxDevices = 64;
+std::mutex g_copy_mu;
+cudaStream_t g_copy_stream[kMaxDevices] = {};
+std::vector<cudaEvent_t> g_sync_events;
+
+cudaError_t copy_stream(cudaStream_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(g_copy_mu);
+    if (!g_copy_stream[dev]) {
+        e = cudaStreamCreateWithFlags(&g_copy_stream[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *out = g_copy_stream[dev];
+    return cudaSuccess;
+}
+
+cudaError_t sync_event(cudaEvent_t *out) {
+    std::lock_guard<std::mutex> g(g_copy_mu);
+    if (!g_sync_events.empty()) {
+        *out = g_sync_events.back();
+        g_sync_events.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreateWithFlags(out, cudaEventDisableTiming);
+}
+
+void release_sync_events(std::vector<cudaEvent_t> &v) {
+    std::lock_guard<std::mutex> g(g_copy_mu);
+    for (cudaEvent_t e : v) g_sync_events.push_back(e);
+    v.clear();
+}
+
+// Host source of hs_argsort_host: where the inputs are and where their
+// device copies go.
+struct HostSrc {
+    const uint8_t *h_bytes;
+    const uint64_t *h_offsets;
+    uint8_t *d_bytes;
+    uint64_t *d_offsets;
+    uint64_t total;
+};
+
+// Strings per transfer chunk: whole 1024-string encoder tiles, about eight
+// chunks per call, at least 2^18 strings so small calls stay one chunk.
+uint64_t host_chunk(uint64_t n) {
+    uint64_t c = n / 8;
+    if (c < (1ull << 18)) c = 1ull << 18;
+    return (c + 1023) / 1024 * 1024;
+}
+
 int num_sms_cached() {
     static int sms = 0;
     if (sms == 0) {
@@ -186,6 +255,8 @@ struct Ctx {
     unsigned int *d_counters;
     int next_counter = 0;
     DevFlags h;  // last host copy of the flags
+    const HostSrc *host = nullptr;    // hs_argsort_host: inputs still on the host
+    std::vector<cudaEvent_t> events;  // chunk hand-off events in use
 
     template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(ws + off); }
 
@@ -249,7 +320,13 @@ struct Ctx {
         }
         pending.clear();
     }
-    ~Ctx() { flush_stats(); }
+    ~Ctx() {
+        flush_stats();
+        if (!events.empty()) {
+            cudaStreamSynchronize(s);  // the waits on them have been passed
+            release_sync_events(events);
+        }
+    }
 };
 
 #define HS_TRY(expr, where)                               \
@@ -275,13 +352,48 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         HS_TRY(cudaMemsetAsync(&c.d_flags->kmin, 0xFF, sizeof(unsigned long long), c.s), "memset kmin");
         c.next_counter = 0;
         const double enc_bytes = 8.0 * (n + 1) + 8.0 * n + (bits ? n / 8.0 : 0.0);
-        HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
-                   return launch_encode(u, sort_key && u == HS_CODER_ASCII7, bytes, offsets, n, codes,
-                                        u == HS_CODER_ASCII7 && sort_key ? nullptr : bits,
-                                        hist ? c.at<unsigned long long>(c.L.hist) : nullptr, c.d_flags, c.sms,
-                                        c.s);
-               }),
-               "encode");
+        const bool kflag = sort_key && u == HS_CODER_ASCII7;
+        uint32_t *ebits = kflag ? nullptr : bits;
+        unsigned long long *ehist = hist ? c.at<unsigned long long>(c.L.hist) : nullptr;
+        if (c.host && attempt == 0) {
+            // Inputs still on the host: copy them chunk by chunk on the
+            // library's copy stream and encode each chunk once it is in.
+            const HostSrc &h = *c.host;
+            cudaStream_t cs = nullptr;
+            HS_TRY(copy_stream(&cs), "copy stream");
+            cudaEvent_t start = nullptr;
+            HS_TRY(sync_event(&start), "event");
+            c.events.push_back(start);
+            HS_TRY(cudaEventRecord(start, c.s), "record start");  // after the caller's earlier work
+            HS_TRY(cudaStreamWaitEvent(cs, start, 0), "copy waits");
+            const uint64_t chunk = host_chunk(n);
+            for (uint64_t s0 = 0; s0 < n; s0 += chunk) {
+                const uint64_t s1 = umin64(n, s0 + chunk);
+                HS_TRY(cudaMemcpyAsync(h.d_offsets + s0, h.h_offsets + s0, (s1 - s0 + 1) * 8,
+                                       cudaMemcpyHostToDevice, cs),
+                       "copy offsets");
+                const uint64_t b0 = h.h_offsets[s0], b1 = h.h_offsets[s1];
+                if (b1 > b0)
+                    HS_TRY(cudaMemcpyAsync(h.d_bytes + b0, h.h_bytes + b0, b1 - b0, cudaMemcpyHostToDevice, cs),
+                           "copy bytes");
+                cudaEvent_t ev = nullptr;
+                HS_TRY(sync_event(&ev), "event");
+                c.events.push_back(ev);
+                HS_TRY(cudaEventRecord(ev, cs), "record chunk");
+                HS_TRY(cudaStreamWaitEvent(c.s, ev, 0), "encode waits");
+                const uint64_t m = s1 - s0;
+                HS_TRY(c.timed(kKEncode, enc_bytes * ((double)m / (double)n), [&] {
+                           return launch_encode(u, kflag, h.d_bytes, h.d_offsets + s0, m, codes + s0,
+                                                ebits ? ebits + s0 / 32 : nullptr, ehist, c.d_flags, c.sms, c.s);
+                       }),
+                       "encode chunk");
+            }
+        } else {
+            HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
+                       return launch_encode(u, kflag, bytes, offsets, n, codes, ebits, ehist, c.d_flags, c.sms, c.s);
+                   }),
+                   "encode");
+        }
         if (hist)
             HS_TRY(c.timed(kKPlan, 8.0 * kBins * 16, [&] {
                        return launch_plan(c.at<unsigned long long>(c.L.hist), kKeyPasses, n,
@@ -767,8 +879,9 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
     return device_error_status(c.h);
 }
 
-bool make_ctx(Ctx &c, void *ws, size_t ws_bytes, uint64_t n, void *stream, hs_status *st, bool learned = false) {
-    c.L = make_layout(n, learned);
+bool make_ctx(Ctx &c, void *ws, size_t ws_bytes, uint64_t n, void *stream, hs_status *st, bool learned = false,
+              const Layout *layout = nullptr) {
+    c.L = layout ? *layout : make_layout(n, learned);
     if (ws == nullptr || ws_bytes < c.L.total) {
         *st = fail(HS_ERR_WORKSPACE, "workspace missing or smaller than hs_workspace_size()");
         return false;
@@ -847,6 +960,74 @@ hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t
         if (st != HS_OK || !fallback) return st;
     }
     return argsort_plain(c, in, coder);
+}
+
+hs_status hs_host_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_t, size_t *out) {
+    g_last_error.clear();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    *out = make_host_layout(n, total_bytes, mode == HS_MODE_LEARNED, out_t == HS_U64 ? 8 : 4).total;
+    return HS_OK;
+}
+
+hs_status hs_argsort_host(const uint8_t *h_bytes, const uint64_t *h_offsets, uint64_t n, int mode, int coder,
+                          int out_t, void *h_perm, void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
+    if (n == 0) return HS_OK;
+    if (!h_bytes || !h_offsets || !h_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    for (const void *p : {(const void *)h_bytes, (const void *)h_offsets, (const void *)h_perm}) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();  // unregistered host memory on older runtimes
+            continue;
+        }
+        if (a.type == cudaMemoryTypeDevice) return fail(HS_ERR_INVALID_ARG, "hs_argsort_host needs host pointers");
+    }
+    // Chunk boundaries must not decrease (the copies are sized from them);
+    // every other offset is checked on the device.
+    const uint64_t total = h_offsets[n];
+    const uint64_t chunk = host_chunk(n);
+    uint64_t prev = h_offsets[0];
+    for (uint64_t s1 = chunk; ; s1 += chunk) {
+        const uint64_t b = h_offsets[umin64(s1, n)];
+        if (b < prev) return fail(HS_ERR_INVALID_ARG, "offsets are decreasing");
+        prev = b;
+        if (s1 >= n) break;
+    }
+    const bool learned = mode == HS_MODE_LEARNED;
+    const size_t isz = out_t == HS_U64 ? 8 : 4;
+    const Layout L = make_host_layout(n, total, learned, isz);
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st, learned, &L)) return st;
+    HostSrc hsrc{h_bytes, h_offsets, c.at<uint8_t>(L.dev_bytes), c.at<uint64_t>(L.dev_offsets), total};
+    void *d_perm = c.at<void>(L.dev_perm);
+    Input in{hsrc.d_bytes, hsrc.d_offsets, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
+    if (learned) {
+        // the learned path reads the inputs before and after its own encode:
+        // copy them whole first
+        HS_TRY(cudaMemcpyAsync(hsrc.d_offsets, h_offsets, (n + 1) * 8, cudaMemcpyHostToDevice, c.s), "copy offsets");
+        if (total > h_offsets[0])
+            HS_TRY(cudaMemcpyAsync(hsrc.d_bytes + h_offsets[0], h_bytes + h_offsets[0], total - h_offsets[0],
+                                   cudaMemcpyHostToDevice, c.s),
+                   "copy bytes");
+        bool fallback = false;
+        st = argsort_learned(c, in, coder, &fallback);
+        if (st == HS_OK && fallback) st = argsort_plain(c, in, coder);
+    } else {
+        c.host = &hsrc;
+        st = argsort_plain(c, in, coder);
+        c.host = nullptr;
+    }
+    if (st != HS_OK) return st;
+    HS_TRY(cudaMemcpyAsync(h_perm, d_perm, n * isz, cudaMemcpyDeviceToHost, c.s), "copy permutation");
+    HS_TRY(cudaStreamSynchronize(c.s), "final sync");
+    return HS_OK;
 }
 
 hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets, const uint64_t *d_seg_offsets,

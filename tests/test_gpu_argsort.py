@@ -224,6 +224,58 @@ def test_host_inputs_roundtrip(cuda_lib):
     assert_oracle_equal(w, perm)
 
 
+@pytest.mark.parametrize("case", ["pinned_u32", "pageable_u64", "learned", "byte8", "offset0"])
+def test_host_entry_point_chunks(cuda_lib, case):
+    """hs_argsort_host: inputs and output in host memory, copied in chunks of
+    whole tiles (1e6 strings = four chunks) with each chunk encoded as it
+    arrives; the permutation must equal the oracle's in every mode."""
+    hs = cuda_lib
+    import torch
+    kind = 5 if case in ("learned", "pageable_u64") else 2
+    w = workloads.generate(kind, 1_000_003, 70 + len(case))
+    if case == "byte8":   # a high byte late in the input: ASCII7 finds it, AUTO re-encodes
+        b = w.bytes.copy()
+        b[int(w.offsets[900_000])] = 0xE9
+        w = workloads.Workload(b, w.offsets)
+    if case == "offset0":  # string 0 starts past the buffer's first byte
+        b = np.concatenate([np.full(37, 0x41, np.uint8), w.bytes])
+        w = workloads.Workload(b, w.offsets + np.uint64(37))
+    data = torch.from_numpy(w.bytes)
+    off = torch.from_numpy(w.offsets.view(np.int64))
+    if case != "pageable_u64":
+        data, off = data.pin_memory(), off.pin_memory()
+    mode = hs.MODE_LEARNED if case == "learned" else hs.MODE_PLAIN
+    perm = hs.argsort(data, off, mode=mode, index_u64=case in ("pageable_u64", "learned"))
+    assert not perm.is_cuda
+    assert_oracle_equal(w, perm)
+
+
+def test_host_entry_point_rejects_bad_input(cuda_lib):
+    hs = cuda_lib
+    import ctypes
+    import torch
+    lib = hs.load()
+    n = 600_000      # three chunks of 262,144
+    w = workloads.generate(1, n, 3)
+    off = w.offsets.copy()
+    off[262_144] = off[262_144 * 2] + 1     # a chunk boundary moves backwards
+    data = torch.from_numpy(w.bytes).pin_memory()
+    bad = torch.from_numpy(off.view(np.int64)).pin_memory()
+    perm = torch.empty(n, dtype=torch.int32).pin_memory()
+    nbytes = hs.host_workspace_size(n, int(off[-1]))
+    ws = hs.workspace(nbytes, "cuda")
+    st = lib.hs_argsort_host(data.data_ptr(), bad.data_ptr(), n, 0, 0, 0, perm.data_ptr(),
+                             ws.data_ptr(), nbytes, None)
+    assert st == hs.ERR_INVALID_ARG
+    d_off = torch.from_numpy(w.offsets.view(np.int64)).cuda()
+    st = lib.hs_argsort_host(data.data_ptr(), d_off.data_ptr(), n, 0, 0, 0, perm.data_ptr(),
+                             ws.data_ptr(), nbytes, None)
+    assert st == hs.ERR_INVALID_ARG and b"host" in lib.hs_last_error()
+    st = lib.hs_argsort_host(data.data_ptr(), bad.data_ptr(), n, 0, 0, 0, perm.data_ptr(),
+                             ws.data_ptr(), 1024, None)
+    assert st in (hs.ERR_INVALID_ARG, hs.ERR_WORKSPACE)
+
+
 def test_repeated_calls_reuse_workspace(cuda_lib):
     hs = cuda_lib
     for seed in range(3):
