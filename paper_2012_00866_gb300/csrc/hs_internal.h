@@ -20,7 +20,9 @@ cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           DevFlags *flags, int num_sms, cudaStream_t s);
 
 // ---- sort.cu -------------------------------------------------------------
-constexpr int kSortTile = 4096;  // elements per onesweep tile
+constexpr int kSortThreads = 512;  // threads per onesweep CTA
+constexpr int kSortMinBlocks = 2;  // onesweep CTAs resident per SM (register budget)
+constexpr int kSortTile = 4096;    // elements per onesweep tile
 inline uint64_t sort_tiles(uint64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
 // Digit plan.  A 64-bit key has 8 digits: seven of 9 bits (bits 0..62) and

@@ -20,12 +20,21 @@
 namespace hs {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = kSortThreads;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = kSortTile / kThreads;  // 8
-constexpr int kLbBatch = 4;                   // look-back words loaded per round trip
+constexpr int kItems = kSortTile / kThreads;   // keys per thread
+constexpr int kDpt = kBins / kThreads;         // digits per thread in the per-digit phases
+constexpr int kMinBlocks = kSortMinBlocks;
+constexpr int kLbBatch = 4;                    // look-back words per digit per round trip
+// Per-item ranks among the warp's earlier items with the same digit are
+// below 32 * kItems; they are packed kRanksPerReg to a register.
+constexpr int kRankBits = 32 * kItems <= 256 ? 8 : 16;
+constexpr int kRanksPerReg = 32 / kRankBits;
+constexpr uint32_t kRankMask = (1u << kRankBits) - 1;
+static_assert(kDpt >= 1 && kDpt * kThreads == kBins, "digits must spread evenly over the threads");
+static_assert(kItems % 4 == 0 && kItems * kThreads == kSortTile, "tile must be whole groups of four items");
 
-// Exclusive scan of one u32 per thread over a 512-thread block.
+// Exclusive scan of one u32 per thread over the block.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -44,7 +53,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 }
 
 template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
 onesweep_kernel(const OnesweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
@@ -66,15 +75,14 @@ onesweep_kernel(const OnesweepArgs a) {
     const int shift = a.shift;
     const unsigned mask = a.mask;
 
-    // Warp-striped load: warp w owns elements [w*256, w*256+256) of the tile,
-    // item k of lane l is element w*256 + k*32 + l, so processing items in k
-    // order visits the warp's elements in input order (stability).
+    // Warp-striped load: warp w owns elements [w*32*kItems, (w+1)*32*kItems)
+    // of the tile, item k of lane l is element w*32*kItems + k*32 + l, so
+    // processing items in k order visits the warp's elements in input order
+    // (stability).
     uint64_t key[kItems];
     uint32_t val[kItems];
     uint32_t seg[kItems];
-    // Rank of item k among the warp's earlier items with the same digit:
-    // below 256 (a warp holds 256 items), so four ranks share a register.
-    uint32_t rank4[kItems / 4] = {};
+    uint32_t rankp[kItems / kRanksPerReg] = {};
     const uint64_t wbase = tile_base + (uint64_t)warp * 32 * kItems;
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
@@ -123,71 +131,117 @@ onesweep_kernel(const OnesweepArgs a) {
             const bool valid = wbase + k * 32 + lane < n;
             const int leader = valid ? __ffs(peers[q]) - 1 : lane;
             const unsigned b = __shfl_sync(kFull, before[q], leader);
-            rank4[k >> 2] |= (b + __popc(peers[q] & lanemask_lt())) << (8 * (k & 3));
+            rankp[k / kRanksPerReg] |= (b + __popc(peers[q] & lanemask_lt())) << (kRankBits * (k % kRanksPerReg));
         }
     }
     __syncthreads();
 
-    // Thread d: tile count of digit d, and exclusive per-warp offsets.
-    uint32_t total = 0;
+    // Thread t owns digits t*kDpt .. t*kDpt + kDpt - 1: their tile counts,
+    // and the exclusive per-warp offsets in place of the warp counts.
+    uint32_t total[kDpt];
+#pragma unroll
+    for (int j = 0; j < kDpt; ++j) total[j] = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_whist[w * kBins + tid];
-        s_whist[w * kBins + tid] = total;
-        total += c;
+        uint32_t *h = s_whist + w * kBins + tid * kDpt;
+        if (kDpt == 2) {
+            const uint2 c = *reinterpret_cast<const uint2 *>(h);
+            *reinterpret_cast<uint2 *>(h) = make_uint2(total[0], total[kDpt - 1]);
+            total[0] += c.x;
+            total[kDpt - 1] += c.y;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kDpt; ++j) {
+                const uint32_t c = h[j];
+                h[j] = total[j];
+                total[j] += c;
+            }
+        }
     }
     uint64_t *lb = a.lookback + tile * kBins;
     const uint32_t epoch = a.epoch;
-    // Publish this tile's count as early as possible: later tiles can sum
-    // past it before its global prefix is known.
-    st_relaxed(&lb[tid], lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, total));
+    // Publish this tile's counts as early as possible: later tiles can sum
+    // past them before its global prefix is known.
+#pragma unroll
+    for (int j = 0; j < kDpt; ++j)
+        st_relaxed(&lb[tid * kDpt + j], lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, total[j]));
 
     // Tile-local digit starts and the shared-memory scatter need no global
     // prefix, so they run before the look-back, which then overlaps with
     // nothing but its own loads.
-    const uint32_t dstart = block_exclusive_scan(total, s_scan);
-    s_dstart[tid] = dstart;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < kDpt; ++j) mine += total[j];
+    uint32_t dstart[kDpt];
+    dstart[0] = block_exclusive_scan(mine, s_scan);
+#pragma unroll
+    for (int j = 1; j < kDpt; ++j) dstart[j] = dstart[j - 1] + total[j - 1];
+#pragma unroll
+    for (int j = 0; j < kDpt; ++j) s_dstart[tid * kDpt + j] = dstart[j];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const uint64_t e = wbase + k * 32 + lane;
         if (e < n) {
             const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-            const uint32_t p = my_hist[d] + s_dstart[d] + ((rank4[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+            const uint32_t r = (rankp[k / kRanksPerReg] >> (kRankBits * (k % kRanksPerReg))) & kRankMask;
+            const uint32_t p = my_hist[d] + s_dstart[d] + r;
             s_keys[p] = key[k];
             s_vals[p] = val[k];
             if (HAS_SEG) s_segs[p] = seg[k];
         }
     }
 
-    uint64_t prefix = 0;
+    // Look-back for the thread's digits, walked together: per round trip
+    // kLbBatch earlier tiles' words per digit; add aggregates until an
+    // inclusive prefix; stop at the first word not yet written and poll it.
+    uint64_t prefix[kDpt];
+#pragma unroll
+    for (int j = 0; j < kDpt; ++j) prefix[j] = 0;
     if (tile > 0) {
-        // Walk back over earlier tiles' words for digit tid, kLbBatch per
-        // round trip: add aggregates until an inclusive prefix; stop at the
-        // first word not yet written and poll it again.
-        int64_t t = (int64_t)tile - 1;
+        int64_t t[kDpt];
+        bool done[kDpt];
+#pragma unroll
+        for (int j = 0; j < kDpt; ++j) {
+            t[j] = (int64_t)tile - 1;
+            done[j] = false;
+        }
         uint32_t spins = 0;
-        while (t >= 0) {
-            uint64_t v[kLbBatch];
+        while (true) {
+            bool all_done = true;
 #pragma unroll
-            for (int i = 0; i < kLbBatch; ++i)
-                v[i] = (t - i >= 0) ? ld_relaxed(&a.lookback[(uint64_t)(t - i) * kBins + tid]) : 0;
-            bool done = false, stalled = false;
-            int used = 0;
+            for (int j = 0; j < kDpt; ++j) all_done &= done[j];
+            if (all_done) break;
+            uint64_t v[kDpt][kLbBatch];
 #pragma unroll
-            for (int i = 0; i < kLbBatch; ++i) {
-                if (done || stalled || t - i < 0) continue;
-                if ((uint32_t)(v[i] >> 58) != epoch) {
-                    stalled = true;
-                    continue;
+            for (int j = 0; j < kDpt; ++j)
+#pragma unroll
+                for (int i = 0; i < kLbBatch; ++i)
+                    v[j][i] = (!done[j] && t[j] - i >= 0)
+                                  ? ld_relaxed(&a.lookback[(uint64_t)(t[j] - i) * kBins + tid * kDpt + j])
+                                  : 0;
+            bool progress = false;
+#pragma unroll
+            for (int j = 0; j < kDpt; ++j) {
+                if (done[j]) continue;
+                bool stalled = false, incl = false;
+                int used = 0;
+#pragma unroll
+                for (int i = 0; i < kLbBatch; ++i) {
+                    if (incl || stalled || t[j] - i < 0) continue;
+                    if ((uint32_t)(v[j][i] >> 58) != epoch) {
+                        stalled = true;
+                        continue;
+                    }
+                    prefix[j] += v[j][i] & kLbValueMask;
+                    used = i + 1;
+                    incl = (v[j][i] & (3ull << 56)) == kLbInclusive;
                 }
-                prefix += v[i] & kLbValueMask;
-                used = i + 1;
-                done = (v[i] & (3ull << 56)) == kLbInclusive;
+                t[j] -= used;
+                done[j] = incl || t[j] < 0;
+                progress |= used > 0;
             }
-            if (done) break;
-            t -= used;
-            if (used == 0) {
+            if (!progress) {
                 if (++spins > kSpinLimit) {
                     atomicOr(&a.flags->error, kErrTimeout);
                     break;
@@ -195,9 +249,13 @@ onesweep_kernel(const OnesweepArgs a) {
                 if (spins > 8) __nanosleep(32);
             }
         }
-        st_relaxed(&lb[tid], lb_word(epoch, kLbInclusive, prefix + total));
+#pragma unroll
+        for (int j = 0; j < kDpt; ++j)
+            st_relaxed(&lb[tid * kDpt + j], lb_word(epoch, kLbInclusive, prefix[j] + total[j]));
     }
-    s_gbase[tid] = a.bucket_base[tid] + prefix - dstart;
+#pragma unroll
+    for (int j = 0; j < kDpt; ++j)
+        s_gbase[tid * kDpt + j] = a.bucket_base[tid * kDpt + j] + prefix[j] - dstart[j];
     __syncthreads();
 
     const int cnt = (int)umin64(kSortTile, n - tile_base);
@@ -238,7 +296,7 @@ cudaError_t launch_os(const OnesweepArgs &a, cudaStream_t s) {
         configured = true;
     }
     const uint64_t tiles = sort_tiles(a.n);
-    kern<<<(unsigned)tiles, kThreads, smem, s>>>(a);
+    kern<<<(unsigned)tiles, kThreads, smem, s>>>(a);  // one CTA per tile
     return cudaGetLastError();
 }
 
