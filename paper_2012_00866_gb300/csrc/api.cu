@@ -37,12 +37,12 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves"};
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large"};
 
 struct StatsTable {
     std::mutex mu;
@@ -92,7 +92,7 @@ struct Layout {
     size_t control_end;
     size_t codes_a, codes_b, vals_a, vals_b, segs_a, segs_b, bits;
     size_t lb;
-    size_t q_small, q_medium, q_large_a, q_large_b, run_base;
+    size_t q_small, q_medium, q_large_a, q_large_b, run_base, large_diff;
     uint64_t cap_small, cap_medium, cap_large;
     // learned mode only
     bool learned;
@@ -140,6 +140,7 @@ Layout make_layout(uint64_t n, bool learned = false) {
     L.q_large_a = c.take(L.cap_large * sizeof(RunEntry));
     L.q_large_b = c.take(L.cap_large * sizeof(RunEntry));
     L.run_base = c.take((L.cap_large + 1) * 8);
+    L.large_diff = c.take(L.cap_large * 4);
     L.learned = learned && n >= kLearnedMinN;
     if (L.learned) {
         L.bucket_bits = learned_bits(n);
@@ -503,14 +504,32 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     HS_TRY(c.counter(&t.tile_counter), "counter");
     const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
     HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
+    // Runs of copies of one string are final already; only the others go on
+    // to refinement (queue B).
+    HS_TRY(cudaMemsetAsync(&c.d_flags->qcount[kQLargeB], 0, sizeof(unsigned long long), c.s), "memset q");
+    unsigned int *done2 = nullptr, *done2b = nullptr;
+    HS_TRY(c.counter(&done2), "counter");
+    HS_TRY(c.counter(&done2b), "counter");
+    if (done2b != done2 + 1) {  // the pair wrapped past the end of the counter block: take a fresh pair
+        HS_TRY(c.counter(&done2), "counter");
+        HS_TRY(c.counter(&done2b), "counter");
+    }
+    HS_TRY(c.timed(kKDistinctLarge, 0.0, [&] {
+               return launch_distinct_large(in.bytes, in.offsets, in.perm, in.perm_u64, q_large[0],
+                                            &c.d_flags->qcount[kQLargeA], c.L.cap_large, n, inst, in.prefix_len,
+                                            c.at<uint32_t>(c.L.large_diff), run_base, q_large[1],
+                                            &c.d_flags->qcount[kQLargeB], c.L.cap_large, c.d_flags, done2, c.sms,
+                                            c.s);
+           }),
+           "distinct large runs");
     HS_TRY(c.read_flags(), "tie sync");
     hs_status st = device_error_status(c.h);
     if (st != HS_OK) return st;
 
     // Large runs: refine 7 bytes per round until every run is constant-and-
     // resolved or has been split into CTA / warp sized pieces.
-    int li = 0;
-    uint64_t large = c.h.qcount[kQLargeA];
+    int li = 1;
+    uint64_t large = c.h.qcount[kQLargeB];
     int rounds = 0;
     while (large > 0) {
         if (++rounds > (1 << 26)) return fail(HS_ERR_INTERNAL, "refinement did not terminate");

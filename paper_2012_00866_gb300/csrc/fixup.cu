@@ -290,6 +290,12 @@ small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict_
             len = offsets[base + idx + 1] - off;
         }
         const uint64_t o = window_offset(prefix_len, e.depth);
+        {
+            // copies of one string are already in index order: nothing to do
+            const uint64_t o0 = __shfl_sync(kFull, off, 0), l0 = __shfl_sync(kFull, len, 0);
+            const bool eq = !mine || equal_from(bytes + off, len, bytes + o0, l0, min(o, l0));
+            if (__all_sync(kFull, eq)) continue;
+        }
         uint32_t rank = 0;
         for (uint32_t m = 0; m < e.len; ++m) {
             const IdxT im = __shfl_sync(kFull, idx, m);
@@ -304,6 +310,126 @@ small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict_
         __syncwarp();
         if (mine) perm[e.start + rank] = idx;
         __syncwarp();
+    }
+}
+
+// ---- >2048: runs of copies of one string ------------------------------------
+// A run whose members are all the same string is already in index order
+// (the stable sort kept input order), so it needs no refinement.  Two
+// launches with fixed grids, every count read on the device:
+//   sample  CTA per run: 64 members spread over the run against the first;
+//           a difference (or a malformed entry, left for the later checks)
+//           marks the run distinct.  The last CTA to finish computes the
+//           exclusive sum of the lengths of the unmarked runs;
+//   full    every member of those runs, flattened over the grid, against its
+//           run's first member.  The last CTA to finish copies the distinct
+//           runs to q_out.
+// "Last CTA" is the usual fence-and-count hand-off: no CTA waits on another.
+
+template <typename IdxT>
+__device__ __forceinline__ bool member_equals_first(const uint8_t *bytes, const uint64_t *offsets,
+                                                    const IdxT *perm, const RunEntry &e, uint64_t base,
+                                                    uint64_t j, int prefix_len) {
+    const uint64_t g0 = base + perm[e.start];
+    const uint64_t o0 = offsets[g0], l0 = offsets[g0 + 1] - o0;
+    const uint64_t g = base + perm[e.start + j];
+    const uint64_t off = offsets[g];
+    return equal_from(bytes + off, offsets[g + 1] - off, bytes + o0, l0, min(window_offset(prefix_len, e.depth), l0));
+}
+
+__device__ __forceinline__ bool odd_run(const RunEntry &e, uint64_t perm_n) {
+    return e.len < 2 || e.start >= perm_n || e.len > perm_n - e.start;
+}
+
+// True in every thread of the CTA that finishes last among gridDim.x.
+__device__ __forceinline__ bool last_cta(unsigned int *done) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    const bool last = s_last != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(256)
+distinct_sample_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                       const IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
+                       const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
+                       Instances inst, int prefix_len, uint32_t *diff, unsigned long long *base,
+                       unsigned int *done) {
+    __shared__ unsigned long long s_warp[8];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t count = umin64(*qcount, cap);
+    for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
+        const RunEntry e = q[r];
+        bool d = odd_run(e, perm_n);  // uniform over the CTA
+        if (!d && tid < 64) {
+            const uint64_t j = (uint64_t)tid * (e.len - 1) / 63;
+            d = !member_equals_first(bytes, offsets, perm, e, instance_base(inst, e.start), j, prefix_len);
+        }
+        d = __syncthreads_or(d);
+        if (tid == 0) diff[r] = d ? 1u : 0u;
+    }
+    if (!last_cta(done)) return;
+    // exclusive sum of the unmarked runs' lengths; base[count] = total
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (uint64_t b0 = 0; b0 < count; b0 += blockDim.x) {
+        const uint64_t r = b0 + tid;
+        const unsigned long long v = (r < count && !((volatile uint32_t *)diff)[r]) ? q[r].len : 0;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned long long wsum = 0;
+        for (int w = 0; w < warp; ++w) wsum += s_warp[w];
+        const unsigned long long carry = s_carry;
+        if (r < count) base[r] = carry + wsum + x - v;
+        __syncthreads();
+        if (tid == blockDim.x - 1) s_carry = carry + wsum + x;
+        __syncthreads();
+    }
+    if (tid == 0) base[count] = s_carry;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(256)
+distinct_full_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                     const IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
+                     const unsigned long long *__restrict__ qcount, uint64_t cap, Instances inst, int prefix_len,
+                     const unsigned long long *__restrict__ base, uint32_t *diff, RunEntry *__restrict__ q_out,
+                     unsigned long long *qcount_out, uint64_t cap_out, DevFlags *flags, unsigned int *done) {
+    const uint64_t count = umin64(*qcount, cap);
+    const uint64_t total = base[count];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        // the last run whose range starts at or before i (empty ranges of
+        // marked runs share their successor's start and come before it)
+        uint64_t lo = 0, hi = count;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (base[mid] <= i) lo = mid; else hi = mid;
+        }
+        const RunEntry e = q[lo];
+        const uint64_t j = i - base[lo];
+        if (j >= e.len) continue;  // cannot happen for a consistent scan
+        if (!member_equals_first(bytes, offsets, perm, e, instance_base(inst, e.start), j, prefix_len))
+            diff[lo] = 1u;
+    }
+    if (!last_cta(done)) return;
+    for (uint64_t r = threadIdx.x; r < count; r += blockDim.x) {
+        if (!((volatile uint32_t *)diff)[r]) continue;
+        const unsigned long long k = atomicAdd(qcount_out, 1ull);
+        if (k < cap_out) q_out[k] = q[r];
+        else atomicOr(&flags->error, kErrInternal);
     }
 }
 
@@ -354,6 +480,20 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
                 s_key[j] = ~0ull;
             }
             s_segact[j] = (j == 0);
+        }
+        {
+            // copies of one string are already in index order: nothing to do
+            __syncthreads();
+            const uint64_t g0 = base + s_idx[0];
+            const uint64_t o0 = offsets[g0], l0 = offsets[g0 + 1] - o0;
+            const uint64_t from = min(window_offset(prefix_len, e.depth), l0);
+            bool eq = true;
+            for (int j = tid; j < len && eq; j += kMedThreads) {
+                const uint64_t g = base + s_idx[j];
+                const uint64_t off = offsets[g];
+                eq = equal_from(bytes + off, offsets[g + 1] - off, bytes + o0, l0, from);
+            }
+            if (__syncthreads_and(eq)) continue;
         }
         uint32_t depth = e.depth;
         for (;;) {
@@ -559,6 +699,29 @@ cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, voi
     else
         small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
                                                          qcount, cap, perm_n, inst, prefix_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_distinct_large(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                                  const RunEntry *q, const unsigned long long *qcount, uint64_t cap,
+                                  uint64_t perm_n, Instances inst, int prefix_len, uint32_t *diff,
+                                  unsigned long long *base, RunEntry *q_out, unsigned long long *qcount_out,
+                                  uint64_t cap_out, DevFlags *flags, unsigned int *done2, int num_sms,
+                                  cudaStream_t s) {
+    const unsigned grid = (unsigned)num_sms * 2;
+    if (perm_u64) {
+        distinct_sample_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint64_t *>(perm), q,
+                                                              qcount, cap, perm_n, inst, prefix_len, diff, base, done2);
+        distinct_full_kernel<uint64_t><<<grid * 4, 256, 0, s>>>(bytes, offsets, static_cast<const uint64_t *>(perm),
+                                                                q, qcount, cap, inst, prefix_len, base, diff, q_out,
+                                                                qcount_out, cap_out, flags, done2 + 1);
+    } else {
+        distinct_sample_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint32_t *>(perm), q,
+                                                              qcount, cap, perm_n, inst, prefix_len, diff, base, done2);
+        distinct_full_kernel<uint32_t><<<grid * 4, 256, 0, s>>>(bytes, offsets, static_cast<const uint32_t *>(perm),
+                                                                q, qcount, cap, inst, prefix_len, base, diff, q_out,
+                                                                qcount_out, cap_out, flags, done2 + 1);
+    }
     return cudaGetLastError();
 }
 

@@ -145,6 +145,16 @@ __device__ __forceinline__ uint64_t window_key(const uint8_t *s, uint64_t len,
 
 // Three-way unsigned-byte comparison of a and b starting at byte `from`
 // (both strings agree before it).
+// True iff strings (a, la) and (b, lb) are equal, given that they already
+// agree on their first `from` bytes (members of one run of equal keys).
+__device__ __forceinline__ bool equal_from(const uint8_t *a, uint64_t la, const uint8_t *b, uint64_t lb,
+                                           uint64_t from) {
+    if (la != lb) return false;
+    for (uint64_t i = from; i < la; ++i)
+        if (a[i] != b[i]) return false;
+    return true;
+}
+
 __device__ __forceinline__ int compare_from(const uint8_t *a, uint64_t la,
                                             const uint8_t *b, uint64_t lb,
                                             uint64_t from) {

@@ -155,6 +155,15 @@ cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets,
                               uint64_t perm_n, Instances inst, int prefix_len,
                               int num_sms, cudaStream_t s);
 
+// Large runs that are not all copies of one string, copied from q to q_out
+// (count in *qcount_out, which the caller zeroes).  diff (cap entries) and
+// base (cap + 1) are scratch; done2 points at two zeroed counters.
+cudaError_t launch_distinct_large(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                                  const RunEntry *q, const unsigned long long *qcount, uint64_t cap,
+                                  uint64_t perm_n, Instances inst, int prefix_len, uint32_t *diff,
+                                  unsigned long long *base, RunEntry *q_out, unsigned long long *qcount_out,
+                                  uint64_t cap_out, DevFlags *flags, unsigned int *done2, int num_sms,
+                                  cudaStream_t s);
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
                                void *perm, int perm_u64, const RunEntry *q,
                                const unsigned long long *qcount, uint64_t cap,

@@ -224,6 +224,33 @@ def test_host_inputs_roundtrip(cuda_lib):
     assert_oracle_equal(w, perm)
 
 
+@pytest.mark.parametrize("n_copies", [40, 3000, 70_001])
+@pytest.mark.parametrize("odd", ["none", "smaller", "greater", "longer", "shorter"])
+def test_runs_of_copies_with_one_odd_member(cuda_lib, n_copies, odd):
+    """Runs of copies of one long string are final after the code sort (the
+    copies stay in index order); a single member that differs after byte 9,
+    placed away from every sampled position, must still be found and
+    sorted.  Sizes cover the warp (<= 32), CTA (<= 2048) and large classes."""
+    hs = cuda_lib
+    base = b"abcdefghijklmnopqrstu"
+    strs = [base] * n_copies
+    j = (n_copies * 7) // 13 + 1
+    if odd == "smaller":
+        strs[j] = base[:15] + b"a" + base[16:]
+    elif odd == "greater":
+        strs[j] = base[:15] + b"z" + base[16:]
+    elif odd == "longer":
+        strs[j] = base + b"!"
+    elif odd == "shorter":
+        strs[j] = base[:-1]
+    rng = np.random.default_rng(n_copies)
+    strs += [bytes(rng.integers(97, 123, size=12).astype(np.uint8)) for _ in range(500)]
+    order = rng.permutation(len(strs))
+    w = workloads.from_strings([strs[i] for i in order])
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
 @pytest.mark.parametrize("case", ["pinned_u32", "pageable_u64", "learned", "byte8", "offset0"])
 def test_host_entry_point_chunks(cuda_lib, case):
     """hs_argsort_host: inputs and output in host memory, copied in chunks of
