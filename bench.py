@@ -248,23 +248,33 @@ def run_ours(args, rank, world, local):
     except Exception:
         uuid = None
     clocks = ClockSampler(uuid)
-    hs.stats_enable(True)
+
+    def timed_steps():
+        ms_list = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms_list.append(e0.elapsed_time(e1))
+        return ms_list
+
+    # the timed region: no per-kernel instrumentation
     clocks.start()
     barrier(world)
     torch.cuda.synchronize(device)
-    step_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    step_ms = timed_steps()
     torch.cuda.synchronize(device)
     barrier(world)
     clock_info = clocks.stop()
+    # the same steps again with per-kernel CUDA events (the stage breakdown
+    # and the roofline's launch durations), outside the timed region
+    hs.stats_enable(True)
+    timed_steps()
+    torch.cuda.synchronize(device)
     kstats = hs.stats_read()
     hs.stats_enable(False)
 

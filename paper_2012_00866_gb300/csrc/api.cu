@@ -37,12 +37,12 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large"};
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate"};
 
 struct StatsTable {
     std::mutex mu;
@@ -58,6 +58,7 @@ struct PendingStat {
     int kind;
     double bytes;
     cudaEvent_t a, b;
+    int launches;
 };
 
 cudaEvent_t pooled_event() {
@@ -294,9 +295,9 @@ struct Ctx {
     // Launch through f(), bracketed by events when timing is enabled.
     std::vector<PendingStat> pending;
     bool timing = false;
-    template <typename F> cudaError_t timed(int kind, double bytes, F f) {
+    template <typename F> cudaError_t timed(int kind, double bytes, F f, int launches = 1) {
         if (!timing) return f();
-        PendingStat p{kind, bytes, pooled_event(), pooled_event()};
+        PendingStat p{kind, bytes, pooled_event(), pooled_event(), launches};
         cudaEventRecord(p.a, s);
         cudaError_t e = f();
         cudaEventRecord(p.b, s);
@@ -312,7 +313,7 @@ struct Ctx {
         for (auto &p : pending) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && g_stats.enabled) {
-                g_stats.launches[p.kind] += 1;
+                g_stats.launches[p.kind] += p.launches;
                 g_stats.ms[p.kind] += ms;
                 g_stats.bytes[p.kind] += p.bytes;
             }
@@ -474,7 +475,11 @@ struct Input {
     int perm_u64;
 };
 
-hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst) {
+// Step 3 on the sorted keys.  When it returns HS_OK with *synced set, every
+// launch has finished and c.h holds the final flags.
+hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst,
+                    bool *synced = nullptr) {
+    if (synced) *synced = false;
     const uint64_t n = in.n;
     RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
     RunEntry *q_medium = c.at<RunEntry>(c.L.q_medium);
@@ -520,11 +525,40 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
                                             c.at<uint32_t>(c.L.large_diff), run_base, q_large[1],
                                             &c.d_flags->qcount[kQLargeB], c.L.cap_large, c.d_flags, done2, c.sms,
                                             c.s);
-           }),
+           }, 2),
            "distinct large runs");
-    HS_TRY(c.read_flags(), "tie sync");
-    hs_status st = device_error_status(c.h);
+    // The warp- and CTA-sized runs tie detection queued need nothing from
+    // the host: their kernels read the queue counts on the device.  Launch
+    // them now; refinement (if any) appends more, handled after it.
+    const double isz = in.perm_u64 ? 8.0 : 4.0;
+    auto launch_med_small = [&](uint64_t med0, uint64_t small0, bool known) -> hs_status {
+        const uint64_t med = c.h.qcount[kQMedium], sm = c.h.qcount[kQSmall];
+        if (!known || med > med0)
+            HS_TRY(c.timed(kKMediumRuns, known ? (double)(med - med0) * 16.0 * (2 * isz + 16.0) : 0.0, [&] {
+                       return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
+                                                 &c.d_flags->qcount[kQMedium], med0, c.L.cap_medium, n, inst,
+                                                 in.prefix_len, c.sms, c.s);
+                   }),
+                   "medium runs");
+        if (!known || sm > small0)
+            HS_TRY(c.timed(kKSmallRuns, known ? (double)(sm - small0) * (16.0 + 2.0 * (2 * isz + 16.0)) : 0.0, [&] {
+                       return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
+                                                &c.d_flags->qcount[kQSmall], small0, c.L.cap_small, n, inst,
+                                                in.prefix_len, c.sms, c.s);
+                   }),
+                   "small runs");
+        return HS_OK;
+    };
+    hs_status st = launch_med_small(0, 0, false);
     if (st != HS_OK) return st;
+    HS_TRY(c.read_flags(), "tie sync");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    const uint64_t med0 = c.h.qcount[kQMedium], small0 = c.h.qcount[kQSmall];
+    if (c.h.qcount[kQLargeB] == 0) {
+        if (synced) *synced = true;
+        return HS_OK;
+    }
 
     // Large runs: refine 7 bytes per round until every run is constant-and-
     // resolved or has been split into CTA / warp sized pieces.
@@ -603,22 +637,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
         li = next;
     }
 
-    const double isz = in.perm_u64 ? 8.0 : 4.0;
-    if (c.h.qcount[kQMedium])
-        HS_TRY(c.timed(kKMediumRuns, (double)c.h.qcount[kQMedium] * 16.0 * (2 * isz + 16.0), [&] {
-                   return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
-                                             &c.d_flags->qcount[kQMedium], c.L.cap_medium, n, inst,
-                                             in.prefix_len, c.sms, c.s);
-               }),
-               "medium runs");
-    if (c.h.qcount[kQSmall])
-        HS_TRY(c.timed(kKSmallRuns, (double)c.h.qcount[kQSmall] * (16.0 + 2.0 * (2 * isz + 16.0)), [&] {
-                   return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
-                                            &c.d_flags->qcount[kQSmall], c.L.cap_small, n, inst,
-                                            in.prefix_len, c.sms, c.s);
-               }),
-               "small runs");
-    return HS_OK;
+    return launch_med_small(med0, small0, true);
 }
 
 hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
@@ -657,11 +676,12 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
                         perm_mode, !perfect);
         if (st != HS_OK) return st;
     }
+    bool synced = false;
     if (!perfect) {
-        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag, Instances{nullptr, 0});
+        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag, Instances{nullptr, 0}, &synced);
         if (st != HS_OK) return st;
     }
-    HS_TRY(c.read_flags(), "final sync");
+    if (!synced) HS_TRY(c.read_flags(), "final sync");
     return device_error_status(c.h);
 }
 
@@ -710,8 +730,8 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     HS_TRY(c.timed(kKRmiSample, 16.0 * m, [&] { return launch_rmi_sample(b.keys[0], n, kRmiSeed, sb.keys[0], m, c.s); }),
            "rmi sample");
     HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
-    HS_TRY(launch_histogram(sb.keys[0], nullptr, m, hist, c.sms, c.s), "sample histogram");
-    HS_TRY(launch_plan(hist, kKeyPasses, m, bucket, c.d_flags, c.s), "sample plan");
+    HS_TRY(c.timed(kKHistogram, 0.0, [&] { return launch_histogram(sb.keys[0], nullptr, m, hist, c.sms, c.s); }), "sample histogram");
+    HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, kKeyPasses, m, bucket, c.d_flags, c.s); }), "sample plan");
     HS_TRY(c.read_flags(), "sample plan sync");
     int passes[kHistPasses], np = 0;
     for (int p = 0; p < kKeyPasses; ++p)
@@ -730,13 +750,13 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     HS_TRY(c.timed(kKRmiFit, 20.0 * m, [&] {
                return launch_rmi_train(sb.keys[sc], m, model, kmin, shift, c.at<uint32_t>(L.samp_X),
                                        c.at<float>(L.samp_x), c.at<float>(L.samp_t), kRmiSteps, kRmiLr, c.s);
-           }),
+           }, 2),
            "rmi train");
-    HS_TRY(c.timed(kKRmiTable, 0.0, [&] { return launch_rmi_table(model, c.s); }), "rmi table");
+    HS_TRY(c.timed(kKRmiTable, 0.0, [&] { return launch_rmi_table(model, c.s); }, 2), "rmi table");
     HS_TRY(c.timed(kKRmiLeaves, 12.0 * m, [&] {
                return launch_rmi_leaves(sb.keys[sc], c.at<uint32_t>(L.samp_X), c.at<float>(L.samp_x),
                                         c.at<float>(L.samp_t), m, model, c.s);
-           }),
+           }, 4),
            "rmi leaves");
 
     // buckets, then the stable partition by bucket digits
@@ -760,7 +780,7 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
                return launch_rmi_bucket(b.keys[0], n, model, bits, 0, b.segs[0], b.vals[0], hist, c.sms, c.s);
            }),
            "rmi bucket");
-    HS_TRY(launch_plan(hist, kHistPasses, n, bucket, c.d_flags, c.s), "bucket plan");
+    HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, kHistPasses, n, bucket, c.d_flags, c.s); }), "bucket plan");
     HS_TRY(c.read_flags(), "bucket plan sync");
     st = device_error_status(c.h);
     if (st != HS_OK) return st;
@@ -793,7 +813,7 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     RunEntry *q_mixed = c.at<RunEntry>(L.q_mixed);
     if (big > 0) {
         unsigned long long *bb = c.at<unsigned long long>(L.over_base);
-        HS_TRY(launch_run_scan(q_over, big, bb, c.s), "big scan");
+        HS_TRY(c.timed(kKRunScan, 0.0, [&] { return launch_run_scan(q_over, big, bb, c.s); }), "big scan");
         unsigned long long big_total = 0;
         HS_TRY(cudaMemcpyAsync(&big_total, bb + big, 8, cudaMemcpyDeviceToHost, c.s), "big total");
         HS_TRY(cudaStreamSynchronize(c.s), "big sync");
@@ -805,7 +825,7 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
                                              in.perm_u64, mixed, c.s);
                }),
                "big buckets");
-        HS_TRY(launch_collect_mixed(q_over, big, mixed, q_mixed, L.cap_over, c.d_flags, c.s), "collect mixed");
+        HS_TRY(c.timed(kKCollectMixed, 0.0, [&] { return launch_collect_mixed(q_over, big, mixed, q_mixed, L.cap_over, c.d_flags, c.s); }), "collect mixed");
         HS_TRY(c.read_flags(), "mixed sync");
         st = device_error_status(c.h);
         if (st != HS_OK) return st;
@@ -814,7 +834,7 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     if (over > 0) {
         q_over = q_mixed;
         unsigned long long *ob = c.at<unsigned long long>(L.mixed_base);
-        HS_TRY(launch_run_scan(q_over, over, ob, c.s), "overflow scan");
+        HS_TRY(c.timed(kKRunScan, 0.0, [&] { return launch_run_scan(q_over, over, ob, c.s); }), "overflow scan");
         unsigned long long total = 0;
         HS_TRY(cudaMemcpyAsync(&total, ob + over, 8, cudaMemcpyDeviceToHost, c.s), "overflow total");
         HS_TRY(cudaStreamSynchronize(c.s), "overflow sync");
@@ -828,8 +848,8 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
                }),
                "overflow gather");
         HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
-        HS_TRY(launch_histogram(ov.keys[0], ov.segs[0], total, hist, c.sms, c.s), "overflow histogram");
-        HS_TRY(launch_plan(hist, kHistPasses, total, bucket, c.d_flags, c.s), "overflow plan");
+        HS_TRY(c.timed(kKHistogram, 0.0, [&] { return launch_histogram(ov.keys[0], ov.segs[0], total, hist, c.sms, c.s); }), "overflow histogram");
+        HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, kHistPasses, total, bucket, c.d_flags, c.s); }), "overflow plan");
         HS_TRY(c.read_flags(), "overflow plan sync");
         np = 0;
         for (int p = 0; p < kHistPasses; ++p)
@@ -862,7 +882,7 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
     uint32_t *bits = c.at<uint32_t>(c.L.bits);
     c.lb_words = sort_tiles(n) * kBins;
     HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
-    HS_TRY(launch_validate_segments(seg_offsets, num_segs, n, c.d_flags, c.s), "validate segments");
+    HS_TRY(c.timed(kKValidate, 0.0, [&] { return launch_validate_segments(seg_offsets, num_segs, n, c.d_flags, c.s); }), "validate segments");
     HS_TRY(c.read_flags(), "validate sync");
     if (c.h.error & kErrOffsets) return fail(HS_ERR_INVALID_ARG, "seg_offsets must start at 0, not decrease, and end at n");
     int used = 0;
@@ -877,7 +897,7 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
                                       hist, c.d_flags, c.sms, c.s);
            }),
            "seg fill");
-    HS_TRY(launch_plan(hist, kHistPasses, n, c.at<unsigned long long>(c.L.bucket), c.d_flags, c.s), "plan");
+    HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, kHistPasses, n, c.at<unsigned long long>(c.L.bucket), c.d_flags, c.s); }), "plan");
     HS_TRY(c.read_flags(), "plan sync");
     st = device_error_status(c.h);
     if (st != HS_OK) return st;

@@ -271,13 +271,13 @@ template <typename IdxT>
 __global__ void __launch_bounds__(256)
 small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                   IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
-                  const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
+                  const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
                   Instances inst, int prefix_len) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t count = umin64(*qcount, cap);
-    for (uint64_t r = warp_id; r < count; r += nwarps) {
+    for (uint64_t r = first + warp_id; r < count; r += nwarps) {
         const RunEntry e = q[r];
         if (e.len > kSmallMax || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
         const bool mine = (uint32_t)lane < e.len;
@@ -449,7 +449,7 @@ template <typename IdxT>
 __global__ void __launch_bounds__(kMedThreads)
 medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
-                   const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
+                   const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
                    Instances inst, int prefix_len) {
     constexpr int CAP = kMediumMax;
     __shared__ uint64_t s_key[CAP];
@@ -462,7 +462,7 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
     const uint64_t count = umin64(*qcount, cap);
     const uint32_t cont_tag = (uint32_t)prefix_len + 8;
 
-    for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
+    for (uint64_t r = first + blockIdx.x; r < count; r += gridDim.x) {
         const RunEntry e = q[r];
         if (e.len > (uint32_t)CAP || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
         const int len = (int)e.len;
@@ -690,15 +690,15 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
 }
 
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
-                              const RunEntry *q, const unsigned long long *qcount, uint64_t cap, uint64_t perm_n,
-                              Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
+                              const RunEntry *q, const unsigned long long *qcount, uint64_t first, uint64_t cap,
+                              uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 8;
     if (perm_u64)
         small_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q,
-                                                         qcount, cap, perm_n, inst, prefix_len);
+                                                         qcount, first, cap, perm_n, inst, prefix_len);
     else
         small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
-                                                         qcount, cap, perm_n, inst, prefix_len);
+                                                         qcount, first, cap, perm_n, inst, prefix_len);
     return cudaGetLastError();
 }
 
@@ -726,15 +726,15 @@ cudaError_t launch_distinct_large(const uint8_t *bytes, const uint64_t *offsets,
 }
 
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
-                               const RunEntry *q, const unsigned long long *qcount, uint64_t cap,
+                               const RunEntry *q, const unsigned long long *qcount, uint64_t first, uint64_t cap,
                                uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
     const unsigned grid = (unsigned)num_sms * 2;
     if (perm_u64)
         medium_runs_kernel<uint64_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm),
-                                                                  q, qcount, cap, perm_n, inst, prefix_len);
+                                                                  q, qcount, first, cap, perm_n, inst, prefix_len);
     else
         medium_runs_kernel<uint32_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm),
-                                                                  q, qcount, cap, perm_n, inst, prefix_len);
+                                                                  q, qcount, first, cap, perm_n, inst, prefix_len);
     return cudaGetLastError();
 }
 

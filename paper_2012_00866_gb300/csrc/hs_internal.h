@@ -151,7 +151,7 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s);
 
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets,
                               void *perm, int perm_u64, const RunEntry *q,
-                              const unsigned long long *qcount, uint64_t cap,
+                              const unsigned long long *qcount, uint64_t first, uint64_t cap,
                               uint64_t perm_n, Instances inst, int prefix_len,
                               int num_sms, cudaStream_t s);
 
@@ -166,7 +166,7 @@ cudaError_t launch_distinct_large(const uint8_t *bytes, const uint64_t *offsets,
                                   cudaStream_t s);
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
                                void *perm, int perm_u64, const RunEntry *q,
-                               const unsigned long long *qcount, uint64_t cap,
+                               const unsigned long long *qcount, uint64_t first, uint64_t cap,
                                uint64_t perm_n, Instances inst, int prefix_len,
                                int num_sms, cudaStream_t s);
 
