@@ -59,6 +59,12 @@ def _load():
         lib.oracle_stable_argsort_batched.argtypes = [vp, vp, vp, u64, vp, ci]
         lib.oracle_check_sorted_batched.restype = ctypes.c_int64
         lib.oracle_check_sorted_batched.argtypes = [vp, vp, vp, u64, vp, ci]
+        lib.oracle_string_to_long_mapped.restype = u64
+        lib.oracle_string_to_long_mapped.argtypes = [vp, u64, ci, ci, vp]
+        lib.oracle_alpha_params.restype = ci
+        lib.oracle_alpha_params.argtypes = [vp, vp, u64, vp, vp, vp]
+        lib.oracle_encode_alpha.restype = ci
+        lib.oracle_encode_alpha.argtypes = [vp, vp, u64, vp, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -99,6 +105,35 @@ def encode(data: np.ndarray, offsets: np.ndarray, coder: int = CODER_ASCII7):
     _load().oracle_encode(_ptr(data), _ptr(offsets), n, coder, _ptr(codes),
                           _ptr(exact), ctypes.addressof(perfect))
     return codes, exact, bool(perfect.value)
+
+
+def alpha_params(data: np.ndarray, offsets: np.ndarray):
+    """Alphabet-rank coder parameters: (rank uint8[256], w, K, applies)."""
+    n = offsets.shape[0] - 1
+    rank = np.zeros(256, dtype=np.uint8)
+    w, k = ctypes.c_int(0), ctypes.c_int(0)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    rc = _load().oracle_alpha_params(_ptr(data), _ptr(offsets), n, _ptr(rank),
+                                     ctypes.addressof(w), ctypes.addressof(k))
+    return rank, w.value, k.value, rc == 0
+
+
+def encode_alpha(data: np.ndarray, offsets: np.ndarray):
+    """Alphabet-rank coder: (codes uint64[n], exact uint8[n], perfect, w, K),
+    or None when the alphabet needs more than 6 bits."""
+    n = offsets.shape[0] - 1
+    codes = np.empty(n, dtype=np.uint64)
+    exact = np.empty(n, dtype=np.uint8)
+    perfect, w, k = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    rc = _load().oracle_encode_alpha(_ptr(data), _ptr(offsets), n, _ptr(codes), _ptr(exact),
+                                     ctypes.addressof(perfect), ctypes.addressof(w),
+                                     ctypes.addressof(k))
+    if rc != 0:
+        return None
+    return codes, exact, bool(perfect.value), w.value, k.value
 
 
 def stable_argsort(data: np.ndarray, offsets: np.ndarray, index_u64: bool = False,

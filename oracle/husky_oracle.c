@@ -109,6 +109,91 @@ int oracle_encode(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
     return 0;
 }
 
+/* ---- alphabet-rank coder ------------------------------------------------
+ * The paper notes (Section 3.2, on perfect encodings) that case-independent
+ * English letters fit 5 bits and case-dependent ones 6 bits, so that more
+ * characters fit in a code.  This project's coder generalises that: every
+ * byte value that occurs in the string data gets its rank 1..s among them
+ * (0 stays the padding), packed by Algorithm 4 with bit_width
+ * w = ceil(log2(s + 1)) in place of the 7-bit mask.  Ranks keep byte order
+ * and the padding stays below every rank, so the code is order preserving.
+ * max_length K: the most characters whose sort key (K*w code bits plus the
+ * not-exact bit) needs no more 9-bit radix digits than K = 9 would, with
+ * K*w <= 63.  Defined for w <= 6 (s <= 63); a string is exactly represented
+ * iff its length is at most K (a NUL byte has a rank of its own). */
+
+/* Algorithm 4 with a character map in place of the mask. */
+uint64_t oracle_string_to_long_mapped(const uint8_t *s, uint64_t len, int max_length,
+                                      int bit_width, const uint8_t *map)
+{
+    uint64_t length = len < (uint64_t)max_length ? len : (uint64_t)max_length;
+    uint64_t padding = (uint64_t)max_length - length;
+    uint64_t result = 0;
+    for (uint64_t i = 0; i < length; i++)
+        result = (result << bit_width) | map[s[i]];
+    uint64_t shift = (uint64_t)bit_width * padding;
+    return shift >= 64 ? 0 : result << shift;
+}
+
+/* Alphabet of bytes[offsets[0] .. offsets[n]) and the coder parameters.
+ * rank_out[c] = rank of byte c (0 if absent).  Returns 0 when w <= 6, else 1
+ * (the coder does not apply; the outputs are still written). */
+int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
+                        uint8_t *rank_out, int *w_out, int *k_out)
+{
+    int present[256] = {0};
+    if (n > 0)
+        for (uint64_t q = offsets[0]; q < offsets[n]; q++)
+            present[bytes[q]] = 1;
+    int s = 0;
+    for (int c = 0; c < 256; c++) {
+        if (present[c])
+            s++;
+        rank_out[c] = present[c] ? (uint8_t)s : 0;
+    }
+    int w = 1;
+    while ((1 << w) < s + 1)
+        w++;
+    int digits9 = (9 * w + 1 + 8) / 9;           /* radix digits at K = 9 */
+    int k = 9;
+    while ((k + 1) * w <= 63 && ((k + 1) * w + 1 + 8) / 9 <= digits9)
+        k++;
+    *w_out = w;
+    *k_out = k;
+    return w <= 6 ? 0 : 1;
+}
+
+/* Encode with the alphabet-rank coder; returns 1 (nothing written) when it
+ * does not apply. */
+int oracle_encode_alpha(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
+                        uint64_t *codes_out, uint8_t *exact_out, int *perfect,
+                        int *w_out, int *k_out)
+{
+    uint8_t rank[256];
+    int w, k;
+    if (oracle_alpha_params(bytes, offsets, n, rank, &w, &k) != 0) {
+        *w_out = w;
+        *k_out = k;
+        return 1;
+    }
+    int is_perfect = 1;
+    for (uint64_t i = 0; i < n; i++) {
+        const uint8_t *str = bytes + offsets[i];
+        uint64_t len = offsets[i + 1] - offsets[i];
+        int ex = len <= (uint64_t)k;
+        if (!ex)
+            is_perfect = 0;
+        if (exact_out)
+            exact_out[i] = (uint8_t)ex;
+        codes_out[i] = oracle_string_to_long_mapped(str, len, k, w, rank);
+    }
+    if (perfect)
+        *perfect = is_perfect;
+    *w_out = w;
+    *k_out = k;
+    return 0;
+}
+
 /* Unsigned-byte lexicographic comparison; a proper prefix is smaller. */
 static int string_compare(const uint8_t *bytes, const uint64_t *offsets,
                           uint64_t i, uint64_t j)

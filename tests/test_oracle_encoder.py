@@ -107,3 +107,61 @@ def test_array_encoder_matches_scalar():
     codes, _, _ = oracle.encode(w.bytes, w.offsets, oracle.CODER_ASCII7)
     for i in range(0, 2000, 37):
         assert codes[i] == oracle.ascii_to_long(w.string(i))
+
+
+# ---- alphabet-rank coder -------------------------------------------------------
+
+@pytest.mark.parametrize("row", read_golden("alpha_codes.txt"))
+def test_alpha_hand_worked_codes(row):
+    strs = literal(row[0])
+    w_, k_ = int(row[1]), int(row[2])
+    want = [int(x, 16) for x in row[3].split()]
+    wl = workloads.from_strings(strs)
+    codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
+    assert (w, k) == (w_, k_)
+    got = [int(c) for c in codes][-len(want):]
+    assert got == want
+
+
+@pytest.mark.parametrize("s_count, w_, k_", [(1, 1, 17), (2, 2, 13), (3, 2, 13), (4, 3, 11), (7, 3, 11),
+                                             (8, 4, 11), (15, 4, 11), (16, 5, 10), (26, 5, 10), (31, 5, 10),
+                                             (32, 6, 10), (62, 6, 10), (63, 6, 10)])
+def test_alpha_width_and_length_table(s_count, w_, k_):
+    """Bit width and length for alphabets of s symbols, worked by hand from
+    the rule (w = ceil(log2(s + 1)); K the most chars within the 9-char digit
+    count); 64 symbols need 7 bits and the coder does not apply."""
+    wl = workloads.from_strings([bytes([40 + i]) for i in range(s_count)])
+    _, w, k, applies = oracle.alpha_params(wl.bytes, wl.offsets)
+    assert (w, k, applies) == (w_, k_, True)
+    wl = workloads.from_strings([bytes([40 + i]) for i in range(64)])
+    assert oracle.alpha_params(wl.bytes, wl.offsets)[3] is False
+
+
+@pytest.mark.parametrize("alphabet", [b"abcd", b"\x00\x01\x7f\x80", b"\x00A\x80\xff"])
+def test_alpha_order_property_pairwise(alphabet):
+    """Section 3.2's rule for the alphabet coder, over every string of length
+    0..3 on a 4-symbol alphabet (high bytes and NUL included): a < b implies
+    code(a) <= code(b), code(a) < code(b) implies a < b, and all these strings
+    (length <= K) get distinct codes."""
+    strs = [b""] + [bytes(t) for L in (1, 2, 3) for t in itertools.product(alphabet, repeat=L)]
+    wl = workloads.from_strings(strs)
+    codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
+    assert perfect and all(exact)
+    for i, a in enumerate(strs):
+        for j, b in enumerate(strs):
+            if a < b:
+                assert codes[i] < codes[j]
+    assert len(set(int(c) for c in codes)) == len(strs)
+
+
+def test_alpha_truncation_and_nul():
+    """Strings agreeing on the first K chars share a code and are not exact;
+    a NUL byte is a symbol of its own, so 'a' and 'a\\0' differ."""
+    strs = [b"abcdefghijk", b"abcdefghijz", b"abcdefghij", b"a", b"a\x00",
+            b"abcdefghijklmnopqrstuvwxyz"]          # 26 letters + NUL: w = 5, K = 10
+    wl = workloads.from_strings(strs)
+    codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
+    assert (w, k) == (5, 10)
+    assert codes[0] == codes[1] == codes[2]
+    assert list(exact) == [0, 0, 1, 1, 1, 0] and not perfect
+    assert codes[3] < codes[4]
