@@ -108,7 +108,7 @@ def encode(data: np.ndarray, offsets: np.ndarray, coder: int = CODER_ASCII7):
 
 
 def alpha_params(data: np.ndarray, offsets: np.ndarray):
-    """Alphabet-rank coder parameters: (rank uint8[256], w, K, applies)."""
+    """Byte-range coder parameters: (map uint8[256], w, K, applies)."""
     n = offsets.shape[0] - 1
     rank = np.zeros(256, dtype=np.uint8)
     w, k = ctypes.c_int(0), ctypes.c_int(0)
@@ -120,8 +120,8 @@ def alpha_params(data: np.ndarray, offsets: np.ndarray):
 
 
 def encode_alpha(data: np.ndarray, offsets: np.ndarray):
-    """Alphabet-rank coder: (codes uint64[n], exact uint8[n], perfect, w, K),
-    or None when the alphabet needs more than 6 bits."""
+    """Byte-range coder: (codes uint64[n], exact uint8[n], perfect, w, K), or
+    None when the byte range needs more than 6 bits."""
     n = offsets.shape[0] - 1
     codes = np.empty(n, dtype=np.uint64)
     exact = np.empty(n, dtype=np.uint8)

@@ -109,18 +109,19 @@ int oracle_encode(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
     return 0;
 }
 
-/* ---- alphabet-rank coder ------------------------------------------------
+/* ---- byte-range coder -------------------------------------------------------
  * The paper notes (Section 3.2, on perfect encodings) that case-independent
  * English letters fit 5 bits and case-dependent ones 6 bits, so that more
- * characters fit in a code.  This project's coder generalises that: every
- * byte value that occurs in the string data gets its rank 1..s among them
- * (0 stays the padding), packed by Algorithm 4 with bit_width
- * w = ceil(log2(s + 1)) in place of the 7-bit mask.  Ranks keep byte order
- * and the padding stays below every rank, so the code is order preserving.
+ * characters fit in a code.  This project's coder generalises that: with lo
+ * and hi the smallest and largest byte in the string data, byte c codes as
+ * c - lo + 1 (0 stays the padding), packed by Algorithm 4 with bit_width
+ * w = ceil(log2(hi - lo + 2)) in place of the 7-bit mask ('a'..'z': 26
+ * values, 5 bits; 'A'..'z': 58 values, 6 bits).  The map keeps byte order and
+ * the padding stays below every value, so the code is order preserving.
  * max_length K: the most characters whose sort key (K*w code bits plus the
  * not-exact bit) needs no more 9-bit radix digits than K = 9 would, with
- * K*w <= 63.  Defined for w <= 6 (s <= 63); a string is exactly represented
- * iff its length is at most K (a NUL byte has a rank of its own). */
+ * K*w <= 63.  Defined for w <= 6; a string is exactly represented iff its
+ * length is at most K (a NUL byte inside the range has a value of its own). */
 
 /* Algorithm 4 with a character map in place of the mask. */
 uint64_t oracle_string_to_long_mapped(const uint8_t *s, uint64_t len, int max_length,
@@ -135,24 +136,27 @@ uint64_t oracle_string_to_long_mapped(const uint8_t *s, uint64_t len, int max_le
     return shift >= 64 ? 0 : result << shift;
 }
 
-/* Alphabet of bytes[offsets[0] .. offsets[n]) and the coder parameters.
- * rank_out[c] = rank of byte c (0 if absent).  Returns 0 when w <= 6, else 1
- * (the coder does not apply; the outputs are still written). */
+/* Byte range of bytes[offsets[0] .. offsets[n]) and the coder parameters.
+ * map_out[c] = c - lo + 1 inside the range, 0 outside.  Returns 0 when
+ * w <= 6, else 1 (the coder does not apply; the outputs are still written). */
 int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
-                        uint8_t *rank_out, int *w_out, int *k_out)
+                        uint8_t *map_out, int *w_out, int *k_out)
 {
-    int present[256] = {0};
+    int lo = 255, hi = 0;
     if (n > 0)
-        for (uint64_t q = offsets[0]; q < offsets[n]; q++)
-            present[bytes[q]] = 1;
-    int s = 0;
-    for (int c = 0; c < 256; c++) {
-        if (present[c])
-            s++;
-        rank_out[c] = present[c] ? (uint8_t)s : 0;
-    }
+        for (uint64_t q = offsets[0]; q < offsets[n]; q++) {
+            if (bytes[q] < lo)
+                lo = bytes[q];
+            if (bytes[q] > hi)
+                hi = bytes[q];
+        }
+    if (hi < lo)  /* no bytes at all */
+        lo = hi = 0;
+    int span = hi - lo + 1;
+    for (int c = 0; c < 256; c++)
+        map_out[c] = (c >= lo && c <= hi) ? (uint8_t)(c - lo + 1) : 0;
     int w = 1;
-    while ((1 << w) < s + 1)
+    while ((1 << w) < span + 1)
         w++;
     int digits9 = (9 * w + 1 + 8) / 9;           /* radix digits at K = 9 */
     int k = 9;
@@ -163,15 +167,15 @@ int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t 
     return w <= 6 ? 0 : 1;
 }
 
-/* Encode with the alphabet-rank coder; returns 1 (nothing written) when it
- * does not apply. */
+/* Encode with the byte-range coder; returns 1 (nothing written) when it does
+ * not apply. */
 int oracle_encode_alpha(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
                         uint64_t *codes_out, uint8_t *exact_out, int *perfect,
                         int *w_out, int *k_out)
 {
-    uint8_t rank[256];
+    uint8_t map[256];
     int w, k;
-    if (oracle_alpha_params(bytes, offsets, n, rank, &w, &k) != 0) {
+    if (oracle_alpha_params(bytes, offsets, n, map, &w, &k) != 0) {
         *w_out = w;
         *k_out = k;
         return 1;
@@ -185,7 +189,7 @@ int oracle_encode_alpha(const uint8_t *bytes, const uint64_t *offsets, uint64_t 
             is_perfect = 0;
         if (exact_out)
             exact_out[i] = (uint8_t)ex;
-        codes_out[i] = oracle_string_to_long_mapped(str, len, k, w, rank);
+        codes_out[i] = oracle_string_to_long_mapped(str, len, k, w, map);
     }
     if (perfect)
         *perfect = is_perfect;

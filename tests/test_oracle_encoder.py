@@ -127,22 +127,26 @@ def test_alpha_hand_worked_codes(row):
                                              (8, 4, 11), (15, 4, 11), (16, 5, 10), (26, 5, 10), (31, 5, 10),
                                              (32, 6, 10), (62, 6, 10), (63, 6, 10)])
 def test_alpha_width_and_length_table(s_count, w_, k_):
-    """Bit width and length for alphabets of s symbols, worked by hand from
+    """Bit width and length for byte ranges of s values, worked by hand from
     the rule (w = ceil(log2(s + 1)); K the most chars within the 9-char digit
-    count); 64 symbols need 7 bits and the coder does not apply."""
-    wl = workloads.from_strings([bytes([40 + i]) for i in range(s_count)])
-    _, w, k, applies = oracle.alpha_params(wl.bytes, wl.offsets)
+    count); a range of 64 needs 7 bits and the coder does not apply.  Only
+    the two ends matter: the bytes in between need not occur."""
+    wl = workloads.from_strings([bytes([40]), bytes([40 + s_count - 1])])
+    m, w, k, applies = oracle.alpha_params(wl.bytes, wl.offsets)
     assert (w, k, applies) == (w_, k_, True)
-    wl = workloads.from_strings([bytes([40 + i]) for i in range(64)])
+    assert m[40] == 1 and m[40 + s_count - 1] == s_count and m[39] == 0
+    wl = workloads.from_strings([bytes([40]), bytes([40 + 63])])
     assert oracle.alpha_params(wl.bytes, wl.offsets)[3] is False
 
 
-@pytest.mark.parametrize("alphabet", [b"abcd", b"\x00\x01\x7f\x80", b"\x00A\x80\xff"])
+@pytest.mark.parametrize("alphabet", [b"abcd", b"\x00\x01\x02\x03", b"\x7e\x7f\x80\x81", b"\xfc\xfd\xfe\xff",
+                                      b"\x00\x10\x20\x30"])
 def test_alpha_order_property_pairwise(alphabet):
-    """Section 3.2's rule for the alphabet coder, over every string of length
-    0..3 on a 4-symbol alphabet (high bytes and NUL included): a < b implies
-    code(a) <= code(b), code(a) < code(b) implies a < b, and all these strings
-    (length <= K) get distinct codes."""
+    """Section 3.2's rule for the byte-range coder, over every string of
+    length 0..3 on a 4-symbol alphabet (NUL, the 0x7F/0x80 boundary and the
+    top bytes included, and one with gaps): a < b implies code(a) <= code(b),
+    code(a) < code(b) implies a < b, and all these strings (length <= K) get
+    distinct codes."""
     strs = [b""] + [bytes(t) for L in (1, 2, 3) for t in itertools.product(alphabet, repeat=L)]
     wl = workloads.from_strings(strs)
     codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
@@ -156,12 +160,22 @@ def test_alpha_order_property_pairwise(alphabet):
 
 def test_alpha_truncation_and_nul():
     """Strings agreeing on the first K chars share a code and are not exact;
-    a NUL byte is a symbol of its own, so 'a' and 'a\\0' differ."""
-    strs = [b"abcdefghijk", b"abcdefghijz", b"abcdefghij", b"a", b"a\x00",
-            b"abcdefghijklmnopqrstuvwxyz"]          # 26 letters + NUL: w = 5, K = 10
+    a NUL byte inside the range has a value of its own, so x and x + NUL
+    differ (unlike ASCII7, where they share a code)."""
+    strs = [b"abcdefghijk", b"abcdefghijz", b"abcdefghij", b"a", b"abcdefghijklmnopqrstuvwxyz"]
     wl = workloads.from_strings(strs)
     codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
     assert (w, k) == (5, 10)
     assert codes[0] == codes[1] == codes[2]
-    assert list(exact) == [0, 0, 1, 1, 1, 0] and not perfect
-    assert codes[3] < codes[4]
+    assert list(exact) == [0, 0, 1, 1, 0] and not perfect
+    strs = [b"\x05", b"\x05\x00", b"\x1f\x1f\x1f"]      # range 0x00..0x1f: 32 values, 6 bits
+    wl = workloads.from_strings(strs)
+    codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
+    assert (w, k) == (6, 10) and perfect
+    assert codes[0] < codes[1] < codes[2]
+    assert oracle.encode_alpha(*_ws([b"a", b"a\x00"])) is None   # 0x00..0x61 needs 7 bits
+
+
+def _ws(strs):
+    wl = workloads.from_strings(strs)
+    return wl.bytes, wl.offsets
