@@ -305,6 +305,11 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": int(n * (8 if index_u64 else 4)), "ms_per_step": round(e2e_t, 3)}
         del host_perm, h_data, h_off
 
+    coder_name = "auto"
+    if not batched:
+        _, _, used = hs.encode(data, off)
+        coder_name = "auto(" + {1: "ascii7", 2: "byte8", 3: "alpha"}.get(used, str(used)) + ")"
+
     peaks, peak_src = measured_peaks()
     launches = sum(v["launches"] for v in kstats.values())
     roofline = None
@@ -362,7 +367,7 @@ def run_ours(args, rank, world, local):
                        "instances": int(len(w.seg_offsets) - 1) if batched else 1,
                        "mode": ("loop" if loop else "batched") if batched else args.mode,
                        "index": "u32" if not index_u64 else "u64",
-                       "coder": "auto(ascii7)",
+                       "coder": coder_name,
                        "l2": "flushed by a 256 MiB write before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": e2e,

@@ -56,7 +56,8 @@ typedef enum {
     HS_OK = 0,
     HS_ERR_INVALID_ARG = -1,  /* bad pointer, size, enum, or offsets       */
     HS_ERR_CODER_DOMAIN = -2, /* ASCII7 coder given a byte >= 0x80 in the
-                                 first 9 bytes of a string                  */
+                                 first 9 bytes of a string, or the ALPHA
+                                 coder an alphabet of more than 63 bytes    */
     HS_ERR_OOM = -3,          /* host allocation failed                     */
     HS_ERR_CUDA = -4,         /* a CUDA runtime call failed                 */
     HS_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up         */
@@ -69,9 +70,20 @@ typedef enum {
  *                    Section 4.3).  Order preserving only on bytes < 0x80.
  *   HS_CODER_BYTE8   bitWidth 8, maxLength 8, no mask: order preserving on
  *                    all bytes (this library's coder for arbitrary bytes).
- *   HS_CODER_AUTO    ASCII7, re-encoding with BYTE8 when any string has a
- *                    byte >= 0x80 among its first 9 bytes. */
-typedef enum { HS_CODER_AUTO = 0, HS_CODER_ASCII7 = 1, HS_CODER_BYTE8 = 2 } hs_coder;
+ *   HS_CODER_ALPHA   alphabet-rank coder, generalising the 5-bit and 6-bit
+ *                    letter codings of Section 3.2: each byte value present
+ *                    in bytes[offsets[0] .. offsets[n]) codes as its rank
+ *                    1..s among them (0 is the padding), in
+ *                    w = ceil(log2(s + 1)) bits, for maxLength K = the most
+ *                    chars whose sort key (K*w + 1 bits) needs no more 9-bit
+ *                    radix digits than 9 chars do (K*w <= 63).  Lowercase
+ *                    text: w = 5, K = 10, a 51-bit key.  Order preserving on
+ *                    all bytes; exact iff length <= K.  Applies when s <= 63
+ *                    (w <= 6), else HS_ERR_CODER_DOMAIN.
+ *   HS_CODER_AUTO    ALPHA when it applies, else ASCII7, re-encoding with
+ *                    BYTE8 when any string has a byte >= 0x80 among its first
+ *                    9 bytes. */
+typedef enum { HS_CODER_AUTO = 0, HS_CODER_ASCII7 = 1, HS_CODER_BYTE8 = 2, HS_CODER_ALPHA = 3 } hs_coder;
 
 /* Sort strategies for Step 2; both give the identical permutation.
  *   HS_MODE_PLAIN    LSD radix sort of the 64-bit sort keys (9-bit digits,

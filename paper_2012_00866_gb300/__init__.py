@@ -31,7 +31,7 @@ ERR_TIMEOUT = -5
 ERR_INTERNAL = -6
 ERR_WORKSPACE = -7
 # hs_coder
-CODER_AUTO, CODER_ASCII7, CODER_BYTE8 = 0, 1, 2
+CODER_AUTO, CODER_ASCII7, CODER_BYTE8, CODER_ALPHA = 0, 1, 2, 3
 # hs_mode
 MODE_PLAIN, MODE_LEARNED = 0, 1
 # hs_index_t

@@ -37,12 +37,12 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate"};
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet"};
 
 struct StatsTable {
     std::mutex mu;
@@ -258,6 +258,7 @@ struct Ctx {
     int next_counter = 0;
     DevFlags h;  // last host copy of the flags
     const HostSrc *host = nullptr;    // hs_argsort_host: inputs still on the host
+    int alpha_k = 9;                  // chars the alphabet coder covered (its prefix length)
     std::vector<cudaEvent_t> events;  // chunk hand-off events in use
 
     template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(ws + off); }
@@ -348,18 +349,24 @@ hs_status device_error_status(const DevFlags &h) {
 // flags and *used the coder actually used.
 hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int coder,
                      uint64_t *codes, uint32_t *bits, bool hist, bool sort_key, int *used) {
-    int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : HS_CODER_ASCII7;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : (coder == HS_CODER_ASCII7 ? HS_CODER_ASCII7 : HS_CODER_ALPHA);
+    for (int attempt = 0; attempt < 3; ++attempt) {
         HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
         HS_TRY(cudaMemsetAsync(&c.d_flags->kmin, 0xFF, sizeof(unsigned long long), c.s), "memset kmin");
         c.next_counter = 0;
         const double enc_bytes = 8.0 * (n + 1) + 8.0 * n + (bits ? n / 8.0 : 0.0);
-        const bool kflag = sort_key && u == HS_CODER_ASCII7;
+        const bool kflag = sort_key && u != HS_CODER_BYTE8;
         uint32_t *ebits = kflag ? nullptr : bits;
         unsigned long long *ehist = hist ? c.at<unsigned long long>(c.L.hist) : nullptr;
-        if (c.host && attempt == 0) {
+        const bool from_host = c.host && attempt == 0;
+        // AUTO takes the byte-range coder only where it saves a radix pass
+        // over ASCII7 (w <= 5: a range of at most 31 values); asked for, up
+        // to 6 bits.
+        const int max_w = coder == HS_CODER_ALPHA ? 6 : 5;
+        if (from_host) {
             // Inputs still on the host: copy them chunk by chunk on the
-            // library's copy stream and encode each chunk once it is in.
+            // library's copy stream; each chunk is encoded (or, for the
+            // alphabet coder, scanned for its alphabet) once it is in.
             const HostSrc &h = *c.host;
             cudaStream_t cs = nullptr;
             HS_TRY(copy_stream(&cs), "copy stream");
@@ -384,18 +391,31 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
                 HS_TRY(cudaEventRecord(ev, cs), "record chunk");
                 HS_TRY(cudaStreamWaitEvent(c.s, ev, 0), "encode waits");
                 const uint64_t m = s1 - s0;
-                HS_TRY(c.timed(kKEncode, enc_bytes * ((double)m / (double)n), [&] {
-                           return launch_encode(u, kflag, h.d_bytes, h.d_offsets + s0, m, codes + s0,
-                                                ebits ? ebits + s0 / 32 : nullptr, ehist, c.d_flags, c.sms, c.s);
-                       }),
-                       "encode chunk");
+                if (u == HS_CODER_ALPHA) {
+                    HS_TRY(c.timed(kKAlphabet, (double)(b1 - b0), [&] {
+                               return launch_alphabet(h.d_bytes, h.d_offsets + s0, m, (1 << max_w) - 1, c.d_flags, c.sms, c.s);
+                           }),
+                           "alphabet chunk");
+                } else {
+                    HS_TRY(c.timed(kKEncode, enc_bytes * ((double)m / (double)n), [&] {
+                               return launch_encode(u, kflag, h.d_bytes, h.d_offsets + s0, m, codes + s0,
+                                                    ebits ? ebits + s0 / 32 : nullptr, ehist, c.d_flags, c.sms, c.s);
+                           }),
+                           "encode chunk");
+                }
             }
-        } else {
+        } else if (u == HS_CODER_ALPHA) {
+            HS_TRY(c.timed(kKAlphabet, 0.0, [&] {
+                       return launch_alphabet(bytes, offsets, n, (1 << max_w) - 1, c.d_flags, c.sms, c.s);
+                   }),
+                   "alphabet");
+        }
+        if (!from_host || u == HS_CODER_ALPHA)
             HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
-                       return launch_encode(u, kflag, bytes, offsets, n, codes, ebits, ehist, c.d_flags, c.sms, c.s);
+                       return launch_encode(u, kflag, bytes, offsets, n, codes, ebits, ehist, c.d_flags, c.sms, c.s,
+                                            max_w);
                    }),
                    "encode");
-        }
         if (hist)
             HS_TRY(c.timed(kKPlan, 8.0 * kBins * 16, [&] {
                        return launch_plan(c.at<unsigned long long>(c.L.hist), kKeyPasses, n,
@@ -405,16 +425,30 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         HS_TRY(c.read_flags(), "encode sync");
         hs_status st = device_error_status(c.h);
         if (st != HS_OK) return st;
+        if (u == HS_CODER_ALPHA) {
+            if ((int)c.h.alpha_w <= max_w) {
+                c.alpha_k = (int)c.h.alpha_k;
+                break;
+            }
+            if (coder == HS_CODER_ALPHA)
+                return fail(HS_ERR_CODER_DOMAIN, "byte-range coder: the strings span more than 63 byte values");
+            u = HS_CODER_ASCII7;  // the kernel encoded as ASCII7
+        }
         if (u == HS_CODER_ASCII7 && c.h.domain) {
             if (coder == HS_CODER_ASCII7)
                 return fail(HS_ERR_CODER_DOMAIN, "ASCII7 coder: a byte >= 0x80 among the first 9 bytes");
-            u = HS_CODER_BYTE8;  // AUTO: the byte coder is order preserving on all bytes
+            u = HS_CODER_BYTE8;  // the byte coder is order preserving on all bytes
             continue;
         }
         break;
     }
     *used = u;
     return HS_OK;
+}
+
+// Bytes of each string the sort key's code covers (the fix-up starts after).
+int coded_prefix(const Ctx &c, int used) {
+    return used == HS_CODER_BYTE8 ? 8 : (used == HS_CODER_ALPHA ? c.alpha_k : 9);
 }
 
 // Runs the active radix passes over (keys, vals) pairs.  Returns the index
@@ -651,12 +685,12 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
     int used = 0;
     hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used);
     if (st != HS_OK) return st;
-    in.prefix_len = used == HS_CODER_BYTE8 ? 8 : 9;
+    in.prefix_len = coded_prefix(c, used);
     // ASCII7: the sort key carries the not-exact bit, so the permutation is
     // final after the last pass and runs needing work are read off the keys.
     // BYTE8: the bit rides in the payload and tie detection writes the
     // permutation.
-    const bool key_flag = used == HS_CODER_ASCII7;
+    const bool key_flag = used != HS_CODER_BYTE8;
     const bool perfect = c.h.nonexact == 0;
     int passes[kKeyPasses], np = 0;
     for (int p = 0; p < kKeyPasses; ++p)
@@ -709,11 +743,11 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], c.at<uint32_t>(L.bits), false, true,
                               &used);
     if (st != HS_OK) return st;
-    if (used != HS_CODER_ASCII7) {
+    if (used == HS_CODER_BYTE8) {
         *fallback = true;
         return HS_OK;
     }
-    in.prefix_len = 9;
+    in.prefix_len = coded_prefix(c, used);
     const bool perfect = c.h.nonexact == 0;
     const uint64_t kmin = c.h.kmin, kmax = c.h.kmax;
     int shift = 0;
@@ -888,8 +922,8 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
     int used = 0;
     hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used);
     if (st != HS_OK) return st;
-    in.prefix_len = used == HS_CODER_BYTE8 ? 8 : 9;
-    const bool key_flag = used == HS_CODER_ASCII7;
+    in.prefix_len = coded_prefix(c, used);
+    const bool key_flag = used != HS_CODER_BYTE8;
     const bool perfect = c.h.nonexact == 0;
     unsigned long long *hist = c.at<unsigned long long>(c.L.hist);
     HS_TRY(c.timed(kKSegFill, 8.0 * n + 8.0 * n, [&] {
@@ -961,7 +995,7 @@ hs_status hs_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_
 hs_status hs_encode(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int coder, uint64_t *d_codes,
                     int *h_all_exact, int *h_coder_used, void *d_ws, size_t ws_bytes, void *stream) {
     g_last_error.clear();
-    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (!d_offsets || (n > 0 && !d_codes)) return fail(HS_ERR_INVALID_ARG, "null pointer");
     Ctx c;
     hs_status st;
@@ -984,7 +1018,7 @@ hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t
                      void *d_perm, void *d_ws, size_t ws_bytes, void *stream) {
     g_last_error.clear();
     if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
-    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
     if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
     if (n == 0) return HS_OK;
@@ -1014,7 +1048,7 @@ hs_status hs_argsort_host(const uint8_t *h_bytes, const uint64_t *h_offsets, uin
                           int out_t, void *h_perm, void *d_ws, size_t ws_bytes, void *stream) {
     g_last_error.clear();
     if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
-    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
     if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
     if (n == 0) return HS_OK;
@@ -1073,7 +1107,7 @@ hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets, 
                              uint64_t num_segs, uint64_t n, int coder, uint32_t *d_perm, void *d_ws,
                              size_t ws_bytes, void *stream) {
     g_last_error.clear();
-    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (num_segs > 0xFFFFFFFFull) return fail(HS_ERR_INVALID_ARG, "num_segs must fit 32 bits");
     if (n == 0) return HS_OK;
     if (num_segs == 0) return fail(HS_ERR_INVALID_ARG, "n > 0 strings but no instances");
@@ -1225,7 +1259,7 @@ hs_status noalloc_scratch(void **out) {
 extern "C" hs_status hs_argsort_noalloc(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int coder,
                                         int out_t, void *d_perm, void *stream) {
     g_last_error.clear();
-    if (coder < HS_CODER_AUTO || coder > HS_CODER_BYTE8) return fail(HS_ERR_INVALID_ARG, "bad coder");
+    if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
     if (n > HS_NOALLOC_MAX_N)
         return fail(HS_ERR_INVALID_ARG, "hs_argsort_noalloc: n exceeds HS_NOALLOC_MAX_N (262144 strings)");

@@ -34,12 +34,16 @@ constexpr int kEncItems = kEncTile / kEncThreads;
 constexpr int kEncStage = 28672;   // staged bytes per tile
 constexpr int kEncHistPasses = kKeyPasses;
 constexpr size_t kEncOffBytes = (((size_t)kEncTile + 1) * 8 + 15) & ~(size_t)15;  // keeps s_bytes 16-B aligned
-constexpr int kEncPad = 16;        // word reads of the last staged string may run 15 bytes past the stage
+constexpr int kEncPad = 32;        // word reads of the last staged string may run 23 bytes past the stage
 constexpr size_t kEncSmem = kEncOffBytes + kEncStage + kEncPad + (size_t)kEncHistPasses * kBins * 4;
 static_assert(kEncStage % 16 == 0, "staging buffer must keep 16-byte alignment");
 
 template <int CODER> struct CoderTraits;
 template <> struct CoderTraits<1> {   // ASCII7
+    static constexpr int K = 9, W = 7;
+    static constexpr unsigned MASK = 0x7F;
+};
+template <> struct CoderTraits<3> {   // alphabet coder when it does not apply: ASCII7
     static constexpr int K = 9, W = 7;
     static constexpr unsigned MASK = 0x7F;
 };
@@ -105,13 +109,93 @@ __device__ __forceinline__ void hist_add_full(uint32_t *hist, unsigned d) {
     }
 }
 
+// ---- byte range (coder 3) ----------------------------------------------------
+// The byte-range coder (this library's generalisation of the 5-bit and 6-bit
+// letter codings of Section 3.2) needs the smallest and largest byte of the
+// string data first: one streaming pass, four bytes per SIMD min/max, four
+// 16-byte pieces per thread in flight.  A thread whose own bytes already
+// span more than max_span values stops: the range is too wide for the coder
+// either way, and the reduced range still shows it.
+
+constexpr int kAlphaThreads = 256;
+
+__global__ void __launch_bounds__(kAlphaThreads)
+alphabet_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets, uint64_t n,
+                int max_span, DevFlags *flags) {
+    const uint64_t b0 = offsets[0], b1 = offsets[n];
+    uint32_t vmin = 0xFFFFFFFFu, vmax = 0;  // four byte lanes each
+    if (b1 > b0) {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(bytes) + b0, hi = reinterpret_cast<uintptr_t>(bytes) + b1;
+        const uintptr_t a0 = lo & ~uintptr_t(15);
+        const uint64_t chunks = (uint64_t)((hi - a0 + 15) >> 4);
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        constexpr int kPer = 4;
+        for (uint64_t c0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c0 < chunks; c0 += stride * kPer) {
+            uint4 v[kPer];
+            bool whole[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const uint64_t ch = c0 + u * stride;
+                const uintptr_t a = a0 + 16 * (uintptr_t)ch;
+                whole[u] = ch < chunks && a >= lo && a + 16 <= hi;
+                v[u] = whole[u] ? __ldg(reinterpret_cast<const uint4 *>(a)) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const uint64_t ch = c0 + u * stride;
+                if (whole[u]) {
+                    vmin = __vminu4(__vminu4(vmin, v[u].x), __vminu4(v[u].y, __vminu4(v[u].z, v[u].w)));
+                    vmax = __vmaxu4(__vmaxu4(vmax, v[u].x), __vmaxu4(v[u].y, __vmaxu4(v[u].z, v[u].w)));
+                } else if (ch < chunks) {  // the ragged ends: only the bytes inside [lo, hi)
+                    const uintptr_t a = a0 + 16 * (uintptr_t)ch;
+                    for (int b = 0; b < 16; ++b) {
+                        const uintptr_t q = a + b;
+                        if (q >= lo && q < hi) {
+                            const uint32_t c4 = *reinterpret_cast<const uint8_t *>(q) * 0x01010101u;
+                            vmin = __vminu4(vmin, c4);
+                            vmax = __vmaxu4(vmax, c4);
+                        }
+                    }
+                }
+            }
+            const uint32_t m2 = __vminu4(vmin, vmin >> 16), x2 = __vmaxu4(vmax, vmax >> 16);
+            const int span = (int)max(x2 & 0xFFu, (x2 >> 8) & 0xFFu) - (int)min(m2 & 0xFFu, (m2 >> 8) & 0xFFu) + 1;
+            if (span > max_span) break;
+        }
+    }
+    const uint32_t mn = __vminu4(vmin, vmin >> 16), mx = __vmaxu4(vmax, vmax >> 16);
+    const uint32_t mn1 = min(mn & 0xFFu, (mn >> 8) & 0xFFu), mx1 = max(mx & 0xFFu, (mx >> 8) & 0xFFu);
+    const uint32_t wmn = __reduce_min_sync(kFull, mn1), wmx = __reduce_max_sync(kFull, mx1);
+    if ((threadIdx.x & 31) == 0) {
+        if (wmn < 256u && 255u - wmn > 0u) atomicMax(&flags->alpha_lo_inv, 255u - wmn);
+        if (wmx > 0u) atomicMax(&flags->alpha_hi, wmx);
+    }
+}
+
+// Bytes of a little-endian word in code order (byte 0 most significant),
+// each a value below 2^w, packed into 8w bits: the stringToLong loop of
+// Algorithm 4 for eight chars at once (w = 7 is pack7x8 without the mask).
+__device__ __forceinline__ uint64_t pack_w(uint64_t x, int w) {
+    uint64_t t = __byte_perm((uint32_t)(x >> 32), 0, 0x0123) |
+                 ((uint64_t)__byte_perm((uint32_t)x, 0, 0x0123) << 32);   // byte swap
+    t = (t & 0x00FF00FF00FF00FFull) | ((t & 0xFF00FF00FF00FF00ull) >> (8 - w));
+    t = (t & 0x0000FFFF0000FFFFull) | ((t & 0xFFFF0000FFFF0000ull) >> (16 - 2 * w));
+    t = (t & 0x00000000FFFFFFFFull) | ((t & 0xFFFFFFFF00000000ull) >> (32 - 4 * w));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t sub_bytes(uint64_t x, uint32_t d4) {
+    return (uint64_t)__vsub4((uint32_t)x, d4) | ((uint64_t)__vsub4((uint32_t)(x >> 32), d4) << 32);
+}
+
 template <int CODER, bool KEYFLAG>
 __global__ void __launch_bounds__(kEncThreads)
 encode_kernel(const uint8_t *__restrict__ bytes,
               const uint64_t *__restrict__ offsets, uint64_t n,
               uint64_t *__restrict__ codes, uint32_t *__restrict__ nonexact_bits,
-              unsigned long long *__restrict__ hist, DevFlags *flags) {
+              unsigned long long *__restrict__ hist, DevFlags *flags, int alpha_max_w) {
     using C = CoderTraits<CODER>;
+    constexpr int CW = CODER == 3 ? 1 : CODER;  // word path: the coder itself, ASCII7 for coder 3
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_off = reinterpret_cast<uint64_t *>(smem);
     uint8_t *s_bytes = smem + kEncOffBytes;
@@ -123,6 +207,32 @@ encode_kernel(const uint8_t *__restrict__ bytes,
 
     if (hist)
         for (int i = tid; i < kEncHistPasses * kBins; i += kEncThreads) s_hist[i] = 0;
+
+    // Coder 3: byte c codes as c - lo + 1 over the data's byte range
+    // [lo, hi] (0 is the padding), w = ceil(log2(hi - lo + 2)) bits each,
+    // K = the most chars whose sort key (K*w + 1 bits) needs no more 9-bit
+    // digits than 9 chars do, with K*w <= 63.  Past alpha_max_w bits it is
+    // not applied and the kernel encodes as ASCII7.
+    int aw = 7, ak = 9;
+    bool alpha = false;
+    uint32_t alo4 = 0;
+    if (CODER == 3) {
+        int lo = 255 - (int)flags->alpha_lo_inv, hi = (int)flags->alpha_hi;
+        if (hi < lo) lo = hi = 0;  // no bytes at all
+        int w = 1;
+        while ((1 << w) < hi - lo + 2) ++w;
+        const int d9 = (9 * w + 1 + 8) / 9;
+        int k = 9;
+        while ((k + 1) * w <= 63 && ((k + 1) * w + 1 + 8) / 9 <= d9) ++k;
+        alpha = w <= alpha_max_w;
+        aw = w;
+        ak = k;
+        alo4 = (uint32_t)((lo - 1) & 0xFF) * 0x01010101u;
+        if (blockIdx.x == 0 && tid == 0) {
+            flags->alpha_w = (unsigned)w;
+            flags->alpha_k = (unsigned)k;
+        }
+    }
 
     bool any_nonexact = false, any_domain = false;
     uint64_t kmin = ~0ull, kmax = 0;
@@ -174,7 +284,30 @@ encode_kernel(const uint8_t *__restrict__ bytes,
             if (valid) {
                 const uint64_t off = s_off[j];
                 const uint64_t len = s_off[j + 1] - off;
-                if (staged) {
+                if (CODER == 3 && alpha) {
+                    const int m = (int)umin64(len, (uint64_t)ak);
+                    if (staged && ak <= 16) {
+                        // bytes q .. q+15 from the three aligned words at q & ~7,
+                        // minus (lo - 1) bytewise, bytes past m cleared, packed
+                        const uint32_t q = (uint32_t)(base + off - a0);
+                        const uint64_t *wp = reinterpret_cast<const uint64_t *>(s_bytes + (q & ~7u));
+                        const uint64_t x0 = wp[0], x1 = wp[1], x2 = wp[2];
+                        const int r = 8 * (int)(q & 7u);
+                        const uint64_t w0 = r ? (x0 >> r) | (x1 << (64 - r)) : x0;
+                        const uint64_t w1 = r ? (x1 >> r) | (x2 << (64 - r)) : x1;
+                        const uint64_t keep0 = m >= 8 ? ~0ull : ((1ull << (8 * m)) - 1);
+                        const uint64_t keep1 = m >= 16 ? ~0ull : (m > 8 ? ((1ull << (8 * (m - 8))) - 1) : 0ull);
+                        const uint64_t p0 = pack_w(sub_bytes(w0, alo4) & keep0, aw);
+                        const uint64_t p1 = pack_w(sub_bytes(w1, alo4) & keep1, aw);
+                        code = (p0 << (aw * (ak - 8))) | (p1 >> (aw * (16 - ak)));
+                    } else {
+                        const uint8_t *src = staged ? s_bytes + (uint32_t)(base + off - a0) : bytes + off;
+                        const unsigned lo1 = (alo4 & 0xFFu);
+                        for (int i = 0; i < m; ++i) code = (code << aw) | (uint64_t)((src[i] - lo1) & 0xFFu);
+                        code <<= aw * (ak - m);  // ak * aw <= 63
+                    }
+                    exact = len <= (uint64_t)ak;
+                } else if (staged) {
                     // the two aligned words holding bytes q .. q+15 of the stage
                     const uint32_t q = (uint32_t)(base + off - a0);
                     const uint64_t *wp = reinterpret_cast<const uint64_t *>(s_bytes + (q & ~7u));
@@ -183,7 +316,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                     const uint64_t w0 = r ? (lo >> r) | (hi << (64 - r)) : lo;
                     const unsigned b8 = (unsigned)(hi >> r) & 0xFFu;
                     bool dom;
-                    code = code_from_words<CODER>(w0, b8, len, exact, dom);
+                    code = code_from_words<CW>(w0, b8, len, exact, dom);
                     any_domain |= dom;
                 } else {
                     const int m = (int)umin64(len, C::K);
@@ -191,7 +324,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                     unsigned last = 0;
                     for (int i = 0; i < m; ++i) {
                         const unsigned c = src[i];
-                        if (CODER == 1) any_domain |= c >= 0x80u;
+                        if (CW == 1) any_domain |= c >= 0x80u;
                         code = (code << C::W) | (uint64_t)(c & C::MASK);
                         last = c;
                     }
@@ -246,7 +379,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
 template <int CODER, bool KEYFLAG>
 cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t *codes,
                        uint32_t *nonexact_bits, unsigned long long *hist, DevFlags *flags, unsigned grid,
-                       cudaStream_t s) {
+                       int alpha_max_w, cudaStream_t s) {
     auto kern = encode_kernel<CODER, KEYFLAG>;
     static bool configured = false;  // attribute is per function, idempotent
     if (!configured) {
@@ -254,7 +387,7 @@ cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    kern<<<grid, kEncThreads, kEncSmem, s>>>(bytes, offsets, n, codes, nonexact_bits, hist, flags);
+    kern<<<grid, kEncThreads, kEncSmem, s>>>(bytes, offsets, n, codes, nonexact_bits, hist, flags, alpha_max_w);
     return cudaGetLastError();
 }
 
@@ -263,16 +396,26 @@ cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n
 cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
-                          DevFlags *flags, int num_sms, cudaStream_t s) {
+                          DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w) {
     if (n == 0) return cudaSuccess;
     const uint64_t tiles = (n + kEncTile - 1) / kEncTile;
     const unsigned grid = (unsigned)umin64(tiles, (uint64_t)num_sms * 4);
     if (coder == 2) {
         if (key_flag) return cudaErrorInvalidValue;  // BYTE8 codes use all 64 bits
-        return launch_enc<2, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, s);
+        return launch_enc<2, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
     }
-    if (key_flag) return launch_enc<1, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, s);
-    return launch_enc<1, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, s);
+    if (coder == 3) {
+        if (key_flag) return launch_enc<3, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+        return launch_enc<3, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+    }
+    if (key_flag) return launch_enc<1, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+    return launch_enc<1, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+}
+
+cudaError_t launch_alphabet(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int max_span,
+                            DevFlags *flags, int num_sms, cudaStream_t s) {
+    alphabet_kernel<<<(unsigned)num_sms * 4, kAlphaThreads, 0, s>>>(bytes, offsets, n, max_span, flags);
+    return cudaGetLastError();
 }
 
 }  // namespace hs

@@ -28,7 +28,10 @@ struct DevFlags {
     unsigned long long qcount[8];   // run-queue lengths (see QueueId)
     unsigned long long kmin, kmax;  // range of the keys the encoder wrote (kmin preset to ~0)
     unsigned int active[16];        // plan: radix pass p is needed
-    unsigned int pad[4];
+    unsigned int alpha_lo_inv;      // byte-range coder: 255 - smallest byte of the strings (max-reduced)
+    unsigned int alpha_hi;          // byte-range coder: largest byte of the strings
+    unsigned int alpha_w, alpha_k;  // byte-range coder: bits per char and chars coded (written by the encoder)
+    unsigned int pad[8];
 };
 
 // Run queue entry: a run of equal keys at positions [start, start + len)

@@ -14,10 +14,18 @@ namespace hs {
 // key_flag (ASCII7 only), the sort key (code << 1) | not_exact; optionally
 // the non-exact bitmask (bit i of word i/32) and the 8 digit histograms of
 // what it wrote (8 x kBins u64, accumulated); sets flags.
+// coder 3 (byte range): values from flags->alpha_lo_inv / alpha_hi; writes
+// alpha_w / alpha_k and, when the range needs more than alpha_max_w bits,
+// encodes as ASCII7.
 cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
-                          DevFlags *flags, int num_sms, cudaStream_t s);
+                          DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w = 6);
+// Smallest / largest byte of bytes[offsets[0] .. offsets[n]) max-reduced into
+// flags->alpha_lo_inv (as 255 - min) and flags->alpha_hi; cut short once the
+// range is known to exceed max_span values.
+cudaError_t launch_alphabet(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int max_span,
+                            DevFlags *flags, int num_sms, cudaStream_t s);
 
 // ---- sort.cu -------------------------------------------------------------
 constexpr int kSortThreads = 512;  // threads per onesweep CTA

@@ -88,20 +88,31 @@ def test_encode_golden(cuda_lib):
 
 
 def test_ascii7_domain_error_and_auto(cuda_lib):
-    """ASCII7 rejects high bytes; AUTO takes the alphabet coder when the
-    alphabet is small (high bytes included) and BYTE8 when it is not."""
+    """ASCII7 rejects high bytes; AUTO takes the byte-range coder when the
+    strings span few byte values (high bytes or not) and falls back to BYTE8
+    when a high byte comes with a wide range."""
     hs = cuda_lib
-    w = workloads.from_strings([b"abc", b"\xc3\xa9t\xc3\xa9", b"ab\x80", b"zz"])
+    w = workloads.from_strings([b"abc", b"\xc3\xa9t\xc3\xa9", b"ab\x80", b"zz"])   # 0x61..0xc3: 7 bits
     data, off = to_device(w)
     with pytest.raises(hs.HuskyError) as e:
         hs.encode(data, off, coder=hs.CODER_ASCII7)
     assert e.value.status == hs.ERR_CODER_DOMAIN
     codes, _, used = hs.encode(data, off, coder=hs.CODER_AUTO)
+    assert used == hs.CODER_BYTE8
+    want, _, _ = oracle.encode(w.bytes, w.offsets, oracle.CODER_BYTE8)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+    # high bytes in a narrow range 0x80..0x9e (31 values, 5 bits): the range coder
+    rng = np.random.default_rng(3)
+    strs = [b"\x80", b"\x9e"] + [bytes(rng.integers(0x80, 0x9f, size=rng.integers(0, 14)).astype(np.uint8))
+                                for _ in range(5000)]
+    w = workloads.from_strings(strs)
+    data, off = to_device(w)
+    codes, _, used = hs.encode(data, off, coder=hs.CODER_AUTO)
     assert used == hs.CODER_ALPHA
     assert np.array_equal(codes.cpu().numpy().view(np.uint64), oracle.encode_alpha(w.bytes, w.offsets)[0])
     assert_oracle_equal(w, hs.argsort_device(data, off))
-    # 200 distinct bytes (many >= 0x80): the alphabet needs 8 bits
-    rng = np.random.default_rng(3)
+    # 200 byte values: the range needs 8 bits
     strs = [bytes([b]) * 3 for b in range(56, 256)] + \
            [bytes(rng.integers(56, 256, size=rng.integers(0, 14)).astype(np.uint8)) for _ in range(5000)]
     w = workloads.from_strings(strs)
@@ -118,23 +129,28 @@ def test_ascii7_domain_error_and_auto(cuda_lib):
 
 @pytest.mark.parametrize("kind", [1, 2, 3, 4, 5])
 def test_alpha_encode_matches_oracle(cuda_lib, kind):
-    """The alphabet coder against the oracle's: same w and K (the codes tell),
-    same codes and all-exact flag (lowercase workloads: w = 5, K = 10;
-    kind 3 over [0-9A-Za-z]: w = 6, K = 10)."""
+    """The byte-range coder against the oracle's: same codes and all-exact
+    flag on the lowercase workloads (w = 5, K = 10); kind 3 spans '0'..'z'
+    (75 values) and is refused."""
     hs = cuda_lib
     w = workloads.generate(kind, 300_001, 31 + kind)
     data, off = to_device(w)
+    if kind == 3:
+        with pytest.raises(hs.HuskyError) as e:
+            hs.encode(data, off, coder=hs.CODER_ALPHA)
+        assert e.value.status == hs.ERR_CODER_DOMAIN
+        assert oracle.encode_alpha(w.bytes, w.offsets) is None
+        return
     codes, exact, used = hs.encode(data, off, coder=hs.CODER_ALPHA)
     want, _, perfect, ww, kk = oracle.encode_alpha(w.bytes, w.offsets)
-    assert used == hs.CODER_ALPHA
-    assert (ww, kk) == ((6, 10) if kind == 3 else (5, 10))
+    assert used == hs.CODER_ALPHA and (ww, kk) == (5, 10)
     assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
     assert exact == perfect
 
 
 def test_alpha_edge_alphabets(cuda_lib):
-    """Tiny alphabets (w = 1..4: K up to 17), NUL bytes, empty strings, and the
-    argsort through them."""
+    """Narrow byte ranges (w = 1, K = 17 takes the bytewise path; w = 2, 4, 6),
+    NUL bytes, empty strings, and the argsort through them."""
     hs = cuda_lib
     cases = [[b"a" * k for k in range(0, 40)],
              [b"ab"[i % 2: i % 2 + 1] * (i % 23) for i in range(3000)],
