@@ -234,6 +234,13 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         }
     }
 
+    // Digits above the key's width are zero for every string: counted in
+    // bin 0 once per tile instead of per string (the byte-range coder's
+    // K*w + 1 bits; the other keys use all eight digits).
+    const int key_bits = (CODER == 3 && alpha) ? ak * aw + (KEYFLAG ? 1 : 0) : 64;
+    int hist_digits = kEncHistPasses;
+    while (hist_digits > 0 && digit_shift(hist_digits - 1) >= key_bits) --hist_digits;
+
     bool any_nonexact = false, any_domain = false;
     uint64_t kmin = ~0ull, kmax = 0;
     const uint64_t num_tiles = (n + kEncTile - 1) / kEncTile;
@@ -253,6 +260,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
             if (tid == 0) atomicOr(&flags->error, kErrOffsets);
             continue;
         }
+        if (hist && tid == 0)
+            for (int p = hist_digits; p < kEncHistPasses; ++p) atomicAdd(&s_hist[p * kBins], (uint32_t)cnt);
         const uint64_t lo = s_off[0], hi = s_off[cnt];
         const uintptr_t a0 = (base + lo) & ~uintptr_t(15);
         const uintptr_t a1 = (base + hi + 15) & ~uintptr_t(15);
@@ -341,11 +350,13 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                 if (k * kEncThreads + warp * 32 + 32 <= cnt) {
 #pragma unroll
                     for (int p = 0; p < kEncHistPasses; ++p)
-                        hist_add_full(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)));
+                        if (p < hist_digits)
+                            hist_add_full(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)));
                 } else {
 #pragma unroll
                     for (int p = 0; p < kEncHistPasses; ++p)
-                        hist_add(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)), valid);
+                        if (p < hist_digits)
+                            hist_add(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)), valid);
                 }
             }
             const unsigned ne = __ballot_sync(kFull, valid && !exact);
