@@ -348,7 +348,8 @@ hs_status device_error_status(const DevFlags &h) {
 // Step 1 into ctx buffers; resolves HS_CODER_AUTO.  On return ctx.h holds the
 // flags and *used the coder actually used.
 hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int coder,
-                     uint64_t *codes, uint32_t *bits, bool hist, bool sort_key, int *used) {
+                     uint64_t *codes, uint32_t *bits, bool hist, bool sort_key, int *used, int max_key_bits = 64,
+                     EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr}) {
     int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : (coder == HS_CODER_ASCII7 ? HS_CODER_ASCII7 : HS_CODER_ALPHA);
     for (int attempt = 0; attempt < 3; ++attempt) {
         HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
@@ -413,7 +414,7 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         if (!from_host || u == HS_CODER_ALPHA)
             HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
                        return launch_encode(u, kflag, bytes, offsets, n, codes, ebits, ehist, c.d_flags, c.sms, c.s,
-                                            max_w);
+                                            max_w, max_key_bits, pack);
                    }),
                    "encode");
         if (hist)
@@ -426,7 +427,8 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         hs_status st = device_error_status(c.h);
         if (st != HS_OK) return st;
         if (u == HS_CODER_ALPHA) {
-            if ((int)c.h.alpha_w <= max_w) {
+            // the encoder's own test: w within max_w and 9 chars within max_key_bits
+            if ((int)c.h.alpha_w <= max_w && 9 * (int)c.h.alpha_w + 1 <= max_key_bits) {
                 c.alpha_k = (int)c.h.alpha_k;
                 break;
             }
@@ -512,7 +514,7 @@ struct Input {
 // Step 3 on the sorted keys.  When it returns HS_OK with *synced set, every
 // launch has finished and c.h holds the final flags.
 hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst,
-                    bool *synced = nullptr) {
+                    bool *synced = nullptr, bool instance_in_key = false) {
     if (synced) *synced = false;
     const uint64_t n = in.n;
     RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
@@ -523,7 +525,9 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
 
     TieArgs t{};
     t.keys = b.keys[cur];
-    t.segs = inst.seg_offsets ? b.segs[cur] : nullptr;  // batched: runs end at instance boundaries
+    // batched: runs end at instance boundaries (implied by the key when the
+    // instance id is packed into it)
+    t.segs = (inst.seg_offsets && !instance_in_key) ? b.segs[cur] : nullptr;
     t.vals = b.vals[cur];
     t.n = n;
     t.prefix_len = in.prefix_len;
@@ -919,13 +923,43 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
     HS_TRY(c.timed(kKValidate, 0.0, [&] { return launch_validate_segments(seg_offsets, num_segs, n, c.d_flags, c.s); }), "validate segments");
     HS_TRY(c.read_flags(), "validate sync");
     if (c.h.error & kErrOffsets) return fail(HS_ERR_INVALID_ARG, "seg_offsets must start at 0, not decrease, and end at n");
+    // With the byte-range coder the key leaves room above it for the
+    // instance id: one key, no separate instance array in the radix passes.
+    int seg_bits = 1;
+    while (seg_bits < 63 && (1ull << seg_bits) < num_segs) ++seg_bits;
+    // the instance of every 1024-string tile's first string, for the encoder
+    uint32_t *tile_seg = b.segs[0];
+    HS_TRY(c.timed(kKSegFill, 0.0, [&] { return launch_tile_segs(seg_offsets, num_segs, n, tile_seg, c.s); }),
+           "tile instances");
     int used = 0;
-    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used);
+    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used, 64 - seg_bits,
+                              EncPack{seg_offsets, num_segs, seg_bits, b.vals[0], tile_seg});
     if (st != HS_OK) return st;
     in.prefix_len = coded_prefix(c, used);
     const bool key_flag = used != HS_CODER_BYTE8;
     const bool perfect = c.h.nonexact == 0;
     unsigned long long *hist = c.at<unsigned long long>(c.L.hist);
+    const Instances inst{seg_offsets, num_segs};
+    if (used == HS_CODER_ALPHA) {
+        // the encoder packed the instance ids, wrote the local indices and
+        // planned the passes over the packed keys
+        const int key_bits = (int)(c.h.alpha_k * c.h.alpha_w) + 1;
+        if (key_bits + seg_bits > 64) return fail(HS_ERR_INTERNAL, "packed batched key does not fit");
+        int passes[kKeyPasses], np = 0;
+        for (int p = 0; p < kKeyPasses; ++p)
+            if (c.h.active[p]) passes[np++] = p;
+        if (np == 0) passes[np++] = 0;  // a no-op pass still writes the permutation
+        int cur = 0;
+        st = run_passes(c, b, &cur, n, passes, np, false, nullptr, false, in.perm, kOutPerm32, !perfect);
+        if (st != HS_OK) return st;
+        bool synced = false;
+        if (!perfect) {
+            st = run_fixup(c, in, b, cur, kTieKeyFlag, inst, &synced, true);
+            if (st != HS_OK) return st;
+        }
+        if (!synced) HS_TRY(c.read_flags(), "final sync");
+        return device_error_status(c.h);
+    }
     HS_TRY(c.timed(kKSegFill, 8.0 * n + 8.0 * n, [&] {
                return launch_seg_fill(seg_offsets, num_segs, n, key_flag ? nullptr : bits, b.segs[0], b.vals[0],
                                       hist, c.d_flags, c.sms, c.s);
@@ -945,7 +979,7 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
                     !perfect);
     if (st != HS_OK) return st;
     if (!perfect) {
-        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag, Instances{seg_offsets, num_segs});
+        st = run_fixup(c, in, b, cur, key_flag ? kTieKeyFlag : kTieValFlag, inst);
         if (st != HS_OK) return st;
     }
     HS_TRY(c.read_flags(), "final sync");

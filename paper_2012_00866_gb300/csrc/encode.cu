@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(kEncThreads)
 encode_kernel(const uint8_t *__restrict__ bytes,
               const uint64_t *__restrict__ offsets, uint64_t n,
               uint64_t *__restrict__ codes, uint32_t *__restrict__ nonexact_bits,
-              unsigned long long *__restrict__ hist, DevFlags *flags, int alpha_max_w) {
+              unsigned long long *__restrict__ hist, DevFlags *flags, int alpha_max_w, int alpha_max_bits,
+              EncPack pk) {
     using C = CoderTraits<CODER>;
     constexpr int CW = CODER == 3 ? 1 : CODER;  // word path: the coder itself, ASCII7 for coder 3
     extern __shared__ __align__(16) unsigned char smem[];
@@ -211,8 +212,10 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     // Coder 3: byte c codes as c - lo + 1 over the data's byte range
     // [lo, hi] (0 is the padding), w = ceil(log2(hi - lo + 2)) bits each,
     // K = the most chars whose sort key (K*w + 1 bits) needs no more 9-bit
-    // digits than 9 chars do, with K*w <= 63.  Past alpha_max_w bits it is
-    // not applied and the kernel encodes as ASCII7.
+    // digits than 9 chars do, with K*w <= 63 and K*w + 1 <= alpha_max_bits
+    // (room the caller keeps above the key).  Past alpha_max_w bits, or when
+    // 9 chars do not fit alpha_max_bits, it is not applied and the kernel
+    // encodes as ASCII7.
     int aw = 7, ak = 9;
     bool alpha = false;
     uint32_t alo4 = 0;
@@ -223,8 +226,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         while ((1 << w) < hi - lo + 2) ++w;
         const int d9 = (9 * w + 1 + 8) / 9;
         int k = 9;
-        while ((k + 1) * w <= 63 && ((k + 1) * w + 1 + 8) / 9 <= d9) ++k;
-        alpha = w <= alpha_max_w;
+        while ((k + 1) * w <= 63 && ((k + 1) * w + 1 + 8) / 9 <= d9 && (k + 1) * w + 1 <= alpha_max_bits) ++k;
+        alpha = w <= alpha_max_w && 9 * w + 1 <= alpha_max_bits;
         aw = w;
         ak = k;
         alo4 = (uint32_t)((lo - 1) & 0xFF) * 0x01010101u;
@@ -237,11 +240,14 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     // Digits above the key's width are zero for every string: counted in
     // bin 0 once per tile instead of per string (the byte-range coder's
     // K*w + 1 bits; the other keys use all eight digits).
-    const int key_bits = (CODER == 3 && alpha) ? ak * aw + (KEYFLAG ? 1 : 0) : 64;
+    // Batched, byte-range coder: the instance id goes above the code.
+    const bool pack = CODER == 3 && alpha && pk.seg_offsets != nullptr;
+    const int code_bits = (CODER == 3 && alpha) ? ak * aw + (KEYFLAG ? 1 : 0) : 64;
+    const int key_bits = pack ? code_bits + pk.seg_bits : code_bits;
     int hist_digits = kEncHistPasses;
     while (hist_digits > 0 && digit_shift(hist_digits - 1) >= key_bits) --hist_digits;
 
-    bool any_nonexact = false, any_domain = false;
+    bool any_nonexact = false, any_domain = false, any_bad_local = false;
     uint64_t kmin = ~0ull, kmax = 0;
     const uint64_t num_tiles = (n + kEncTile - 1) / kEncTile;
     for (uint64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
@@ -342,6 +348,20 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                     exact = len <= (uint64_t)C::K && (len == 0 || last != 0);
                 }
                 if (KEYFLAG) code = (code << 1) | (exact ? 0u : 1u);
+                if (pack) {
+                    // the instance of string i lies between the tile's first and last
+                    const uint64_t i = t0 + j;
+                    uint64_t lo = pk.tile_seg[tile], hi = (uint64_t)pk.tile_seg[tile + 1] + 1;
+                    if (hi > pk.num_segs) hi = pk.num_segs;
+                    while (hi - lo > 1) {
+                        const uint64_t mid = (lo + hi) >> 1;
+                        if (pk.seg_offsets[mid] <= i) lo = mid; else hi = mid;
+                    }
+                    const uint64_t local = i - pk.seg_offsets[lo];
+                    if (local > kIdxMask) any_bad_local = true;
+                    code |= lo << code_bits;
+                    pk.vals[i] = (uint32_t)local & kIdxMask;
+                }
                 codes[t0 + j] = code;
                 kmin = code < kmin ? code : kmin;
                 kmax = code > kmax ? code : kmax;
@@ -369,6 +389,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     if (hist)
         for (int i = tid; i < kEncHistPasses * kBins; i += kEncThreads)
             if (s_hist[i]) atomicAdd(&hist[i], (unsigned long long)s_hist[i]);
+    if (__syncthreads_or(any_bad_local) && tid == 0) atomicOr(&flags->error, kErrInternal);
     any_nonexact = __syncthreads_or(any_nonexact);
     any_domain = __syncthreads_or(any_domain);
     if (tid == 0) {
@@ -390,7 +411,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
 template <int CODER, bool KEYFLAG>
 cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t *codes,
                        uint32_t *nonexact_bits, unsigned long long *hist, DevFlags *flags, unsigned grid,
-                       int alpha_max_w, cudaStream_t s) {
+                       int alpha_max_w, int alpha_max_bits, EncPack pk, cudaStream_t s) {
     auto kern = encode_kernel<CODER, KEYFLAG>;
     static bool configured = false;  // attribute is per function, idempotent
     if (!configured) {
@@ -398,7 +419,8 @@ cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    kern<<<grid, kEncThreads, kEncSmem, s>>>(bytes, offsets, n, codes, nonexact_bits, hist, flags, alpha_max_w);
+    kern<<<grid, kEncThreads, kEncSmem, s>>>(bytes, offsets, n, codes, nonexact_bits, hist, flags, alpha_max_w,
+                                              alpha_max_bits, pk);
     return cudaGetLastError();
 }
 
@@ -407,20 +429,42 @@ cudaError_t launch_enc(const uint8_t *bytes, const uint64_t *offsets, uint64_t n
 cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
-                          DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w) {
+                          DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w, int alpha_max_bits,
+                          EncPack pack) {
     if (n == 0) return cudaSuccess;
     const uint64_t tiles = (n + kEncTile - 1) / kEncTile;
     const unsigned grid = (unsigned)umin64(tiles, (uint64_t)num_sms * 4);
     if (coder == 2) {
         if (key_flag) return cudaErrorInvalidValue;  // BYTE8 codes use all 64 bits
-        return launch_enc<2, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+        return launch_enc<2, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, alpha_max_bits, pack, s);
     }
     if (coder == 3) {
-        if (key_flag) return launch_enc<3, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
-        return launch_enc<3, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+        if (key_flag) return launch_enc<3, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, alpha_max_bits, pack, s);
+        return launch_enc<3, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, alpha_max_bits, pack, s);
     }
-    if (key_flag) return launch_enc<1, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
-    return launch_enc<1, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, s);
+    if (key_flag) return launch_enc<1, true>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, alpha_max_bits, pack, s);
+    return launch_enc<1, false>(bytes, offsets, n, codes, nonexact_bits, hist, flags, grid, alpha_max_w, alpha_max_bits, pack, s);
+}
+
+__global__ void tile_segs_kernel(const uint64_t *__restrict__ seg_offsets, uint64_t num_segs, uint64_t n,
+                                 uint64_t tiles, uint32_t *__restrict__ tile_seg) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > tiles) return;
+    const uint64_t i = umin64(t * (uint64_t)kEncTile, n - 1);
+    uint64_t lo = 0, hi = num_segs;  // seg_offsets[lo] <= i < seg_offsets[hi]
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (seg_offsets[mid] <= i) lo = mid; else hi = mid;
+    }
+    tile_seg[t] = (uint32_t)lo;
+}
+
+cudaError_t launch_tile_segs(const uint64_t *seg_offsets, uint64_t num_segs, uint64_t n, uint32_t *tile_seg,
+                             cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t tiles = (n + kEncTile - 1) / kEncTile;
+    tile_segs_kernel<<<(unsigned)((tiles + 256) / 256), 256, 0, s>>>(seg_offsets, num_segs, n, tiles, tile_seg);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_alphabet(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int max_span,

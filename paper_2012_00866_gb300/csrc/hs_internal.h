@@ -14,13 +14,28 @@ namespace hs {
 // key_flag (ASCII7 only), the sort key (code << 1) | not_exact; optionally
 // the non-exact bitmask (bit i of word i/32) and the 8 digit histograms of
 // what it wrote (8 x kBins u64, accumulated); sets flags.
+// Batched packing for the encoder (byte-range coder only): the instance id
+// of string i goes above its key (key_bits + seg_bits <= 64), vals[i] gets
+// its local index; tile_seg[t] = instance of string t * 1024 (t <= tiles).
+struct EncPack {
+    const uint64_t *seg_offsets;  // nullptr: no packing
+    uint64_t num_segs;
+    int seg_bits;
+    uint32_t *vals;
+    const uint32_t *tile_seg;
+};
+// tile_seg[t] for t = 0 .. ceil(n / 1024): the instance holding string
+// min(t * 1024, n - 1).
+cudaError_t launch_tile_segs(const uint64_t *seg_offsets, uint64_t num_segs, uint64_t n, uint32_t *tile_seg,
+                             cudaStream_t s);
 // coder 3 (byte range): values from flags->alpha_lo_inv / alpha_hi; writes
-// alpha_w / alpha_k and, when the range needs more than alpha_max_w bits,
-// encodes as ASCII7.
+// alpha_w / alpha_k (keys of at most alpha_max_bits bits) and, when the range
+// needs more than alpha_max_w bits or 9 chars do not fit, encodes as ASCII7.
 cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
-                          DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w = 6);
+                          DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w = 6,
+                          int alpha_max_bits = 64, EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr});
 // Smallest / largest byte of bytes[offsets[0] .. offsets[n]) max-reduced into
 // flags->alpha_lo_inv (as 255 - min) and flags->alpha_hi; cut short once the
 // range is known to exceed max_span values.

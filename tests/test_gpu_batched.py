@@ -106,3 +106,21 @@ def test_batched_2000_instances(cuda_lib):
     w = workloads.standard("batched_20000", scale=0.1)
     got = _run(hs, w, w.seg_offsets)
     assert oracle.check_sorted_batched(w.bytes, w.offsets, w.seg_offsets, got) == -1
+
+
+@pytest.mark.parametrize("num_segs", [3, 511, 20_000, 300_000])
+def test_instance_id_packed_into_the_key(cuda_lib, num_segs):
+    """Lowercase strings (the byte-range coder's 5 bits) with the instance id
+    packed above the code: 3 and 511 instances leave the full 10 chars; 20,000
+    (15 bits) cap the code at 9 chars; 300,000 (19 bits) leave no room for 9
+    and fall back to the separate instance array.  Duplicates and strings
+    longer than the code stress the fix-up across instance boundaries."""
+    hs = cuda_lib
+    rng = np.random.default_rng(num_segs)
+    n = 1_200_000
+    cuts = np.sort(rng.choice(np.arange(1, n), size=num_segs - 1, replace=False))
+    seg = np.concatenate([[0], cuts, [n]]).astype(np.uint64)
+    vocab = [bytes(rng.integers(97, 123, size=rng.integers(3, 16)).astype(np.uint8)) for _ in range(3000)]
+    strs = [vocab[i] for i in rng.integers(0, len(vocab), size=n)]
+    w = workloads.from_strings(strs)
+    _check(w, seg, _run(hs, w, seg))
