@@ -78,6 +78,12 @@ def barrier(world):
         dist.barrier()
 
 
+def job_throughput(n_per_rank, world, ms):
+    """Whole-job M keys/s: the strings all ranks sorted over the slowest
+    rank's time (replicas: every rank sorts its own copy of the workload)."""
+    return n_per_rank * world / (ms / 1e3) / 1e6
+
+
 def max_over_ranks(x, world, device):
     if world == 1:
         return x
@@ -280,7 +286,7 @@ def run_ours(args, rank, world, local):
 
     ms = sum(step_ms) / len(step_ms)
     ms = max_over_ranks(ms, world, device)
-    value = n * world / (ms / 1e3) / 1e6
+    value = job_throughput(n, world, ms)
 
     # end to end through the public API: pinned host inputs in, host perm out
     e2e = None

@@ -1,0 +1,64 @@
+"""The bench's multi-rank plumbing on CPU: two gloo ranks agree on the
+maximum step time and pass the barrier; the reference arm's non-zero ranks
+exit without work; the whole-job figure counts every rank's strings."""
+
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    r, w, local = bench.dist_env()
+    assert (r, w, local) == (rank, world, rank)
+    bench.dist_init(w, local, backend="gloo")
+    bench.barrier(w)
+    slowest = bench.max_over_ranks(10.0 + rank, w, torch.device("cpu"))
+    with open(os.path.join(out_dir, f"rank{rank}"), "w") as f:
+        f.write(repr(slowest))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max(tmp_path):
+    world = 2
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    got = [float(open(tmp_path / f"rank{r}").read()) for r in range(world)]
+    assert got == [11.0, 11.0]
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(3.5, 1, torch.device("cpu")) == 3.5
+    bench.barrier(1)   # no-op
+
+
+def test_job_throughput_counts_every_rank():
+    # 1e7 strings per rank, 4 ranks, slowest rank 2 ms: 4e7 strings in 2 ms
+    assert bench.job_throughput(10_000_000, 4, 2.0) == pytest.approx(20_000.0)
+    assert bench.job_throughput(10_000_000, 1, 2.0) == pytest.approx(5_000.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1", "--workload", "random_lower_1e5"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
