@@ -235,6 +235,15 @@ HS_API hs_status hs_stats_enable(int on);
  * exist to *count. */
 HS_API hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count);
 
+/* hs_shutdown -- release what the library keeps between calls: the copy
+ * streams of hs_argsort_host (one per device it ran on), the pooled CUDA
+ * events of the host hand-offs and of the per-kernel timing, and the timing
+ * table (timing is switched off).  Call it with no library call in flight;
+ * later calls recreate what they need.  The allocation-free entry point's
+ * static scratch is part of the loaded image and is not released.
+ * Safe to call without a GPU or twice; returns HS_OK (HS_ERR_CUDA if a
+ * destroy call failed; the rest is still released). */
+HS_API hs_status hs_shutdown(void);
 /* Message describing the calling thread's last failure ("" if none).  The
  * pointer stays valid until the next library call on this thread. */
 HS_API const char *hs_last_error(void);

@@ -42,7 +42,7 @@ MAX_N = 0x7FFFFFFF
 # Every symbol include/husky.h declares (checked by the export test).
 EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
-           "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size",
+           "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size", "hs_shutdown",
            "hs_last_error", "hs_version",
            "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile")
 
@@ -97,6 +97,8 @@ def load(path: str | None = None):
     lib.hs_argsort_host.argtypes = [vp, vp, u64, ci, ci, ci, vp, vp, sz, vp]
     lib.hs_host_workspace_size.restype = ci
     lib.hs_host_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
+    lib.hs_shutdown.restype = ci
+    lib.hs_shutdown.argtypes = []
     lib.hs_argsort_noalloc.restype = ci
     lib.hs_argsort_noalloc.argtypes = [vp, vp, u64, ci, ci, vp, vp]
     lib.hs_stats_enable.restype = ci
@@ -325,6 +327,13 @@ def learned_profile(data: torch.Tensor, offsets: torch.Tensor, linear: bool = Fa
     _check(load().hs_learned_profile(_ptr(data), _ptr(offsets), n, 1 if linear else 0, _ptr(keys),
                                      _ptr(buckets), info, _ptr(ws), ws.numel(), _stream_handle(stream)))
     return keys, buckets, dict(bits=int(info[0]), sample=int(info[1]), loss0=info[2], loss1=info[3])
+
+
+def shutdown():
+    """Release the library's cached streams, events and timing table, and
+    the binding's cached workspaces."""
+    free_workspace()
+    _check(load().hs_shutdown())
 
 
 def version() -> int:

@@ -1161,6 +1161,38 @@ hs_status hs_batched_workspace_size(uint64_t n, uint64_t num_segs, size_t *out) 
     return HS_OK;
 }
 
+hs_status hs_shutdown(void) {
+    g_last_error.clear();
+    bool ok = true;
+    {
+        std::lock_guard<std::mutex> g(g_copy_mu);
+        int cur = -1;
+        const bool have_dev = cudaGetDevice(&cur) == cudaSuccess;
+        for (int d = 0; d < kMaxDevices; ++d) {
+            if (!g_copy_stream[d]) continue;
+            if (have_dev) cudaSetDevice(d);
+            ok &= cudaStreamDestroy(g_copy_stream[d]) == cudaSuccess;
+            g_copy_stream[d] = nullptr;
+        }
+        if (have_dev && cur >= 0) cudaSetDevice(cur);
+        for (cudaEvent_t e : g_sync_events) ok &= cudaEventDestroy(e) == cudaSuccess;
+        g_sync_events.clear();
+    }
+    {
+        std::lock_guard<std::mutex> g(g_stats.mu);
+        for (cudaEvent_t e : g_stats.pool) ok &= cudaEventDestroy(e) == cudaSuccess;
+        g_stats.pool.clear();
+        g_stats.enabled = false;
+        for (int k = 0; k < kKNumKinds; ++k) {
+            g_stats.launches[k] = 0;
+            g_stats.ms[k] = 0.0;
+            g_stats.bytes[k] = 0.0;
+        }
+    }
+    cudaGetLastError();  // leave no sticky error from the destroys behind
+    return ok ? HS_OK : fail(HS_ERR_CUDA, "a stream or event could not be destroyed");
+}
+
 hs_status hs_stats_enable(int on) {
     g_last_error.clear();
     std::lock_guard<std::mutex> g(g_stats.mu);

@@ -81,3 +81,10 @@ def test_no_cpu_fallback_without_gpu():
     off = torch.zeros(3, dtype=torch.int64)
     with pytest.raises(Exception):
         hs.argsort(data, off)
+
+
+def test_shutdown_without_gpu(lib):
+    """hs_shutdown releases nothing it never made and may be called twice."""
+    import paper_2012_00866_gb300 as hs
+    assert lib.hs_shutdown() == hs.OK
+    assert lib.hs_shutdown() == hs.OK

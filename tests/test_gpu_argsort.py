@@ -401,3 +401,21 @@ def test_random_lower_1e5(cuda_lib):
     w = workloads.standard("random_lower_1e5")
     data, off = to_device(w)
     assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
+def test_shutdown_then_sort_again(cuda_lib):
+    """hs_shutdown after host-path calls and timed calls releases the cached
+    streams and events; the next calls recreate them and stay exact."""
+    hs = cuda_lib
+    import torch
+    w = workloads.generate(2, 300_000, 9)
+    data = torch.from_numpy(w.bytes).pin_memory()
+    off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+    hs.stats_enable(True)
+    assert_oracle_equal(w, hs.argsort(data, off))
+    hs.stats_enable(False)
+    hs.shutdown()
+    hs.shutdown()
+    assert_oracle_equal(w, hs.argsort(data, off))
+    d_data, d_off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(d_data, d_off))
