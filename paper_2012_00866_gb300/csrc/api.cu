@@ -349,7 +349,7 @@ hs_status device_error_status(const DevFlags &h) {
 // flags and *used the coder actually used.
 hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int coder,
                      uint64_t *codes, uint32_t *bits, bool hist, bool sort_key, int *used, int max_key_bits = 64,
-                     EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr}) {
+                     EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr, 0}) {
     int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : (coder == HS_CODER_ASCII7 ? HS_CODER_ASCII7 : HS_CODER_ALPHA);
     for (int attempt = 0; attempt < 3; ++attempt) {
         HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
@@ -364,10 +364,13 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         // over ASCII7 (w <= 5: a range of at most 31 values); asked for, up
         // to 6 bits.
         const int max_w = coder == HS_CODER_ALPHA ? 6 : 5;
+        bool spec = false;
         if (from_host) {
             // Inputs still on the host: copy them chunk by chunk on the
-            // library's copy stream; each chunk is encoded (or, for the
-            // alphabet coder, scanned for its alphabet) once it is in.
+            // library's copy stream; each chunk is encoded once it is in.
+            // The byte-range coder scans each chunk's range as well and
+            // encodes with the first chunk's range, checked against the
+            // whole range after the last chunk (re-encoded on a mismatch).
             const HostSrc &h = *c.host;
             cudaStream_t cs = nullptr;
             HS_TRY(copy_stream(&cs), "copy stream");
@@ -394,16 +397,24 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
                 const uint64_t m = s1 - s0;
                 if (u == HS_CODER_ALPHA) {
                     HS_TRY(c.timed(kKAlphabet, (double)(b1 - b0), [&] {
-                               return launch_alphabet(h.d_bytes, h.d_offsets + s0, m, (1 << max_w) - 1, c.d_flags, c.sms, c.s);
+                               return launch_alphabet(h.d_bytes, h.d_offsets + s0, m, (1 << max_w) - 1, c.d_flags,
+                                                      c.sms, c.s);
                            }),
                            "alphabet chunk");
-                } else {
-                    HS_TRY(c.timed(kKEncode, enc_bytes * ((double)m / (double)n), [&] {
-                               return launch_encode(u, kflag, h.d_bytes, h.d_offsets + s0, m, codes + s0,
-                                                    ebits ? ebits + s0 / 32 : nullptr, ehist, c.d_flags, c.sms, c.s);
-                           }),
-                           "encode chunk");
+                    if (s0 == 0)
+                        HS_TRY(cudaMemcpyAsync(&c.d_flags->alpha_spec_lo_inv, &c.d_flags->alpha_lo_inv,
+                                               2 * sizeof(unsigned int), cudaMemcpyDeviceToDevice, c.s),
+                               "speculative range");
+                    spec = true;
                 }
+                EncPack pk = pack;
+                pk.spec_range = spec ? 1 : 0;
+                HS_TRY(c.timed(kKEncode, enc_bytes * ((double)m / (double)n), [&] {
+                           return launch_encode(u, kflag, h.d_bytes, h.d_offsets + s0, m, codes + s0,
+                                                ebits ? ebits + s0 / 32 : nullptr, ehist, c.d_flags, c.sms, c.s,
+                                                max_w, max_key_bits, pk);
+                       }),
+                       "encode chunk");
             }
         } else if (u == HS_CODER_ALPHA) {
             HS_TRY(c.timed(kKAlphabet, 0.0, [&] {
@@ -411,7 +422,7 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
                    }),
                    "alphabet");
         }
-        if (!from_host || u == HS_CODER_ALPHA)
+        if (!from_host)
             HS_TRY(c.timed(kKEncode, enc_bytes, [&] {
                        return launch_encode(u, kflag, bytes, offsets, n, codes, ebits, ehist, c.d_flags, c.sms, c.s,
                                             max_w, max_key_bits, pack);
@@ -426,6 +437,8 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         HS_TRY(c.read_flags(), "encode sync");
         hs_status st = device_error_status(c.h);
         if (st != HS_OK) return st;
+        if (spec && (c.h.alpha_spec_lo_inv != c.h.alpha_lo_inv || c.h.alpha_spec_hi != c.h.alpha_hi))
+            continue;  // a later chunk widened the byte range: encode again from the device copies
         if (u == HS_CODER_ALPHA) {
             // the encoder's own test: w within max_w and 9 chars within max_key_bits
             if ((int)c.h.alpha_w <= max_w && 9 * (int)c.h.alpha_w + 1 <= max_key_bits) {

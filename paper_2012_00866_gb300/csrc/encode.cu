@@ -220,7 +220,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     bool alpha = false;
     uint32_t alo4 = 0;
     if (CODER == 3) {
-        int lo = 255 - (int)flags->alpha_lo_inv, hi = (int)flags->alpha_hi;
+        int lo = 255 - (int)(pk.spec_range ? flags->alpha_spec_lo_inv : flags->alpha_lo_inv);
+        int hi = (int)(pk.spec_range ? flags->alpha_spec_hi : flags->alpha_hi);
         if (hi < lo) lo = hi = 0;  // no bytes at all
         int w = 1;
         while ((1 << w) < hi - lo + 2) ++w;

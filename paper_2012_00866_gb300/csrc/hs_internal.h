@@ -23,6 +23,7 @@ struct EncPack {
     int seg_bits;
     uint32_t *vals;
     const uint32_t *tile_seg;
+    int spec_range;               // byte-range coder: use flags->alpha_spec_* (the range of a first chunk)
 };
 // tile_seg[t] for t = 0 .. ceil(n / 1024): the instance holding string
 // min(t * 1024, n - 1).
@@ -35,7 +36,7 @@ cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
                           DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w = 6,
-                          int alpha_max_bits = 64, EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr});
+                          int alpha_max_bits = 64, EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr, 0});
 // Smallest / largest byte of bytes[offsets[0] .. offsets[n]) max-reduced into
 // flags->alpha_lo_inv (as 255 - min) and flags->alpha_hi; cut short once the
 // range is known to exceed max_span values.
