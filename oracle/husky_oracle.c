@@ -118,10 +118,11 @@ int oracle_encode(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
  * w = ceil(log2(hi - lo + 2)) in place of the 7-bit mask ('a'..'z': 26
  * values, 5 bits; 'A'..'z': 58 values, 6 bits).  The map keeps byte order and
  * the padding stays below every value, so the code is order preserving.
- * max_length K: the most characters whose sort key (K*w code bits plus the
- * not-exact bit) needs no more 9-bit radix digits than K = 9 would, with
- * K*w <= 63.  Defined for w <= 6; a string is exactly represented iff its
- * length is at most K (a NUL byte inside the range has a value of its own). */
+ * max_length K = 8: as many characters as BYTE8 codes, in a sort key of
+ * 8*w + 1 bits (41 for letters: five 9-bit radix digits where ASCII7's 64 bits
+ * take seven); longer strings are left to Step 3.  Defined for w <= 6; a
+ * string is exactly represented iff its length is at most 8 (a NUL byte
+ * inside the range has a value of its own). */
 
 /* Algorithm 4 with a character map in place of the mask. */
 uint64_t oracle_string_to_long_mapped(const uint8_t *s, uint64_t len, int max_length,
@@ -158,12 +159,8 @@ int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t 
     int w = 1;
     while ((1 << w) < span + 1)
         w++;
-    int digits9 = (9 * w + 1 + 8) / 9;           /* radix digits at K = 9 */
-    int k = 9;
-    while ((k + 1) * w <= 63 && ((k + 1) * w + 1 + 8) / 9 <= digits9)
-        k++;
     *w_out = w;
-    *k_out = k;
+    *k_out = 8;
     return w <= 6 ? 0 : 1;
 }
 

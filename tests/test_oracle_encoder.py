@@ -123,17 +123,16 @@ def test_alpha_hand_worked_codes(row):
     assert got == want
 
 
-@pytest.mark.parametrize("s_count, w_, k_", [(1, 1, 17), (2, 2, 13), (3, 2, 13), (4, 3, 11), (7, 3, 11),
-                                             (8, 4, 11), (15, 4, 11), (16, 5, 10), (26, 5, 10), (31, 5, 10),
-                                             (32, 6, 10), (62, 6, 10), (63, 6, 10)])
-def test_alpha_width_and_length_table(s_count, w_, k_):
-    """Bit width and length for byte ranges of s values, worked by hand from
-    the rule (w = ceil(log2(s + 1)); K the most chars within the 9-char digit
-    count); a range of 64 needs 7 bits and the coder does not apply.  Only
-    the two ends matter: the bytes in between need not occur."""
+@pytest.mark.parametrize("s_count, w_", [(1, 1), (2, 2), (3, 2), (4, 3), (7, 3), (8, 4), (15, 4), (16, 5),
+                                        (26, 5), (31, 5), (32, 6), (62, 6), (63, 6)])
+def test_alpha_width_and_length_table(s_count, w_):
+    """Bit width for byte ranges of s values, worked by hand from
+    w = ceil(log2(s + 1)); the length is 8 chars throughout; a range of 64
+    needs 7 bits and the coder does not apply.  Only the two ends matter:
+    the bytes in between need not occur."""
     wl = workloads.from_strings([bytes([40]), bytes([40 + s_count - 1])])
     m, w, k, applies = oracle.alpha_params(wl.bytes, wl.offsets)
-    assert (w, k, applies) == (w_, k_, True)
+    assert (w, k, applies) == (w_, 8, True)
     assert m[40] == 1 and m[40 + s_count - 1] == s_count and m[39] == 0
     wl = workloads.from_strings([bytes([40]), bytes([40 + 63])])
     assert oracle.alpha_params(wl.bytes, wl.offsets)[3] is False
@@ -159,19 +158,19 @@ def test_alpha_order_property_pairwise(alphabet):
 
 
 def test_alpha_truncation_and_nul():
-    """Strings agreeing on the first K chars share a code and are not exact;
+    """Strings agreeing on the first 8 chars share a code and are not exact;
     a NUL byte inside the range has a value of its own, so x and x + NUL
     differ (unlike ASCII7, where they share a code)."""
-    strs = [b"abcdefghijk", b"abcdefghijz", b"abcdefghij", b"a", b"abcdefghijklmnopqrstuvwxyz"]
+    strs = [b"abcdefghi", b"abcdefghz", b"abcdefgh", b"a", b"abcdefghijklmnopqrstuvwxyz"]
     wl = workloads.from_strings(strs)
     codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
-    assert (w, k) == (5, 10)
+    assert (w, k) == (5, 8)
     assert codes[0] == codes[1] == codes[2]
     assert list(exact) == [0, 0, 1, 1, 0] and not perfect
     strs = [b"\x05", b"\x05\x00", b"\x1f\x1f\x1f"]      # range 0x00..0x1f: 32 values, 6 bits
     wl = workloads.from_strings(strs)
     codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets)
-    assert (w, k) == (6, 10) and perfect
+    assert (w, k) == (6, 8) and perfect
     assert codes[0] < codes[1] < codes[2]
     assert oracle.encode_alpha(*_ws([b"a", b"a\x00"])) is None   # 0x00..0x61 needs 7 bits
 
