@@ -70,17 +70,19 @@ typedef enum {
  *                    Section 4.3).  Order preserving only on bytes < 0x80.
  *   HS_CODER_BYTE8   bitWidth 8, maxLength 8, no mask: order preserving on
  *                    all bytes (this library's coder for arbitrary bytes).
- *   HS_CODER_ALPHA   alphabet-rank coder, generalising the 5-bit and 6-bit
- *                    letter codings of Section 3.2: each byte value present
- *                    in bytes[offsets[0] .. offsets[n]) codes as its rank
- *                    1..s among them (0 is the padding), in
- *                    w = ceil(log2(s + 1)) bits, for maxLength K = the most
- *                    chars whose sort key (K*w + 1 bits) needs no more 9-bit
- *                    radix digits than 9 chars do (K*w <= 63).  Lowercase
- *                    text: w = 5, K = 10, a 51-bit key.  Order preserving on
- *                    all bytes; exact iff length <= K.  Applies when s <= 63
- *                    (w <= 6), else HS_ERR_CODER_DOMAIN.
- *   HS_CODER_AUTO    ALPHA when it applies, else ASCII7, re-encoding with
+ *   HS_CODER_ALPHA   byte-range coder, generalising the 5-bit and 6-bit
+ *                    letter codings of Section 3.2: with lo / hi the smallest
+ *                    / largest byte of bytes[offsets[0] .. offsets[n]), byte
+ *                    c codes as c - lo + 1 (0 is the padding) in
+ *                    w = ceil(log2(hi - lo + 2)) bits ('a'..'z': 5 bits,
+ *                    'A'..'z': 6), for maxLength 8: a sort key of 8w + 1
+ *                    bits.  Lowercase text: a 41-bit key, five 9-bit radix
+ *                    passes where ASCII7 needs seven.  Order preserving on
+ *                    all bytes; exact iff length <= 8.  Applies when the
+ *                    range has at most 63 values (w <= 6), else
+ *                    HS_ERR_CODER_DOMAIN.
+ *   HS_CODER_AUTO    ALPHA when the range has at most 31 values (w <= 5, where
+ *                    it saves radix passes), else ASCII7, re-encoding with
  *                    BYTE8 when any string has a byte >= 0x80 among its first
  *                    9 bytes. */
 typedef enum { HS_CODER_AUTO = 0, HS_CODER_ASCII7 = 1, HS_CODER_BYTE8 = 2, HS_CODER_ALPHA = 3 } hs_coder;

@@ -440,8 +440,8 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
         if (spec && (c.h.alpha_spec_lo_inv != c.h.alpha_lo_inv || c.h.alpha_spec_hi != c.h.alpha_hi))
             continue;  // a later chunk widened the byte range: encode again from the device copies
         if (u == HS_CODER_ALPHA) {
-            // the encoder's own test: w within max_w and 9 chars within max_key_bits
-            if ((int)c.h.alpha_w <= max_w && 9 * (int)c.h.alpha_w + 1 <= max_key_bits) {
+            // the encoder's own test: w within max_w and the 8-char key within max_key_bits
+            if ((int)c.h.alpha_w <= max_w && 8 * (int)c.h.alpha_w + 1 <= max_key_bits) {
                 c.alpha_k = (int)c.h.alpha_k;
                 break;
             }

@@ -34,7 +34,7 @@ constexpr int kEncItems = kEncTile / kEncThreads;
 constexpr int kEncStage = 28672;   // staged bytes per tile
 constexpr int kEncHistPasses = kKeyPasses;
 constexpr size_t kEncOffBytes = (((size_t)kEncTile + 1) * 8 + 15) & ~(size_t)15;  // keeps s_bytes 16-B aligned
-constexpr int kEncPad = 32;        // word reads of the last staged string may run 23 bytes past the stage
+constexpr int kEncPad = 16;        // word reads of the last staged string may run 15 bytes past the stage
 constexpr size_t kEncSmem = kEncOffBytes + kEncStage + kEncPad + (size_t)kEncHistPasses * kBins * 4;
 static_assert(kEncStage % 16 == 0, "staging buffer must keep 16-byte alignment");
 
@@ -211,11 +211,9 @@ encode_kernel(const uint8_t *__restrict__ bytes,
 
     // Coder 3: byte c codes as c - lo + 1 over the data's byte range
     // [lo, hi] (0 is the padding), w = ceil(log2(hi - lo + 2)) bits each,
-    // K = the most chars whose sort key (K*w + 1 bits) needs no more 9-bit
-    // digits than 9 chars do, with K*w <= 63 and K*w + 1 <= alpha_max_bits
-    // (room the caller keeps above the key).  Past alpha_max_w bits, or when
-    // 9 chars do not fit alpha_max_bits, it is not applied and the kernel
-    // encodes as ASCII7.
+    // K = 8 chars: a sort key of 8w + 1 bits.  Past alpha_max_w bits, or
+    // when the key does not fit alpha_max_bits (room the caller keeps above
+    // it), it is not applied and the kernel encodes as ASCII7.
     int aw = 7, ak = 9;
     bool alpha = false;
     uint32_t alo4 = 0;
@@ -225,10 +223,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         if (hi < lo) lo = hi = 0;  // no bytes at all
         int w = 1;
         while ((1 << w) < hi - lo + 2) ++w;
-        const int d9 = (9 * w + 1 + 8) / 9;
-        int k = 9;
-        while ((k + 1) * w <= 63 && ((k + 1) * w + 1 + 8) / 9 <= d9 && (k + 1) * w + 1 <= alpha_max_bits) ++k;
-        alpha = w <= alpha_max_w && 9 * w + 1 <= alpha_max_bits;
+        const int k = 8;
+        alpha = w <= alpha_max_w && k * w + 1 <= alpha_max_bits;
         aw = w;
         ak = k;
         alo4 = (uint32_t)((lo - 1) & 0xFF) * 0x01010101u;
@@ -302,20 +298,16 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                 const uint64_t len = s_off[j + 1] - off;
                 if (CODER == 3 && alpha) {
                     const int m = (int)umin64(len, (uint64_t)ak);
-                    if (staged && ak <= 16) {
-                        // bytes q .. q+15 from the three aligned words at q & ~7,
+                    if (staged) {
+                        // bytes q .. q+7 from the two aligned words at q & ~7,
                         // minus (lo - 1) bytewise, bytes past m cleared, packed
                         const uint32_t q = (uint32_t)(base + off - a0);
                         const uint64_t *wp = reinterpret_cast<const uint64_t *>(s_bytes + (q & ~7u));
-                        const uint64_t x0 = wp[0], x1 = wp[1], x2 = wp[2];
+                        const uint64_t x0 = wp[0], x1 = wp[1];
                         const int r = 8 * (int)(q & 7u);
                         const uint64_t w0 = r ? (x0 >> r) | (x1 << (64 - r)) : x0;
-                        const uint64_t w1 = r ? (x1 >> r) | (x2 << (64 - r)) : x1;
-                        const uint64_t keep0 = m >= 8 ? ~0ull : ((1ull << (8 * m)) - 1);
-                        const uint64_t keep1 = m >= 16 ? ~0ull : (m > 8 ? ((1ull << (8 * (m - 8))) - 1) : 0ull);
-                        const uint64_t p0 = pack_w(sub_bytes(w0, alo4) & keep0, aw);
-                        const uint64_t p1 = pack_w(sub_bytes(w1, alo4) & keep1, aw);
-                        code = (p0 << (aw * (ak - 8))) | (p1 >> (aw * (16 - ak)));
+                        const uint64_t keep = m >= 8 ? ~0ull : ((1ull << (8 * m)) - 1);
+                        code = pack_w(sub_bytes(w0, alo4) & keep, aw);  // the 8 chars, 8w bits
                     } else {
                         const uint8_t *src = staged ? s_bytes + (uint32_t)(base + off - a0) : bytes + off;
                         const unsigned lo1 = (alo4 & 0xFFu);

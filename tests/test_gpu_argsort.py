@@ -130,7 +130,7 @@ def test_ascii7_domain_error_and_auto(cuda_lib):
 @pytest.mark.parametrize("kind", [1, 2, 3, 4, 5])
 def test_alpha_encode_matches_oracle(cuda_lib, kind):
     """The byte-range coder against the oracle's: same codes and all-exact
-    flag on the lowercase workloads (w = 5, K = 10); kind 3 spans '0'..'z'
+    flag on the lowercase workloads (w = 5, K = 8); kind 3 spans '0'..'z'
     (75 values) and is refused."""
     hs = cuda_lib
     w = workloads.generate(kind, 300_001, 31 + kind)
@@ -143,14 +143,14 @@ def test_alpha_encode_matches_oracle(cuda_lib, kind):
         return
     codes, exact, used = hs.encode(data, off, coder=hs.CODER_ALPHA)
     want, _, perfect, ww, kk = oracle.encode_alpha(w.bytes, w.offsets)
-    assert used == hs.CODER_ALPHA and (ww, kk) == (5, 10)
+    assert used == hs.CODER_ALPHA and (ww, kk) == (5, 8)
     assert np.array_equal(codes.cpu().numpy().view(np.uint64), want)
     assert exact == perfect
 
 
 def test_alpha_edge_alphabets(cuda_lib):
-    """Narrow byte ranges (w = 1, K = 17 takes the bytewise path; w = 2, 4, 6),
-    NUL bytes, empty strings, and the argsort through them."""
+    """Narrow byte ranges (w = 1, 2, 4, 6), NUL bytes, empty strings, and the
+    argsort through them."""
     hs = cuda_lib
     cases = [[b"a" * k for k in range(0, 40)],
              [b"ab"[i % 2: i % 2 + 1] * (i % 23) for i in range(3000)],

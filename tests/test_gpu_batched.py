@@ -110,11 +110,10 @@ def test_batched_2000_instances(cuda_lib):
 
 @pytest.mark.parametrize("num_segs", [3, 511, 20_000, 300_000])
 def test_instance_id_packed_into_the_key(cuda_lib, num_segs):
-    """Lowercase strings (the byte-range coder's 5 bits) with the instance id
-    packed above the code: 3 and 511 instances leave the full 10 chars; 20,000
-    (15 bits) cap the code at 9 chars; 300,000 (19 bits) leave no room for 9
-    and fall back to the separate instance array.  Duplicates and strings
-    longer than the code stress the fix-up across instance boundaries."""
+    """Lowercase strings (the byte-range coder's 5 bits, a 41-bit key) with the
+    instance id packed above the key: 3 .. 300,000 instances (up to 19 bits)
+    all fit; duplicates and strings longer than the code stress the fix-up
+    across instance boundaries."""
     hs = cuda_lib
     rng = np.random.default_rng(num_segs)
     n = 1_200_000
@@ -123,4 +122,19 @@ def test_instance_id_packed_into_the_key(cuda_lib, num_segs):
     vocab = [bytes(rng.integers(97, 123, size=rng.integers(3, 16)).astype(np.uint8)) for _ in range(3000)]
     strs = [vocab[i] for i in rng.integers(0, len(vocab), size=n)]
     w = workloads.from_strings(strs)
+    _check(w, seg, _run(hs, w, seg))
+
+
+def test_instance_ids_too_wide_for_the_packed_key(cuda_lib):
+    """2**23 + 5 instances need 24 bits: with the 41-bit key of lowercase
+    text that passes 64, so the batched sort keeps the instance ids in their
+    own array.  Mostly single-string instances, some longer, an empty one."""
+    hs = cuda_lib
+    rng = np.random.default_rng(11)
+    num_segs = (1 << 23) + 5
+    sizes = np.ones(num_segs, np.int64)
+    np.add.at(sizes, rng.integers(1, num_segs, size=200_000), 1)
+    sizes[0] = 0
+    seg = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    w = workloads.generate(1, int(seg[-1]), 12)     # lowercase, lengths 4..12
     _check(w, seg, _run(hs, w, seg))
