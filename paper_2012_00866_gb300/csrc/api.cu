@@ -259,6 +259,9 @@ struct Ctx {
     DevFlags h;  // last host copy of the flags
     const HostSrc *host = nullptr;    // hs_argsort_host: inputs still on the host
     int alpha_k = 9;                  // chars the alphabet coder covered (its prefix length)
+    int alpha_w = 0;                  // its bits per char
+    bool idx_packed = false;          // the encoder packed each string's index below its code
+    int idx_bits = 0;                 // ... in this many bits
     std::vector<cudaEvent_t> events;  // chunk hand-off events in use
 
     template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(ws + off); }
@@ -349,15 +352,18 @@ hs_status device_error_status(const DevFlags &h) {
 // flags and *used the coder actually used.
 hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int coder,
                      uint64_t *codes, uint32_t *bits, bool hist, bool sort_key, int *used, int max_key_bits = 64,
-                     EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr, 0}) {
+                     EncPack pack = EncPack{}) {
     int u = coder == HS_CODER_BYTE8 ? HS_CODER_BYTE8 : (coder == HS_CODER_ASCII7 ? HS_CODER_ASCII7 : HS_CODER_ALPHA);
+    c.idx_packed = false;
+    c.idx_bits = pack.idx_bits;
     for (int attempt = 0; attempt < 3; ++attempt) {
         HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
         HS_TRY(cudaMemsetAsync(&c.d_flags->kmin, 0xFF, sizeof(unsigned long long), c.s), "memset kmin");
         c.next_counter = 0;
         const double enc_bytes = 8.0 * (n + 1) + 8.0 * n + (bits ? n / 8.0 : 0.0);
         const bool kflag = sort_key && u != HS_CODER_BYTE8;
-        uint32_t *ebits = kflag ? nullptr : bits;
+        // a packed index leaves the not-exact bit out of the key: the bitmap holds it
+        uint32_t *ebits = (kflag && !(u == HS_CODER_ALPHA && pack.idx_bits > 0)) ? nullptr : bits;
         unsigned long long *ehist = hist ? c.at<unsigned long long>(c.L.hist) : nullptr;
         const bool from_host = c.host && attempt == 0;
         // AUTO takes the byte-range coder only where it saves a radix pass
@@ -409,6 +415,7 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
                 }
                 EncPack pk = pack;
                 pk.spec_range = spec ? 1 : 0;
+                pk.idx_base = s0;
                 HS_TRY(c.timed(kKEncode, enc_bytes * ((double)m / (double)n), [&] {
                            return launch_encode(u, kflag, h.d_bytes, h.d_offsets + s0, m, codes + s0,
                                                 ebits ? ebits + s0 / 32 : nullptr, ehist, c.d_flags, c.sms, c.s,
@@ -443,6 +450,8 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
             // the encoder's own test: w within max_w and the 8-char key within max_key_bits
             if ((int)c.h.alpha_w <= max_w && 8 * (int)c.h.alpha_w + 1 <= max_key_bits) {
                 c.alpha_k = (int)c.h.alpha_k;
+                c.alpha_w = (int)c.h.alpha_w;
+                c.idx_packed = c.h.idx_packed != 0;
                 break;
             }
             if (coder == HS_CODER_ALPHA)
@@ -477,8 +486,13 @@ struct SortBufs {
 
 hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passes, int npasses,
                      bool segmented, const uint32_t *flag_bits, bool synth_first, void *final_out,
-                     OutMode final_mode, bool keep_keys) {
+                     OutMode final_mode, bool keep_keys, int pack_bits = 0) {
     uint64_t *lb = c.at<uint64_t>(c.L.lb);
+    if (pack_bits > 0) {  // (key << pack_bits) | index words: nothing else moves
+        if (segmented || (!keep_keys && final_out == nullptr)) return fail(HS_ERR_INTERNAL, "packed passes");
+        synth_first = false;
+        flag_bits = nullptr;
+    }
     for (int i = 0; i < npasses; ++i) {
         const int p = passes[i];
         const bool first = i == 0, last = i == npasses - 1;
@@ -488,12 +502,13 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
         a.keys_out = (last && !keep_keys) ? nullptr : b.keys[*cur ^ 1];
         a.segs_in = segmented ? b.segs[*cur] : nullptr;
         a.segs_out = segmented ? b.segs[*cur ^ 1] : nullptr;
-        a.vals_in = (first && synth_first) ? nullptr : b.vals[*cur];
+        a.vals_in = ((first && synth_first) || pack_bits > 0) ? nullptr : b.vals[*cur];
         const bool to_final = last && final_out != nullptr;
-        a.vals_out = to_final ? final_out : b.vals[*cur ^ 1];
+        a.vals_out = to_final ? final_out : (pack_bits > 0 ? nullptr : b.vals[*cur ^ 1]);
         a.flag_bits = flag_bits;
         a.n = n;
-        a.shift = digit_shift(p);
+        a.pack_bits = pack_bits;
+        a.shift = digit_shift(p) + pack_bits;
         a.mask = digit_mask(p);
         a.bucket_base = c.at<unsigned long long>(c.L.bucket) + (size_t)p * kBins;
         a.lookback = lb;
@@ -502,10 +517,14 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
         a.flags = c.d_flags;
         const OutMode om = to_final ? final_mode : kOutVals;
         double ob = 8.0 * n;                                   // keys read
-        ob += (first && synth_first) ? (flag_bits ? n / 8.0 : 0.0) : 4.0 * n;  // vals read
-        ob += a.keys_out ? 8.0 * n : 0.0;                      // keys written
-        ob += om == kOutPerm64 ? 8.0 * n : 4.0 * n;            // vals written
-        ob += segmented ? 8.0 * n : 0.0;                       // segs read + written
+        if (pack_bits > 0) {
+            ob += om == kOutPerm32 ? 4.0 * n : 8.0 * n;        // words or indices written
+        } else {
+            ob += (first && synth_first) ? (flag_bits ? n / 8.0 : 0.0) : 4.0 * n;  // vals read
+            ob += a.keys_out ? 8.0 * n : 0.0;                  // keys written
+            ob += om == kOutPerm64 ? 8.0 * n : 4.0 * n;        // vals written
+            ob += segmented ? 8.0 * n : 0.0;                   // segs read + written
+        }
         HS_TRY(c.timed(kKOnesweep, ob, [&] {
                    return launch_onesweep(a, segmented, digit_seg, first && synth_first, om, c.s);
                }),
@@ -542,6 +561,11 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     // instance id is packed into it)
     t.segs = (inst.seg_offsets && !instance_in_key) ? b.segs[cur] : nullptr;
     t.vals = b.vals[cur];
+    if (mode == kTiePacked) {
+        t.bits = c.at<uint32_t>(c.L.bits);
+        t.pack_bits = c.idx_bits;
+        t.last_char_mask = (1ull << c.alpha_w) - 1;
+    }
     t.n = n;
     t.prefix_len = in.prefix_len;
     t.perm = in.perm;
@@ -558,7 +582,9 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     t.flags = c.d_flags;
     HS_TRY(c.next_epoch(&t.epoch), "epoch");
     HS_TRY(c.counter(&t.tile_counter), "counter");
-    const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
+    const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n
+                             : mode == kTiePacked ? 8.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n
+                                                  : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
     HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
     // Runs of copies of one string are final already; only the others go on
     // to refinement (queue B).
@@ -700,9 +726,40 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
     uint32_t *bits = c.at<uint32_t>(c.L.bits);
     c.lb_words = sort_tiles(n) * kBins;
     int used = 0;
-    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used);
+    // Up to 2^idx_bits strings: the byte-range coder's 8w-bit codes and
+    // their indices share one word when they fit, so a pass moves 8 bytes
+    // a string instead of 12 and the not-exact bit rides in the bitmap.
+    int idx_bits = 0;
+    while (idx_bits < 63 && (1ull << idx_bits) < n) ++idx_bits;
+    EncPack pk{};
+    pk.idx_bits = n >= 2 ? idx_bits : 0;
+    hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used, 64, pk);
     if (st != HS_OK) return st;
     in.prefix_len = coded_prefix(c, used);
+    const OutMode pmode = in.perm_u64 ? kOutPerm64 : kOutPerm32;
+    if (used == HS_CODER_ALPHA && c.idx_packed) {
+        const bool perfect = c.h.nonexact == 0;
+        int passes[kKeyPasses], np = 0;
+        for (int p = 0; p < kKeyPasses; ++p)
+            if (c.h.active[p]) passes[np++] = p;
+        int cur = 0;
+        if (np == 0) {
+            if (perfect)
+                HS_TRY(c.timed(kKIdentity, 4.0 * n, [&] { return launch_identity(nullptr, n, in.perm, pmode, c.s); }),
+                       "identity");
+        } else {
+            st = run_passes(c, b, &cur, n, passes, np, false, nullptr, false, perfect ? in.perm : nullptr, pmode,
+                            !perfect, c.idx_bits);
+            if (st != HS_OK) return st;
+        }
+        bool synced = false;
+        if (!perfect) {
+            st = run_fixup(c, in, b, cur, kTiePacked, Instances{nullptr, 0}, &synced);
+            if (st != HS_OK) return st;
+        }
+        if (!synced) HS_TRY(c.read_flags(), "final sync");
+        return device_error_status(c.h);
+    }
     // ASCII7: the sort key carries the not-exact bit, so the permutation is
     // final after the last pass and runs needing work are read off the keys.
     // BYTE8: the bit rides in the payload and tie detection writes the

@@ -238,8 +238,12 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     // bin 0 once per tile instead of per string (the byte-range coder's
     // K*w + 1 bits; the other keys use all eight digits).
     // Batched, byte-range coder: the instance id goes above the code.
+    // Single sort, byte-range coder: the string's index goes below it when
+    // both fit one word (the not-exact bit then stays out of the key).
     const bool pack = CODER == 3 && alpha && pk.seg_offsets != nullptr;
-    const int code_bits = (CODER == 3 && alpha) ? ak * aw + (KEYFLAG ? 1 : 0) : 64;
+    const bool pack_idx = CODER == 3 && alpha && !pack && pk.idx_bits > 0 && ak * aw + pk.idx_bits <= 64;
+    if (CODER == 3 && blockIdx.x == 0 && tid == 0) flags->idx_packed = pack_idx ? 1u : 0u;
+    const int code_bits = (CODER == 3 && alpha) ? ak * aw + ((KEYFLAG && !pack_idx) ? 1 : 0) : 64;
     const int key_bits = pack ? code_bits + pk.seg_bits : code_bits;
     int hist_digits = kEncHistPasses;
     while (hist_digits > 0 && digit_shift(hist_digits - 1) >= key_bits) --hist_digits;
@@ -291,7 +295,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         for (int k = 0; k < kEncItems; ++k) {
             const int j = k * kEncThreads + tid;   // a warp covers 32 consecutive strings
             const bool valid = j < cnt;
-            uint64_t code = 0;
+            uint64_t code = 0, hkey = 0;  // hkey: the key the digit histograms count
             bool exact = true;
             if (valid) {
                 const uint64_t off = s_off[j];
@@ -340,7 +344,13 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                     code = shift >= 64 ? 0 : (code << shift);
                     exact = len <= (uint64_t)C::K && (len == 0 || last != 0);
                 }
-                if (KEYFLAG) code = (code << 1) | (exact ? 0u : 1u);
+                hkey = code;
+                if (pack_idx) {
+                    code = (code << pk.idx_bits) | (pk.idx_base + t0 + j);
+                } else if (KEYFLAG) {
+                    code = (code << 1) | (exact ? 0u : 1u);
+                    hkey = code;
+                }
                 if (pack) {
                     // the instance of string i lies between the tile's first and last
                     const uint64_t i = t0 + j;
@@ -352,7 +362,8 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                     }
                     const uint64_t local = i - pk.seg_offsets[lo];
                     if (local > kIdxMask) any_bad_local = true;
-                    code |= lo << code_bits;
+                    code |= lo << (code_bits & 63);
+                    hkey = code;
                     pk.vals[i] = (uint32_t)local & kIdxMask;
                 }
                 codes[t0 + j] = code;
@@ -364,12 +375,12 @@ encode_kernel(const uint8_t *__restrict__ bytes,
 #pragma unroll
                     for (int p = 0; p < kEncHistPasses; ++p)
                         if (p < hist_digits)
-                            hist_add_full(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)));
+                            hist_add_full(s_hist + p * kBins, (unsigned)((hkey >> digit_shift(p)) & digit_mask(p)));
                 } else {
 #pragma unroll
                     for (int p = 0; p < kEncHistPasses; ++p)
                         if (p < hist_digits)
-                            hist_add(s_hist + p * kBins, (unsigned)((code >> digit_shift(p)) & digit_mask(p)), valid);
+                            hist_add(s_hist + p * kBins, (unsigned)((hkey >> digit_shift(p)) & digit_mask(p)), valid);
                 }
             }
             const unsigned ne = __ballot_sync(kFull, valid && !exact);

@@ -85,9 +85,10 @@ __device__ __forceinline__ int tie_slot(int x) { return x + (x >> 4); }
 constexpr size_t kTieSmem = (size_t)(kTieSlots + kTieSlots / 16 + 1) * 8;
 
 template <int MODE>
-__global__ void __launch_bounds__(kTieThreads)
+__global__ void __launch_bounds__(kTieThreads, MODE == kTiePacked || MODE == kTieRefine ? 4 : 6)
 tie_detect_kernel(const TieArgs a) {
     constexpr bool REFINE = MODE == kTieRefine;
+    constexpr bool PACKED = MODE == kTiePacked;  // s_key holds (code << pack_bits) | index
     extern __shared__ __align__(16) unsigned char tie_smem[];
     uint64_t *s_key = reinterpret_cast<uint64_t *>(tie_smem);  // s_key[tie_slot(i + 1)] = keys[t0 + i]
     __shared__ uint64_t s_state[kTieThreads / 32];
@@ -116,23 +117,71 @@ tie_detect_kernel(const TieArgs a) {
     if (SEGS && j0 > 0 && j0 - 1 < n) seg_prev = a.segs[j0 - 1];
     uint32_t heads = 0, flagsb = 0;
     RunState mine{0, 0, 0};
-    uint64_t k_prev = s_key[tie_slot(i0)];
+    if (PACKED) {
+        // Words (code << pack_bits) | index.  Heads from the codes; only
+        // strings with a neighbour of equal code and all coded chars present
+        // can be longer than the code, and their not-exact bits are looked
+        // up, four loads in flight at a time.
+        const int pb = a.pack_bits;
+        const uint64_t imask = (1ull << pb) - 1;
+        uint32_t need = 0;
+        uint64_t kp = s_key[tie_slot(i0)] >> pb, kc = s_key[tie_slot(i0 + 1)] >> pb;
+#pragma unroll 4
+        for (int i = 0; i < kTieItems; ++i) {
+            const uint64_t j = j0 + i;
+            const uint64_t kn = s_key[tie_slot(i0 + i + 2)] >> pb;
+            const bool head = j == 0 || kc != kp;
+            const bool tied = j < n && (!head || (j + 1 < n && kn == kc));
+            heads |= (uint32_t)(j < n && head) << i;
+            if (tied && (kc & a.last_char_mask) != 0) need |= 1u << i;
+            kp = kc;
+            kc = kn;
+        }
 #pragma unroll
-    for (int i = 0; i < kTieItems; ++i) {
-        const uint64_t j = j0 + i;
-        if (j < n) {
-            const uint64_t k = s_key[tie_slot(i0 + i + 1)];
-            const uint32_t sg = SEGS ? a.segs[j] : 0;
-            const bool head = (j == 0) || k != k_prev || (SEGS && sg != seg_prev);
-            k_prev = k;
-            bool f;
-            if (MODE == kTieKeyFlag) f = (k & 1u) != 0;
-            else if (MODE == kTieValFlag) f = (a.vals[j] >> 31) != 0;
-            else f = window_tag(k) == cont_tag;
-            heads |= (uint32_t)head << i;
-            flagsb |= (uint32_t)f << i;
-            mine = combine(mine, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
-            seg_prev = sg;
+        for (int g = 0; g < kTieItems; g += 4) {
+            if (((need >> g) & 0xFu) == 0) continue;
+            uint32_t word[4], sh[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t idx = (uint32_t)(s_key[tie_slot(i0 + g + q + 1)] & imask);
+                sh[q] = idx & 31u;
+                word[q] = ((need >> (g + q)) & 1u) ? __ldg(&a.bits[idx >> 5]) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) flagsb |= ((word[q] >> sh[q]) & 1u) << (g + q);
+        }
+#pragma unroll
+        for (int i = 0; i < kTieItems; ++i)
+            if (j0 + i < n) mine = combine(mine, RunState{j0 + i, (heads >> i) & 1u, (flagsb >> i) & 1u});
+        // The permutation is the words' index fields in tile order:
+        // written with coalesced stores.
+        const int cnt = (int)umin64(kTieTile, n - t0);
+        for (int i = tid; i < cnt; i += kTieThreads) {
+            const uint64_t idx = s_key[tie_slot(i + 1)] & imask;
+            if (a.perm_u64)
+                static_cast<uint64_t *>(a.perm)[t0 + i] = idx;
+            else
+                static_cast<uint32_t *>(a.perm)[t0 + i] = (uint32_t)idx;
+        }
+    } else {
+        uint64_t k_prev = s_key[tie_slot(i0)];
+#pragma unroll
+        for (int i = 0; i < kTieItems; ++i) {
+            const uint64_t j = j0 + i;
+            if (j < n) {
+                const uint64_t k = s_key[tie_slot(i0 + i + 1)];
+                const uint32_t sg = SEGS ? a.segs[j] : 0;
+                const bool head = (j == 0) || k != k_prev || (SEGS && sg != seg_prev);
+                k_prev = k;
+                bool f;
+                if (MODE == kTieKeyFlag) f = (k & 1u) != 0;
+                else if (MODE == kTieValFlag) f = (a.vals[j] >> 31) != 0;
+                else f = window_tag(k) == cont_tag;
+                heads |= (uint32_t)head << i;
+                flagsb |= (uint32_t)f << i;
+                mine = combine(mine, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
+                seg_prev = sg;
+            }
         }
     }
 
@@ -242,7 +291,7 @@ tie_detect_kernel(const TieArgs a) {
             run_start = r.start + (st.last - a.run_base[sg]);
             depth = r.depth + 1;
         }
-        if (MODE != kTieKeyFlag) {
+        if (MODE == kTieValFlag || REFINE) {
             const uint32_t v = a.vals[j];
             const uint32_t out = REFINE ? v : (v & kIdxMask);
             if (a.perm_u64)
@@ -256,7 +305,9 @@ tie_detect_kernel(const TieArgs a) {
         } else if (jn >= n) {
             tail = true;
         } else {
-            tail = s_key[tie_slot(i0 + i + 2)] != s_key[tie_slot(i0 + i + 1)] || (SEGS && next_seg != a.segs[j]);
+            const int pb = PACKED ? a.pack_bits : 0;
+            tail = (s_key[tie_slot(i0 + i + 2)] >> pb) != (s_key[tie_slot(i0 + i + 1)] >> pb) ||
+                   (SEGS && next_seg != a.segs[j]);
         }
         if (tail) {
             const uint64_t len = j - st.last + 1;
@@ -684,6 +735,11 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
     switch (mode) {
         case kTieKeyFlag: tie_detect_kernel<kTieKeyFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
         case kTieValFlag: tie_detect_kernel<kTieValFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
+        case kTiePacked:
+            if (a.bits == nullptr || a.pack_bits <= 0 || a.pack_bits > 63 || a.segs != nullptr)
+                return cudaErrorInvalidValue;
+            tie_detect_kernel<kTiePacked><<<tiles, kTieThreads, kTieSmem, s>>>(a);
+            break;
         default: tie_detect_kernel<kTieRefine><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
     }
     return cudaGetLastError();

@@ -32,7 +32,8 @@ struct DevFlags {
     unsigned int alpha_hi;          // byte-range coder: largest byte of the strings
     unsigned int alpha_w, alpha_k;  // byte-range coder: bits per char and chars coded (written by the encoder)
     unsigned int alpha_spec_lo_inv, alpha_spec_hi;  // byte-range coder: the range a speculative encode used
-    unsigned int pad[6];
+    unsigned int idx_packed;        // byte-range coder: codes written as (code << idx_bits) | index
+    unsigned int pad[5];
 };
 
 // Run queue entry: a run of equal keys at positions [start, start + len)

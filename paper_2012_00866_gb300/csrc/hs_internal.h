@@ -24,6 +24,12 @@ struct EncPack {
     uint32_t *vals;
     const uint32_t *tile_seg;
     int spec_range;               // byte-range coder: use flags->alpha_spec_* (the range of a first chunk)
+    // Single sorts, byte-range coder: when 8w + idx_bits <= 64 the encoder
+    // writes (code << idx_bits) | (idx_base + i) -- the string's index below
+    // its code, no not-exact bit in the key (it goes to nonexact_bits) --
+    // and sets flags->idx_packed.  0: never.
+    int idx_bits;
+    uint64_t idx_base;            // index of the launch's first string
 };
 // tile_seg[t] for t = 0 .. ceil(n / 1024): the instance holding string
 // min(t * 1024, n - 1).
@@ -32,11 +38,12 @@ cudaError_t launch_tile_segs(const uint64_t *seg_offsets, uint64_t num_segs, uin
 // coder 3 (byte range): values from flags->alpha_lo_inv / alpha_hi; writes
 // alpha_w / alpha_k (keys of at most alpha_max_bits bits) and, when the range
 // needs more than alpha_max_w bits or 9 chars do not fit, encodes as ASCII7.
+// Digit histograms count the key without a packed index.
 cudaError_t launch_encode(int coder, bool key_flag, const uint8_t *bytes,
                           const uint64_t *offsets, uint64_t n, uint64_t *codes,
                           uint32_t *nonexact_bits, unsigned long long *hist,
                           DevFlags *flags, int num_sms, cudaStream_t s, int alpha_max_w = 6,
-                          int alpha_max_bits = 64, EncPack pack = EncPack{nullptr, 0, 0, nullptr, nullptr, 0});
+                          int alpha_max_bits = 64, EncPack pack = EncPack{});
 // Smallest / largest byte of bytes[offsets[0] .. offsets[n]) max-reduced into
 // flags->alpha_lo_inv (as 255 - min) and flags->alpha_hi; cut short once the
 // range is known to exceed max_span values.
@@ -71,6 +78,7 @@ struct OnesweepArgs {
     void *vals_out;
     const uint32_t *flag_bits;   // synthesised vals: bit 31 source (nullable)
     uint64_t n;
+    int pack_bits;               // > 0: elements are (key << pack_bits) | index, no vals
     int shift;                   // digit = (source >> shift) & mask
     unsigned mask;
     const unsigned long long *bucket_base;  // kBins entries for this pass
@@ -82,7 +90,10 @@ struct OnesweepArgs {
 
 // One stable LSD pass.  has_seg: elements carry a u32 segment id; digit_seg:
 // the digit comes from the segment id instead of the key; synth: vals are
-// generated as i | flag_bit(i) << 31; out: what vals_out receives.
+// generated as i | flag_bit(i) << 31; out: what vals_out receives.  With
+// a.pack_bits > 0 the keys are packed (key, index) words and nothing else
+// moves: kOutVals writes the words to keys_out, kOutPerm32/64 the indices
+// to vals_out.
 cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg,
                             bool digit_seg, bool synth, OutMode out,
                             cudaStream_t s);
@@ -146,13 +157,18 @@ constexpr uint32_t kMediumMax = 2048;  // block per run
 enum TieMode {
     kTieKeyFlag = 0,   // flag = key bit 0 (ASCII7 sort key); perm already written
     kTieValFlag = 1,   // flag = payload bit 31; perm[j] = payload & kIdxMask
-    kTieRefine = 2     // flag = window tag "continues"; perm[pos(j)] = payload
+    kTieRefine = 2,    // flag = window tag "continues"; perm[pos(j)] = payload
+    kTiePacked = 3     // keys are (code << pack_bits) | index; flag = bits[index], looked up
+                       // only where the code's last char is not padding; perm[j] = index
 };
 
 struct TieArgs {
     const uint64_t *keys;
     const uint32_t *segs;           // refinement run ids, or instance ids (batched); NULL otherwise
     const uint32_t *vals;
+    const uint32_t *bits;           // kTiePacked: not-exact bit of string i (bit i of word i/32)
+    int pack_bits;                  // kTiePacked: index bits below the code
+    uint64_t last_char_mask;        // kTiePacked: the code's last char (0: shorter string, exact)
     uint64_t n;
     int prefix_len;                 // bytes covered by the husky code
     void *perm;                     // output permutation

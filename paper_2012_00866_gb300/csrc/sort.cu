@@ -5,16 +5,18 @@
 //
 // Each pass is a single "onesweep" kernel (Adinets and Merrill, 2022): the
 // global digit offsets come from histograms computed up front (fused into the
-// encoder), each CTA ranks a tile of 4096 keys with warp-private digit
-// counters (lanes with equal digits found by a warp match), publishes its
-// per-digit counts, scatters the tile into shared memory in digit order,
-// resolves its global prefix by decoupled look-back over earlier tiles, and
-// writes the tile out so that runs of equal digits leave as coalesced
-// stores.  Digits are 9 bits wide (512 bins, one per thread in
-// the per-digit phase); 512 threads x 8 keys per CTA at <= 64 registers keep
-// two CTAs (32 warps) resident per SM.  Tile ids come from an atomic counter,
-// so every tile a CTA waits on is already running; each wait is bounded and
-// reports kErrTimeout.
+// encoder), each CTA ranks a tile of keys with warp-private digit counters
+// (lanes with equal digits found by a warp match), publishes its per-digit
+// counts, scatters the tile into shared memory in digit order, resolves its
+// global prefix by decoupled look-back over earlier tiles, and writes the
+// tile out so that runs of equal digits leave as coalesced stores.  Digits
+// are 9 bits wide (512 bins, one per thread in the per-digit phase); 512
+// threads at <= 64 registers keep two CTAs (32 warps) resident per SM, with
+// 12 keys a thread (8 when a segment id moves too).  The pairs are either a
+// 64-bit key plus a 32-bit payload or, when the code and the string index
+// fit one word together, that word alone.  Tile ids come from an atomic
+// counter, so every tile a CTA waits on is already running; each wait is
+// bounded and reports kErrTimeout.
 #include "hs_internal.h"
 
 namespace hs {
@@ -27,12 +29,17 @@ constexpr int kDpt = kBins / kThreads;         // digits per thread in the per-d
 constexpr int kMinBlocks = kSortMinBlocks;
 constexpr int kLbBatch = 4;                    // look-back words per digit per round trip
 // Per-item ranks among the warp's earlier items with the same digit are
-// below 32 * kItems; they are packed kRanksPerReg to a register.
-constexpr int kRankBits = 32 * kItems <= 256 ? 8 : 16;
-constexpr int kRanksPerReg = 32 / kRankBits;
-constexpr uint32_t kRankMask = (1u << kRankBits) - 1;
+// below 32 * items; they are packed 4 (8-bit) or 2 (16-bit) to a register.
 static_assert(kDpt >= 1 && kDpt * kThreads == kBins, "digits must spread evenly over the threads");
-static_assert(kItems % 4 == 0 && kItems * kThreads == kSortTile, "tile must be whole groups of four items");
+static_assert(kItems * kThreads == kSortTile, "tile must be whole threads");
+// Keys per thread by element layout.  Larger tiles mean fewer look-backs
+// per key; (key, index) pairs and packed words take 12 (6144-key tiles, two
+// CTAs per SM in shared memory); with a segment id as well a 6144-key tile
+// would leave one CTA per SM, so segmented passes keep 8.  Look-back words
+// are sized for kSortTile, the smallest tile.
+constexpr int kWideItems = 12;
+constexpr int items_for(bool has_seg) { return has_seg ? kItems : kWideItems; }
+static_assert(kWideItems * kThreads >= kSortTile, "look-back words are sized for tiles of kSortTile keys");
 
 // Exclusive scan of one u32 per thread over the block.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
@@ -52,14 +59,21 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return wsum + x - v;
 }
 
-template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT>
+// PACKED: each element is one word (key << pack_bits) | index; no payload
+// is loaded, staged or stored.  ITEMS keys per thread.
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED, int ITEMS>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 onesweep_kernel(const OnesweepArgs a) {
+    constexpr int TILE = kThreads * ITEMS;
+    constexpr int RBITS = 32 * ITEMS <= 256 ? 8 : 16;  // rank bits (ranks < 32 * ITEMS)
+    constexpr int RPR = 32 / RBITS;
+    constexpr uint32_t RMASK = (1u << (SYNTH ? RBITS - 1 : RBITS)) - 1;  // SYNTH: top bit is the flag
+    static_assert(ITEMS % 4 == 0, "tile must be whole groups of four items");
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + kSortTile);
-    uint32_t *s_segs = s_vals + kSortTile;
-    uint32_t *s_whist = s_segs + (HAS_SEG ? kSortTile : 0);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
+    uint32_t *s_segs = s_vals + (PACKED ? 0 : TILE);
+    uint32_t *s_whist = s_segs + (HAS_SEG ? TILE : 0);
     unsigned long long *s_gbase = reinterpret_cast<unsigned long long *>(s_whist + kWarps * kBins);
     __shared__ uint32_t s_scan[kWarps];
     __shared__ uint32_t s_tile;
@@ -71,31 +85,30 @@ onesweep_kernel(const OnesweepArgs a) {
     __syncthreads();
     const uint64_t tile = s_tile;
     const uint64_t n = a.n;
-    const uint64_t tile_base = tile * kSortTile;
+    const uint64_t tile_base = tile * TILE;
     const int shift = a.shift;
     const unsigned mask = a.mask;
 
-    // Warp-striped load: warp w owns elements [w*32*kItems, (w+1)*32*kItems)
-    // of the tile, item k of lane l is element w*32*kItems + k*32 + l, so
+    // Warp-striped load: warp w owns elements [w*32*ITEMS, (w+1)*32*ITEMS)
+    // of the tile, item k of lane l is element w*32*ITEMS + k*32 + l, so
     // processing items in k order visits the warp's elements in input order
-    // (stability).
-    uint64_t key[kItems];
-    uint32_t val[kItems];
-    uint32_t seg[kItems];
-    uint32_t rankp[kItems / kRanksPerReg] = {};
-    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * kItems;
+    // (stability).  Synthesised payloads (the element's own index) are made
+    // at the scatter instead of being held; their not-exact bit waits in the
+    // top bit of the item's 16-bit rank slot (ranks stay below 32 * ITEMS).
+    static_assert(!SYNTH || (RBITS == 16 && 32 * ITEMS < (1 << 15)), "synthesised flags ride in 16-bit rank slots");
+    uint64_t key[ITEMS];
+    uint32_t val[ITEMS];
+    uint32_t seg[ITEMS];
+    uint32_t rankp[ITEMS / RPR] = {};
+    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const uint64_t e = wbase + k * 32 + lane;
         const bool valid = e < n;
         key[k] = valid ? a.keys_in[e] : 0;
-        if (SYNTH) {
-            uint32_t bit = 0;
-            if (valid && a.flag_bits) bit = (a.flag_bits[e >> 5] >> lane) & 1u;
-            val[k] = (uint32_t)e | (bit << 31);
-        } else {
-            val[k] = valid ? a.vals_in[e] : 0;
-        }
+        val[k] = (PACKED || SYNTH || !valid) ? 0u : a.vals_in[e];
+        if (SYNTH && valid && a.flag_bits)
+            rankp[k / RPR] |= ((a.flag_bits[e >> 5] >> lane) & 1u) << (RBITS * (k % RPR) + RBITS - 1);
         seg[k] = (HAS_SEG && valid) ? a.segs_in[e] : 0;
     }
 
@@ -107,7 +120,7 @@ onesweep_kernel(const OnesweepArgs a) {
     // adds are broadcast to the groups last.
     uint32_t *my_hist = s_whist + warp * kBins;
 #pragma unroll
-    for (int g = 0; g < kItems; g += 4) {
+    for (int g = 0; g < ITEMS; g += 4) {
         unsigned peers[4], before[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -131,7 +144,7 @@ onesweep_kernel(const OnesweepArgs a) {
             const bool valid = wbase + k * 32 + lane < n;
             const int leader = valid ? __ffs(peers[q]) - 1 : lane;
             const unsigned b = __shfl_sync(kFull, before[q], leader);
-            rankp[k / kRanksPerReg] |= (b + __popc(peers[q] & lanemask_lt())) << (kRankBits * (k % kRanksPerReg));
+            rankp[k / RPR] |= (b + __popc(peers[q] & lanemask_lt())) << (RBITS * (k % RPR));
         }
     }
     __syncthreads();
@@ -180,14 +193,19 @@ onesweep_kernel(const OnesweepArgs a) {
     for (int j = 0; j < kDpt; ++j) s_dstart[tid * kDpt + j] = dstart[j];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const uint64_t e = wbase + k * 32 + lane;
         if (e < n) {
             const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-            const uint32_t r = (rankp[k / kRanksPerReg] >> (kRankBits * (k % kRanksPerReg))) & kRankMask;
+            const uint32_t r = (rankp[k / RPR] >> (RBITS * (k % RPR))) & RMASK;
             const uint32_t p = my_hist[d] + s_dstart[d] + r;
             s_keys[p] = key[k];
-            s_vals[p] = val[k];
+            if (SYNTH) {
+                const uint32_t bit = (rankp[k / RPR] >> (RBITS * (k % RPR) + RBITS - 1)) & 1u;
+                s_vals[p] = (uint32_t)e | (bit << 31);
+            } else if (!PACKED) {
+                s_vals[p] = val[k];
+            }
             if (HAS_SEG) s_segs[p] = seg[k];
         }
     }
@@ -258,7 +276,7 @@ onesweep_kernel(const OnesweepArgs a) {
         s_gbase[tid * kDpt + j] = a.bucket_base[tid * kDpt + j] + prefix[j] - dstart[j];
     __syncthreads();
 
-    const int cnt = (int)umin64(kSortTile, n - tile_base);
+    const int cnt = (int)umin64(TILE, n - tile_base);
     for (int i = tid; i < cnt; i += kThreads) {
         const uint64_t k = s_keys[i];
         const uint32_t sg = HAS_SEG ? s_segs[i] : 0;
@@ -266,6 +284,16 @@ onesweep_kernel(const OnesweepArgs a) {
         const uint64_t pos = s_gbase[d] + (uint64_t)i;
         if (pos >= n) {
             atomicOr(&a.flags->error, kErrInternal);
+            continue;
+        }
+        if (PACKED) {
+            const uint64_t idx = k & ((1ull << a.pack_bits) - 1);
+            if (OUT == kOutVals)
+                a.keys_out[pos] = k;
+            else if (OUT == kOutPerm32)
+                static_cast<uint32_t *>(a.vals_out)[pos] = (uint32_t)idx;
+            else
+                static_cast<uint64_t *>(a.vals_out)[pos] = idx;
             continue;
         }
         if (a.keys_out) a.keys_out[pos] = k;
@@ -280,22 +308,24 @@ onesweep_kernel(const OnesweepArgs a) {
     }
 }
 
-size_t onesweep_smem(bool has_seg) {
-    return (size_t)kSortTile * 8 + (size_t)kSortTile * 4 + (has_seg ? (size_t)kSortTile * 4 : 0) +
-           (size_t)kWarps * kBins * 4 + (size_t)kBins * 8;
+size_t onesweep_smem(bool has_seg, bool packed) {
+    const size_t tile = (size_t)kThreads * items_for(has_seg);
+    return tile * 8 + (packed ? 0 : tile * 4) + (has_seg ? tile * 4 : 0) + (size_t)kWarps * kBins * 4 +
+           (size_t)kBins * 8;
 }
 
-template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT>
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED = false>
 cudaError_t launch_os(const OnesweepArgs &a, cudaStream_t s) {
-    auto kern = onesweep_kernel<HAS_SEG, DIGIT_SEG, SYNTH, OUT>;
-    const size_t smem = onesweep_smem(HAS_SEG);
+    constexpr int items = items_for(HAS_SEG);
+    auto kern = onesweep_kernel<HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, items>;
+    const size_t smem = onesweep_smem(HAS_SEG, PACKED);
     static bool configured = false;  // attribute is per function, idempotent
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const uint64_t tiles = sort_tiles(a.n);
+    const uint64_t tiles = (a.n + kThreads * items - 1) / (kThreads * items);
     kern<<<(unsigned)tiles, kThreads, smem, s>>>(a);  // one CTA per tile
     return cudaGetLastError();
 }
@@ -413,6 +443,15 @@ __global__ void identity_kernel(const uint32_t *__restrict__ flag_bits, uint64_t
 cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg, bool digit_seg, bool synth,
                             OutMode out, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
+    if (a.pack_bits > 0) {
+        if (has_seg || digit_seg || synth || a.pack_bits > 63) return cudaErrorInvalidValue;
+        if (out == kOutVals && a.keys_out == nullptr) return cudaErrorInvalidValue;
+        switch (out) {
+            case kOutVals: return launch_os<false, false, false, kOutVals, true>(a, s);
+            case kOutPerm32: return launch_os<false, false, false, kOutPerm32, true>(a, s);
+            default: return launch_os<false, false, false, kOutPerm64, true>(a, s);
+        }
+    }
     if (has_seg) {
         if (synth || out == kOutPerm64) return cudaErrorInvalidValue;
         if (out == kOutPerm32)

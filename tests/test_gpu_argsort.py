@@ -419,3 +419,82 @@ def test_shutdown_then_sort_again(cuda_lib):
     assert_oracle_equal(w, hs.argsort(data, off))
     d_data, d_off = to_device(w)
     assert_oracle_equal(w, hs.argsort_device(d_data, d_off))
+
+
+# ---- packed (code, index) words ---------------------------------------------
+
+def _onesweep_bytes_per_key(hs, w, **kw):
+    """Sorts w and returns the onesweep passes' algorithmic bytes per key and
+    launch: 16 or less when the codes and indices travel as one word (the
+    fix-up's refinement sorts count there too: keep large mixed runs out)."""
+    data, off = to_device(w)
+    hs.stats_enable(True)
+    try:
+        perm = hs.argsort_device(data, off, **kw)
+        st = hs.stats_read().get("onesweep")
+    finally:
+        hs.stats_enable(False)
+    assert_oracle_equal(w, perm)
+    n = w.offsets.size - 1
+    return None if st is None else st["algo_bytes"] / (st["launches"] * n)
+
+
+@pytest.mark.parametrize("n", [5_000, 300_000])
+def test_packed_runs_mixing_exact_and_longer(cuda_lib, n):
+    """With the index packed below the code the not-exact bit is not in the
+    key, so one run of equal codes can hold 8-char strings and the longer
+    strings they begin; the 8-char ones must come first, each group in index
+    order.  Shorter strings (the code's last char is padding) and copies of
+    long strings are mixed in."""
+    hs = cuda_lib
+    rng = np.random.default_rng(n)
+    # runs of a few hundred: CTA-sized, so no refinement sort adds to the figure
+    stems = [bytes(rng.integers(97, 123, size=8).astype(np.uint8)) for _ in range(max(40, n // 750))]
+    strs = []
+    for _ in range(n):
+        s = stems[int(rng.integers(0, len(stems)))]
+        r = int(rng.integers(0, 4))
+        if r == 1:
+            s = s + bytes(rng.integers(97, 100, size=int(rng.integers(1, 4))).astype(np.uint8))
+        elif r == 2:
+            s = s[: int(rng.integers(0, 8))]
+        strs.append(s)
+    w = workloads.from_strings(strs)
+    assert _onesweep_bytes_per_key(hs, w) <= 16.0
+
+
+@pytest.mark.parametrize("n,packed", [(65_536, True), (65_537, False)])
+@pytest.mark.parametrize("index_u64", [False, True])
+def test_packed_index_width_boundary(cuda_lib, n, packed, index_u64):
+    """Asked for, a 58-value byte range codes at w = 6 (48-bit codes): 2^16 strings
+    still pack their 16-bit index below the code, one more does not and
+    sorts (key, index) pairs with the not-exact bit in the key."""
+    hs = cuda_lib
+    rng = np.random.default_rng(n)
+    lens = rng.integers(0, 14, size=n)
+    strs = [bytes(rng.integers(65, 123, size=int(m)).astype(np.uint8)) for m in lens]
+    strs[0] = b"A" * 3
+    strs[1] = b"z" * 12 + b"A"
+    w = workloads.from_strings(strs)
+    per_key = _onesweep_bytes_per_key(hs, w, index_u64=index_u64, coder=hs.CODER_ALPHA)
+    assert (per_key <= 16.0) == packed
+
+
+@pytest.mark.parametrize("case", ["perfect", "perfect_u64", "same_long", "same_short", "two"])
+def test_packed_degenerate(cuda_lib, case):
+    """Packed words when every string is exact (the last pass writes the
+    permutation), when all codes are equal (no pass runs), and at n = 2."""
+    hs = cuda_lib
+    rng = np.random.default_rng(11)
+    if case.startswith("perfect"):
+        strs = [bytes(rng.integers(97, 123, size=int(rng.integers(0, 9))).astype(np.uint8)) for _ in range(50_000)]
+    elif case == "same_long":
+        strs = [b"abcdefghijk"] * 9_000 + [b"abcdefghij"] * 5
+    elif case == "same_short":
+        strs = [b"abcd"] * 9_000
+    else:
+        strs = [b"bbbbbbbbb", b"bbbbbbbb"]
+    order = rng.permutation(len(strs))
+    w = workloads.from_strings([strs[i] for i in order])
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off, index_u64=case == "perfect_u64"))
