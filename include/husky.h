@@ -239,8 +239,9 @@ HS_API hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count);
 
 /* hs_shutdown -- release what the library keeps between calls: the copy
  * streams of hs_argsort_host (one per device it ran on), the pooled CUDA
- * events of the host hand-offs and of the per-kernel timing, and the timing
- * table (timing is switched off).  Call it with no library call in flight;
+ * events of the host hand-offs and of the per-kernel timing, the pooled
+ * pinned host buffers that receive the device-side control block, and the
+ * timing table (timing is switched off).  Call it with no library call in flight;
  * later calls recreate what they need.  The allocation-free entry point's
  * static scratch is part of the loaded image and is not released.
  * Safe to call without a GPU or twice; returns HS_OK (HS_ERR_CUDA if a

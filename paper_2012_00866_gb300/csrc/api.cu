@@ -218,6 +218,26 @@ void release_sync_events(std::vector<cudaEvent_t> &v) {
     v.clear();
 }
 
+// Pinned host copies of the control block: a device-to-host copy into
+// pageable memory is staged and blocking, into pinned memory it is one DMA.
+std::vector<DevFlags *> g_pinned_flags;
+
+cudaError_t pinned_flags(DevFlags **out) {
+    std::lock_guard<std::mutex> g(g_copy_mu);
+    if (!g_pinned_flags.empty()) {
+        *out = g_pinned_flags.back();
+        g_pinned_flags.pop_back();
+        return cudaSuccess;
+    }
+    return cudaHostAlloc(reinterpret_cast<void **>(out), sizeof(DevFlags), cudaHostAllocDefault);
+}
+
+void release_pinned_flags(DevFlags *p) {
+    if (p == nullptr) return;
+    std::lock_guard<std::mutex> g(g_copy_mu);
+    g_pinned_flags.push_back(p);
+}
+
 // Host source of hs_argsort_host: where the inputs are and where their
 // device copies go.
 struct HostSrc {
@@ -290,10 +310,25 @@ struct Ctx {
         return cudaSuccess;
     }
 
+    DevFlags *h_pinned = nullptr;  // staging for h
+    bool pinned_ok = true;         // may take a pinned buffer (not on the allocation-free path)
     cudaError_t read_flags() {
-        cudaError_t e = cudaMemcpyAsync(&h, d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaSuccess;
+        if (!pinned_ok) {
+            e = cudaMemcpyAsync(&h, d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return e;
+            return cudaStreamSynchronize(s);
+        }
+        if (!h_pinned && (e = pinned_flags(&h_pinned)) != cudaSuccess) {
+            h_pinned = nullptr;
+            return e;
+        }
+        e = cudaMemcpyAsync(h_pinned, d_flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return e;
-        return cudaStreamSynchronize(s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        h = *h_pinned;
+        return cudaSuccess;
     }
 
     // Launch through f(), bracketed by events when timing is enabled.
@@ -328,10 +363,9 @@ struct Ctx {
     }
     ~Ctx() {
         flush_stats();
-        if (!events.empty()) {
-            cudaStreamSynchronize(s);  // the waits on them have been passed
-            release_sync_events(events);
-        }
+        if (!events.empty() || h_pinned) cudaStreamSynchronize(s);  // no copy or wait still uses them
+        if (!events.empty()) release_sync_events(events);
+        release_pinned_flags(h_pinned);
     }
 };
 
@@ -1247,6 +1281,8 @@ hs_status hs_shutdown(void) {
         if (have_dev && cur >= 0) cudaSetDevice(cur);
         for (cudaEvent_t e : g_sync_events) ok &= cudaEventDestroy(e) == cudaSuccess;
         g_sync_events.clear();
+        for (DevFlags *p : g_pinned_flags) ok &= cudaFreeHost(p) == cudaSuccess;
+        g_pinned_flags.clear();
     }
     {
         std::lock_guard<std::mutex> g(g_stats.mu);
@@ -1408,7 +1444,8 @@ extern "C" hs_status hs_argsort_noalloc(const uint8_t *d_bytes, const uint64_t *
     if (st != HS_OK) return st;
     Ctx c;
     if (!make_ctx(c, ws, HS_NOALLOC_SCRATCH_BYTES, n, stream, &st)) return st;
-    c.timing = false;  // no event objects on this path
+    c.timing = false;      // no event objects on this path
+    c.pinned_ok = false;   // and no host allocation
     Input in{d_bytes, d_offsets, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
     return argsort_plain(c, in, coder);
 }
