@@ -70,6 +70,11 @@ typedef enum {
  *                    Section 4.3).  Order preserving only on bytes < 0x80.
  *   HS_CODER_BYTE8   bitWidth 8, maxLength 8, no mask: order preserving on
  *                    all bytes (this library's coder for arbitrary bytes).
+ *                    UTF-16 text passed as big-endian bytes sorts in
+ *                    code-unit order (a Java String's order), and this coder
+ *                    is then the Unicode coder of Section 4.3 (unicodeToLong:
+ *                    4 units x 16 bits) without its final >>> 1, which only
+ *                    served Java's signed long compare.
  *   HS_CODER_ALPHA   byte-range coder, generalising the 5-bit and 6-bit
  *                    letter codings of Section 3.2: with lo / hi the smallest
  *                    / largest byte of bytes[offsets[0] .. offsets[n]), byte
@@ -77,8 +82,10 @@ typedef enum {
  *                    w = ceil(log2(hi - lo + 2)) bits ('a'..'z': 5 bits,
  *                    'A'..'z': 6), for maxLength 8: a sort key of 8w + 1
  *                    bits.  Lowercase text: a 41-bit key, five 9-bit radix
- *                    passes where ASCII7 needs seven.  Order preserving on
- *                    all bytes; exact iff length <= 8.  Applies when the
+ *                    passes where ASCII7 needs seven (and, for up to
+ *                    2^(64 - 8w) strings, the code and the string's index
+ *                    share one 64-bit word through the sort).  Order
+ *                    preserving on all bytes; exact iff length <= 8.  Applies when the
  *                    range has at most 63 values (w <= 6), else
  *                    HS_ERR_CODER_DOMAIN.
  *   HS_CODER_AUTO    ALPHA when the range has at most 31 values (w <= 5, where

@@ -63,6 +63,10 @@ def _load():
         lib.oracle_string_to_long_mapped.argtypes = [vp, u64, ci, ci, vp]
         lib.oracle_alpha_params.restype = ci
         lib.oracle_alpha_params.argtypes = [vp, vp, u64, vp, vp, vp]
+        lib.oracle_units_to_long.restype = u64
+        lib.oracle_units_to_long.argtypes = [vp, u64, ci, ci, u64]
+        lib.oracle_unicode_to_long.restype = u64
+        lib.oracle_unicode_to_long.argtypes = [vp, u64]
         lib.oracle_encode_alpha.restype = ci
         lib.oracle_encode_alpha.argtypes = [vp, vp, u64, vp, vp, vp, vp, vp]
         _lib = lib
@@ -92,6 +96,20 @@ def ascii_to_long(s: bytes) -> int:
 def byte_to_long(s: bytes) -> int:
     """The byte coder: 8 bits x 8 chars, no mask."""
     return string_to_long(s, 8, 8, 0)
+
+
+def unicode_to_long(units) -> int:
+    """The paper's Unicode coder on one string of UTF-16 code units:
+    Algorithm 4 with 16 bits x 4 units, mask 0xFFFF, then >>> 1."""
+    buf = np.asarray(units, dtype=np.uint16) if len(units) else np.zeros(1, np.uint16)
+    return int(_load().oracle_unicode_to_long(_ptr(np.ascontiguousarray(buf)), len(units)))
+
+
+def units_to_long(units, max_length: int, bit_width: int, mask: int) -> int:
+    """Algorithm 4 over 16-bit chars."""
+    buf = np.asarray(units, dtype=np.uint16) if len(units) else np.zeros(1, np.uint16)
+    return int(_load().oracle_units_to_long(_ptr(np.ascontiguousarray(buf)), len(units), max_length,
+                                            bit_width, mask))
 
 
 def encode(data: np.ndarray, offsets: np.ndarray, coder: int = CODER_ASCII7):

@@ -8,6 +8,8 @@
  *
  * Contents
  *   oracle_string_to_long   Algorithm 4 (stringToLong), literally.
+ *   oracle_unicode_to_long  The Unicode coder (Section 4.3): Algorithm 4 over
+ *                           UTF-16 code units, 4 x 16 bits, then >>> 1.
  *   oracle_encode           Algorithms 2/3 (huskyEncode over an array, with
  *                           the per-element perfection test).
  *   oracle_stable_argsort   The result the whole method must reach: the stable
@@ -53,6 +55,35 @@ uint64_t oracle_string_to_long(const uint8_t *s, uint64_t len, int max_length,
     else
         result = result << shift;
     return result;
+}
+
+/* Algorithm 4 over 16-bit chars (a Java String's UTF-16 code units). */
+uint64_t oracle_units_to_long(const uint16_t *u, uint64_t len, int max_length,
+                              int bit_width, uint64_t mask)
+{
+    uint64_t length = len < (uint64_t)max_length ? len : (uint64_t)max_length;
+    uint64_t padding = (uint64_t)max_length - length;
+    uint64_t result = 0;
+    for (uint64_t i = 0; i < length; i++) {
+        uint64_t c = u[i];
+        if (mask != 0)
+            c = c & mask;
+        result = (result << bit_width) | c;
+    }
+    uint64_t shift = (uint64_t)bit_width * padding;
+    if (shift >= 64)
+        result = 0;
+    else
+        result = result << shift;
+    return result;
+}
+
+/* The paper's Unicode coder (Section 4.3, unicodeToLong and its constants):
+ * 16 bits x 64/16 = 4 code units with mask 0xFFFF, then an unsigned shift
+ * right by one so that Java's signed long compare keeps the order. */
+uint64_t oracle_unicode_to_long(const uint16_t *u, uint64_t len)
+{
+    return oracle_units_to_long(u, len, 64 / 16, 16, 0xFFFF) >> 1;
 }
 
 /* Coder constants (Section 4.3 "Constants" listing): ASCII uses 7 bits per

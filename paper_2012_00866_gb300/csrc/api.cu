@@ -37,12 +37,12 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet"};
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test"};
 
 struct StatsTable {
     std::mutex mu;
@@ -469,6 +469,12 @@ hs_status run_encode(Ctx &c, const uint8_t *bytes, const uint64_t *offsets, uint
                                             max_w, max_key_bits, pack);
                    }),
                    "encode");
+        if (pack.sorted_check)
+            HS_TRY(c.timed(kKSorted, 0.0, [&] {
+                       return launch_sorted_test(codes, ebits, n, kflag, pack.idx_bits, pack.pairs, pack.pairs_cap,
+                                                 c.d_flags, c.sms, c.s);
+                   }),
+                   "sorted test");
         if (hist)
             HS_TRY(c.timed(kKPlan, 8.0 * kBins * 16, [&] {
                        return launch_plan(c.at<unsigned long long>(c.L.hist), kKeyPasses, n,
@@ -767,10 +773,35 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
     while (idx_bits < 63 && (1ull << idx_bits) < n) ++idx_bits;
     EncPack pk{};
     pk.idx_bits = n >= 2 ? idx_bits : 0;
+    // Already-sorted inputs (the partially-sorted case the paper's appendix
+    // discusses, at its extreme): the encoder compares neighbours' order
+    // keys on the way, so an ordered input costs the encode, a comparison
+    // of the pairs it could not decide and the identity permutation.
+    pk.sorted_check = n >= 2 ? 1 : 0;
+    pk.pairs = b.keys[1];
+    pk.pairs_cap = n;
     hs_status st = run_encode(c, in.bytes, in.offsets, n, coder, b.keys[0], bits, true, true, &used, 64, pk);
     if (st != HS_OK) return st;
     in.prefix_len = coded_prefix(c, used);
     const OutMode pmode = in.perm_u64 ? kOutPerm64 : kOutPerm32;
+    if (pk.sorted_check && !c.h.descent && c.h.pairs <= pk.pairs_cap) {
+        if (c.h.pairs > 0) {
+            const uint64_t pairs = c.h.pairs;
+            HS_TRY(c.timed(kKPairs, 24.0 * pairs, [&] {
+                       return launch_pairs_ordered(in.bytes, in.offsets, b.keys[1], pairs, c.d_flags, c.sms, c.s);
+                   }),
+                   "pairs ordered");
+            HS_TRY(c.read_flags(), "pairs sync");
+            st = device_error_status(c.h);
+            if (st != HS_OK) return st;
+        }
+        if (!c.h.descent) {
+            HS_TRY(c.timed(kKIdentity, 4.0 * n, [&] { return launch_identity(nullptr, n, in.perm, pmode, c.s); }),
+                   "identity");
+            HS_TRY(c.read_flags(), "final sync");
+            return device_error_status(c.h);
+        }
+    }
     if (used == HS_CODER_ALPHA && c.idx_packed) {
         const bool perfect = c.h.nonexact == 0;
         int passes[kKeyPasses], np = 0;

@@ -471,6 +471,74 @@ cudaError_t launch_tile_segs(const uint64_t *seg_offsets, uint64_t num_segs, uin
     return cudaGetLastError();
 }
 
+// Sorted-input test over the keys the encoder wrote: each string's order
+// key (the key, or the code above a packed index) against its
+// predecessor's.  The key preserves the order, so a descent proves the input
+// unsorted; equal keys of strings that are not both exact leave the pair to a
+// full comparison.  Every tile first looks whether some tile has already
+// found a descent and stops if so, so an unsorted input costs about one wave.
+constexpr int kSortedThreads = 256;
+constexpr int kSortedItems = 4;
+
+__global__ void __launch_bounds__(kSortedThreads)
+sorted_test_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ nonexact_bits, uint64_t n,
+                   int flag_in_key_requested, int idx_bits, uint64_t *__restrict__ pairs, uint64_t pairs_cap,
+                   DevFlags *flags) {
+    constexpr int kTile = kSortedThreads * kSortedItems;
+    const int tid = threadIdx.x;
+    const bool packed = flags->idx_packed != 0;  // written by the encoder this call
+    const int sh = packed ? idx_bits : 0;
+    const bool flag_in_key = flag_in_key_requested && !packed;
+    const uint64_t tiles = (n + kTile - 1) / kTile;
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        if (__syncthreads_or(tid == 0 && *reinterpret_cast<volatile unsigned int *>(&flags->descent) != 0u)) return;
+        bool desc = false;
+        uint32_t cand = 0;
+#pragma unroll
+        for (int k = 0; k < kSortedItems; ++k) {
+            const uint64_t i = tile * kTile + (uint64_t)k * kSortedThreads + tid;  // pair (i - 1, i)
+            if (i == 0 || i >= n) continue;
+            const uint64_t va = keys[i - 1], vb = keys[i];
+            const uint64_t a = va >> sh, b = vb >> sh;
+            if (a > b) {
+                desc = true;
+            } else if (a == b) {
+                bool both_exact;
+                if (flag_in_key) {
+                    both_exact = ((va | vb) & 1u) == 0;
+                } else {
+                    const bool ea = ((nonexact_bits[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u) == 0;
+                    const bool eb = ((nonexact_bits[i >> 5] >> (i & 31)) & 1u) == 0;
+                    both_exact = ea && eb;
+                }
+                if (!both_exact) cand |= 1u << k;
+            }
+        }
+        if (__syncthreads_or(desc)) {
+            if (tid == 0) atomicOr(&flags->descent, 1u);
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < kSortedItems; ++k) {
+            if (!((cand >> k) & 1u)) continue;
+            const unsigned long long q = atomicAdd(&flags->pairs, 1ull);
+            if (q < pairs_cap) pairs[q] = tile * kTile + (uint64_t)k * kSortedThreads + tid - 1;
+        }
+    }
+}
+
+cudaError_t launch_sorted_test(const uint64_t *keys, const uint32_t *nonexact_bits, uint64_t n, bool flag_in_key,
+                               int idx_bits, uint64_t *pairs, uint64_t pairs_cap, DevFlags *flags, int num_sms,
+                               cudaStream_t s) {
+    if (n < 2) return cudaSuccess;
+    if (!flag_in_key && nonexact_bits == nullptr) return cudaErrorInvalidValue;
+    const uint64_t tiles = (n + kSortedThreads * kSortedItems - 1) / (kSortedThreads * kSortedItems);
+    const unsigned grid = (unsigned)umin64(tiles, (uint64_t)num_sms * 2);  // a small first wave
+    sorted_test_kernel<<<grid, kSortedThreads, 0, s>>>(keys, nonexact_bits, n, flag_in_key ? 1 : 0, idx_bits, pairs,
+                                                        pairs_cap, flags);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_alphabet(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int max_span,
                             DevFlags *flags, int num_sms, cudaStream_t s) {
     alphabet_kernel<<<(unsigned)num_sms * 4, kAlphaThreads, 0, s>>>(bytes, offsets, n, max_span, flags);

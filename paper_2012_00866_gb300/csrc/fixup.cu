@@ -729,6 +729,29 @@ __global__ void push_constant_runs_kernel(const RunEntry *__restrict__ runs, uin
 
 }  // namespace
 
+// Sorted-input test, second half: each queued adjacent pair (equal order
+// keys, not both exact) compared in full; any pair out of order makes the
+// input unsorted.
+__global__ void pairs_ordered_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                                     const uint64_t *__restrict__ pairs, uint64_t count, DevFlags *flags) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint64_t p = pairs[i];
+        const uint64_t a0 = offsets[p], a1 = offsets[p + 1], b1 = offsets[p + 2];
+        bad |= compare_from(bytes + a0, a1 - a0, bytes + a1, b1 - a1, 0) > 0;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags->descent, 1u);
+}
+
+cudaError_t launch_pairs_ordered(const uint8_t *bytes, const uint64_t *offsets, const uint64_t *pairs,
+                                 uint64_t count, DevFlags *flags, int num_sms, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((count + 255) / 256, (uint64_t)num_sms * 8);
+    pairs_ordered_kernel<<<grid, 256, 0, s>>>(bytes, offsets, pairs, count, flags);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     const unsigned tiles = (unsigned)((a.n + kTieTile - 1) / kTieTile);

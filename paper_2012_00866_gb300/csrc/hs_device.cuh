@@ -33,7 +33,9 @@ struct DevFlags {
     unsigned int alpha_w, alpha_k;  // byte-range coder: bits per char and chars coded (written by the encoder)
     unsigned int alpha_spec_lo_inv, alpha_spec_hi;  // byte-range coder: the range a speculative encode used
     unsigned int idx_packed;        // byte-range coder: codes written as (code << idx_bits) | index
-    unsigned int pad[5];
+    unsigned int descent;           // sorted-input test: some string is smaller than its predecessor
+    unsigned long long pairs;       // sorted-input test: adjacent pairs left to a full comparison
+    unsigned int pad[2];
 };
 
 // Run queue entry: a run of equal keys at positions [start, start + len)

@@ -30,7 +30,24 @@ struct EncPack {
     // and sets flags->idx_packed.  0: never.
     int idx_bits;
     uint64_t idx_base;            // index of the launch's first string
+    // Sorted-input test after the encode (single sorts): see launch_sorted_test.
+    int sorted_check;
+    uint64_t *pairs;
+    uint64_t pairs_cap;
 };
+// Sorted-input test over n encoded keys: flags->descent |= 1 if some key is
+// below its predecessor's (the code above a packed index when the encoder set
+// flags->idx_packed); otherwise the equal-key pairs not both exact (the
+// not-exact bit in the key when flag_in_key and unpacked, else in the bitmap)
+// are queued in pairs[] by the index of their first string, counted in
+// flags->pairs.
+cudaError_t launch_sorted_test(const uint64_t *keys, const uint32_t *nonexact_bits, uint64_t n, bool flag_in_key,
+                               int idx_bits, uint64_t *pairs, uint64_t pairs_cap, DevFlags *flags, int num_sms,
+                               cudaStream_t s);
+// flags->descent |= 1 if some queued pair i (strings pairs[i], pairs[i] + 1)
+// is out of order; count = flags->pairs as the host read it.
+cudaError_t launch_pairs_ordered(const uint8_t *bytes, const uint64_t *offsets, const uint64_t *pairs,
+                                 uint64_t count, DevFlags *flags, int num_sms, cudaStream_t s);
 // tile_seg[t] for t = 0 .. ceil(n / 1024): the instance holding string
 // min(t * 1024, n - 1).
 cudaError_t launch_tile_segs(const uint64_t *seg_offsets, uint64_t num_segs, uint64_t n, uint32_t *tile_seg,

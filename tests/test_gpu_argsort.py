@@ -498,3 +498,132 @@ def test_packed_degenerate(cuda_lib, case):
     w = workloads.from_strings([strs[i] for i in order])
     data, off = to_device(w)
     assert_oracle_equal(w, hs.argsort_device(data, off, index_u64=case == "perfect_u64"))
+
+
+# ---- UTF-16 strings (the paper's Unicode coder) ------------------------------
+
+def _utf16_units(rng, n):
+    """Code units from ASCII, Latin-1, CJK, surrogate and private-use ranges,
+    0..10 units long, with repeated strings and shared prefixes."""
+    ranges = [(0x20, 0x7F), (0xC0, 0x100), (0x4E00, 0xA000), (0xD800, 0xE000), (0xE000, 0x10000)]
+    out = []
+    for _ in range(n):
+        r = int(rng.integers(0, 10))
+        if r == 0 and out:
+            out.append(list(out[int(rng.integers(0, len(out)))]))
+            continue
+        u = []
+        for _k in range(int(rng.integers(0, 11))):
+            lo, hi = ranges[int(rng.integers(0, len(ranges)))]
+            u.append(int(rng.integers(lo, hi)))
+        if r == 1 and out:
+            u = out[int(rng.integers(0, len(out)))][:4] + u
+        out.append(u)
+    return out
+
+
+@pytest.mark.parametrize("n", [3_000, 200_000])
+def test_utf16_big_endian_code_unit_order(cuda_lib, n):
+    """UTF-16 strings passed as big-endian bytes: the byte coder's code is the
+    paper's Unicode code (4 x 16-bit units) before its >>> 1, which unsigned
+    keys do not need, and the permutation is the stable sort in code-unit
+    order (a Java String's order), checked against Python's sort of the unit
+    tuples as well as the oracle."""
+    hs = cuda_lib
+    rng = np.random.default_rng(n)
+    units = _utf16_units(rng, n)
+    w = workloads.from_strings([b"".join(x.to_bytes(2, "big") for x in u) for u in units])
+    data, off = to_device(w)
+    codes, _, coder = hs.encode(data, off, coder=hs.CODER_BYTE8)
+    assert coder == hs.CODER_BYTE8
+    got = codes.cpu().numpy().view(np.uint64)
+    for i in range(0, n, max(1, n // 3000)):
+        assert int(got[i]) >> 1 == oracle.unicode_to_long(units[i])
+    p = hs.argsort_device(data, off)
+    assert list(perm_numpy(p)) == sorted(range(n), key=lambda i: units[i])
+    assert_oracle_equal(w, p)
+
+
+# ---- already-sorted inputs ----------------------------------------------------
+
+def _strings(w):
+    return [w.bytes[int(w.offsets[i]):int(w.offsets[i + 1])].tobytes() for i in range(w.offsets.size - 1)]
+
+
+def _sorted_strings(kind, n, seed):
+    w0 = workloads.generate(kind, n, seed)
+    s = _strings(w0)
+    return [s[i] for i in oracle.stable_argsort(w0.bytes, w0.offsets)]
+
+
+def _launches(st, kind):
+    return st.get(kind, {}).get("launches", 0)
+
+
+def _sort_with_stats(hs, fn):
+    hs.stats_enable(True)
+    try:
+        perm = fn()
+        st = hs.stats_read()
+    finally:
+        hs.stats_enable(False)
+    return perm, st
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 5])
+@pytest.mark.parametrize("index_u64", [False, True])
+def test_sorted_input_short_circuits(cuda_lib, kind, index_u64):
+    """An input already in order (its ties in index order) is recognised
+    during the encode: no radix pass runs and the permutation is the
+    identity.  Sorted shared-prefix strings have equal codes throughout and
+    go through the pair comparison."""
+    hs = cuda_lib
+    w = workloads.from_strings(_sorted_strings(kind, 200_003, 40 + kind))
+    data, off = to_device(w)
+    perm, st = _sort_with_stats(hs, lambda: hs.argsort_device(data, off, index_u64=index_u64))
+    assert _launches(st, "onesweep") == 0 and _launches(st, "identity") == 1
+    assert np.array_equal(perm_numpy(perm), np.arange(w.offsets.size - 1, dtype=perm_numpy(perm).dtype))
+    assert_oracle_equal(w, perm)
+
+
+@pytest.mark.parametrize("where", ["inside", "tile_boundary", "second_tile_boundary", "last", "equal_code"])
+def test_one_inversion_in_sorted_input(cuda_lib, where):
+    """A sorted input with one adjacent pair swapped is sorted in full, wherever
+    the pair falls: inside an encoder tile, across a tile boundary, at the
+    end, or as two strings with equal codes that only the full comparison
+    tells apart."""
+    hs = cuda_lib
+    strs = _sorted_strings(2, 300_000, 77)
+    if where == "equal_code":
+        strs = sorted(set(strs) | {b"abcdefghij", b"abcdefghik", b"abcdefgh"})
+        i = strs.index(b"abcdefghij")
+    else:
+        i = {"inside": 5_000, "tile_boundary": 1_023, "second_tile_boundary": 2_047,
+             "last": len(strs) - 2}[where]
+        while strs[i] == strs[i + 1]:
+            i -= 1
+    strs[i], strs[i + 1] = strs[i + 1], strs[i]
+    w = workloads.from_strings(strs)
+    data, off = to_device(w)
+    perm, st = _sort_with_stats(hs, lambda: hs.argsort_device(data, off))
+    assert _launches(st, "onesweep") > 0
+    assert_oracle_equal(w, perm)
+
+
+@pytest.mark.parametrize("swap", [None, 262_143, 600_000])
+def test_sorted_input_through_host_entry_point(cuda_lib, swap):
+    """Host inputs arrive in chunks of 262,144 strings, each encoded as it
+    lands; the test of a chunk's first string against the previous chunk's
+    last must see an inversion placed exactly there."""
+    hs = cuda_lib
+    import torch
+    strs = _sorted_strings(1, 1_000_003, 91)  # random lowercase: neighbours differ
+    if swap is not None:
+        assert strs[swap] != strs[swap + 1]
+        strs[swap], strs[swap + 1] = strs[swap + 1], strs[swap]
+    w = workloads.from_strings(strs)
+    data = torch.from_numpy(w.bytes).pin_memory()
+    off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+    perm, st = _sort_with_stats(hs, lambda: hs.argsort(data, off))
+    assert (_launches(st, "onesweep") == 0) == (swap is None)
+    assert_oracle_equal(w, perm)

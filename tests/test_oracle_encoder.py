@@ -178,3 +178,48 @@ def test_alpha_truncation_and_nul():
 def _ws(strs):
     wl = workloads.from_strings(strs)
     return wl.bytes, wl.offsets
+
+
+# ---- the Unicode coder (Section 4.3 unicodeToLong) -------------------------
+
+def test_unicode_hand_worked_codes():
+    """Worked by hand: units packed 16 bits each, most significant first,
+    zero-padded to four, then shifted right by one."""
+    assert oracle.unicode_to_long([]) == 0
+    assert oracle.unicode_to_long([0x0041, 0x4E2D]) == 0x0020A71680000000
+    assert oracle.unicode_to_long([0xFFFF] * 4) == 0x7FFFFFFFFFFFFFFF
+    assert oracle.unicode_to_long([1, 2, 3, 4, 5]) == 0x0000800100018002  # 0x0001000200030004 >>> 1
+
+
+UNITS = [0x0000, 0x0041, 0x00E9, 0x7FFF, 0x8000, 0xD800, 0xFFFF]
+
+
+def test_unicode_order_property_pairwise():
+    """a < b in code-unit order implies code(a) <= code(b), and code(a) <
+    code(b) implies a < b, over every string of 0..3 units from a set with
+    surrogate and high units; the >>> 1 only merges neighbours."""
+    strs = [list(t) for L in range(4) for t in itertools.product(UNITS, repeat=L)]
+    codes = [oracle.unicode_to_long(s) for s in strs]
+    for (a, ca), (b, cb) in itertools.product(zip(strs, codes), repeat=2):
+        if a < b:
+            assert ca <= cb
+        if ca < cb:
+            assert a < b
+
+
+def test_unicode_shift_merges_only_the_last_bit():
+    """The shift loses the low bit of the fourth unit and nothing else."""
+    assert oracle.unicode_to_long([7, 7, 7, 0x100]) == oracle.unicode_to_long([7, 7, 7, 0x101])
+    assert oracle.unicode_to_long([7, 7, 7, 0x100]) < oracle.unicode_to_long([7, 7, 7, 0x102])
+    assert oracle.unicode_to_long([7, 7, 6, 0xFFFF]) < oracle.unicode_to_long([7, 7, 7, 0])
+
+
+def test_unicode_coder_is_the_byte_coder_on_big_endian_bytes():
+    """On the UTF-16BE bytes of a string the byte coder (8 bits x 8) packs the
+    same four units; the Unicode code is that code shifted right by one."""
+    rng = np.random.default_rng(5)
+    for _ in range(2000):
+        u = [int(x) for x in rng.integers(0, 65536, size=int(rng.integers(0, 7)))]
+        be = b"".join(x.to_bytes(2, "big") for x in u)
+        assert oracle.byte_to_long(be) >> 1 == oracle.unicode_to_long(u)
+        assert oracle.byte_to_long(be) == oracle.units_to_long(u, 4, 16, 0xFFFF)
