@@ -37,12 +37,12 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKCopies, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test"};
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test", "copies_filter"};
 
 struct StatsTable {
     std::mutex mu;
@@ -650,6 +650,13 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     const double isz = in.perm_u64 ? 8.0 : 4.0;
     auto launch_med_small = [&](uint64_t med0, uint64_t small0, bool known) -> hs_status {
         const uint64_t med = c.h.qcount[kQMedium], sm = c.h.qcount[kQSmall];
+        if (!known)
+            HS_TRY(c.timed(kKCopies, 0.0, [&] {
+                       return launch_copies_filter(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
+                                                   &c.d_flags->qcount[kQMedium], c.L.cap_medium, n, inst,
+                                                   in.prefix_len, c.sms, c.s);
+                   }),
+                   "copies filter");
         if (!known || med > med0)
             HS_TRY(c.timed(kKMediumRuns, known ? (double)(med - med0) * 16.0 * (2 * isz + 16.0) : 0.0, [&] {
                        return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,

@@ -491,7 +491,9 @@ sorted_test_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict
     const bool flag_in_key = flag_in_key_requested && !packed;
     const uint64_t tiles = (n + kTile - 1) / kTile;
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        if (__syncthreads_or(tid == 0 && *reinterpret_cast<volatile unsigned int *>(&flags->descent) != 0u)) return;
+        if (tile != blockIdx.x &&  // a block's first tile does not wait for the flag
+            __syncthreads_or(tid == 0 && *reinterpret_cast<volatile unsigned int *>(&flags->descent) != 0u))
+            return;
         bool desc = false;
         uint32_t cand = 0;
 #pragma unroll

@@ -382,10 +382,12 @@ __device__ __forceinline__ bool member_equals_first(const uint8_t *bytes, const 
                                                     const IdxT *perm, const RunEntry &e, uint64_t base,
                                                     uint64_t j, int prefix_len) {
     const uint64_t g0 = base + perm[e.start];
-    const uint64_t o0 = offsets[g0], l0 = offsets[g0 + 1] - o0;
     const uint64_t g = base + perm[e.start + j];
-    const uint64_t off = offsets[g];
-    return equal_from(bytes + off, offsets[g + 1] - off, bytes + o0, l0, min(window_offset(prefix_len, e.depth), l0));
+    const uint64_t o0 = offsets[g0], l0 = offsets[g0 + 1] - o0;
+    const uint64_t off = offsets[g], len = offsets[g + 1] - off;
+    const uint64_t from = min(window_offset(prefix_len, e.depth), l0);
+    return len == l0 && same_from(bytes + off, bytes + o0, l0, from, suffix_word(bytes + off, l0, from),
+                                  suffix_word(bytes + o0, l0, from));
 }
 
 __device__ __forceinline__ bool odd_run(const RunEntry &e, uint64_t perm_n) {
@@ -484,6 +486,58 @@ distinct_full_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restri
     }
 }
 
+// ---- copies filter for CTA-sized runs ----------------------------------------
+//
+// A run whose members are all copies of one string is final already (the
+// stable code sort kept them in index order).  A CTA of 512 per run compares
+// every member with the first: each thread's four members and the first have
+// their index, offset and byte loads issued together (three round trips a
+// run), and a run of copies gets length 0 so that the sorting
+// kernel passes over it.  The sorting kernel keeps its own test for the runs
+// that arrive later, from refinement.
+
+constexpr int kCopiesThreads = 512;
+constexpr int kCopiesPer = kMediumMax / kCopiesThreads;  // members a thread checks
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kCopiesThreads)
+copies_filter_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                     const IdxT *__restrict__ perm, RunEntry *__restrict__ q,
+                     const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n, Instances inst,
+                     int prefix_len) {
+    static_assert(kCopiesPer * kCopiesThreads == kMediumMax, "a thread's members must cover the class");
+    const int tid = threadIdx.x;
+    const uint64_t count = umin64(*qcount, cap);
+    for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
+        const RunEntry e = q[r];
+        if (odd_run(e, perm_n) || e.len > (uint32_t)kMediumMax) continue;  // uniform over the CTA
+        const uint64_t base = instance_base(inst, e.start);
+        uint64_t g[kCopiesPer + 1];  // g[0]: the first member
+        g[0] = base + perm[e.start];
+#pragma unroll
+        for (int u = 0; u < kCopiesPer; ++u) {
+            const uint32_t j = (uint32_t)(u * kCopiesThreads + tid);
+            g[u + 1] = j < e.len ? base + perm[e.start + j] : ~0ull;
+        }
+        uint64_t off[kCopiesPer + 1], len[kCopiesPer + 1];
+#pragma unroll
+        for (int u = 0; u <= kCopiesPer; ++u) {
+            const uint64_t gg = g[u] == ~0ull ? g[0] : g[u];
+            off[u] = offsets[gg];
+            len[u] = offsets[gg + 1] - off[u];
+        }
+        const uint64_t l0 = len[0], from = min(window_offset(prefix_len, e.depth), l0);
+        uint64_t w[kCopiesPer + 1];
+#pragma unroll
+        for (int u = 0; u <= kCopiesPer; ++u) w[u] = suffix_word(bytes + off[u], l0, from);
+        bool eq = true;
+#pragma unroll
+        for (int u = 1; u <= kCopiesPer; ++u)
+            eq &= len[u] == l0 && same_from(bytes + off[u], bytes + off[0], l0, from, w[u], w[0]);
+        if (__syncthreads_and(eq) && tid == 0) q[r].len = 0;
+    }
+}
+
 // ---- 33..2048: CTA per run ---------------------------------------------------
 
 constexpr int kMedThreads = 512;
@@ -515,7 +569,8 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
 
     for (uint64_t r = first + blockIdx.x; r < count; r += gridDim.x) {
         const RunEntry e = q[r];
-        if (e.len > (uint32_t)CAP || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
+        // length 0: copies of one string (marked by the copies filter)
+        if (e.len < 2 || e.len > (uint32_t)CAP || e.start >= perm_n || e.len > perm_n - e.start) continue;
         const int len = (int)e.len;
         const uint64_t base = instance_base(inst, e.start);
         int P = 1;
@@ -814,6 +869,19 @@ cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets, vo
     else
         medium_runs_kernel<uint32_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm),
                                                                   q, qcount, first, cap, perm_n, inst, prefix_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copies_filter(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                                 RunEntry *q, const unsigned long long *qcount, uint64_t cap, uint64_t perm_n,
+                                 Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
+    const unsigned grid = (unsigned)num_sms * 8;
+    if (perm_u64)
+        copies_filter_kernel<uint64_t><<<grid, kCopiesThreads, 0, s>>>(bytes, offsets, static_cast<const uint64_t *>(perm),
+                                                                       q, qcount, cap, perm_n, inst, prefix_len);
+    else
+        copies_filter_kernel<uint32_t><<<grid, kCopiesThreads, 0, s>>>(bytes, offsets, static_cast<const uint32_t *>(perm),
+                                                                       q, qcount, cap, perm_n, inst, prefix_len);
     return cudaGetLastError();
 }
 

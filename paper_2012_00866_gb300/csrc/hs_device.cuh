@@ -162,6 +162,26 @@ __device__ __forceinline__ bool equal_from(const uint8_t *a, uint64_t la, const 
     return true;
 }
 
+// Bytes [from, min(len, from + 8)) of a string as a little-endian word, each
+// loaded independently (no chain of early exits).
+__device__ __forceinline__ uint64_t suffix_word(const uint8_t *s, uint64_t len, uint64_t from) {
+    uint64_t x = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (from + k < len) x |= (uint64_t)s[from + k] << (8 * k);
+    return x;
+}
+
+// Two strings of length len agree on [from, len), given their suffix words
+// (bytes from .. from + 7); the rest is compared bytewise.
+__device__ __forceinline__ bool same_from(const uint8_t *a, const uint8_t *b, uint64_t len, uint64_t from,
+                                          uint64_t wa, uint64_t wb) {
+    if (wa != wb) return false;
+    for (uint64_t i = from + 8; i < len; ++i)
+        if (a[i] != b[i]) return false;
+    return true;
+}
+
 __device__ __forceinline__ int compare_from(const uint8_t *a, uint64_t la,
                                             const uint8_t *b, uint64_t lb,
                                             uint64_t from) {

@@ -221,6 +221,12 @@ cudaError_t launch_distinct_large(const uint8_t *bytes, const uint64_t *offsets,
                                   unsigned long long *base, RunEntry *q_out, unsigned long long *qcount_out,
                                   uint64_t cap_out, DevFlags *flags, unsigned int *done2, int num_sms,
                                   cudaStream_t s);
+// Runs of q[0 .. min(*qcount, cap)) (CTA-sized) whose members are all copies
+// of one string get length 0, which launch_medium_runs skips.
+cudaError_t launch_copies_filter(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                                 RunEntry *q, const unsigned long long *qcount, uint64_t cap, uint64_t perm_n,
+                                 Instances inst, int prefix_len, int num_sms, cudaStream_t s);
+
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
                                void *perm, int perm_u64, const RunEntry *q,
                                const unsigned long long *qcount, uint64_t first, uint64_t cap,
