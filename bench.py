@@ -43,7 +43,8 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                   help="one of workloads.STANDARD (batched_* use hs_argsort_batched)")
+                   help="one of workloads.STANDARD (batched_* use hs_argsort_batched) or NUMERIC "
+                        "(arrays sorted by hs_argsort_numeric)")
     p.add_argument("--scale", type=float, default=1.0, help="scale the workload's size")
     p.add_argument("--mode", default="plain", choices=["plain", "learned", "loop"],
                    help="loop: a batched workload sorted one instance at a time with hs_argsort")
@@ -393,6 +394,146 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---- numeric workloads: hs_argsort_numeric --------------------------------------
+
+# name: (type, n, seed).  f64: normal values over many decades with 1% of
+# +-0, +-infinity, NaN and subnormals; datetime: ns instants over 1900..2100
+# with repeats; i32: full-range integers.
+NUMERIC = {"f64_1e8": ("f64", 100_000_000, 11), "datetime_1e8": ("datetime", 100_000_000, 12),
+           "i32_1e8": ("i32", 100_000_000, 13)}
+
+
+def numeric_values(name, scale):
+    kind, n, seed = NUMERIC[name]
+    n = max(2, int(n * scale))
+    rng = np.random.default_rng(seed)
+    if kind == "f64":
+        v = rng.standard_normal(n) * 10.0 ** rng.integers(-300, 300, size=n)
+        pick = rng.random(n) < 0.01
+        v[pick] = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324])[rng.integers(0, 6, size=int(pick.sum()))]
+        return v, 3
+    if kind == "datetime":
+        v = rng.integers(-70 * 365 * 86400 * 10**9, 130 * 365 * 86400 * 10**9, size=n, dtype=np.int64)
+        rep = rng.random(n) < 0.3
+        v[rep] = v[rng.integers(0, n, size=int(rep.sum()))]
+        return v, 5
+    return rng.integers(-(1 << 31), 1 << 31, size=n, dtype=np.int64).astype(np.int32), 2
+
+
+def run_numeric(args, rank, world, local):
+    import torch
+    import paper_2012_00866_gb300 as hs
+
+    dist_init(world, local)
+    device = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(device)
+    hs.load()
+    v, t = numeric_values(args.workload, args.scale)
+    n = v.size
+    index_u64 = args.index == "u64"
+    x = torch.from_numpy(v).to(device)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        return hs.argsort_numeric(x, type=t, index_u64=index_u64)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(device).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+
+    def timed_steps():
+        out = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out
+
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(device)
+    step_ms = timed_steps()
+    torch.cuda.synchronize(device)
+    barrier(world)
+    clock_info = clocks.stop()
+    hs.stats_enable(True)
+    timed_steps()
+    torch.cuda.synchronize(device)
+    kstats = hs.stats_read()
+    hs.stats_enable(False)
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, device)
+    value = job_throughput(n, world, ms)
+
+    # end to end through the public call: pinned host values in, host permutation out
+    h_vals = torch.from_numpy(v).pin_memory()
+    h_perm = torch.empty(n, dtype=torch.int64 if index_u64 else torch.int32).pin_memory()
+    for _ in range(2):
+        h_perm.copy_(hs.argsort_numeric(h_vals.to(device, non_blocking=True), type=t, index_u64=index_u64))
+    torch.cuda.synchronize(device)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        h_perm.copy_(hs.argsort_numeric(h_vals.to(device, non_blocking=True), type=t, index_u64=index_u64))
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, device)
+    e2e = {"value": round(n * world / (e2e_t / 1e3) / 1e6, 3), "unit": UNIT,
+           "h2d_bytes_per_step": int(v.nbytes), "d2h_bytes_per_step": int(n * (8 if index_u64 else 4)),
+           "ms_per_step": round(e2e_t, 3)}
+
+    peaks, peak_src = measured_peaks()
+    timed = {k: s for k, s in kstats.items() if s["launches"] and s["total_ms"] > 0}
+    top = max(timed, key=lambda k: timed[k]["total_ms"])
+    st = timed[top]
+    achieved = st["algo_bytes"] / (st["total_ms"] / 1e3) / 1e9
+    roofline = {"kernel": top + "_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algo_bytes_per_launch": st["algo_bytes"] / st["launches"],
+                "launch_ms": round(st["total_ms"] / st["launches"], 5),
+                "share_of_step": round(st["total_ms"] / args.steps / ms, 3), "traffic": None}
+    stages = {k: {"launches_per_step": s["launches"] / args.steps, "ms_per_step": round(s["total_ms"] / args.steps, 4),
+                  "GBps": round(s["algo_bytes"] / (s["total_ms"] / 1e3) / 1e9, 1) if s["total_ms"] > 0 else None}
+              for k, s in kstats.items() if s["launches"]}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        m = min(n, CPU_SAMPLE_MAX)
+        t0 = time.perf_counter()
+        oracle.numeric_argsort(v[:m], t)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(m / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {m} values of {args.workload}, one run, numpy stable sort (one thread)"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload + (f"@{args.scale:g}" if args.scale != 1.0 else ""), "n": n,
+                       "index": "u64" if index_u64 else "u32", "coder": f"numeric({NUMERIC[args.workload][0]})",
+                       "l2": "flushed by a 256 MiB write before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": e2e, "gpu_launches": int(sum(s["launches"] for s in kstats.values())),
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clock_info, "stages": stages}), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ---- reference arm: the oracle on the host cores --------------------------------
 
 def run_reference(args, rank, world, local):
@@ -400,6 +541,29 @@ def run_reference(args, rank, world, local):
         return
     import oracle
     import workloads
+    threads = os.cpu_count() or 1
+    if args.workload in NUMERIC:
+        v, t = numeric_values(args.workload, args.scale)
+        m = min(v.size, CPU_SAMPLE_MAX)
+        times = []
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.numeric_argsort(v[:m], t)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        ms = sum(times) / len(times) * 1e3
+        value = m / (ms / 1e3) / 1e6
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload + (f"@{args.scale:g}" if args.scale != 1.0 else ""), "n": int(v.size),
+                       "mode": "oracle", "index": "u32", "parallelism": "host (numpy, one thread)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the first {m} values of {args.workload} each step"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+            flush=True)
+        return
     w = workloads.standard(args.workload, scale=args.scale)
     full_n = w.n
     if w.seg_offsets is not None:   # batched: the leading instances up to the sample bound
@@ -414,7 +578,6 @@ def run_reference(args, rank, world, local):
         sw = _sample(w, CPU_SAMPLE_MAX)
         sort = lambda: oracle.stable_argsort(sw.bytes, sw.offsets, threads=threads)
         n = sw.n
-    threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         sort()
     times = []
@@ -445,6 +608,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world, local)
+    elif args.workload in NUMERIC:
+        run_numeric(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -254,6 +254,54 @@ HS_API hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count);
  * Safe to call without a GPU or twice; returns HS_OK (HS_ERR_CUDA if a
  * destroy call failed; the rest is still released). */
 HS_API hs_status hs_shutdown(void);
+/* Numeric coders.  Section 5 benchmarks Huskysort on Integer, Long and
+ * Double arrays and Section 3.2 names a perfect coding for date-times (one
+ * nanosecond over 128 years fits 64 bits); the paper gives no bit layout for
+ * them.  Each value is coded here as an unsigned 64-bit key whose order is the
+ * values' order (Java's compareTo for each type), distinct values getting
+ * distinct keys: a perfect coding, so Step 3 never runs.
+ *   HS_NUM_U64       uint64: the value itself.
+ *   HS_NUM_I64       int64 (two's complement): value XOR 2^63.
+ *   HS_NUM_I32       int32: (value XOR 2^31) in the low 32 bits.
+ *   HS_NUM_F64       IEEE 754 binary64, as Double.compare orders it: every
+ *                    NaN is first replaced by the canonical quiet NaN
+ *                    0x7FF8000000000000 (all NaNs equal, above +infinity),
+ *                    then a value with the sign bit set is complemented and
+ *                    any other gets the sign bit set (so -0.0 < 0.0).
+ *   HS_NUM_F32       IEEE 754 binary32 the same way (canonical NaN
+ *                    0x7FC00000), in the low 32 bits.
+ *   HS_NUM_DATETIME  int64 nanoseconds from the epoch (a date-time as
+ *                    epoch second * 10^9 + nanosecond; about +-292 years
+ *                    around 1970), coded as HS_NUM_I64.
+ * 32-bit types leave the top 32 key bits zero, so their sort needs four
+ * radix passes instead of eight. */
+typedef enum {
+    HS_NUM_U64 = 0,
+    HS_NUM_I64 = 1,
+    HS_NUM_I32 = 2,
+    HS_NUM_F64 = 3,
+    HS_NUM_F32 = 4,
+    HS_NUM_DATETIME = 5
+} hs_numeric;
+
+/* Codes of n values (device, 8 bytes each, 4 for HS_NUM_I32 / HS_NUM_F32)
+ * into d_codes (device, n uint64).  No workspace; asynchronous on stream.
+ * HS_ERR_INVALID_ARG for a bad type or a NULL pointer with n > 0. */
+HS_API hs_status hs_encode_numeric(const void *d_values, uint64_t n, int type,
+                                   uint64_t *d_codes, void *stream);
+
+/* Workspace needed by hs_argsort_numeric for n values. */
+HS_API hs_status hs_numeric_workspace_size(uint64_t n, int out_t, size_t *out);
+
+/* Stable argsort of n numeric values (device) by the order above: d_perm[k]
+ * (device, uint32 or uint64 by out_t) is the index of the k-th smallest
+ * value, equal values in index order.  The codes are sorted by the same
+ * radix passes as the string codes; the last pass writes the permutation.
+ * 0 <= n <= HS_MAX_N; workspace and stream as in hs_argsort. */
+HS_API hs_status hs_argsort_numeric(const void *d_values, uint64_t n, int type,
+                                    int out_t, void *d_perm, void *d_ws,
+                                    size_t ws_bytes, void *stream);
+
 /* Message describing the calling thread's last failure ("" if none).  The
  * pointer stays valid until the next library call on this thread. */
 HS_API const char *hs_last_error(void);

@@ -214,3 +214,49 @@ def check_sorted_batched(data: np.ndarray, offsets: np.ndarray, seg_offsets: np.
 
 def string_compare(data: np.ndarray, offsets: np.ndarray, i: int, j: int) -> int:
     return int(_load().oracle_string_compare(_ptr(data), _ptr(offsets), i, j))
+
+
+# ---- numeric coders ---------------------------------------------------------
+#
+# The paper benchmarks Integer, Long and Double arrays (Section 5) and names a
+# perfect date-time coding (Section 3.2) without giving bit layouts.  Two
+# plain definitions serve as the oracle: the order itself, written from each
+# type's compareTo semantics (integers by value; doubles as Double.compare:
+# NaN equal to NaN and above everything, -0.0 below 0.0), and the code of each
+# value written from the two's complement and IEEE 754 layouts.
+
+NUM_U64, NUM_I64, NUM_I32, NUM_F64, NUM_F32, NUM_DATETIME = 0, 1, 2, 3, 4, 5
+
+
+def numeric_argsort(values: np.ndarray, type: int) -> np.ndarray:
+    """Stable argsort in compareTo order, by numeric comparisons only."""
+    idx = np.arange(values.size, dtype=np.int64)
+    if type in (NUM_F64, NUM_F32):
+        with np.errstate(invalid="ignore"):  # signalling NaNs widen to NaNs
+            v = values.astype(np.float64)
+        nan = np.isnan(v)
+        val = np.where(nan, 0.0, v)
+        zero_sign = np.where((v == 0.0) & ~np.signbit(v), 1, 0)  # -0.0 before 0.0
+        return np.lexsort((idx, zero_sign, val, nan.astype(np.int8))).astype(np.int64)
+    if type == NUM_U64:
+        return np.argsort(values.astype(np.uint64), kind="stable").astype(np.int64)
+    return np.argsort(values.astype(np.int64), kind="stable").astype(np.int64)
+
+
+def numeric_code(values: np.ndarray, type: int) -> np.ndarray:
+    """The order-preserving unsigned key of each value, from its bit layout."""
+    if type in (NUM_I64, NUM_DATETIME):
+        return values.astype(np.int64).view(np.uint64) ^ np.uint64(1 << 63)
+    if type == NUM_I32:
+        return (values.astype(np.int32).view(np.uint32) ^ np.uint32(1 << 31)).astype(np.uint64)
+    if type == NUM_F64:
+        x = values.astype(np.float64).view(np.uint64).copy()
+        x[np.isnan(values)] = np.uint64(0x7FF8000000000000)
+        neg = (x >> np.uint64(63)) == 1
+        return np.where(neg, ~x, x | np.uint64(1 << 63))
+    if type == NUM_F32:
+        x = values.astype(np.float32).view(np.uint32).copy()
+        x[np.isnan(values)] = np.uint32(0x7FC00000)
+        neg = (x >> np.uint32(31)) == 1
+        return np.where(neg, ~x, x | np.uint32(1 << 31)).astype(np.uint64)
+    return values.astype(np.uint64)

@@ -36,6 +36,8 @@ CODER_AUTO, CODER_ASCII7, CODER_BYTE8, CODER_ALPHA = 0, 1, 2, 3
 MODE_PLAIN, MODE_LEARNED = 0, 1
 # hs_index_t
 U32, U64 = 0, 1
+# hs_numeric
+NUM_U64, NUM_I64, NUM_I32, NUM_F64, NUM_F32, NUM_DATETIME = 0, 1, 2, 3, 4, 5
 
 MAX_N = 0x7FFFFFFF
 
@@ -43,7 +45,7 @@ MAX_N = 0x7FFFFFFF
 EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
            "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size", "hs_shutdown",
-           "hs_last_error", "hs_version",
+           "hs_last_error", "hs_version", "hs_encode_numeric", "hs_numeric_workspace_size", "hs_argsort_numeric",
            "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile")
 
 NOALLOC_MAX_N = 262144
@@ -99,6 +101,12 @@ def load(path: str | None = None):
     lib.hs_host_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
     lib.hs_shutdown.restype = ci
     lib.hs_shutdown.argtypes = []
+    lib.hs_encode_numeric.restype = ci
+    lib.hs_encode_numeric.argtypes = [vp, u64, ci, vp, vp]
+    lib.hs_numeric_workspace_size.restype = ci
+    lib.hs_numeric_workspace_size.argtypes = [u64, ci, ctypes.POINTER(ctypes.c_size_t)]
+    lib.hs_argsort_numeric.restype = ci
+    lib.hs_argsort_numeric.argtypes = [vp, u64, ci, ci, vp, vp, ctypes.c_size_t, vp]
     lib.hs_argsort_noalloc.restype = ci
     lib.hs_argsort_noalloc.argtypes = [vp, vp, u64, ci, ci, vp, vp]
     lib.hs_stats_enable.restype = ci
@@ -192,6 +200,48 @@ def encode(data: torch.Tensor, offsets: torch.Tensor, coder: int = CODER_AUTO,
                             ctypes.byref(exact), ctypes.byref(used), _ptr(ws),
                             ws.numel(), _stream_handle(stream)))
     return codes, bool(exact.value), int(used.value)
+
+
+_NUM_TYPES = {torch.int64: NUM_I64, torch.int32: NUM_I32, torch.float64: NUM_F64, torch.float32: NUM_F32}
+
+
+def _numeric_input(values: torch.Tensor, type):
+    if not values.is_cuda:
+        raise ValueError("values must be a CUDA tensor")
+    values = values.contiguous()
+    if type is None:
+        if values.dtype not in _NUM_TYPES:
+            raise ValueError(f"no numeric coder for {values.dtype}; pass type=")
+        type = _NUM_TYPES[values.dtype]
+    width = 4 if type in (NUM_I32, NUM_F32) else 8
+    if values.element_size() != width:
+        raise ValueError(f"numeric type {type} needs {width}-byte elements")
+    return values, type
+
+
+def encode_numeric(values: torch.Tensor, type: int | None = None, stream=None) -> torch.Tensor:
+    """Order-preserving uint64 codes of numeric values (an int64 tensor holding
+    the codes' bits).  type defaults from the dtype (int64, int32, float64,
+    float32); NUM_U64 and NUM_DATETIME take int64 tensors."""
+    values, type = _numeric_input(values, type)
+    codes = torch.empty(values.numel(), dtype=torch.int64, device=values.device)
+    _check(load().hs_encode_numeric(_ptr(values), values.numel(), type, _ptr(codes), _stream_handle(stream)))
+    return codes
+
+
+def argsort_numeric(values: torch.Tensor, type: int | None = None, index_u64: bool = False,
+                    stream=None) -> torch.Tensor:
+    """Stable argsort of device-resident numeric values in the order of their
+    numeric coder (Java's compareTo order; see hs_numeric in husky.h)."""
+    values, type = _numeric_input(values, type)
+    n = values.numel()
+    out = torch.empty(n, dtype=torch.int64 if index_u64 else torch.int32, device=values.device)
+    need = ctypes.c_size_t(0)
+    _check(load().hs_numeric_workspace_size(n, U64 if index_u64 else U32, ctypes.byref(need)))
+    ws = workspace(need.value, values.device)
+    _check(load().hs_argsort_numeric(_ptr(values), n, type, U64 if index_u64 else U32, _ptr(out), _ptr(ws),
+                                     ws.numel(), _stream_handle(stream)))
+    return out
 
 
 def argsort_device(data: torch.Tensor, offsets: torch.Tensor,

@@ -1211,6 +1211,74 @@ hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t
     return argsort_plain(c, in, coder);
 }
 
+hs_status hs_encode_numeric(const void *d_values, uint64_t n, int type, uint64_t *d_codes, void *stream) {
+    g_last_error.clear();
+    if (type < HS_NUM_U64 || type > HS_NUM_DATETIME) return fail(HS_ERR_INVALID_ARG, "bad numeric type");
+    if (n == 0) return HS_OK;
+    if (!d_values || !d_codes) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    const cudaError_t e = launch_numeric_encode(d_values, n, type, d_codes, nullptr, num_sms_cached(),
+                                                static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HS_OK : fail_cuda(e, "numeric encode");
+}
+
+hs_status hs_numeric_workspace_size(uint64_t n, int out_t, size_t *out) {
+    g_last_error.clear();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    *out = make_layout(n).total;
+    return HS_OK;
+}
+
+hs_status hs_argsort_numeric(const void *d_values, uint64_t n, int type, int out_t, void *d_perm, void *d_ws,
+                             size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (type < HS_NUM_U64 || type > HS_NUM_DATETIME) return fail(HS_ERR_INVALID_ARG, "bad numeric type");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
+    if (n == 0) return HS_OK;
+    if (!d_values || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, ws_bytes, n, stream, &st)) return st;
+    SortBufs b{{c.at<uint64_t>(c.L.codes_a), c.at<uint64_t>(c.L.codes_b)},
+               {c.at<uint32_t>(c.L.vals_a), c.at<uint32_t>(c.L.vals_b)},
+               {c.at<uint32_t>(c.L.segs_a), c.at<uint32_t>(c.L.segs_b)}};
+    c.lb_words = sort_tiles(n) * kBins;
+    unsigned long long *hist = c.at<unsigned long long>(c.L.hist);
+    HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
+    // Perfect codes (distinct values, distinct codes): Step 2 alone, the last
+    // pass writing the permutation; no tie detection or fix-up.  A 32-bit
+    // code and the index share one word (32 + 31 bits at most), so those
+    // passes move 8 bytes a value instead of 12.
+    const bool narrow = type == HS_NUM_I32 || type == HS_NUM_F32;
+    int idx_bits = 1;
+    while (idx_bits < 32 && (1ull << idx_bits) < n) ++idx_bits;
+    const int pack_bits = narrow ? idx_bits : 0;
+    HS_TRY(c.timed(kKEncode, (narrow ? 4.0 : 8.0) * n + 8.0 * n, [&] {
+               return launch_numeric_encode(d_values, n, type, b.keys[0], hist, c.sms, c.s, pack_bits);
+           }),
+           "numeric encode");
+    HS_TRY(c.timed(kKPlan, 8.0 * kBins * 16, [&] {
+               return launch_plan(hist, kKeyPasses, n, c.at<unsigned long long>(c.L.bucket), c.d_flags, c.s);
+           }),
+           "plan");
+    HS_TRY(c.read_flags(), "plan sync");
+    int passes[kKeyPasses], np = 0;
+    for (int p = 0; p < kKeyPasses; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    const OutMode pmode = out_t == HS_U64 ? kOutPerm64 : kOutPerm32;
+    int cur = 0;
+    if (np == 0) {
+        HS_TRY(c.timed(kKIdentity, 4.0 * n, [&] { return launch_identity(nullptr, n, d_perm, pmode, c.s); }),
+               "identity");
+    } else {
+        st = run_passes(c, b, &cur, n, passes, np, false, nullptr, pack_bits == 0, d_perm, pmode, false, pack_bits);
+        if (st != HS_OK) return st;
+    }
+    HS_TRY(c.read_flags(), "final sync");
+    return device_error_status(c.h);
+}
+
 hs_status hs_host_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_t, size_t *out) {
     g_last_error.clear();
     if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");

@@ -541,6 +541,79 @@ cudaError_t launch_sorted_test(const uint64_t *keys, const uint32_t *nonexact_bi
     return cudaGetLastError();
 }
 
+// Numeric coders (the order-preserving unsigned keys of husky.h's hs_numeric).
+__device__ __forceinline__ uint64_t numeric_code(const void *values, uint64_t i, int type) {
+    switch (type) {
+        case 1:    // int64
+        case 5: {  // date-time, int64 ns
+            return static_cast<const uint64_t *>(values)[i] ^ 0x8000000000000000ull;
+        }
+        case 2:  // int32
+            return (uint64_t)(static_cast<const uint32_t *>(values)[i] ^ 0x80000000u);
+        case 3: {  // binary64
+            uint64_t x = static_cast<const uint64_t *>(values)[i];
+            if ((x & 0x7FF0000000000000ull) == 0x7FF0000000000000ull && (x & 0x000FFFFFFFFFFFFFull) != 0)
+                x = 0x7FF8000000000000ull;
+            return (x >> 63) ? ~x : (x | 0x8000000000000000ull);
+        }
+        case 4: {  // binary32
+            uint32_t x = static_cast<const uint32_t *>(values)[i];
+            if ((x & 0x7F800000u) == 0x7F800000u && (x & 0x007FFFFFu) != 0) x = 0x7FC00000u;
+            return (uint64_t)((x >> 31) ? ~x : (x | 0x80000000u));
+        }
+        default:
+            return static_cast<const uint64_t *>(values)[i];
+    }
+}
+
+constexpr int kNumThreads = 512;
+
+// codes[i] = numeric code of values[i], or with pack_bits > 0 the word
+// (code << pack_bits) | i; with hist, the 8 digit histograms of the codes
+// (accumulated).
+__global__ void __launch_bounds__(kNumThreads)
+numeric_encode_kernel(const void *__restrict__ values, uint64_t n, int type, uint64_t *__restrict__ codes,
+                      unsigned long long *__restrict__ hist, int pack_bits) {
+    __shared__ uint32_t s_hist[kKeyPasses * kBins];
+    if (hist)
+        for (int i = threadIdx.x; i < kKeyPasses * kBins; i += kNumThreads) s_hist[i] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * kNumThreads;
+    const uint64_t n_round = (n + 31) & ~31ull;  // whole warps iterate together
+    // 32-bit codes: the digits above bit 35 are zero for every value, counted
+    // in bin 0 at the end instead of per value
+    const int nd = (type == 2 || type == 4) ? 4 : kKeyPasses;
+    uint32_t valid_count = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * kNumThreads + threadIdx.x; i < n_round; i += stride) {
+        const bool valid = i < n;
+        const uint64_t k = valid ? numeric_code(values, i, type) : 0;
+        if (valid) codes[i] = pack_bits > 0 ? (k << pack_bits) | i : k;
+        valid_count += valid ? 1u : 0u;
+        if (hist) {
+#pragma unroll
+            for (int p = 0; p < kKeyPasses; ++p)
+                if (p < nd) hist_add(s_hist + p * kBins, (unsigned)((k >> digit_shift(p)) & digit_mask(p)), valid);
+        }
+    }
+    if (!hist) return;
+    const uint32_t warp_count = __reduce_add_sync(kFull, valid_count);
+    if ((threadIdx.x & 31) == 0 && warp_count)
+        for (int p = nd; p < kKeyPasses; ++p) atomicAdd(&s_hist[p * kBins], warp_count);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kKeyPasses * kBins; i += kNumThreads)
+        if (s_hist[i]) atomicAdd(&hist[i], (unsigned long long)s_hist[i]);
+}
+
+cudaError_t launch_numeric_encode(const void *values, uint64_t n, int type, uint64_t *codes,
+                                  unsigned long long *hist, int num_sms, cudaStream_t s, int pack_bits) {
+    if (n == 0) return cudaSuccess;
+    if (pack_bits < 0 || pack_bits > 32) return cudaErrorInvalidValue;  // 32-bit codes only
+    const uint64_t blocks = (n + kNumThreads * 8 - 1) / (kNumThreads * 8);
+    const unsigned grid = (unsigned)umin64(blocks, (uint64_t)num_sms * 4);
+    numeric_encode_kernel<<<grid, kNumThreads, 0, s>>>(values, n, type, codes, hist, pack_bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_alphabet(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int max_span,
                             DevFlags *flags, int num_sms, cudaStream_t s) {
     alphabet_kernel<<<(unsigned)num_sms * 4, kAlphaThreads, 0, s>>>(bytes, offsets, n, max_span, flags);

@@ -44,6 +44,11 @@ struct EncPack {
 cudaError_t launch_sorted_test(const uint64_t *keys, const uint32_t *nonexact_bits, uint64_t n, bool flag_in_key,
                                int idx_bits, uint64_t *pairs, uint64_t pairs_cap, DevFlags *flags, int num_sms,
                                cudaStream_t s);
+// Numeric coders: codes[i] of values[i] (type as hs_numeric), or for a
+// 32-bit type with pack_bits > 0 the word (code << pack_bits) | i; with hist
+// the 8 digit histograms of the codes (accumulated).
+cudaError_t launch_numeric_encode(const void *values, uint64_t n, int type, uint64_t *codes,
+                                  unsigned long long *hist, int num_sms, cudaStream_t s, int pack_bits = 0);
 // flags->descent |= 1 if some queued pair i (strings pairs[i], pairs[i] + 1)
 // is out of order; count = flags->pairs as the host read it.
 cudaError_t launch_pairs_ordered(const uint8_t *bytes, const uint64_t *offsets, const uint64_t *pairs,
