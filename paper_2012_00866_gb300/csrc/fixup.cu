@@ -23,31 +23,31 @@ namespace {
 //
 // Scan state over positions: has_head, position of the last run head, OR of
 // the "needs work" flags since that head.  (a then b) = b if b has a head,
-// else (a.has, a.last, a.or | b.or).  Packed into the 56-bit look-back value:
-// bit 55 has, bit 54 or, bits 0..53 last.
-
-struct RunState {
-    uint64_t last;
-    uint32_t has;
-    uint32_t orf;
-};
-
-__device__ __forceinline__ RunState combine(const RunState &a, const RunState &b) {
-    if (b.has) return b;
-    return RunState{a.last, a.has, a.orf | b.orf};
-}
+// else (a.has, a.last, a.or | b.or).  Held packed in one word, as the 56-bit
+// look-back value: bit 55 has, bit 54 or, bits 0..53 last; so combining is a
+// select and an OR, and a shuffle moves one word.
 
 constexpr uint64_t kRunLastMask = (1ull << 54) - 1;
-static_assert(((1ull << 55) | (1ull << 54) | kRunLastMask) <= kLbValueMask,
-              "packed run state must fit the look-back value");
+constexpr uint64_t kRunHas = 1ull << 55;
+constexpr uint64_t kRunOr = 1ull << 54;
+static_assert((kRunHas | kRunOr | kRunLastMask) <= kLbValueMask, "packed run state must fit the look-back value");
 
-__device__ __forceinline__ uint64_t pack(const RunState &s) {
-    return ((uint64_t)s.has << 55) | ((uint64_t)s.orf << 54) | (s.last & kRunLastMask);
+struct RunState {
+    uint64_t v;
+    __device__ __forceinline__ uint64_t last() const { return v & kRunLastMask; }
+    __device__ __forceinline__ bool orf() const { return (v & kRunOr) != 0; }
+};
+
+__device__ __forceinline__ RunState run_state(uint64_t last, bool has, bool orf) {
+    return RunState{(has ? kRunHas : 0ull) | (orf ? kRunOr : 0ull) | (last & kRunLastMask)};
 }
 
-__device__ __forceinline__ RunState unpack(uint64_t v) {
-    return RunState{v & kRunLastMask, (uint32_t)((v >> 55) & 1), (uint32_t)((v >> 54) & 1)};
+__device__ __forceinline__ RunState combine(const RunState &a, const RunState &b) {
+    return (b.v & kRunHas) ? b : RunState{a.v | (b.v & kRunOr)};
 }
+
+__device__ __forceinline__ uint64_t pack(const RunState &s) { return s.v; }
+__device__ __forceinline__ RunState unpack(uint64_t v) { return RunState{v}; }
 
 constexpr int kTieThreads = 256;
 constexpr int kTieItems = 16;
@@ -116,7 +116,7 @@ tie_detect_kernel(const TieArgs a) {
     uint32_t seg_prev = 0;
     if (SEGS && j0 > 0 && j0 - 1 < n) seg_prev = a.segs[j0 - 1];
     uint32_t heads = 0, flagsb = 0;
-    RunState mine{0, 0, 0};
+    RunState mine{0};
     if (PACKED) {
         // Words (code << pack_bits) | index.  Heads from the codes; only
         // strings with a neighbour of equal code and all coded chars present
@@ -152,7 +152,7 @@ tie_detect_kernel(const TieArgs a) {
         }
 #pragma unroll
         for (int i = 0; i < kTieItems; ++i)
-            if (j0 + i < n) mine = combine(mine, RunState{j0 + i, (heads >> i) & 1u, (flagsb >> i) & 1u});
+            if (j0 + i < n) mine = combine(mine, run_state(j0 + i, (heads >> i) & 1u, (flagsb >> i) & 1u));
         // The permutation is the words' index fields in tile order:
         // written with coalesced stores.
         const int cnt = (int)umin64(kTieTile, n - t0);
@@ -179,7 +179,7 @@ tie_detect_kernel(const TieArgs a) {
                 else f = window_tag(k) == cont_tag;
                 heads |= (uint32_t)head << i;
                 flagsb |= (uint32_t)f << i;
-                mine = combine(mine, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
+                mine = combine(mine, run_state(j, head, f));
                 seg_prev = sg;
             }
         }
@@ -189,22 +189,16 @@ tie_detect_kernel(const TieArgs a) {
     RunState x = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        RunState y;
-        y.last = __shfl_up_sync(kFull, x.last, o);
-        y.has = __shfl_up_sync(kFull, x.has, o);
-        y.orf = __shfl_up_sync(kFull, x.orf, o);
+        const RunState y{__shfl_up_sync(kFull, x.v, o)};
         if (lane >= o) x = combine(y, x);
     }
     if (lane == 31) s_state[warp] = pack(x);
     __syncthreads();
-    RunState wpre{0, 0, 0};
+    RunState wpre{0};
     for (int w = 0; w < warp; ++w) wpre = combine(wpre, unpack(s_state[w]));
     RunState excl;
     {
-        RunState xp;
-        xp.last = __shfl_up_sync(kFull, x.last, 1);
-        xp.has = __shfl_up_sync(kFull, x.has, 1);
-        xp.orf = __shfl_up_sync(kFull, x.orf, 1);
+        const RunState xp{__shfl_up_sync(kFull, x.v, 1)};
         excl = lane == 0 ? wpre : combine(wpre, xp);
     }
 
@@ -213,11 +207,11 @@ tie_detect_kernel(const TieArgs a) {
     // inclusive one (or before the first unwritten one) are folded in
     // position order by a shuffle reduction.
     if (warp == 0) {
-        RunState agg{0, 0, 0};
+        RunState agg{0};
         for (int w = 0; w < kTieThreads / 32; ++w) agg = combine(agg, unpack(s_state[w]));
         uint64_t *lb = a.lookback + tile;
         const uint32_t epoch = a.epoch;
-        RunState prefix{0, 0, 0};
+        RunState prefix{0};
         if (tile == 0) {
             if (lane == 0) st_relaxed(lb, lb_word(epoch, kLbInclusive, pack(agg)));
         } else {
@@ -238,19 +232,13 @@ tie_detect_kernel(const TieArgs a) {
                 const int last = stop < avail - 1 ? stop : avail - 1;
                 if (last >= 0) {
                     // fold lanes 0..last; lane i holds the word of an earlier tile than lane i-1
-                    RunState x = lane <= last ? unpack(v & kLbValueMask) : RunState{0, 0, 0};
+                    RunState x = lane <= last ? unpack(v & kLbValueMask) : RunState{0};
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
-                        RunState y;
-                        y.last = __shfl_down_sync(kFull, x.last, o);
-                        y.has = __shfl_down_sync(kFull, x.has, o);
-                        y.orf = __shfl_down_sync(kFull, x.orf, o);
+                        const RunState y{__shfl_down_sync(kFull, x.v, o)};
                         if (lane + o < 32) x = combine(y, x);
                     }
-                    RunState folded;
-                    folded.last = __shfl_sync(kFull, x.last, 0);
-                    folded.has = __shfl_sync(kFull, x.has, 0);
-                    folded.orf = __shfl_sync(kFull, x.orf, 0);
+                    const RunState folded{__shfl_sync(kFull, x.v, 0)};
                     prefix = combine(folded, prefix);
                 }
                 if (first_in < first_nr) break;  // folded through an inclusive prefix
@@ -281,14 +269,14 @@ tie_detect_kernel(const TieArgs a) {
         if (j >= n) break;
         const bool head = (heads >> i) & 1u;
         const bool f = (flagsb >> i) & 1u;
-        st = combine(st, RunState{j, head ? 1u : 0u, f ? 1u : 0u});
-        uint64_t pos = j, run_start = st.last;
+        st = combine(st, run_state(j, head, f));
+        uint64_t pos = j, run_start = st.last();
         uint32_t depth = 0;
         if (REFINE) {
             const uint32_t sg = a.segs[j];
             const RunEntry r = a.runs[sg];
             pos = r.start + (j - a.run_base[sg]);
-            run_start = r.start + (st.last - a.run_base[sg]);
+            run_start = r.start + (st.last() - a.run_base[sg]);
             depth = r.depth + 1;
         }
         if (MODE == kTieValFlag || REFINE) {
@@ -310,8 +298,8 @@ tie_detect_kernel(const TieArgs a) {
                    (SEGS && next_seg != a.segs[j]);
         }
         if (tail) {
-            const uint64_t len = j - st.last + 1;
-            if (len >= 2 && st.orf) push_run(a, run_start, len, depth);
+            const uint64_t len = j - st.last() + 1;
+            if (len >= 2 && st.orf()) push_run(a, run_start, len, depth);
         }
     }
 }

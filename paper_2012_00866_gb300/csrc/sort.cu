@@ -364,12 +364,13 @@ histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__
 
 // ---- pass plan -------------------------------------------------------------
 
+// One CTA per pass: the histograms are independent.
 __global__ void __launch_bounds__(kBins)
 plan_kernel(const unsigned long long *__restrict__ hist, int npass, uint64_t n,
             unsigned long long *__restrict__ bucket_base, DevFlags *flags) {
     __shared__ unsigned long long s_warp[kBins / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int p = 0; p < npass; ++p) {
+    for (int p = blockIdx.x; p < npass; p += gridDim.x) {
         const unsigned long long c = hist[p * kBins + tid];
         unsigned long long x = c;
 #pragma unroll
@@ -499,7 +500,8 @@ cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs, uint64_
 
 cudaError_t launch_plan(const unsigned long long *hist, int npass, uint64_t n,
                         unsigned long long *bucket_base, DevFlags *flags, cudaStream_t s) {
-    plan_kernel<<<1, kBins, 0, s>>>(hist, npass, n, bucket_base, flags);
+    if (npass <= 0) return cudaSuccess;
+    plan_kernel<<<(unsigned)npass, kBins, 0, s>>>(hist, npass, n, bucket_base, flags);
     return cudaGetLastError();
 }
 
