@@ -333,7 +333,7 @@ def run_ours(args, rank, world, local):
                     "algo_bytes_per_launch": st["algo_bytes"] / st["launches"],
                     "launch_ms": round(st["total_ms"] / st["launches"], 5),
                     "share_of_step": round(st["total_ms"] / args.steps / ms, 3),
-                    "traffic": profile_traffic(f"{top}/{args.workload}")}
+                    "traffic": profile_traffic(f"{top}_kernel/{args.workload}")}
 
     stages = {k: {"launches_per_step": v["launches"] / args.steps,
                   "ms_per_step": round(v["total_ms"] / args.steps, 4),

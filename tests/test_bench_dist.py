@@ -62,3 +62,19 @@ def test_reference_arm_other_ranks_exit_without_work():
                        capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_profile_traffic_lookup(tmp_path, monkeypatch):
+    """roofline.traffic comes from profiles/traffic.json under the key
+    '<kernel>_kernel/<workload>' while the sources digest matches, else None."""
+    import json
+    import bench
+    (tmp_path / "profiles").mkdir()
+    entry = {"dram_bytes_per_launch": 123, "sources_sha256": bench.sources_digest()}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"onesweep_kernel/w": entry}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "sources_digest", lambda paths=None: entry["sources_sha256"])
+    assert bench.profile_traffic("onesweep_kernel/w") == 123
+    assert bench.profile_traffic("onesweep/w") is None
+    monkeypatch.setattr(bench, "sources_digest", lambda paths=None: "other")
+    assert bench.profile_traffic("onesweep_kernel/w") is None
