@@ -282,6 +282,14 @@ struct Ctx {
     int alpha_w = 0;                  // its bits per char
     bool idx_packed = false;          // the encoder packed each string's index below its code
     int idx_bits = 0;                 // ... in this many bits
+    // hs_argsort_host: the permutation's copy to h_out may start once tie
+    // detection has written it; early_copy marks its end, and the fix-up's
+    // rewrites (DevFlags::dirty_lo / dirty_hi, or all of it after refinement
+    // rounds) are copied again afterwards.
+    void *h_out = nullptr;
+    size_t h_out_isz = 0;
+    cudaEvent_t early_copy = nullptr;
+    bool dirty_all = false;
     std::vector<cudaEvent_t> events;  // chunk hand-off events in use
 
     template <typename T> T *at(size_t off) { return reinterpret_cast<T *>(ws + off); }
@@ -363,6 +371,7 @@ struct Ctx {
     }
     ~Ctx() {
         flush_stats();
+        if (early_copy) cudaEventSynchronize(early_copy);  // the caller's buffer is not written after return
         if (!events.empty() || h_pinned) cudaStreamSynchronize(s);  // no copy or wait still uses them
         if (!events.empty()) release_sync_events(events);
         release_pinned_flags(h_pinned);
@@ -622,10 +631,19 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     t.flags = c.d_flags;
     HS_TRY(c.next_epoch(&t.epoch), "epoch");
     HS_TRY(c.counter(&t.tile_counter), "counter");
+    const bool early = c.h_out != nullptr && mode == kTiePacked && !inst.seg_offsets;
+    if (early)
+        HS_TRY(cudaMemsetAsync(&c.d_flags->dirty_lo, 0xFF, sizeof(unsigned long long), c.s), "memset dirty");
     const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n
                              : mode == kTiePacked ? 8.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n
                                                   : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
     HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
+    cudaEvent_t tie_done = nullptr;
+    if (early) {
+        HS_TRY(sync_event(&tie_done), "event");
+        c.events.push_back(tie_done);
+        HS_TRY(cudaEventRecord(tie_done, c.s), "record tie detect");
+    }
     // Runs of copies of one string are final already; only the others go on
     // to refinement (queue B).
     HS_TRY(cudaMemsetAsync(&c.d_flags->qcount[kQLargeB], 0, sizeof(unsigned long long), c.s), "memset q");
@@ -661,20 +679,31 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
             HS_TRY(c.timed(kKMediumRuns, known ? (double)(med - med0) * 16.0 * (2 * isz + 16.0) : 0.0, [&] {
                        return launch_medium_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_medium,
                                                  &c.d_flags->qcount[kQMedium], med0, c.L.cap_medium, n, inst,
-                                                 in.prefix_len, c.sms, c.s);
+                                                 in.prefix_len, c.sms, c.s, early ? c.d_flags : nullptr);
                    }),
                    "medium runs");
         if (!known || sm > small0)
             HS_TRY(c.timed(kKSmallRuns, known ? (double)(sm - small0) * (16.0 + 2.0 * (2 * isz + 16.0)) : 0.0, [&] {
                        return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
                                                 &c.d_flags->qcount[kQSmall], small0, c.L.cap_small, n, inst,
-                                                in.prefix_len, c.sms, c.s);
+                                                in.prefix_len, c.sms, c.s, early ? c.d_flags : nullptr);
                    }),
                    "small runs");
         return HS_OK;
     };
     hs_status st = launch_med_small(0, 0, false);
     if (st != HS_OK) return st;
+    if (early) {
+        // the permutation leaves while the fix-up runs (issued after the
+        // fix-up launches: a copy to pageable memory blocks the host)
+        cudaStream_t cs = nullptr;
+        HS_TRY(copy_stream(&cs), "copy stream");
+        HS_TRY(cudaStreamWaitEvent(cs, tie_done, 0), "copy waits");
+        HS_TRY(cudaMemcpyAsync(c.h_out, in.perm, n * c.h_out_isz, cudaMemcpyDeviceToHost, cs), "early copy");
+        HS_TRY(sync_event(&c.early_copy), "event");
+        c.events.push_back(c.early_copy);
+        HS_TRY(cudaEventRecord(c.early_copy, cs), "record early copy");
+    }
     HS_TRY(c.read_flags(), "tie sync");
     st = device_error_status(c.h);
     if (st != HS_OK) return st;
@@ -689,6 +718,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     int li = 1;
     uint64_t large = c.h.qcount[kQLargeB];
     int rounds = 0;
+    if (early) c.dirty_all = true;  // refinement rewrites positions all over
     while (large > 0) {
         if (++rounds > (1 << 26)) return fail(HS_ERR_INTERNAL, "refinement did not terminate");
         if (large > c.L.cap_large) return fail(HS_ERR_INTERNAL, "large-run queue overflow");
@@ -1338,11 +1368,30 @@ hs_status hs_argsort_host(const uint8_t *h_bytes, const uint64_t *h_offsets, uin
         if (st == HS_OK && fallback) st = argsort_plain(c, in, coder);
     } else {
         c.host = &hsrc;
+        c.h_out = h_perm;
+        c.h_out_isz = isz;
         st = argsort_plain(c, in, coder);
         c.host = nullptr;
     }
     if (st != HS_OK) return st;
-    HS_TRY(cudaMemcpyAsync(h_perm, d_perm, n * isz, cudaMemcpyDeviceToHost, c.s), "copy permutation");
+    if (c.early_copy) {
+        // the copy issued after tie detection has to finish first; then the
+        // positions the fix-up rewrote go again
+        HS_TRY(cudaStreamWaitEvent(c.s, c.early_copy, 0), "wait early copy");
+        uint64_t lo = 0, hi = n - 1;
+        bool again = c.dirty_all;
+        if (!again && c.h.dirty_lo <= c.h.dirty_hi && c.h.dirty_hi < n) {
+            again = true;
+            lo = c.h.dirty_lo;
+            hi = c.h.dirty_hi;
+        }
+        if (again)
+            HS_TRY(cudaMemcpyAsync(static_cast<char *>(h_perm) + lo * isz, static_cast<char *>(d_perm) + lo * isz,
+                                   (hi - lo + 1) * isz, cudaMemcpyDeviceToHost, c.s),
+                   "copy rewritten positions");
+    } else {
+        HS_TRY(cudaMemcpyAsync(h_perm, d_perm, n * isz, cudaMemcpyDeviceToHost, c.s), "copy permutation");
+    }
     HS_TRY(cudaStreamSynchronize(c.s), "final sync");
     return HS_OK;
 }

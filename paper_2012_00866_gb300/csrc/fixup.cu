@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256)
 small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                   IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
                   const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
-                  Instances inst, int prefix_len) {
+                  Instances inst, int prefix_len, DevFlags *dirty) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -348,6 +348,7 @@ small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict_
         }
         __syncwarp();
         if (mine) perm[e.start + rank] = idx;
+        if (lane == 0) mark_dirty(dirty, e.start, e.len);
         __syncwarp();
     }
 }
@@ -543,7 +544,7 @@ __global__ void __launch_bounds__(kMedThreads)
 medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                    IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
                    const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
-                   Instances inst, int prefix_len) {
+                   Instances inst, int prefix_len, DevFlags *dirty) {
     constexpr int CAP = kMediumMax;
     __shared__ uint64_t s_key[CAP];
     __shared__ uint32_t s_seg[CAP];
@@ -689,6 +690,7 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
             ++depth;
         }
         for (int j = tid; j < len; j += kMedThreads) perm[e.start + j] = s_idx[j];
+        if (tid == 0) mark_dirty(dirty, e.start, (uint64_t)len);
     }
 }
 
@@ -813,14 +815,15 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
 
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
                               const RunEntry *q, const unsigned long long *qcount, uint64_t first, uint64_t cap,
-                              uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
+                              uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s,
+                              DevFlags *dirty) {
     const unsigned grid = (unsigned)num_sms * 8;
     if (perm_u64)
         small_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q,
-                                                         qcount, first, cap, perm_n, inst, prefix_len);
+                                                         qcount, first, cap, perm_n, inst, prefix_len, dirty);
     else
         small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
-                                                         qcount, first, cap, perm_n, inst, prefix_len);
+                                                         qcount, first, cap, perm_n, inst, prefix_len, dirty);
     return cudaGetLastError();
 }
 
@@ -849,14 +852,15 @@ cudaError_t launch_distinct_large(const uint8_t *bytes, const uint64_t *offsets,
 
 cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets, void *perm, int perm_u64,
                                const RunEntry *q, const unsigned long long *qcount, uint64_t first, uint64_t cap,
-                               uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s) {
+                               uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s,
+                               DevFlags *dirty) {
     const unsigned grid = (unsigned)num_sms * 2;
     if (perm_u64)
         medium_runs_kernel<uint64_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm),
-                                                                  q, qcount, first, cap, perm_n, inst, prefix_len);
+                                                                  q, qcount, first, cap, perm_n, inst, prefix_len, dirty);
     else
         medium_runs_kernel<uint32_t><<<grid, kMedThreads, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm),
-                                                                  q, qcount, first, cap, perm_n, inst, prefix_len);
+                                                                  q, qcount, first, cap, perm_n, inst, prefix_len, dirty);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ struct DevFlags {
     unsigned int descent;           // sorted-input test: some string is smaller than its predecessor
     unsigned long long pairs;       // sorted-input test: adjacent pairs left to a full comparison
     unsigned int pad[2];
+    unsigned long long dirty_lo, dirty_hi;  // fix-up: permutation positions rewritten (lo preset to ~0)
 };
 
 // Run queue entry: a run of equal keys at positions [start, start + len)
@@ -180,6 +181,13 @@ __device__ __forceinline__ bool same_from(const uint8_t *a, const uint8_t *b, ui
     for (uint64_t i = from + 8; i < len; ++i)
         if (a[i] != b[i]) return false;
     return true;
+}
+
+// Positions [start, start + len) of the permutation were rewritten.
+__device__ __forceinline__ void mark_dirty(DevFlags *flags, uint64_t start, uint64_t len) {
+    if (flags == nullptr || len == 0) return;
+    atomicMin(&flags->dirty_lo, (unsigned long long)start);
+    atomicMax(&flags->dirty_hi, (unsigned long long)(start + len - 1));
 }
 
 __device__ __forceinline__ int compare_from(const uint8_t *a, uint64_t la,

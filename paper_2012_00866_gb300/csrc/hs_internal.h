@@ -211,11 +211,13 @@ struct TieArgs {
 // size-class queues; writes the permutation as the mode says.
 cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s);
 
+// dirty (nullable): flags whose dirty_lo / dirty_hi widen over the positions
+// a launch rewrites (the small and medium kernels alike).
 cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets,
                               void *perm, int perm_u64, const RunEntry *q,
                               const unsigned long long *qcount, uint64_t first, uint64_t cap,
                               uint64_t perm_n, Instances inst, int prefix_len,
-                              int num_sms, cudaStream_t s);
+                              int num_sms, cudaStream_t s, DevFlags *dirty = nullptr);
 
 // Large runs that are not all copies of one string, copied from q to q_out
 // (count in *qcount_out, which the caller zeroes).  diff (cap entries) and
@@ -236,7 +238,7 @@ cudaError_t launch_medium_runs(const uint8_t *bytes, const uint64_t *offsets,
                                void *perm, int perm_u64, const RunEntry *q,
                                const unsigned long long *qcount, uint64_t first, uint64_t cap,
                                uint64_t perm_n, Instances inst, int prefix_len,
-                               int num_sms, cudaStream_t s);
+                               int num_sms, cudaStream_t s, DevFlags *dirty = nullptr);
 
 // Large-run refinement helpers.
 cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count,

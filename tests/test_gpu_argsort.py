@@ -627,3 +627,53 @@ def test_sorted_input_through_host_entry_point(cuda_lib, swap):
     perm, st = _sort_with_stats(hs, lambda: hs.argsort(data, off))
     assert (_launches(st, "onesweep") == 0) == (swap is None)
     assert_oracle_equal(w, perm)
+
+
+# ---- host entry point: the permutation leaves while the fix-up runs ----------
+
+def _host_case(case, n=400_000):
+    rng = np.random.default_rng(hash(case) % 1000)
+    if case == "rewrites":      # packed words, a few runs of different strings after 8 equal chars
+        strs = [bytes(rng.integers(97, 123, size=int(rng.integers(4, 12))).astype(np.uint8)) for _ in range(n)]
+        for k in range(0, n, 997):
+            strs[k] = b"qqqqqqqq" + bytes(rng.integers(97, 100, size=int(rng.integers(1, 5))).astype(np.uint8))
+    elif case == "refinement":  # one huge run of equal codes that is not copies: refinement rounds
+        strs = [b"abcdefgh" + bytes(rng.integers(97, 100, size=int(rng.integers(0, 24))).astype(np.uint8))
+                for _ in range(n)]
+    else:                       # runs of copies only: nothing is rewritten
+        words = [bytes(rng.integers(97, 123, size=int(rng.integers(9, 14))).astype(np.uint8)) for _ in range(300)]
+        strs = [words[int(i)] for i in rng.integers(0, len(words), size=n)]
+    return workloads.from_strings(strs)
+
+
+@pytest.mark.parametrize("case", ["rewrites", "refinement", "copies"])
+@pytest.mark.parametrize("index_u64", [False, True])
+def test_host_entry_point_copy_during_fixup(cuda_lib, case, index_u64):
+    """With packed words the permutation is copied out as soon as tie
+    detection has written it; what the fix-up rewrites afterwards (a range,
+    or everything after refinement rounds) is copied again."""
+    hs = cuda_lib
+    import torch
+    w = _host_case(case)
+    data = torch.from_numpy(w.bytes).pin_memory()
+    off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+    assert_oracle_equal(w, hs.argsort(data, off, index_u64=index_u64))
+
+
+def test_host_entry_point_pageable_output(cuda_lib):
+    """The C entry point with pageable (numpy) inputs and output: the early
+    copy then blocks the host, after the fix-up has been launched."""
+    import ctypes
+    import torch
+    hs = cuda_lib
+    w = _host_case("rewrites", 300_000)
+    n = w.offsets.size - 1
+    out = np.zeros(n, np.uint32)
+    need = ctypes.c_size_t(0)
+    lib = hs.load()
+    assert lib.hs_host_workspace_size(n, int(w.offsets[-1]), hs.MODE_PLAIN, hs.U32, ctypes.byref(need)) == 0
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    st = lib.hs_argsort_host(w.bytes.ctypes.data, w.offsets.ctypes.data, n, hs.MODE_PLAIN, hs.CODER_AUTO, hs.U32,
+                             out.ctypes.data, ws.data_ptr(), ws.numel(), None)
+    assert st == 0, hs.load().hs_last_error()
+    assert_oracle_equal(w, torch.from_numpy(out.view(np.int32)))
