@@ -21,7 +21,7 @@
  *                           argsort (unique), so this pins results too large to
  *                           re-sort on the host.
  *
- * Readings of the paper taken here (each listed in the design doc):
+ * Readings of the paper taken here:
  *   - a "char" is one byte of the input buffer (charAt on ASCII text);
  *   - perfectForLength(len) is undefined in the paper; an element is exactly
  *     represented iff len <= maxLength and (len == 0 or its last byte != 0),
