@@ -376,6 +376,8 @@ def run_ours(args, rank, world, local):
                        "mode": ("loop" if loop else "batched") if batched else args.mode,
                        "index": "u32" if not index_u64 else "u64",
                        "coder": coder_name,
+                       "tile_keys_per_thread": {"packed_words": hs.autotune_choice(0, n),
+                                                "pairs": hs.autotune_choice(1, n)},
                        "l2": "flushed by a 256 MiB write before every timed step",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": e2e,

@@ -254,6 +254,19 @@ HS_API hs_status hs_stats_read(hs_kernel_stat *out, int max, int *count);
  * Safe to call without a GPU or twice; returns HS_OK (HS_ERR_CUDA if a
  * destroy call failed; the rest is still released). */
 HS_API hs_status hs_shutdown(void);
+/* Tile-shape tuner (no counterpart in the paper: a tuning aid for the
+ * radix passes).  The first sort of each layout -- packed (code, index)
+ * words (layout 0) or (key, payload) pairs (layout 1) -- in each size class
+ * floor(log2 n), for n >= 2^20, runs two of its radix passes with 12 and with
+ * 8 keys per thread, times them with CUDA events and keeps the faster shape
+ * for later sorts of that class in the process.  The shape never changes a
+ * result.  mode 1: tune (the default); 0: use the default shape (12) for
+ * classes not tuned yet; 2: forget every choice and tune again.
+ * hs_autotune_choice writes the keys per thread chosen for (layout, n), or 0
+ * when that class is not tuned. */
+HS_API hs_status hs_autotune(int mode);
+HS_API hs_status hs_autotune_choice(int layout, uint64_t n, int *items);
+
 /* Numeric coders.  Section 5 benchmarks Huskysort on Integer, Long and
  * Double arrays and Section 3.2 names a perfect coding for date-times (one
  * nanosecond over 128 years fits 64 bits); the paper gives no bit layout for

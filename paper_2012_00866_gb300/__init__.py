@@ -46,6 +46,7 @@ EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_batched_workspace_size", "hs_stats_enable", "hs_stats_read",
            "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size", "hs_shutdown",
            "hs_last_error", "hs_version", "hs_encode_numeric", "hs_numeric_workspace_size", "hs_argsort_numeric",
+           "hs_autotune", "hs_autotune_choice",
            "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile")
 
 NOALLOC_MAX_N = 262144
@@ -101,6 +102,10 @@ def load(path: str | None = None):
     lib.hs_host_workspace_size.argtypes = [u64, u64, ci, ci, ctypes.POINTER(sz)]
     lib.hs_shutdown.restype = ci
     lib.hs_shutdown.argtypes = []
+    lib.hs_autotune.restype = ci
+    lib.hs_autotune.argtypes = [ci]
+    lib.hs_autotune_choice.restype = ci
+    lib.hs_autotune_choice.argtypes = [ci, u64, ctypes.POINTER(ctypes.c_int)]
     lib.hs_encode_numeric.restype = ci
     lib.hs_encode_numeric.argtypes = [vp, u64, ci, vp, vp]
     lib.hs_numeric_workspace_size.restype = ci
@@ -217,6 +222,18 @@ def _numeric_input(values: torch.Tensor, type):
     if values.element_size() != width:
         raise ValueError(f"numeric type {type} needs {width}-byte elements")
     return values, type
+
+
+def autotune(mode: int = 1):
+    """Tile-shape tuner: 1 tune new size classes (default), 0 off, 2 forget and re-tune."""
+    _check(load().hs_autotune(mode))
+
+
+def autotune_choice(layout: int, n: int) -> int:
+    """Keys per thread the tuner chose for layout (0 packed words, 1 pairs) at n, 0 if none."""
+    v = ctypes.c_int(0)
+    _check(load().hs_autotune_choice(layout, n, ctypes.byref(v)))
+    return v.value
 
 
 def encode_numeric(values: torch.Tensor, type: int | None = None, stream=None) -> torch.Tensor:

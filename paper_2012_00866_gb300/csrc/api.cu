@@ -238,6 +238,24 @@ void release_pinned_flags(DevFlags *p) {
     g_pinned_flags.push_back(p);
 }
 
+// Tile-shape tuner.  The first sort of a layout (packed words, or key and
+// payload pairs) in a size class (floor(log2 n), n >= 2^20) runs its second
+// and third radix passes with the two shapes of kOnesweepShapes, timed with
+// events, and keeps the faster for that class.  The shape only changes how a
+// pass is tiled, never its result.
+struct ShapeTuner {
+    std::mutex mu;
+    bool enabled = true;
+    int choice[2][64] = {};  // keys per thread, 0 = not tuned yet
+};
+ShapeTuner g_tuner;
+
+int size_class(uint64_t n) {
+    int c = 0;
+    while (c < 63 && (2ull << c) <= n) ++c;
+    return c;
+}
+
 // Host source of hs_argsort_host: where the inputs are and where their
 // device copies go.
 struct HostSrc {
@@ -537,6 +555,19 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
                      bool segmented, const uint32_t *flag_bits, bool synth_first, void *final_out,
                      OutMode final_mode, bool keep_keys, int pack_bits = 0) {
     uint64_t *lb = c.at<uint64_t>(c.L.lb);
+    const int layout = segmented ? -1 : (pack_bits > 0 ? 0 : 1);
+    const int cls = size_class(n);
+    int items = 0;
+    bool tune = false;
+    if (layout >= 0 && n >= (1ull << 20)) {
+        std::lock_guard<std::mutex> g(g_tuner.mu);
+        items = g_tuner.choice[layout][cls];
+        tune = g_tuner.enabled && items == 0 && npasses >= 4;
+    }
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (tune)
+        for (auto &e : tev)
+            if ((e = pooled_event()) == nullptr) tune = false;
     if (pack_bits > 0) {  // (key << pack_bits) | index words: nothing else moves
         if (segmented || (!keep_keys && final_out == nullptr)) return fail(HS_ERR_INTERNAL, "packed passes");
         synth_first = false;
@@ -574,11 +605,28 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
             ob += om == kOutPerm64 ? 8.0 * n : 4.0 * n;        // vals written
             ob += segmented ? 8.0 * n : 0.0;                   // segs read + written
         }
+        const bool timed_shape = tune && (i == 1 || i == 2);
+        const int shape = timed_shape ? kOnesweepShapes[i - 1] : items;
+        if (timed_shape) HS_TRY(cudaEventRecord(tev[2 * (i - 1)], c.s), "tuner event");
         HS_TRY(c.timed(kKOnesweep, ob, [&] {
-                   return launch_onesweep(a, segmented, digit_seg, first && synth_first, om, c.s);
+                   return launch_onesweep(a, segmented, digit_seg, first && synth_first, om, c.s, shape);
                }),
                "onesweep");
+        if (timed_shape) HS_TRY(cudaEventRecord(tev[2 * (i - 1) + 1], c.s), "tuner event");
+        if (tune && i == 2) {
+            float ms0 = 0.f, ms1 = 0.f;
+            HS_TRY(cudaEventSynchronize(tev[3]), "tuner sync");
+            HS_TRY(cudaEventElapsedTime(&ms0, tev[0], tev[1]), "tuner time");
+            HS_TRY(cudaEventElapsedTime(&ms1, tev[2], tev[3]), "tuner time");
+            items = ms1 < ms0 ? kOnesweepShapes[1] : kOnesweepShapes[0];
+            std::lock_guard<std::mutex> g(g_tuner.mu);
+            g_tuner.choice[layout][cls] = items;
+        }
         *cur ^= 1;
+    }
+    if (tune) {
+        std::lock_guard<std::mutex> g(g_stats.mu);
+        for (auto e : tev) g_stats.pool.push_back(e);
     }
     return HS_OK;
 }
@@ -1417,6 +1465,28 @@ hs_status hs_batched_workspace_size(uint64_t n, uint64_t num_segs, size_t *out) 
     g_last_error.clear();
     if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
     *out = make_layout(n).total;
+    return HS_OK;
+}
+
+hs_status hs_autotune(int mode) {
+    g_last_error.clear();
+    if (mode < 0 || mode > 2) return fail(HS_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+    std::lock_guard<std::mutex> g(g_tuner.mu);
+    if (mode == 2) {
+        for (auto &row : g_tuner.choice)
+            for (auto &v : row) v = 0;
+        g_tuner.enabled = true;
+    } else {
+        g_tuner.enabled = mode == 1;
+    }
+    return HS_OK;
+}
+
+hs_status hs_autotune_choice(int layout, uint64_t n, int *items) {
+    g_last_error.clear();
+    if (layout < 0 || layout > 1 || !items) return fail(HS_ERR_INVALID_ARG, "bad layout or NULL");
+    std::lock_guard<std::mutex> g(g_tuner.mu);
+    *items = n >= (1ull << 20) ? g_tuner.choice[layout][size_class(n)] : 0;
     return HS_OK;
 }
 

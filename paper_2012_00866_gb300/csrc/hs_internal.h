@@ -116,9 +116,14 @@ struct OnesweepArgs {
 // a.pack_bits > 0 the keys are packed (key, index) words and nothing else
 // moves: kOutVals writes the words to keys_out, kOutPerm32/64 the indices
 // to vals_out.
+// items: keys per thread, 0 (the default shape) or one of onesweep_shapes()
+// (segmented passes always use 8).
 cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg,
                             bool digit_seg, bool synth, OutMode out,
-                            cudaStream_t s);
+                            cudaStream_t s, int items = 0);
+// The tile shapes (keys per thread) unsegmented passes can run with; [0] is
+// the default.
+constexpr int kOnesweepShapes[2] = {12, 8};
 
 // Digit histograms of keys (8 digits) and optionally segs (4 digits):
 // hist[p * kBins + d], p < 8 for keys, 8..11 for segs; accumulated.

@@ -65,7 +65,7 @@ template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED, int IT
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 onesweep_kernel(const OnesweepArgs a) {
     constexpr int TILE = kThreads * ITEMS;
-    constexpr int RBITS = 32 * ITEMS <= 256 ? 8 : 16;  // rank bits (ranks < 32 * ITEMS)
+    constexpr int RBITS = (32 * ITEMS <= 256 && !SYNTH) ? 8 : 16;  // rank bits (ranks < 32 * ITEMS; SYNTH: + a flag)
     constexpr int RPR = 32 / RBITS;
     constexpr uint32_t RMASK = (1u << (SYNTH ? RBITS - 1 : RBITS)) - 1;  // SYNTH: top bit is the flag
     static_assert(ITEMS % 4 == 0, "tile must be whole groups of four items");
@@ -308,17 +308,17 @@ onesweep_kernel(const OnesweepArgs a) {
     }
 }
 
-size_t onesweep_smem(bool has_seg, bool packed) {
-    const size_t tile = (size_t)kThreads * items_for(has_seg);
+size_t onesweep_smem(bool has_seg, bool packed, int items) {
+    const size_t tile = (size_t)kThreads * items;
     return tile * 8 + (packed ? 0 : tile * 4) + (has_seg ? tile * 4 : 0) + (size_t)kWarps * kBins * 4 +
            (size_t)kBins * 8;
 }
 
-template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED = false>
-cudaError_t launch_os(const OnesweepArgs &a, cudaStream_t s) {
-    constexpr int items = items_for(HAS_SEG);
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED, int ITEMS>
+cudaError_t launch_os_shape(const OnesweepArgs &a, cudaStream_t s) {
+    constexpr int items = ITEMS;
     auto kern = onesweep_kernel<HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, items>;
-    const size_t smem = onesweep_smem(HAS_SEG, PACKED);
+    const size_t smem = onesweep_smem(HAS_SEG, PACKED, items);
     static bool configured = false;  // attribute is per function, idempotent
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -328,6 +328,18 @@ cudaError_t launch_os(const OnesweepArgs &a, cudaStream_t s) {
     const uint64_t tiles = (a.n + kThreads * items - 1) / (kThreads * items);
     kern<<<(unsigned)tiles, kThreads, smem, s>>>(a);  // one CTA per tile
     return cudaGetLastError();
+}
+
+// Keys per thread: segmented passes have one shape (8); the others run with
+// 8 or 12 (items == 0: the default, 12), the choice of the tile-shape tuner.
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED = false>
+cudaError_t launch_os(const OnesweepArgs &a, cudaStream_t s, int items) {
+    if constexpr (HAS_SEG) {
+        return launch_os_shape<HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, kItems>(a, s);
+    } else {
+        if (items == kItems) return launch_os_shape<HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, kItems>(a, s);
+        return launch_os_shape<HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, kWideItems>(a, s);
+    }
 }
 
 // ---- up-front histograms -------------------------------------------------
@@ -442,37 +454,38 @@ __global__ void identity_kernel(const uint32_t *__restrict__ flag_bits, uint64_t
 }  // namespace
 
 cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg, bool digit_seg, bool synth,
-                            OutMode out, cudaStream_t s) {
+                            OutMode out, cudaStream_t s, int items) {
+    if (items != 0 && items != kItems && items != kWideItems) return cudaErrorInvalidValue;
     if (a.n == 0) return cudaSuccess;
     if (a.pack_bits > 0) {
         if (has_seg || digit_seg || synth || a.pack_bits > 63) return cudaErrorInvalidValue;
         if (out == kOutVals && a.keys_out == nullptr) return cudaErrorInvalidValue;
         switch (out) {
-            case kOutVals: return launch_os<false, false, false, kOutVals, true>(a, s);
-            case kOutPerm32: return launch_os<false, false, false, kOutPerm32, true>(a, s);
-            default: return launch_os<false, false, false, kOutPerm64, true>(a, s);
+            case kOutVals: return launch_os<false, false, false, kOutVals, true>(a, s, items);
+            case kOutPerm32: return launch_os<false, false, false, kOutPerm32, true>(a, s, items);
+            default: return launch_os<false, false, false, kOutPerm64, true>(a, s, items);
         }
     }
     if (has_seg) {
         if (synth || out == kOutPerm64) return cudaErrorInvalidValue;
         if (out == kOutPerm32)
-            return digit_seg ? launch_os<true, true, false, kOutPerm32>(a, s)
-                             : launch_os<true, false, false, kOutPerm32>(a, s);
-        return digit_seg ? launch_os<true, true, false, kOutVals>(a, s)
-                         : launch_os<true, false, false, kOutVals>(a, s);
+            return digit_seg ? launch_os<true, true, false, kOutPerm32>(a, s, items)
+                             : launch_os<true, false, false, kOutPerm32>(a, s, items);
+        return digit_seg ? launch_os<true, true, false, kOutVals>(a, s, items)
+                         : launch_os<true, false, false, kOutVals>(a, s, items);
     }
     if (digit_seg) return cudaErrorInvalidValue;
     if (synth) {
         switch (out) {
-            case kOutVals: return launch_os<false, false, true, kOutVals>(a, s);
-            case kOutPerm32: return launch_os<false, false, true, kOutPerm32>(a, s);
-            default: return launch_os<false, false, true, kOutPerm64>(a, s);
+            case kOutVals: return launch_os<false, false, true, kOutVals>(a, s, items);
+            case kOutPerm32: return launch_os<false, false, true, kOutPerm32>(a, s, items);
+            default: return launch_os<false, false, true, kOutPerm64>(a, s, items);
         }
     }
     switch (out) {
-        case kOutVals: return launch_os<false, false, false, kOutVals>(a, s);
-        case kOutPerm32: return launch_os<false, false, false, kOutPerm32>(a, s);
-        default: return launch_os<false, false, false, kOutPerm64>(a, s);
+        case kOutVals: return launch_os<false, false, false, kOutVals>(a, s, items);
+        case kOutPerm32: return launch_os<false, false, false, kOutPerm32>(a, s, items);
+        default: return launch_os<false, false, false, kOutPerm64>(a, s, items);
     }
 }
 

@@ -677,3 +677,32 @@ def test_host_entry_point_pageable_output(cuda_lib):
                              out.ctypes.data, ws.data_ptr(), ws.numel(), None)
     assert st == 0, hs.load().hs_last_error()
     assert_oracle_equal(w, torch.from_numpy(out.view(np.int32)))
+
+
+# ---- tile-shape tuner ------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,layout", [(2, 0), (5, 1)])
+def test_tile_shape_tuner(cuda_lib, kind, layout):
+    """The first sort of a size class times two passes in each shape and
+    keeps one; the sort that tunes and the sorts after it are exact, and a
+    tuner switched off leaves new classes on the default shape."""
+    hs = cuda_lib
+    hs.autotune(2)
+    try:
+        # zipf words pack their codes with the index; ASCII7 keys on skewed words travel as pairs
+        w = workloads.generate(kind, 1_500_000, 17 + kind)
+        data, off = to_device(w)
+        coder = hs.CODER_AUTO if layout == 0 else hs.CODER_ASCII7
+        n = w.offsets.size - 1
+        assert hs.autotune_choice(layout, n) == 0
+        assert_oracle_equal(w, hs.argsort_device(data, off, coder=coder))
+        chosen = hs.autotune_choice(layout, n)
+        assert chosen in (8, 12)
+        assert_oracle_equal(w, hs.argsort_device(data, off, coder=coder))
+        assert hs.autotune_choice(layout, n) == chosen
+        hs.autotune(2)
+        hs.autotune(0)
+        assert_oracle_equal(w, hs.argsort_device(data, off, coder=coder))
+        assert hs.autotune_choice(layout, n) == 0
+    finally:
+        hs.autotune(2)
