@@ -706,3 +706,22 @@ def test_tile_shape_tuner(cuda_lib, kind, layout):
         assert hs.autotune_choice(layout, n) == 0
     finally:
         hs.autotune(2)
+
+
+@pytest.mark.parametrize("n,packed", [(1 << 24, True), ((1 << 24) + 1, False)])
+def test_packed_index_width_boundary_lowercase(cuda_lib, n, packed):
+    """Lowercase text codes in 40 bits: 2^24 strings fill the word with their
+    24-bit index, one more takes the (key, payload) pairs.  Checked by the
+    order property at this size, and the pass layout by its bytes."""
+    hs = cuda_lib
+    w = workloads.generate(1, n, 5)
+    data, off = to_device(w)
+    hs.stats_enable(True)
+    try:
+        perm = hs.argsort_device(data, off)
+        st = hs.stats_read()["onesweep"]
+    finally:
+        hs.stats_enable(False)
+    per_key = st["algo_bytes"] / (st["launches"] * n)
+    assert (per_key <= 16.0) == packed
+    assert_stable_sorted(w, perm)
