@@ -679,19 +679,23 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     t.flags = c.d_flags;
     HS_TRY(c.next_epoch(&t.epoch), "epoch");
     HS_TRY(c.counter(&t.tile_counter), "counter");
-    const bool early = c.h_out != nullptr && mode == kTiePacked && !inst.seg_offsets;
-    if (early)
+    // Packed words: the permutation is final but for the fix-up's runs once
+    // tie detection has written it, and those runs are few (the byte-range
+    // code covers 8 chars).  With (key, payload) pairs the fix-up's rewrites
+    // spread over the whole permutation (measured: the copy then goes twice),
+    // so the copy waits for the end there.
+    const bool early = c.h_out != nullptr && !inst.seg_offsets && mode == kTiePacked;
+    cudaEvent_t perm_done = nullptr;
+    if (early) {
         HS_TRY(cudaMemsetAsync(&c.d_flags->dirty_lo, 0xFF, sizeof(unsigned long long), c.s), "memset dirty");
+        HS_TRY(sync_event(&perm_done), "event");
+        c.events.push_back(perm_done);
+    }
     const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n
                              : mode == kTiePacked ? 8.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n
                                                   : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
     HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
-    cudaEvent_t tie_done = nullptr;
-    if (early) {
-        HS_TRY(sync_event(&tie_done), "event");
-        c.events.push_back(tie_done);
-        HS_TRY(cudaEventRecord(tie_done, c.s), "record tie detect");
-    }
+    if (early) HS_TRY(cudaEventRecord(perm_done, c.s), "record tie detect");
     // Runs of copies of one string are final already; only the others go on
     // to refinement (queue B).
     HS_TRY(cudaMemsetAsync(&c.d_flags->qcount[kQLargeB], 0, sizeof(unsigned long long), c.s), "memset q");
@@ -746,7 +750,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
         // fix-up launches: a copy to pageable memory blocks the host)
         cudaStream_t cs = nullptr;
         HS_TRY(copy_stream(&cs), "copy stream");
-        HS_TRY(cudaStreamWaitEvent(cs, tie_done, 0), "copy waits");
+        HS_TRY(cudaStreamWaitEvent(cs, perm_done, 0), "copy waits");
         HS_TRY(cudaMemcpyAsync(c.h_out, in.perm, n * c.h_out_isz, cudaMemcpyDeviceToHost, cs), "early copy");
         HS_TRY(sync_event(&c.early_copy), "event");
         c.events.push_back(c.early_copy);

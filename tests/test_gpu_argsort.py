@@ -648,16 +648,19 @@ def _host_case(case, n=400_000):
 
 @pytest.mark.parametrize("case", ["rewrites", "refinement", "copies"])
 @pytest.mark.parametrize("index_u64", [False, True])
-def test_host_entry_point_copy_during_fixup(cuda_lib, case, index_u64):
-    """With packed words the permutation is copied out as soon as tie
-    detection has written it; what the fix-up rewrites afterwards (a range,
-    or everything after refinement rounds) is copied again."""
+@pytest.mark.parametrize("coder", ["auto", "ascii7", "byte8"])
+def test_host_entry_point_copy_during_fixup(cuda_lib, case, index_u64, coder):
+    """The permutation is copied out as soon as it is written (by tie
+    detection for packed words and BYTE8, by the last radix pass for ASCII7
+    keys); what the fix-up rewrites afterwards (a range, or everything after
+    refinement rounds) is copied again."""
     hs = cuda_lib
     import torch
     w = _host_case(case)
     data = torch.from_numpy(w.bytes).pin_memory()
     off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
-    assert_oracle_equal(w, hs.argsort(data, off, index_u64=index_u64))
+    c = {"auto": hs.CODER_AUTO, "ascii7": hs.CODER_ASCII7, "byte8": hs.CODER_BYTE8}[coder]
+    assert_oracle_equal(w, hs.argsort(data, off, coder=c, index_u64=index_u64))
 
 
 def test_host_entry_point_pageable_output(cuda_lib):
