@@ -134,7 +134,12 @@ HS_API hs_status hs_encode(const uint8_t *d_bytes, const uint64_t *d_offsets,
  *            unique stable ascending argsort under unsigned-byte
  *            lexicographic order.
  *   mode     hs_mode; coder hs_coder.
- *   n        0 <= n <= HS_MAX_N; n = 0 is a no-op. */
+ *   n        0 <= n <= HS_MAX_N; n = 0 is a no-op.
+ * Plain mode also recognises an input already in order: right after Step 1
+ * each string's code is compared with its predecessor's; without a descent
+ * (and with the pairs of equal codes compared in full) the call writes the
+ * identity permutation and skips Steps 2 and 3.  An unsorted input pays one
+ * early-exit kernel for the test. */
 HS_API hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets,
                      uint64_t n, int mode, int coder, int out_t, void *d_perm,
                      void *d_ws, size_t ws_bytes, void *stream);
