@@ -320,6 +320,25 @@ HS_API hs_status hs_argsort_numeric(const void *d_values, uint64_t n, int type,
                                     int out_t, void *d_perm, void *d_ws,
                                     size_t ws_bytes, void *stream);
 
+/* BigInteger coder.  Section 5 sorts BigInteger arrays; the paper gives no
+ * coder.  Value i is its minimal two's complement bytes, big-endian (Java's
+ * BigInteger.toByteArray), at d_bytes[d_offsets[i] .. d_offsets[i+1]), at
+ * most 32767 bytes.  Each is turned into the byte string header || value,
+ * header the big-endian u16 0x8000 + L (value >= 0) or 0x7FFF - L (value < 0)
+ * for a value of L bytes, whose unsigned-byte order is numeric order; the
+ * strings then go through hs_argsort's path with the byte coder.  d_perm
+ * (device, uint32 or uint64 by out_t) receives the stable argsort by numeric
+ * value.  total_bytes: the size of the byte buffer (d_offsets[n] - d_offsets[0]
+ * must not exceed it).  Returns HS_ERR_INVALID_ARG if a value is empty, not
+ * minimal (a redundant leading 0x00 or 0xFF) or too long. */
+HS_API hs_status hs_bigint_workspace_size(uint64_t n, uint64_t total_bytes,
+                                          int out_t, size_t *out);
+HS_API hs_status hs_argsort_bigint(const uint8_t *d_bytes,
+                                   const uint64_t *d_offsets, uint64_t n,
+                                   uint64_t total_bytes, int out_t,
+                                   void *d_perm, void *d_ws, size_t ws_bytes,
+                                   void *stream);
+
 /* Message describing the calling thread's last failure ("" if none).  The
  * pointer stays valid until the next library call on this thread. */
 HS_API const char *hs_last_error(void);

@@ -260,3 +260,22 @@ def numeric_code(values: np.ndarray, type: int) -> np.ndarray:
         neg = (x >> np.uint32(31)) == 1
         return np.where(neg, ~x, x | np.uint32(1 << 31)).astype(np.uint64)
     return values.astype(np.uint64)
+
+
+# ---- BigInteger ---------------------------------------------------------------
+
+def bigint_values(data: np.ndarray, offsets: np.ndarray):
+    """Each value's minimal two's complement big-endian bytes as a Python int."""
+    return [int.from_bytes(data[int(offsets[i]):int(offsets[i + 1])].tobytes(), "big", signed=True)
+            for i in range(offsets.size - 1)]
+
+
+def bigint_argsort(data: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """Stable argsort by numeric value (Python's sort is stable)."""
+    v = bigint_values(data, offsets)
+    return np.array(sorted(range(len(v)), key=v.__getitem__), dtype=np.int64)
+
+
+def bigint_bytes(x: int) -> bytes:
+    """The minimal two's complement big-endian bytes of x (toByteArray)."""
+    return x.to_bytes(((x if x >= 0 else ~x).bit_length() + 8) // 8, "big", signed=True)

@@ -16,6 +16,7 @@
 #include "husky.h"
 #include "husky_learned.h"
 #include "hs_internal.h"
+#include "hs_bignum.h"
 
 namespace hs {
 namespace {
@@ -1291,6 +1292,56 @@ hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t
         if (st != HS_OK || !fallback) return st;
     }
     return argsort_plain(c, in, coder);
+}
+
+// Workspace of hs_argsort_bigint: the string sort's, then the encoded
+// strings (total_bytes + 2n) and their offsets.
+struct BigLayout {
+    size_t sort_bytes, enc_bytes, enc_offsets, total;
+    uint64_t enc_cap;
+};
+BigLayout bigint_layout(uint64_t n, uint64_t total_bytes) {
+    auto up = [](size_t x) { return (x + kAlign - 1) / kAlign * kAlign; };
+    BigLayout b{};
+    b.sort_bytes = up(make_layout(n).total);
+    b.enc_cap = total_bytes + 2 * n;
+    b.enc_bytes = b.sort_bytes;
+    b.enc_offsets = b.enc_bytes + up(b.enc_cap + 16);
+    b.total = b.enc_offsets + up(8 * (n + 1));
+    return b;
+}
+
+hs_status hs_bigint_workspace_size(uint64_t n, uint64_t total_bytes, int out_t, size_t *out) {
+    g_last_error.clear();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    *out = bigint_layout(n, total_bytes).total;
+    return HS_OK;
+}
+
+hs_status hs_argsort_bigint(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, uint64_t total_bytes,
+                            int out_t, void *d_perm, void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
+    if (n == 0) return HS_OK;
+    if (!d_bytes || !d_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    const BigLayout bl = bigint_layout(n, total_bytes);
+    if (d_ws == nullptr || ws_bytes < bl.total) return fail(HS_ERR_WORKSPACE, "workspace smaller than hs_bigint_workspace_size()");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, bl.sort_bytes, n, stream, &st)) return st;
+    uint8_t *eb = c.at<uint8_t>(bl.enc_bytes);
+    uint64_t *eo = c.at<uint64_t>(bl.enc_offsets);
+    HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
+    HS_TRY(launch_bigint_encode(d_bytes, d_offsets, n, eb, bl.enc_cap, eo, c.d_flags, c.sms, c.s), "bigint encode");
+    HS_TRY(c.read_flags(), "bigint sync");
+    if (c.h.error & kErrOffsets)
+        return fail(HS_ERR_INVALID_ARG, "a value is empty, not minimal, longer than 32767 bytes or past total_bytes");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    Input in{eb, eo, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
+    return argsort_plain(c, in, HS_CODER_BYTE8);
 }
 
 hs_status hs_encode_numeric(const void *d_values, uint64_t n, int type, uint64_t *d_codes, void *stream) {
