@@ -402,7 +402,37 @@ def run_ours(args, rank, world, local):
 # +-0, +-infinity, NaN and subnormals; datetime: ns instants over 1900..2100
 # with repeats; i32: full-range integers.
 NUMERIC = {"f64_1e8": ("f64", 100_000_000, 11), "datetime_1e8": ("datetime", 100_000_000, 12),
-           "i32_1e8": ("i32", 100_000_000, 13)}
+           "i32_1e8": ("i32", 100_000_000, 13), "bigint_1e7": ("bigint", 10_000_000, 14)}
+
+
+def bigint_workload(n, seed):
+    """n big integers as minimal two's complement bytes (Java's toByteArray):
+    lengths U{1..32}, random bytes, the leading byte adjusted where it would
+    be a redundant sign byte; 10% repeats of earlier values."""
+    import workloads
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(1, 33, size=n).astype(np.uint64)
+    rep = rng.random(n) < 0.1
+    src = rng.integers(0, n, size=n)
+    rep &= ~rep[src]  # a repeat copies a value that is not itself a repeat
+    lens[rep] = lens[src[rep]]
+    off = np.zeros(n + 1, np.uint64)
+    np.cumsum(lens, out=off[1:])
+    data = rng.integers(0, 256, size=int(off[-1]), dtype=np.uint8)
+    first = off[:-1].astype(np.int64)
+    multi = lens >= 2
+    b0, b1 = data[first[multi]], data[first[multi] + 1]
+    fix0 = (b0 == 0x00) & (b1 < 0x80)
+    fixf = (b0 == 0xFF) & (b1 >= 0x80)
+    idx = first[multi]
+    data[idx[fix0]] = 0x01
+    data[idx[fixf]] = 0xFE
+    # repeats take the bytes of their source value (same length)
+    s = np.where(rep, src, np.arange(n))
+    vid = np.repeat(np.arange(n), lens.astype(np.int64))
+    rel = np.arange(int(off[-1]), dtype=np.int64) - first[vid]
+    data = data[first[s[vid]] + rel]
+    return workloads.Workload(data, off)
 
 
 def numeric_values(name, scale):
@@ -430,14 +460,24 @@ def run_numeric(args, rank, world, local):
     device = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(device)
     hs.load()
-    v, t = numeric_values(args.workload, args.scale)
-    n = v.size
+    kind = NUMERIC[args.workload][0]
     index_u64 = args.index == "u64"
-    x = torch.from_numpy(v).to(device)
+    if kind == "bigint":
+        bw = bigint_workload(max(2, int(NUMERIC[args.workload][1] * args.scale)), NUMERIC[args.workload][2])
+        n = bw.offsets.size - 1
+        v = None
+        xb = torch.from_numpy(bw.bytes).to(device)
+        xo = torch.from_numpy(bw.offsets.view(np.int64)).to(device)
+    else:
+        v, t = numeric_values(args.workload, args.scale)
+        n = v.size
+        x = torch.from_numpy(v).to(device)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
     stream = torch.cuda.current_stream(device)
 
     def step():
+        if kind == "bigint":
+            return hs.argsort_bigint(xb, xo, index_u64=index_u64)
         return hs.argsort_numeric(x, type=t, index_u64=index_u64)
 
     for _ in range(args.warmup):
@@ -480,21 +520,34 @@ def run_numeric(args, rank, world, local):
     value = job_throughput(n, world, ms)
 
     # end to end through the public call: pinned host values in, host permutation out
-    h_vals = torch.from_numpy(v).pin_memory()
     h_perm = torch.empty(n, dtype=torch.int64 if index_u64 else torch.int32).pin_memory()
+    if kind == "bigint":
+        hb = torch.from_numpy(bw.bytes).pin_memory()
+        ho = torch.from_numpy(bw.offsets.view(np.int64)).pin_memory()
+        h2d = int(bw.bytes.nbytes + bw.offsets.nbytes)
+
+        def host_call():
+            return hs.argsort_bigint(hb.to(device, non_blocking=True), ho.to(device, non_blocking=True),
+                                     index_u64=index_u64)
+    else:
+        h_vals = torch.from_numpy(v).pin_memory()
+        h2d = int(v.nbytes)
+
+        def host_call():
+            return hs.argsort_numeric(h_vals.to(device, non_blocking=True), type=t, index_u64=index_u64)
     for _ in range(2):
-        h_perm.copy_(hs.argsort_numeric(h_vals.to(device, non_blocking=True), type=t, index_u64=index_u64))
+        h_perm.copy_(host_call())
     torch.cuda.synchronize(device)
     e2e_ms = []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
-        h_perm.copy_(hs.argsort_numeric(h_vals.to(device, non_blocking=True), type=t, index_u64=index_u64))
+        h_perm.copy_(host_call())
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_t = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, device)
     e2e = {"value": round(n * world / (e2e_t / 1e3) / 1e6, 3), "unit": UNIT,
-           "h2d_bytes_per_step": int(v.nbytes), "d2h_bytes_per_step": int(n * (8 if index_u64 else 4)),
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(n * (8 if index_u64 else 4)),
            "ms_per_step": round(e2e_t, 3)}
 
     peaks, peak_src = measured_peaks()
@@ -514,12 +567,20 @@ def run_numeric(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        m = min(n, CPU_SAMPLE_MAX)
-        t0 = time.perf_counter()
-        oracle.numeric_argsort(v[:m], t)
-        dt = time.perf_counter() - t0
+        if kind == "bigint":
+            m = min(n, 1_000_000)
+            t0 = time.perf_counter()
+            oracle.bigint_argsort(bw.bytes, bw.offsets[: m + 1])
+            dt = time.perf_counter() - t0
+            how = "Python int sort (one thread)"
+        else:
+            m = min(n, CPU_SAMPLE_MAX)
+            t0 = time.perf_counter()
+            oracle.numeric_argsort(v[:m], t)
+            dt = time.perf_counter() - t0
+            how = "numpy stable sort (one thread)"
         cpu = {"value": round(m / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the first {m} values of {args.workload}, one run, numpy stable sort (one thread)"}
+               "sample": f"the first {m} values of {args.workload}, one run, {how}"}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -545,12 +606,19 @@ def run_reference(args, rank, world, local):
     import workloads
     threads = os.cpu_count() or 1
     if args.workload in NUMERIC:
-        v, t = numeric_values(args.workload, args.scale)
-        m = min(v.size, CPU_SAMPLE_MAX)
+        if NUMERIC[args.workload][0] == "bigint":
+            bw = bigint_workload(max(2, int(NUMERIC[args.workload][1] * args.scale)), NUMERIC[args.workload][2])
+            m = min(bw.offsets.size - 1, 1_000_000)
+            sort = lambda: oracle.bigint_argsort(bw.bytes, bw.offsets[: m + 1])
+            v = np.zeros(bw.offsets.size - 1)
+        else:
+            v, t = numeric_values(args.workload, args.scale)
+            m = min(v.size, CPU_SAMPLE_MAX)
+            sort = lambda: oracle.numeric_argsort(v[:m], t)
         times = []
         for k in range(args.warmup + args.steps):
             t0 = time.perf_counter()
-            oracle.numeric_argsort(v[:m], t)
+            sort()
             if k >= args.warmup:
                 times.append(time.perf_counter() - t0)
         ms = sum(times) / len(times) * 1e3
