@@ -103,8 +103,14 @@ typedef enum { HS_CODER_AUTO = 0, HS_CODER_ASCII7 = 1, HS_CODER_BYTE8 = 2, HS_CO
  *                    partitioned by bucket and each bucket sorted by code;
  *                    buckets over 4096 keys that hold different codes go
  *                    through a segmented radix sort.  Runs as PLAIN when
- *                    n < 65536 or when the strings need the BYTE8 coder. */
-typedef enum { HS_MODE_PLAIN = 0, HS_MODE_LEARNED = 1 } hs_mode;
+ *                    n < 65536 or when the strings need the BYTE8 coder.
+ *   HS_MODE_AUTO     the library's choice; currently HS_MODE_PLAIN: on every
+ *                    measured workload the plain path is faster (2-3x on
+ *                    zipf words and skewed strings) or within 1% (strings
+ *                    with long shared prefixes).  Its workspace is the plain
+ *                    mode's.
+ */
+typedef enum { HS_MODE_PLAIN = 0, HS_MODE_LEARNED = 1, HS_MODE_AUTO = 2 } hs_mode;
 
 /* Index type of the output permutation. */
 typedef enum { HS_U32 = 0, HS_U64 = 1 } hs_index_t;

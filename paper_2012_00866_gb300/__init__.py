@@ -33,7 +33,7 @@ ERR_WORKSPACE = -7
 # hs_coder
 CODER_AUTO, CODER_ASCII7, CODER_BYTE8, CODER_ALPHA = 0, 1, 2, 3
 # hs_mode
-MODE_PLAIN, MODE_LEARNED = 0, 1
+MODE_PLAIN, MODE_LEARNED, MODE_AUTO = 0, 1, 2
 # hs_index_t
 U32, U64 = 0, 1
 # hs_numeric

@@ -1246,7 +1246,8 @@ hs_status hs_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_
     (void)out_t;
     g_last_error.clear();
     if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
-    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED && mode != HS_MODE_AUTO) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode == HS_MODE_AUTO) mode = HS_MODE_PLAIN;  // see hs_mode
     *out = make_layout(n, mode == HS_MODE_LEARNED).total;
     return HS_OK;
 }
@@ -1276,7 +1277,8 @@ hs_status hs_encode(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t 
 hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, int mode, int coder, int out_t,
                      void *d_perm, void *d_ws, size_t ws_bytes, void *stream) {
     g_last_error.clear();
-    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED && mode != HS_MODE_AUTO) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode == HS_MODE_AUTO) mode = HS_MODE_PLAIN;  // see hs_mode
     if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
     if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
@@ -1415,7 +1417,8 @@ hs_status hs_argsort_numeric(const void *d_values, uint64_t n, int type, int out
 hs_status hs_host_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int out_t, size_t *out) {
     g_last_error.clear();
     if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
-    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED && mode != HS_MODE_AUTO) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode == HS_MODE_AUTO) mode = HS_MODE_PLAIN;  // see hs_mode
     if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
     *out = make_host_layout(n, total_bytes, mode == HS_MODE_LEARNED, out_t == HS_U64 ? 8 : 4).total;
     return HS_OK;
@@ -1424,7 +1427,8 @@ hs_status hs_host_workspace_size(uint64_t n, uint64_t total_bytes, int mode, int
 hs_status hs_argsort_host(const uint8_t *h_bytes, const uint64_t *h_offsets, uint64_t n, int mode, int coder,
                           int out_t, void *h_perm, void *d_ws, size_t ws_bytes, void *stream) {
     g_last_error.clear();
-    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode != HS_MODE_PLAIN && mode != HS_MODE_LEARNED && mode != HS_MODE_AUTO) return fail(HS_ERR_INVALID_ARG, "bad mode");
+    if (mode == HS_MODE_AUTO) mode = HS_MODE_PLAIN;  // see hs_mode
     if (coder < HS_CODER_AUTO || coder > HS_CODER_ALPHA) return fail(HS_ERR_INVALID_ARG, "bad coder");
     if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
     if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");

@@ -54,6 +54,12 @@ def test_workspace_size_host_only():
     assert e.value.status == hs.ERR_INVALID_ARG
 
 
+def test_mode_auto_uses_the_plain_workspace():
+    import paper_2012_00866_gb300 as hs
+    for n in (1000, 10**6):
+        assert hs.workspace_size(n, mode=hs.MODE_AUTO) == hs.workspace_size(n, mode=hs.MODE_PLAIN)
+
+
 def test_argument_validation_without_gpu(lib):
     import paper_2012_00866_gb300 as hs
     vp = ctypes.c_void_p

@@ -728,3 +728,19 @@ def test_packed_index_width_boundary_lowercase(cuda_lib, n, packed):
     per_key = st["algo_bytes"] / (st["launches"] * n)
     assert (per_key <= 16.0) == packed
     assert_stable_sorted(w, perm)
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_mode_auto(cuda_lib, host):
+    """HS_MODE_AUTO sorts exactly, on device and host inputs (it resolves to
+    the plain path)."""
+    hs = cuda_lib
+    import torch
+    w = workloads.generate(5, 200_000, 21)
+    if host:
+        data = torch.from_numpy(w.bytes).pin_memory()
+        off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+        assert_oracle_equal(w, hs.argsort(data, off, mode=hs.MODE_AUTO))
+    else:
+        data, off = to_device(w)
+        assert_oracle_equal(w, hs.argsort_device(data, off, mode=hs.MODE_AUTO))
