@@ -341,6 +341,39 @@ def test_host_entry_point_chunks(cuda_lib, case):
     assert_oracle_equal(w, perm)
 
 
+def _letters(n, lo, hi, seed, maxlen=12):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(1, maxlen + 1, size=n).astype(np.uint64)
+    offsets = np.zeros(n + 1, np.uint64)
+    np.cumsum(lens, out=offsets[1:])
+    return workloads.Workload(rng.integers(lo, hi + 1, size=int(offsets[-1])).astype(np.uint8), offsets)
+
+
+def test_host_entry_point_range_widened_by_a_later_chunk(cuda_lib):
+    """Host inputs under the byte-range coder: the chunks are encoded with
+    the first chunk's range.  Letters 'c'..'x' with one 'a' in the last
+    chunk keep the width (5 bits) but shift every code, so that sort is
+    encoded once more with the whole range; with the 'a' in the first
+    chunk it is not."""
+    hs = cuda_lib
+    import torch
+    encodes = {}
+    for where in ("none", "first", "last"):
+        w = _letters(3_000_000, 99, 120, 51)
+        if where != "none":
+            w.bytes[int(w.offsets[5 if where == "first" else w.n - 7])] = 97
+        data = torch.from_numpy(w.bytes).pin_memory()
+        off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+        hs.stats_enable(True)
+        try:
+            perm = hs.argsort(data, off)
+            encodes[where] = hs.stats_read()["encode"]["launches"]
+        finally:
+            hs.stats_enable(False)
+        assert_oracle_equal(w, perm)
+    assert encodes["first"] == encodes["none"] and encodes["last"] == encodes["none"] + 1, encodes
+
+
 def test_host_entry_point_rejects_bad_input(cuda_lib):
     hs = cuda_lib
     import ctypes
