@@ -51,6 +51,9 @@ def parse_args():
     p.add_argument("--index", default=None, choices=["u32", "u64"],
                    help="permutation index type (default: u64 above 2^31 strings or for skewed_1e9, else u32)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default radix tile shape instead of timing the candidates on the first sort "
+                        "(for profiler runs, whose serialised launches distort the comparison)")
     p.add_argument("--stats", default=None, help="write per-kernel stats JSON here")
     return p.parse_args()
 
@@ -211,6 +214,8 @@ def run_ours(args, rank, world, local):
     device = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(device)
     hs.load()
+    if args.no_autotune:
+        hs.autotune(0)
     mode = hs.MODE_LEARNED if args.mode == "learned" else hs.MODE_PLAIN
 
     w = workloads.standard(args.workload, scale=args.scale)
@@ -460,6 +465,8 @@ def run_numeric(args, rank, world, local):
     device = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(device)
     hs.load()
+    if args.no_autotune:
+        hs.autotune(0)
     kind = NUMERIC[args.workload][0]
     index_u64 = args.index == "u64"
     if kind == "bigint":

@@ -301,8 +301,9 @@ struct Ctx {
     int alpha_w = 0;                  // its bits per char
     bool idx_packed = false;          // the encoder packed each string's index below its code
     int idx_bits = 0;                 // ... in this many bits
-    // hs_argsort_host: the permutation's copy to h_out may start once tie
-    // detection has written it; early_copy marks its end, and the fix-up's
+    // hs_argsort_host: the permutation's copy to h_out may start once it is
+    // written (packed words: by the last radix pass, or by tie detection
+    // when no pass ran); early_copy marks its end, and the fix-up's
     // rewrites (DevFlags::dirty_lo / dirty_hi, or all of it after refinement
     // rounds) are copied again afterwards.
     void *h_out = nullptr;
@@ -599,7 +600,8 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
         const OutMode om = to_final ? final_mode : kOutVals;
         double ob = 8.0 * n;                                   // keys read
         if (pack_bits > 0) {
-            ob += om == kOutPerm32 ? 4.0 * n : 8.0 * n;        // words or indices written
+            ob += a.keys_out ? 8.0 * n : 0.0;                  // words written
+            ob += om == kOutPerm32 ? 4.0 * n : (om == kOutPerm64 ? 8.0 * n : 0.0);  // indices written
         } else {
             ob += (first && synth_first) ? (flag_bits ? n / 8.0 : 0.0) : 4.0 * n;  // vals read
             ob += a.keys_out ? 8.0 * n : 0.0;                  // keys written
@@ -643,8 +645,10 @@ struct Input {
 
 // Step 3 on the sorted keys.  When it returns HS_OK with *synced set, every
 // launch has finished and c.h holds the final flags.
+// perm_written: packed words whose last radix pass wrote the permutation
+// beside them (tie detection then only finds the runs).
 hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst,
-                    bool *synced = nullptr, bool instance_in_key = false) {
+                    bool *synced = nullptr, bool instance_in_key = false, bool perm_written = false) {
     if (synced) *synced = false;
     const uint64_t n = in.n;
     RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
@@ -666,7 +670,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     }
     t.n = n;
     t.prefix_len = in.prefix_len;
-    t.perm = in.perm;
+    t.perm = (mode == kTiePacked && perm_written) ? nullptr : in.perm;
     t.perm_u64 = in.perm_u64;
     t.perm_n = n;
     t.q_small = q_small;
@@ -681,22 +685,23 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     HS_TRY(c.next_epoch(&t.epoch), "epoch");
     HS_TRY(c.counter(&t.tile_counter), "counter");
     // Packed words: the permutation is final but for the fix-up's runs once
-    // tie detection has written it, and those runs are few (the byte-range
-    // code covers 8 chars).  With (key, payload) pairs the fix-up's rewrites
-    // spread over the whole permutation (measured: the copy then goes twice),
-    // so the copy waits for the end there.
+    // written (by the last radix pass, or by tie detection), and those runs
+    // are few (the byte-range code covers 8 chars).  With (key, payload)
+    // pairs the fix-up's rewrites spread over the whole permutation
+    // (measured: the copy then goes twice), so the copy waits for the end.
     const bool early = c.h_out != nullptr && !inst.seg_offsets && mode == kTiePacked;
     cudaEvent_t perm_done = nullptr;
     if (early) {
         HS_TRY(cudaMemsetAsync(&c.d_flags->dirty_lo, 0xFF, sizeof(unsigned long long), c.s), "memset dirty");
         HS_TRY(sync_event(&perm_done), "event");
         c.events.push_back(perm_done);
+        if (perm_written) HS_TRY(cudaEventRecord(perm_done, c.s), "record last pass");
     }
     const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n
-                             : mode == kTiePacked ? 8.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n
+                             : mode == kTiePacked ? 8.0 * n + (t.perm ? (in.perm_u64 ? 8.0 : 4.0) * n : 0.0)
                                                   : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
     HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
-    if (early) HS_TRY(cudaEventRecord(perm_done, c.s), "record tie detect");
+    if (early && !perm_written) HS_TRY(cudaEventRecord(perm_done, c.s), "record tie detect");
     // Runs of copies of one string are final already; only the others go on
     // to refinement (queue B).
     HS_TRY(cudaMemsetAsync(&c.d_flags->qcount[kQLargeB], 0, sizeof(unsigned long long), c.s), "memset q");
@@ -902,14 +907,18 @@ hs_status argsort_plain(Ctx &c, const Input &in0, int coder) {
             if (perfect)
                 HS_TRY(c.timed(kKIdentity, 4.0 * n, [&] { return launch_identity(nullptr, n, in.perm, pmode, c.s); }),
                        "identity");
-        } else {
-            st = run_passes(c, b, &cur, n, passes, np, false, nullptr, false, perfect ? in.perm : nullptr, pmode,
+        }
+        // Host output: the last pass writes the permutation beside the
+        // words, so its copy leaves before tie detection.
+        const bool perm_written = np > 0 && (perfect || c.h_out != nullptr);
+        if (np > 0) {
+            st = run_passes(c, b, &cur, n, passes, np, false, nullptr, false, perm_written ? in.perm : nullptr, pmode,
                             !perfect, c.idx_bits);
             if (st != HS_OK) return st;
         }
         bool synced = false;
         if (!perfect) {
-            st = run_fixup(c, in, b, cur, kTiePacked, Instances{nullptr, 0}, &synced);
+            st = run_fixup(c, in, b, cur, kTiePacked, Instances{nullptr, 0}, &synced, false, perm_written);
             if (st != HS_OK) return st;
         }
         if (!synced) HS_TRY(c.read_flags(), "final sync");
@@ -1482,8 +1491,8 @@ hs_status hs_argsort_host(const uint8_t *h_bytes, const uint64_t *h_offsets, uin
     }
     if (st != HS_OK) return st;
     if (c.early_copy) {
-        // the copy issued after tie detection has to finish first; then the
-        // positions the fix-up rewrote go again
+        // the copy issued once the permutation was written has to finish
+        // first; then the positions the fix-up rewrote go again
         HS_TRY(cudaStreamWaitEvent(c.s, c.early_copy, 0), "wait early copy");
         uint64_t lo = 0, hi = n - 1;
         bool again = c.dirty_all;

@@ -154,8 +154,8 @@ tie_detect_kernel(const TieArgs a) {
         for (int i = 0; i < kTieItems; ++i)
             if (j0 + i < n) mine = combine(mine, run_state(j0 + i, (heads >> i) & 1u, (flagsb >> i) & 1u));
         // The permutation is the words' index fields in tile order:
-        // written with coalesced stores.
-        const int cnt = (int)umin64(kTieTile, n - t0);
+        // written with coalesced stores (unless the last radix pass wrote it).
+        const int cnt = a.perm ? (int)umin64(kTieTile, n - t0) : 0;
         for (int i = tid; i < cnt; i += kTieThreads) {
             const uint64_t idx = s_key[tie_slot(i + 1)] & imask;
             if (a.perm_u64)

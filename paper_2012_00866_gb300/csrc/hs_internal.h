@@ -115,7 +115,7 @@ struct OnesweepArgs {
 // generated as i | flag_bit(i) << 31; out: what vals_out receives.  With
 // a.pack_bits > 0 the keys are packed (key, index) words and nothing else
 // moves: kOutVals writes the words to keys_out, kOutPerm32/64 the indices
-// to vals_out.
+// to vals_out (and the words to keys_out as well when it is set).
 // items: keys per thread, 0 (the default shape) or one of onesweep_shapes()
 // (segmented passes always use 8).
 cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg,

@@ -288,11 +288,10 @@ onesweep_kernel(const OnesweepArgs a) {
         }
         if (PACKED) {
             const uint64_t idx = k & ((1ull << a.pack_bits) - 1);
-            if (OUT == kOutVals)
-                a.keys_out[pos] = k;
-            else if (OUT == kOutPerm32)
+            if (OUT == kOutVals || a.keys_out) a.keys_out[pos] = k;
+            if (OUT == kOutPerm32)
                 static_cast<uint32_t *>(a.vals_out)[pos] = (uint32_t)idx;
-            else
+            else if (OUT == kOutPerm64)
                 static_cast<uint64_t *>(a.vals_out)[pos] = idx;
             continue;
         }

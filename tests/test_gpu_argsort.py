@@ -429,6 +429,20 @@ def test_full_shared_prefix_1e8(cuda_lib):
 
 
 @pytest.mark.slow
+def test_full_skewed_1e9(cuda_lib):
+    """1e9 skewed words (10 GB of bytes) with the u64 permutation, as the
+    bench runs them; checked by the property check (a permutation, in
+    order, equal strings by index), which fixes the stable argsort."""
+    hs = cuda_lib
+    w = workloads.standard("skewed_1e9")
+    data, off = to_device(w)
+    perm = hs.argsort_device(data, off, index_u64=True)
+    del data, off
+    assert perm.dtype.itemsize == 8
+    assert_stable_sorted(w, perm)
+
+
+@pytest.mark.slow
 def test_random_lower_1e5(cuda_lib):
     hs = cuda_lib
     w = workloads.standard("random_lower_1e5")
