@@ -184,9 +184,6 @@ __device__ __forceinline__ uint64_t pack_w(uint64_t x, int w) {
     return t;
 }
 
-__device__ __forceinline__ uint64_t sub_bytes(uint64_t x, uint32_t d4) {
-    return (uint64_t)__vsub4((uint32_t)x, d4) | ((uint64_t)__vsub4((uint32_t)(x >> 32), d4) << 32);
-}
 
 template <int CODER, bool KEYFLAG>
 __global__ void __launch_bounds__(kEncThreads)
@@ -217,6 +214,11 @@ encode_kernel(const uint8_t *__restrict__ bytes,
     int aw = 7, ak = 9;
     bool alpha = false;
     uint32_t alo4 = 0;
+    // c - lo + 1 for all eight bytes of a word at once: x + d8 with d8 the
+    // byte (1 - lo) repeated, as one 64-bit add.  No byte of the string
+    // carries or borrows (lo <= c <= hi and hi - lo + 1 < 2^w <= 64), and
+    // the bytes past its end, which may, sit above it and are cleared.
+    uint64_t d8 = 0;
     if (CODER == 3) {
         int lo = 255 - (int)(pk.spec_range ? flags->alpha_spec_lo_inv : flags->alpha_lo_inv);
         int hi = (int)(pk.spec_range ? flags->alpha_spec_hi : flags->alpha_hi);
@@ -228,6 +230,7 @@ encode_kernel(const uint8_t *__restrict__ bytes,
         aw = w;
         ak = k;
         alo4 = (uint32_t)((lo - 1) & 0xFF) * 0x01010101u;
+        d8 = (uint64_t)(int64_t)(1 - lo) * 0x0101010101010101ull;
         if (blockIdx.x == 0 && tid == 0) {
             flags->alpha_w = (unsigned)w;
             flags->alpha_k = (unsigned)k;
@@ -304,14 +307,14 @@ encode_kernel(const uint8_t *__restrict__ bytes,
                     const int m = (int)umin64(len, (uint64_t)ak);
                     if (staged) {
                         // bytes q .. q+7 from the two aligned words at q & ~7,
-                        // minus (lo - 1) bytewise, bytes past m cleared, packed
+                        // mapped to c - lo + 1, bytes past m cleared, packed
                         const uint32_t q = (uint32_t)(base + off - a0);
                         const uint64_t *wp = reinterpret_cast<const uint64_t *>(s_bytes + (q & ~7u));
                         const uint64_t x0 = wp[0], x1 = wp[1];
                         const int r = 8 * (int)(q & 7u);
                         const uint64_t w0 = r ? (x0 >> r) | (x1 << (64 - r)) : x0;
                         const uint64_t keep = m >= 8 ? ~0ull : ((1ull << (8 * m)) - 1);
-                        code = pack_w(sub_bytes(w0, alo4) & keep, aw);  // the 8 chars, 8w bits
+                        code = pack_w((w0 + d8) & keep, aw);  // the 8 chars, 8w bits
                     } else {
                         const uint8_t *src = staged ? s_bytes + (uint32_t)(base + off - a0) : bytes + off;
                         const unsigned lo1 = (alo4 & 0xFFu);
