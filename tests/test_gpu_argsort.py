@@ -315,6 +315,36 @@ def test_runs_of_copies_with_one_odd_member(cuda_lib, n_copies, odd):
     assert_oracle_equal(w, hs.argsort_device(data, off))
 
 
+@pytest.mark.parametrize("n_copies", [40, 3000, 70_001])
+@pytest.mark.parametrize("case", ["none", "tail_byte", "len15_last", "len16_last", "shorter", "exact8"])
+def test_runs_of_copies_of_short_long_strings(cuda_lib, n_copies, case):
+    """Packed words, runs of copies of 12-16 byte strings (the code covers
+    8): the fix-up's filters must find one odd member that differs at byte
+    11, at the last byte of a 15- or 16-byte string, by its length, or is
+    the 8-byte prefix itself (exactly coded, same code).  Sizes cover the
+    CTA-sized (copies filter) and large classes."""
+    hs = cuda_lib
+    base = {"len15_last": b"abcdefghijklmno", "len16_last": b"abcdefghijklmnop"}.get(case, b"abcdefghijkl")
+    strs = [base] * n_copies
+    j = (n_copies * 5) // 11 + 1
+    if case == "tail_byte":
+        strs[j] = base[:11] + b"a" + base[12:]
+    elif case == "len15_last":
+        strs[j] = base[:14] + b"a"
+    elif case == "len16_last":
+        strs[j] = base[:15] + b"a"
+    elif case == "shorter":
+        strs[j] = base[:-1]
+    elif case == "exact8":
+        strs[j] = base[:8]
+    rng = np.random.default_rng(n_copies)
+    strs += [bytes(rng.integers(97, 123, size=int(rng.integers(3, 14))).astype(np.uint8)) for _ in range(500)]
+    order = rng.permutation(len(strs))
+    w = workloads.from_strings([strs[i] for i in order])
+    data, off = to_device(w)
+    assert_oracle_equal(w, hs.argsort_device(data, off))
+
+
 @pytest.mark.parametrize("case", ["pinned_u32", "pageable_u64", "learned", "byte8", "offset0"])
 def test_host_entry_point_chunks(cuda_lib, case):
     """hs_argsort_host: inputs and output in host memory, copied in chunks of
