@@ -78,3 +78,24 @@ def test_profile_traffic_lookup(tmp_path, monkeypatch):
     assert bench.profile_traffic("onesweep/w") is None
     monkeypatch.setattr(bench, "sources_digest", lambda paths=None: "other")
     assert bench.profile_traffic("onesweep_kernel/w") is None
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference on one rank: the oracle timed on the host
+    cores prints one JSON line with the contract's keys, its cpu_baseline
+    and an e2e with no transfers."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--workload", "random_lower_1e5", "--scale", "0.1"],
+                       capture_output=True, text=True, timeout=300,
+                       env={k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["higher_is_better"] is True and d["unit"] == "M keys/s" and d["value"] > 0
+    assert d["config"]["workload"] == "random_lower_1e5@0.1" and d["config"]["n"] == 10_000
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
