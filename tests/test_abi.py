@@ -54,6 +54,14 @@ def test_workspace_size_host_only():
     assert e.value.status == hs.ERR_INVALID_ARG
 
 
+def test_noalloc_limit_fits_its_scratch():
+    """hs_argsort_noalloc carves the hs_argsort layout out of its 16 MiB
+    static array: at HS_NOALLOC_MAX_N strings that layout must still fit."""
+    import paper_2012_00866_gb300 as hs
+    assert hs.workspace_size(hs.NOALLOC_MAX_N) <= 16 << 20
+    assert hs.workspace_size(hs.NOALLOC_MAX_N + 1) >= hs.workspace_size(hs.NOALLOC_MAX_N)
+
+
 def test_mode_auto_uses_the_plain_workspace():
     import paper_2012_00866_gb300 as hs
     for n in (1000, 10**6):
