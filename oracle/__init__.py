@@ -61,14 +61,14 @@ def _load():
         lib.oracle_check_sorted_batched.argtypes = [vp, vp, vp, u64, vp, ci]
         lib.oracle_string_to_long_mapped.restype = u64
         lib.oracle_string_to_long_mapped.argtypes = [vp, u64, ci, ci, vp]
-        lib.oracle_alpha_params.restype = ci
-        lib.oracle_alpha_params.argtypes = [vp, vp, u64, vp, vp, vp]
+        lib.oracle_alpha_params_k.restype = ci
+        lib.oracle_alpha_params_k.argtypes = [vp, vp, u64, ci, vp, vp, vp]
         lib.oracle_units_to_long.restype = u64
         lib.oracle_units_to_long.argtypes = [vp, u64, ci, ci, u64]
         lib.oracle_unicode_to_long.restype = u64
         lib.oracle_unicode_to_long.argtypes = [vp, u64]
-        lib.oracle_encode_alpha.restype = ci
-        lib.oracle_encode_alpha.argtypes = [vp, vp, u64, vp, vp, vp, vp, vp]
+        lib.oracle_encode_alpha_k.restype = ci
+        lib.oracle_encode_alpha_k.argtypes = [vp, vp, u64, ci, vp, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -125,30 +125,34 @@ def encode(data: np.ndarray, offsets: np.ndarray, coder: int = CODER_ASCII7):
     return codes, exact, bool(perfect.value)
 
 
-def alpha_params(data: np.ndarray, offsets: np.ndarray):
-    """Byte-range coder parameters: (map uint8[256], w, K, applies)."""
+def alpha_params(data: np.ndarray, offsets: np.ndarray, max_length: int | None = 8):
+    """Byte-range coder parameters: (map uint8[256], w, K, applies).
+    max_length: K; None takes the paper's longest K that fits 64 bits,
+    floor(64 / w) (Section 3.2: 12 letters in 5 bits, 10 in 6).  The GPU
+    library codes K = 8."""
     n = offsets.shape[0] - 1
     rank = np.zeros(256, dtype=np.uint8)
     w, k = ctypes.c_int(0), ctypes.c_int(0)
     data = np.ascontiguousarray(data, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
-    rc = _load().oracle_alpha_params(_ptr(data), _ptr(offsets), n, _ptr(rank),
-                                     ctypes.addressof(w), ctypes.addressof(k))
+    rc = _load().oracle_alpha_params_k(_ptr(data), _ptr(offsets), n, int(max_length or 0), _ptr(rank),
+                                       ctypes.addressof(w), ctypes.addressof(k))
     return rank, w.value, k.value, rc == 0
 
 
-def encode_alpha(data: np.ndarray, offsets: np.ndarray):
+def encode_alpha(data: np.ndarray, offsets: np.ndarray, max_length: int | None = 8):
     """Byte-range coder: (codes uint64[n], exact uint8[n], perfect, w, K), or
-    None when the byte range needs more than 6 bits."""
+    None when the byte range needs more than 6 bits (or K * w > 64).
+    max_length as in alpha_params."""
     n = offsets.shape[0] - 1
     codes = np.empty(n, dtype=np.uint64)
     exact = np.empty(n, dtype=np.uint8)
     perfect, w, k = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     data = np.ascontiguousarray(data, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
-    rc = _load().oracle_encode_alpha(_ptr(data), _ptr(offsets), n, _ptr(codes), _ptr(exact),
-                                     ctypes.addressof(perfect), ctypes.addressof(w),
-                                     ctypes.addressof(k))
+    rc = _load().oracle_encode_alpha_k(_ptr(data), _ptr(offsets), n, int(max_length or 0), _ptr(codes),
+                                       _ptr(exact), ctypes.addressof(perfect), ctypes.addressof(w),
+                                       ctypes.addressof(k))
     if rc != 0:
         return None
     return codes, exact, bool(perfect.value), w.value, k.value

@@ -149,11 +149,14 @@ int oracle_encode(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
  * w = ceil(log2(hi - lo + 2)) in place of the 7-bit mask ('a'..'z': 26
  * values, 5 bits; 'A'..'z': 58 values, 6 bits).  The map keeps byte order and
  * the padding stays below every value, so the code is order preserving.
- * max_length K = 8: as many characters as BYTE8 codes, in a sort key of
- * 8*w + 1 bits (41 for letters: five 9-bit radix digits where ASCII7's 64 bits
- * take seven); longer strings are left to Step 3.  Defined for w <= 6; a
- * string is exactly represented iff its length is at most 8 (a NUL byte
- * inside the range has a value of its own). */
+ * max_length K is a parameter.  The paper's own choice is the longest K that
+ * fits 64 bits, K = floor(64 / w): 12 case-independent letters in 5 bits, 10
+ * case-dependent ones in 6 bits, each string of up to K letters coded
+ * perfectly.  The GPU library codes K = 8 (as many characters as BYTE8), a
+ * sort key of 8*w + 1 bits (41 for letters: five 9-bit radix digits where 12
+ * letters would take seven) and leaves longer strings to Step 3.  Defined for
+ * w <= 6; a string is exactly represented iff its length is at most K (a NUL
+ * byte inside the range has a value of its own). */
 
 /* Algorithm 4 with a character map in place of the mask. */
 uint64_t oracle_string_to_long_mapped(const uint8_t *s, uint64_t len, int max_length,
@@ -169,10 +172,11 @@ uint64_t oracle_string_to_long_mapped(const uint8_t *s, uint64_t len, int max_le
 }
 
 /* Byte range of bytes[offsets[0] .. offsets[n]) and the coder parameters.
- * map_out[c] = c - lo + 1 inside the range, 0 outside.  Returns 0 when
- * w <= 6, else 1 (the coder does not apply; the outputs are still written). */
-int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
-                        uint8_t *map_out, int *w_out, int *k_out)
+ * map_out[c] = c - lo + 1 inside the range, 0 outside.  k_req: the K to use,
+ * or 0 for the paper's floor(64 / w).  Returns 0 when w <= 6 and K * w <= 64,
+ * else 1 (the coder does not apply; the outputs are still written). */
+int oracle_alpha_params_k(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int k_req,
+                          uint8_t *map_out, int *w_out, int *k_out)
 {
     int lo = 255, hi = 0;
     if (n > 0)
@@ -190,20 +194,28 @@ int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t 
     int w = 1;
     while ((1 << w) < span + 1)
         w++;
+    int k = k_req > 0 ? k_req : 64 / w;
     *w_out = w;
-    *k_out = 8;
-    return w <= 6 ? 0 : 1;
+    *k_out = k;
+    return (w <= 6 && k >= 1 && k * w <= 64) ? 0 : 1;
 }
 
-/* Encode with the byte-range coder; returns 1 (nothing written) when it does
- * not apply. */
-int oracle_encode_alpha(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
-                        uint64_t *codes_out, uint8_t *exact_out, int *perfect,
-                        int *w_out, int *k_out)
+/* The GPU library's parameters: K = 8. */
+int oracle_alpha_params(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
+                        uint8_t *map_out, int *w_out, int *k_out)
+{
+    return oracle_alpha_params_k(bytes, offsets, n, 8, map_out, w_out, k_out);
+}
+
+/* Encode with the byte-range coder at max_length k_req (0: floor(64 / w));
+ * returns 1 (nothing written) when it does not apply. */
+int oracle_encode_alpha_k(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int k_req,
+                          uint64_t *codes_out, uint8_t *exact_out, int *perfect,
+                          int *w_out, int *k_out)
 {
     uint8_t map[256];
     int w, k;
-    if (oracle_alpha_params(bytes, offsets, n, map, &w, &k) != 0) {
+    if (oracle_alpha_params_k(bytes, offsets, n, k_req, map, &w, &k) != 0) {
         *w_out = w;
         *k_out = k;
         return 1;
@@ -224,6 +236,13 @@ int oracle_encode_alpha(const uint8_t *bytes, const uint64_t *offsets, uint64_t 
     *w_out = w;
     *k_out = k;
     return 0;
+}
+
+int oracle_encode_alpha(const uint8_t *bytes, const uint64_t *offsets, uint64_t n,
+                        uint64_t *codes_out, uint8_t *exact_out, int *perfect,
+                        int *w_out, int *k_out)
+{
+    return oracle_encode_alpha_k(bytes, offsets, n, 8, codes_out, exact_out, perfect, w_out, k_out);
 }
 
 /* Unsigned-byte lexicographic comparison; a proper prefix is smaller. */

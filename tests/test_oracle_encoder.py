@@ -175,6 +175,54 @@ def test_alpha_truncation_and_nul():
     assert oracle.encode_alpha(*_ws([b"a", b"a\x00"])) is None   # 0x00..0x61 needs 7 bits
 
 
+# ---- the byte-range coder at the paper's own length (Section 3.2) ------------
+
+@pytest.mark.parametrize("alphabet, w_, k_", [(b"abcdefghijklmnopqrstuvwxyz", 5, 12),
+                                             (b"ABCDEFGHIJKLMNOPQRSTUVWXYZ[\\]^_`abcdefghijklmnopqrstuvwxyz", 6, 10)])
+def test_alpha_paper_length_is_perfect_for_letters(alphabet, w_, k_):
+    """Section 3.2: case-independent letters code in 5 bits and case-dependent
+    ones in 6, so 12 and 10 of them fit 64 bits.  At that length every string
+    of up to K letters is coded exactly: distinct strings get distinct codes,
+    in the strings' order.  Checked on 3,000 random strings of length 0..K
+    (all pairs), every string of length <= 2, and strings that differ only in
+    their K-th letter; a (K+1)-th letter is truncated away."""
+    rng = np.random.default_rng(len(alphabet))
+    al = list(alphabet)
+    strs = {b"", bytes([al[0]]), bytes([al[-1]])}
+    strs |= {bytes([a, b]) for a in al[:6] + al[-3:] for b in al[:4] + al[-2:]}
+    for _ in range(3000):
+        L = int(rng.integers(0, k_ + 1))
+        strs.add(bytes(al[int(x)] for x in rng.integers(0, len(al), size=L)))
+    stem = bytes(al[int(x)] for x in rng.integers(0, len(al), size=k_ - 1))
+    strs |= {stem + bytes([c]) for c in (al[0], al[1], al[-1])}
+    strs = sorted(strs)
+    wl = workloads.from_strings(strs)
+    codes, exact, perfect, w, k = oracle.encode_alpha(wl.bytes, wl.offsets, max_length=None)
+    assert (w, k) == (w_, k_)
+    assert perfect and all(exact)
+    c = [int(x) for x in codes]
+    assert all(a < b for a, b in zip(c, c[1:]))      # sorted strings, strictly increasing codes
+    assert max(c) < (1 << (k_ * w_))
+    long_ = workloads.from_strings([stem + bytes([al[3]]) + bytes([al[5]]), stem + bytes([al[3]])])
+    lc, le, lp, _, _ = oracle.encode_alpha(long_.bytes, long_.offsets, max_length=None)
+    assert lc[0] == lc[1] and list(le) == [0, 1] and not lp
+
+
+def test_alpha_length_parameter():
+    """K is a parameter: the same letters at K = 8 (the GPU library's length)
+    and at the paper's K = 12 give codes that agree on the first 8 letters:
+    the K = 12 code shifted right by 4 letters (20 bits) is the K = 8 code for
+    strings of up to 8 letters; K * w above 64 bits does not apply."""
+    strs = [b"", b"a", b"abc", b"zzzzzzzz", b"hello", b"abcdefgh"]
+    wl = workloads.from_strings(strs + [b"z"])
+    c8, _, _, w8, k8 = oracle.encode_alpha(wl.bytes, wl.offsets)
+    c12, _, _, w12, k12 = oracle.encode_alpha(wl.bytes, wl.offsets, max_length=None)
+    assert (w8, k8, w12, k12) == (5, 8, 5, 12)
+    for a, b in zip(c8, c12):
+        assert int(b) >> 20 == int(a)
+    assert oracle.encode_alpha(wl.bytes, wl.offsets, max_length=13) is None   # 65 bits
+
+
 def _ws(strs):
     wl = workloads.from_strings(strs)
     return wl.bytes, wl.offsets
