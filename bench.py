@@ -2,10 +2,14 @@
 """Throughput of the GB300 Huskysort string argsort.
 
 One step = one full stable argsort (encode, radix sort of the codes, tie
-fix-up) of the 1e7-string English-like workload (Zipf(1.1) draws over a
-50,000-word synthetic vocabulary), inputs resident in HBM.  Prints one JSON
+fix-up) of the largest single-GPU workload, 1e9 skewed strings (first letter
+Zipf(1.5) over a..z, lengths normal(10, 3) clipped to 1..24) with a u64
+permutation, inputs resident in HBM.  The same line carries the metric's
+comparison: the learned bucketer on the same strings, and the batched form
+(2,000 of the 20,000 log-uniform instances by default) against a loop of
+single sorts and against one plain sort of all its strings.  Prints one JSON
 line.  `--impl reference` times the CPU oracle (the plain stable merge sort)
-on the host cores instead.
+on the host cores instead, on a bounded sample of the same workload.
 
 Under torchrun (N > 1) every rank sorts its own copy of the workload
 (replicas: a single sort has no shard-local form without an exchange step);
@@ -31,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "strings sorted/sec (M keys/s) and % of HBM roofline, learned/batched vs plain radix"
 UNIT = "M keys/s"
-DEFAULT_WORKLOAD = "zipf_words_1e7"
+DEFAULT_WORKLOAD = "skewed_1e9"
 L2_FLUSH_BYTES = 256 << 20
 CPU_SAMPLE_MAX = 10_000_000   # strings the CPU baseline sorts at most
 
@@ -55,6 +59,12 @@ def parse_args():
                    help="keep the default radix tile shape instead of timing the candidates on the first sort "
                         "(for profiler runs, whose serialised launches distort the comparison)")
     p.add_argument("--stats", default=None, help="write per-kernel stats JSON here")
+    p.add_argument("--no-compare", dest="compare", action="store_false",
+                   help="skip the learned and batched comparison blocks of a plain single-sort run")
+    p.add_argument("--batched-scale", type=float, default=0.1,
+                   help="size of the batched comparison block as a fraction of batched_20000's 20,000 instances")
+    p.add_argument("--parity-samples", type=int, default=100_000,
+                   help="adjacent output pairs checked with the oracle's comparison at full size (0: none)")
     return p.parse_args()
 
 
@@ -205,6 +215,204 @@ def _sample(w, limit):
     return workloads.Workload(w.bytes[: int(off[-1])], off.copy())
 
 
+def _prefix(name, scale, limit):
+    """The first `limit` strings of a standard single-sort workload, generated
+    on their own (the generators are keyed by string index, so these are the
+    same strings as in the full workload)."""
+    import workloads
+    spec = workloads.STANDARD[name]
+    n = max(1, int(round(spec["n"] * scale)))
+    return workloads.generate(spec["kind"], min(n, limit), spec["seed"]), n
+
+
+def _gpu_uuid(device):
+    import torch
+    try:
+        uuid = str(torch.cuda.get_device_properties(device).uuid)
+        return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        return None
+
+
+def _time_steps(step, steps, flush, stream):
+    """CUDA-event times (ms) of `steps` calls of step(), the L2 flushed by a
+    256 MiB write before each."""
+    import torch
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _kernel_stats(hs, step, steps, flush, stream):
+    """Per-kernel CUDA-event stats of `steps` more calls, outside any timed
+    region (the launches are bracketed by events)."""
+    import torch
+    hs.stats_enable(True)
+    _time_steps(step, steps, flush, stream)
+    torch.cuda.synchronize()
+    kstats = hs.stats_read()
+    hs.stats_enable(False)
+    return kstats
+
+
+def _roofline(kstats, steps, ms, traffic_key=None):
+    """Roofline of the kernel with the most time: algorithmic bytes per launch
+    over its mean CUDA-event launch time, against the measured copy peak."""
+    peaks, peak_src = measured_peaks()
+    timed = {k: v for k, v in kstats.items() if v["launches"] and v["total_ms"] > 0}
+    if not timed:
+        return None
+    top = max(timed, key=lambda k: timed[k]["total_ms"])
+    st = timed[top]
+    achieved = st["algo_bytes"] / (st["total_ms"] / 1e3) / 1e9
+    return {"kernel": top + "_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                            else "fallback 6.8 TB/s"),
+            "algo_bytes_per_launch": st["algo_bytes"] / st["launches"],
+            "launch_ms": round(st["total_ms"] / st["launches"], 5),
+            "share_of_step": round(st["total_ms"] / steps / ms, 3),
+            "traffic": profile_traffic(f"{top}_kernel/{traffic_key}") if traffic_key else None}
+
+
+def _stages(kstats, steps):
+    return {k: {"launches_per_step": v["launches"] / steps, "ms_per_step": round(v["total_ms"] / steps, 4),
+                "GBps": round(v["algo_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1) if v["total_ms"] > 0 else None}
+            for k, v in kstats.items() if v["launches"]}
+
+
+def _sampled_pairs_in_order(w, perm_np, samples, seed=0):
+    """Sampled parity at full size: `samples` random adjacent positions k of
+    the permutation are checked with the oracle's string comparison (string
+    perm[k] before string perm[k+1], ties by index).  Returns the number of
+    pairs out of order."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    n = perm_np.size
+    if n < 2:
+        return 0
+    bad = 0
+    for k in rng.integers(0, n - 1, size=min(samples, n - 1)):
+        a, b = int(perm_np[k]), int(perm_np[k + 1])
+        c = oracle.string_compare(w.bytes, w.offsets, a, b)
+        bad += c > 0 or (c == 0 and a > b)
+    return bad
+
+
+def _learned_block(hs, args, w, data, off, perm_plain, index_u64, flush, stream, n):
+    """The learned bucketer on the same strings: throughput, its roofline and
+    its parity (equal to the plain path's permutation, and sampled adjacent
+    pairs in order by the oracle's comparison)."""
+    import torch
+    perm = torch.empty_like(perm_plain)
+
+    def step():
+        return hs.argsort_device(data, off, mode=hs.MODE_LEARNED, index_u64=index_u64, out=perm)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms_list = _time_steps(step, args.steps, flush, stream)
+    ms = sum(ms_list) / len(ms_list)
+    kstats = _kernel_stats(hs, step, args.steps, flush, stream)
+    equal = bool(torch.equal(perm, perm_plain))
+    sample = None
+    if args.parity_samples:
+        sample = _sampled_pairs_in_order(w, perm.cpu().numpy().view(np.uint64 if index_u64 else np.uint32),
+                                         args.parity_samples)
+    return {"value": round(n / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "vs_plain": None,
+            "parity": {"equal_to_plain_permutation": equal,
+                       "oracle_sampled_pairs": args.parity_samples, "pairs_out_of_order": sample},
+            "roofline": _roofline(kstats, args.steps, ms, f"{args.workload}/learned"),
+            "gpu_launches": int(sum(v["launches"] for v in kstats.values()) / args.steps),
+            "stages": _stages(kstats, args.steps)}
+
+
+def _batched_block(hs, args, device, flush, stream):
+    """hs_argsort_batched on the batched workload (at --batched-scale of its
+    20,000 instances) against two references on the same GPU: the
+    per-instance loop of hs_argsort calls, and one plain hs_argsort of all
+    the strings as a single instance."""
+    import torch
+    import oracle
+    import workloads
+    w = workloads.standard("batched_20000", scale=args.batched_scale)
+    n = w.n
+    data = torch.from_numpy(w.bytes).to(device)
+    off = torch.from_numpy(w.offsets.view(np.int64)).to(device)
+    seg = torch.from_numpy(w.seg_offsets.view(np.int64)).to(device)
+    perm = torch.empty(n, dtype=torch.int32, device=device)
+
+    def batched():
+        return hs.argsort_batched(data, off, seg, out=perm)
+
+    for _ in range(args.warmup):
+        batched()
+    torch.cuda.synchronize()
+    ms_list = _time_steps(batched, args.steps, flush, stream)
+    ms = sum(ms_list) / len(ms_list)
+    kstats = _kernel_stats(hs, batched, args.steps, flush, stream)
+    got = perm.cpu().numpy().view(np.uint32)
+    # parity: every instance of at most 20,000 strings among the first 400
+    # instances, against the oracle's stable argsort of that instance
+    checked, bad = 0, 0
+    for k in range(min(400, len(w.seg_offsets) - 1)):
+        lo, hi = int(w.seg_offsets[k]), int(w.seg_offsets[k + 1])
+        if hi - lo > 20_000:
+            continue
+        o = w.offsets[lo:hi + 1]
+        want = oracle.stable_argsort(w.bytes[int(o[0]):int(o[-1])], o - o[0])
+        bad += int(not np.array_equal(got[lo:hi], want))
+        checked += 1
+
+    views = []
+    for k in range(len(w.seg_offsets) - 1):
+        lo, hi = int(w.seg_offsets[k]), int(w.seg_offsets[k + 1])
+        if hi > lo:
+            views.append((data[int(w.offsets[lo]):int(w.offsets[hi])],
+                          off[lo:hi + 1] - int(w.offsets[lo]), perm[lo:hi]))
+
+    def loop():
+        for d, o, p in views:
+            hs.argsort_device(d, o, out=p)
+
+    loop_steps = max(1, min(args.steps, 5))
+    loop()
+    torch.cuda.synchronize()
+    loop_ms = sum(_time_steps(loop, loop_steps, flush, stream)) / loop_steps
+
+    def single():
+        return hs.argsort_device(data, off, out=perm)
+
+    for _ in range(args.warmup):
+        single()
+    torch.cuda.synchronize()
+    single_ms = sum(_time_steps(single, args.steps, flush, stream)) / args.steps
+    del data, off, seg, perm, views
+    torch.cuda.synchronize()
+    return {"workload": "batched_20000" + (f"@{args.batched_scale:g}" if args.batched_scale != 1.0 else ""),
+            "instances": int(len(w.seg_offsets) - 1), "n": n, "bytes": int(w.bytes.size),
+            "value": round(n / (ms / 1e3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "per_instance_loop": {"value": round(n / (loop_ms / 1e3) / 1e6, 3), "ms_per_step": round(loop_ms, 3),
+                                  "steps": loop_steps},
+            "one_plain_sort_of_all_strings": {"value": round(n / (single_ms / 1e3) / 1e6, 3),
+                                              "ms_per_step": round(single_ms, 4)},
+            "vs_loop": round(loop_ms / ms, 2), "vs_one_plain_sort": round(single_ms / ms, 3),
+            "parity": {"instances_checked_against_oracle": checked, "instances_differing": bad},
+            "roofline": _roofline(kstats, args.steps, ms, "batched_20000"),
+            "gpu_launches": int(sum(v["launches"] for v in kstats.values()) / args.steps),
+            "stages": _stages(kstats, args.steps)}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import workloads
@@ -245,50 +453,25 @@ def run_ours(args, rank, world, local):
                 hs.argsort_device(d, o, out=p)
             return perm
         if batched:
-            return hs.argsort_batched(data, off, seg)
+            return hs.argsort_batched(data, off, seg, out=perm)
         return hs.argsort_device(data, off, mode=mode, index_u64=index_u64, out=perm)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(device)
 
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(device).uuid)
-        if not uuid.startswith("GPU-"):
-            uuid = "GPU-" + uuid
-    except Exception:
-        uuid = None
-    clocks = ClockSampler(uuid)
-
-    def timed_steps():
-        ms_list = []
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            ms_list.append(e0.elapsed_time(e1))
-        return ms_list
-
+    clocks = ClockSampler(_gpu_uuid(device))
     # the timed region: no per-kernel instrumentation
     clocks.start()
     barrier(world)
     torch.cuda.synchronize(device)
-    step_ms = timed_steps()
+    step_ms = _time_steps(step, args.steps, flush, stream)
     torch.cuda.synchronize(device)
     barrier(world)
     clock_info = clocks.stop()
     # the same steps again with per-kernel CUDA events (the stage breakdown
     # and the roofline's launch durations), outside the timed region
-    hs.stats_enable(True)
-    timed_steps()
-    torch.cuda.synchronize(device)
-    kstats = hs.stats_read()
-    hs.stats_enable(False)
+    kstats = _kernel_stats(hs, step, args.steps, flush, stream)
 
     ms = sum(step_ms) / len(step_ms)
     ms = max_over_ranks(ms, world, device)
@@ -323,27 +506,26 @@ def run_ours(args, rank, world, local):
         _, _, used = hs.encode(data, off)
         coder_name = "auto(" + {1: "ascii7", 2: "byte8", 3: "alpha"}.get(used, str(used)) + ")"
 
-    peaks, peak_src = measured_peaks()
-    launches = sum(v["launches"] for v in kstats.values())
-    roofline = None
-    timed = {k: v for k, v in kstats.items() if v["launches"] and v["total_ms"] > 0}
-    if timed:
-        top = max(timed, key=lambda k: timed[k]["total_ms"])
-        st = timed[top]
-        achieved = st["algo_bytes"] / (st["total_ms"] / 1e3) / 1e9
-        roofline = {"kernel": top + "_kernel", "bound": "hbm", "achieved": round(achieved, 1),
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": round(achieved / peaks["hbm_gbs"], 4),
-                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
-                    "algo_bytes_per_launch": st["algo_bytes"] / st["launches"],
-                    "launch_ms": round(st["total_ms"] / st["launches"], 5),
-                    "share_of_step": round(st["total_ms"] / args.steps / ms, 3),
-                    "traffic": profile_traffic(f"{top}_kernel/{args.workload}")}
+    roofline = _roofline(kstats, args.steps, ms, args.workload)
+    launches = sum(v["launches"] for v in kstats.values()) / args.steps * args.steps
+    stages = _stages(kstats, args.steps)
 
-    stages = {k: {"launches_per_step": v["launches"] / args.steps,
-                  "ms_per_step": round(v["total_ms"] / args.steps, 4),
-                  "GBps": round(v["algo_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1) if v["total_ms"] > 0 else None}
-              for k, v in kstats.items() if v["launches"]}
+    # the metric's comparison: learned and batched forms against plain radix
+    learned = None
+    if (rank == 0 and world == 1 and not batched and not loop and mode == hs.MODE_PLAIN
+            and args.compare and n >= 65536):
+        learned = _learned_block(hs, args, w, data, off, perm, index_u64, flush, stream, n)
+        learned["vs_plain"] = round(learned["value"] / value, 3)
+    parity_plain = None
+    if rank == 0 and not batched and not loop and args.parity_samples:
+        parity_plain = {"oracle_sampled_pairs": args.parity_samples,
+                        "pairs_out_of_order": _sampled_pairs_in_order(
+                            w, perm.cpu().numpy().view(np.uint64 if index_u64 else np.uint32), args.parity_samples)}
+    del data, off, seg
+    batched_block = None
+    if rank == 0 and world == 1 and not batched and args.compare:
+        torch.cuda.synchronize(device)
+        batched_block = _batched_block(hs, args, device, flush, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -388,6 +570,9 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "roofline": roofline,
+            "parity": parity_plain,
+            "learned": learned,
+            "batched": batched_block,
             "cpu_baseline": cpu,
             "clocks": clock_info,
             "stages": stages,
@@ -641,8 +826,13 @@ def run_reference(args, rank, world, local):
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
             flush=True)
         return
-    w = workloads.standard(args.workload, scale=args.scale)
-    full_n = w.n
+    if workloads.STANDARD[args.workload]["kind"] != 4:
+        # single sorts: only the sampled prefix is generated (the same strings
+        # as the workload's first ones)
+        w, full_n = _prefix(args.workload, args.scale, CPU_SAMPLE_MAX)
+    else:
+        w = workloads.standard(args.workload, scale=args.scale)
+        full_n = w.n
     if w.seg_offsets is not None:   # batched: the leading instances up to the sample bound
         k = 1
         while k < len(w.seg_offsets) - 1 and int(w.seg_offsets[k + 1]) <= CPU_SAMPLE_MAX:
@@ -653,7 +843,8 @@ def run_reference(args, rank, world, local):
         n = cut
     else:
         sw = _sample(w, CPU_SAMPLE_MAX)
-        sort = lambda: oracle.stable_argsort(sw.bytes, sw.offsets, threads=threads)
+        index_u64 = (args.index or ("u64" if args.workload.startswith("skewed") else "u32")) == "u64"
+        sort = lambda: oracle.stable_argsort(sw.bytes, sw.offsets, index_u64=index_u64, threads=threads)
         n = sw.n
     for _ in range(args.warmup):
         sort()
@@ -670,8 +861,10 @@ def run_reference(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
         "config": {"workload": args.workload + (f"@{args.scale:g}" if args.scale != 1.0 else ""),
-                   "n": full_n, "bytes": int(w.bytes.size), "mode": "oracle",
-                   "index": "u32", "parallelism": "host threads"},
+                   "n": full_n, "sample_bytes": int(w.bytes.size), "mode": "oracle",
+                   "index": ("u64" if (w.seg_offsets is None and (args.index or (
+                       "u64" if args.workload.startswith("skewed") else "u32")) == "u64") else "u32"),
+                   "parallelism": "host threads"},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": (f"the full {args.workload} workload each step" if n == full_n else
                                     f"the first {n} strings of {args.workload} each step")},

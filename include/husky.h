@@ -158,7 +158,9 @@ HS_API hs_status hs_argsort(const uint8_t *d_bytes, const uint64_t *d_offsets,
  *                  d_perm[seg_offsets[s] .. seg_offsets[s+1]) hold the stable
  *                  argsort of that instance as LOCAL indices (0-based within
  *                  the instance).
- *   Each instance must hold fewer than 2^31 strings; n may exceed 2^32. */
+ *   Each instance must hold fewer than 2^31 strings (HS_ERR_INVALID_ARG
+ *   otherwise: at once when n > num_segs * (2^31 - 1), else from the device
+ *   check of seg_offsets); n may exceed 2^32. */
 HS_API hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets,
                              const uint64_t *d_seg_offsets, uint64_t num_segs,
                              uint64_t n, int coder, uint32_t *d_perm,
@@ -204,9 +206,12 @@ HS_API hs_status hs_host_workspace_size(uint64_t n, uint64_t total_bytes,
  * Scratch comes from one static device array of HS_NOALLOC_SCRATCH_BYTES
  * (16 MiB) inside the library; every GPU on which the library is loaded holds
  * it until the process exits.  No cudaMalloc, cudaFree or other allocating
- * routine is called.  The first call on each device looks up the array's
- * device address with cudaGetSymbolAddress while that device is current;
- * make that first call before any stream capture begins on the device.
+ * routine is called.  The first call in each CUDA context looks up the
+ * array's device address with cudaGetSymbolAddress while that context's
+ * device is current, and later calls in the context reuse it; make that first
+ * call before any stream capture begins on the device.  After a device reset
+ * the next call runs in a new context and looks the address up again (again
+ * before any capture).
  *
  * All calls share the one array and it keeps the previous call's contents
  * (the call clears what must start at zero itself).  Calls whose GPU work
@@ -344,6 +349,18 @@ HS_API hs_status hs_argsort_bigint(const uint8_t *d_bytes,
                                    uint64_t total_bytes, int out_t,
                                    void *d_perm, void *d_ws, size_t ws_bytes,
                                    void *stream);
+
+/* Test support for the bounded device-side waits.  A radix pass's tiles wait
+ * on the counts that earlier tiles publish (decoupled look-back); each wait
+ * gives up after a poll budget, records HS_ERR_TIMEOUT and lets its kernel
+ * finish, and the fix-up kernels then do nothing.  This call sets, on the
+ * current device, the budget in polls (0 restores the default of 2^22) and
+ * the id of one tile per pass whose counts are never published
+ * (withhold_tile; -1, the default, publishes all), so that a test can make a
+ * wait run out and check that the status reaches the caller and the next call
+ * succeeds.  Results are wrong while a tile is withheld.  Not for use while
+ * other library calls run.  HS_ERR_INVALID_ARG for withhold_tile < -1. */
+HS_API hs_status hs_test_bounded_waits(uint32_t spin_limit, int64_t withhold_tile);
 
 /* Message describing the calling thread's last failure ("" if none).  The
  * pointer stays valid until the next library call on this thread. */

@@ -64,6 +64,15 @@ HS_API hs_status hs_learned_profile(const uint8_t *d_bytes,
                                     uint32_t *d_buckets, double *h_info,
                                     void *d_ws, size_t ws_bytes, void *stream);
 
+/* Test support: the number of bucket-id bits the learned path uses.  By
+ * default (bits = 0) it takes about n/256 buckets rounded to whole 9-bit
+ * partition passes: 18 bits up to about 2.7e8 keys, 23 or 24 above.  A value
+ * of 9..24 forces that many bits for every later learned sort in the process,
+ * so that the three-pass branches can be checked at sizes the oracle sorts
+ * quickly; the result never depends on it.  Workspace sizes follow the
+ * setting.  HS_ERR_INVALID_ARG for other values. */
+HS_API hs_status hs_learned_force_bucket_bits(int bits);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,7 +47,8 @@ EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size", "hs_shutdown",
            "hs_last_error", "hs_version", "hs_encode_numeric", "hs_numeric_workspace_size", "hs_argsort_numeric",
            "hs_autotune", "hs_autotune_choice", "hs_bigint_workspace_size", "hs_argsort_bigint",
-           "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile")
+           "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile",
+           "hs_learned_force_bucket_bits", "hs_test_bounded_waits")
 
 NOALLOC_MAX_N = 262144
 
@@ -96,6 +97,10 @@ def load(path: str | None = None):
     lib.hs_rmi_sample_indices.argtypes = [u64, u64, vp, vp]
     lib.hs_learned_profile.restype = ci
     lib.hs_learned_profile.argtypes = [vp, vp, u64, ci, vp, vp, vp, vp, sz, vp]
+    lib.hs_learned_force_bucket_bits.restype = ci
+    lib.hs_test_bounded_waits.restype = ci
+    lib.hs_test_bounded_waits.argtypes = [ctypes.c_uint32, ctypes.c_int64]
+    lib.hs_learned_force_bucket_bits.argtypes = [ci]
     lib.hs_argsort_host.restype = ci
     lib.hs_argsort_host.argtypes = [vp, vp, u64, ci, ci, ci, vp, vp, sz, vp]
     lib.hs_host_workspace_size.restype = ci
@@ -143,6 +148,18 @@ def _stream_handle(stream) -> int:
 
 def _ptr(t: torch.Tensor | None) -> int:
     return 0 if t is None else int(t.data_ptr())
+
+
+def test_bounded_waits(spin_limit: int = 0, withhold_tile: int = -1):
+    """Test support: the look-back poll budget (0: default) and a tile whose
+    counts are never published (-1: none), on the current device."""
+    _check(load().hs_test_bounded_waits(spin_limit, withhold_tile))
+
+
+def learned_force_bucket_bits(bits: int):
+    """Test support: force the learned path's bucket-id bits (9..24), or 0
+    for its own choice (about n/256 buckets)."""
+    _check(load().hs_learned_force_bucket_bits(bits))
 
 
 def workspace_size(n: int, mode: int = MODE_PLAIN, out_t: int = U32,
@@ -343,17 +360,20 @@ def argsort(data: torch.Tensor, offsets: torch.Tensor, mode: int = MODE_PLAIN,
 
 def argsort_batched(data: torch.Tensor, offsets: torch.Tensor,
                     seg_offsets: torch.Tensor, coder: int = CODER_AUTO,
-                    stream=None) -> torch.Tensor:
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Independent stable argsorts of the instances delimited by seg_offsets
     (string-index boundaries); returns local indices (int32) laid out like
-    the strings."""
+    the strings (written into `out` when given)."""
     data, offsets = _as_device_inputs(data, offsets)
     if seg_offsets.dtype not in (torch.int64, torch.uint64) or not seg_offsets.is_cuda:
         raise TypeError("seg_offsets must be an int64 device tensor")
     seg_offsets = seg_offsets.contiguous()
     n = offsets.numel() - 1
     num_segs = seg_offsets.numel() - 1
-    out = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+    elif out.dtype != torch.int32 or out.numel() != n or not out.is_cuda:
+        raise ValueError("out has the wrong dtype, size or device")
     ws = workspace(batched_workspace_size(n, num_segs), offsets.device)
     _check(load().hs_argsort_batched(_ptr(data), _ptr(offsets), _ptr(seg_offsets),
                                      num_segs, n, coder, _ptr(out), _ptr(ws),

@@ -7,8 +7,11 @@
 //   if not perfect: tie detection, then large-run
 //   refinement rounds, then CTA and warp run sorts       -- Step 3
 // The caller owns every device buffer; scratch is carved from d_ws.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+
+#include <cuda.h>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -111,8 +114,14 @@ struct Layout {
 constexpr uint64_t kLearnedMinN = 1ull << 16;  // below this the plain path is used
 
 // Bucket-id bits: about n/256 buckets, rounded to whole 9-bit partition
-// passes -- 18 bits (two passes) up to ~2.7e8 keys, 24 bits (three) above.
+// passes -- 18 bits (two passes) up to ~2.7e8 keys, 23-24 bits (three)
+// above.  g_forced_bucket_bits (hs_learned_force_bucket_bits) overrides the
+// choice so that the wider branches can be checked at small n.
+std::atomic<int> g_forced_bucket_bits{0};
+
 int learned_bits(uint64_t n) {
+    const int forced = g_forced_bucket_bits.load();
+    if (forced > 0) return forced;
     int want = 1;
     while (want < 30 && (1ull << want) * 256 < n) ++want;
     return want <= 20 ? 18 : (want + 2 < 24 ? want + 2 : 24);
@@ -647,9 +656,11 @@ struct Input {
 // launch has finished and c.h holds the final flags.
 // perm_written: packed words whose last radix pass wrote the permutation
 // beside them (tie detection then only finds the runs).
-hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst,
+hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst0,
                     bool *synced = nullptr, bool instance_in_key = false, bool perm_written = false) {
     if (synced) *synced = false;
+    Instances inst = inst0;
+    inst.stop = &c.d_flags->error;  // after a give-up the fix-up kernels do nothing
     const uint64_t n = in.n;
     RunEntry *q_small = c.at<RunEntry>(c.L.q_small);
     RunEntry *q_medium = c.at<RunEntry>(c.L.q_medium);
@@ -1156,7 +1167,9 @@ hs_status argsort_batched(Ctx &c, const Input &in0, const uint64_t *seg_offsets,
     HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
     HS_TRY(c.timed(kKValidate, 0.0, [&] { return launch_validate_segments(seg_offsets, num_segs, n, c.d_flags, c.s); }), "validate segments");
     HS_TRY(c.read_flags(), "validate sync");
-    if (c.h.error & kErrOffsets) return fail(HS_ERR_INVALID_ARG, "seg_offsets must start at 0, not decrease, and end at n");
+    if (c.h.error & kErrOffsets)
+        return fail(HS_ERR_INVALID_ARG,
+                    "seg_offsets must start at 0, not decrease, end at n, and give no instance 2^31 or more strings");
     // With the byte-range coder the key leaves room above it for the
     // instance id: one key, no separate instance array in the radix passes.
     int seg_bits = 1;
@@ -1520,6 +1533,10 @@ hs_status hs_argsort_batched(const uint8_t *d_bytes, const uint64_t *d_offsets, 
     if (num_segs > 0xFFFFFFFFull) return fail(HS_ERR_INVALID_ARG, "num_segs must fit 32 bits");
     if (n == 0) return HS_OK;
     if (num_segs == 0) return fail(HS_ERR_INVALID_ARG, "n > 0 strings but no instances");
+    // Local indices are 31-bit: more strings than num_segs instances of
+    // 2^31 - 1 means some instance is too large (the device checks each one).
+    if (n > num_segs * (uint64_t)kIdxMask)
+        return fail(HS_ERR_INVALID_ARG, "an instance holds 2^31 or more strings");
     if (!d_bytes || !d_offsets || !d_seg_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
     Ctx c;
     hs_status st;
@@ -1676,6 +1693,21 @@ hs_status hs_learned_profile(const uint8_t *d_bytes, const uint64_t *d_offsets, 
     return HS_OK;
 }
 
+hs_status hs_test_bounded_waits(uint32_t spin_limit, int64_t withhold_tile) {
+    g_last_error.clear();
+    if (withhold_tile < -1) return fail(HS_ERR_INVALID_ARG, "withhold_tile must be -1 or a tile id");
+    HS_TRY(set_wait_test(spin_limit, (long long)withhold_tile), "bounded-wait test setting");
+    return HS_OK;
+}
+
+hs_status hs_learned_force_bucket_bits(int bits) {
+    g_last_error.clear();
+    if (bits != 0 && (bits < kRadixBits || bits > 24))
+        return fail(HS_ERR_INVALID_ARG, "bucket bits must be 0 or 9..24");
+    g_forced_bucket_bits.store(bits);
+    return HS_OK;
+}
+
 const char *hs_last_error(void) { return g_last_error.c_str(); }
 
 int hs_version(void) { return 100; }
@@ -1686,35 +1718,75 @@ int hs_version(void) { return 100; }
 //
 // The scratch of hs_argsort, carved from one static device array instead of
 // a caller-supplied workspace.  Host code must not use the array's name as a
-// device address: its device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current, and that pointer is what
-// the kernels receive.
+// device address: its device address is looked up with cudaGetSymbolAddress
+// once per CUDA context, while that context's device is current, and that
+// pointer is what the kernels receive.
 
 static __device__ __align__(256) unsigned char hs_noalloc_scratch[HS_NOALLOC_SCRATCH_BYTES];
 
 namespace hs {
 namespace {
 
-constexpr int kNoAllocMaxDevices = 64;
+// One cached address per CUDA context.  The key is the context's id, not the
+// device number: after a device reset the module is loaded again in a new
+// context, possibly at another address, and the lookup must be repeated.
+struct NoAllocEntry {
+    unsigned long long ctx_id;
+    void *ptr;
+};
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::vector<NoAllocEntry> g_noalloc_cache;
 
-// Device address of the static scratch on the current device (set-up on the
-// first call per device).
+// The two driver calls, found through the runtime (the library does not
+// link the driver, so that it loads on machines without one).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+hs_status driver_calls() {
+    if (g_ctx_get_current && g_ctx_get_id) return HS_OK;
+    void *a = nullptr, *b = nullptr;
+    cudaDriverEntryPointQueryResult qa{}, qb{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+        return fail(HS_ERR_CUDA, "hs_argsort_noalloc: driver entry points cuCtxGetCurrent / cuCtxGetId not found");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(b);
+    return HS_OK;
+}
+
+// Device address of the static scratch in the current context (looked up on
+// the first call in each context, with that context's device current).
 hs_status noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail_cuda(e, "hs_argsort_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HS_ERR_INVALID_ARG, "hs_argsort_noalloc: device id too large");
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, hs_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            return fail_cuda(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "hs_argsort_noalloc: cudaGetSymbolAddress");
-        g_noalloc_ptr[dev] = p;
+    hs_status st = driver_calls();
+    if (st != HS_OK) return st;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) {
+        // no context bound to this thread yet: bind the device's primary one
+        e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return fail_cuda(e, "hs_argsort_noalloc: cudaSetDevice");
+        if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr)
+            return fail(HS_ERR_CUDA, "hs_argsort_noalloc: no current CUDA context");
     }
-    *out = g_noalloc_ptr[dev];
+    unsigned long long id = 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return fail(HS_ERR_CUDA, "hs_argsort_noalloc: cuCtxGetId failed");
+    for (const NoAllocEntry &en : g_noalloc_cache)
+        if (en.ctx_id == id) {
+            *out = en.ptr;
+            return HS_OK;
+        }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, hs_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+        return fail_cuda(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "hs_argsort_noalloc: cudaGetSymbolAddress");
+    g_noalloc_cache.push_back(NoAllocEntry{id, p});
+    *out = p;
     return HS_OK;
 }
 

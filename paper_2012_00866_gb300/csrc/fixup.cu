@@ -312,6 +312,7 @@ small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict_
                   IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
                   const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
                   Instances inst, int prefix_len, DevFlags *dirty) {
+    if (stopped(inst)) return;
     const int lane = threadIdx.x & 31;
     const uint64_t warp_id = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -402,6 +403,7 @@ distinct_sample_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__rest
                        const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n,
                        Instances inst, int prefix_len, uint32_t *diff, unsigned long long *base,
                        unsigned int *done) {
+    if (stopped(inst)) return;
     __shared__ unsigned long long s_warp[8];
     __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -449,6 +451,7 @@ distinct_full_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restri
                      const unsigned long long *__restrict__ qcount, uint64_t cap, Instances inst, int prefix_len,
                      const unsigned long long *__restrict__ base, uint32_t *diff, RunEntry *__restrict__ q_out,
                      unsigned long long *qcount_out, uint64_t cap_out, DevFlags *flags, unsigned int *done) {
+    if (stopped(inst)) return;
     const uint64_t count = umin64(*qcount, cap);
     const uint64_t total = base[count];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -494,6 +497,7 @@ copies_filter_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restri
                      const IdxT *__restrict__ perm, RunEntry *__restrict__ q,
                      const unsigned long long *__restrict__ qcount, uint64_t cap, uint64_t perm_n, Instances inst,
                      int prefix_len) {
+    if (stopped(inst)) return;
     static_assert(kCopiesPer * kCopiesThreads == kMediumMax, "a thread's members must cover the class");
     const int tid = threadIdx.x;
     const uint64_t count = umin64(*qcount, cap);
@@ -545,6 +549,7 @@ medium_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict
                    IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
                    const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
                    Instances inst, int prefix_len, DevFlags *dirty) {
+    if (stopped(inst)) return;
     constexpr int CAP = kMediumMax;
     __shared__ uint64_t s_key[CAP];
     __shared__ uint32_t s_seg[CAP];
@@ -733,6 +738,7 @@ __global__ void refine_keys_kernel(const uint8_t *__restrict__ bytes, const uint
                                    uint64_t total, Instances inst, int prefix_len, uint64_t *__restrict__ keys,
                                    uint32_t *__restrict__ segs, uint32_t *__restrict__ vals,
                                    DevFlags *flags) {
+    if (stopped(inst)) return;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     bool nonconst = false;
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {

@@ -121,6 +121,10 @@ struct OnesweepArgs {
 cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg,
                             bool digit_seg, bool synth, OutMode out,
                             cudaStream_t s, int items = 0);
+// Bounded-wait test support on the current device: the onesweep look-back's
+// poll budget (0: the default kSpinLimit) and a tile id whose look-back words
+// are never published (-1: none).
+cudaError_t set_wait_test(uint32_t spin_limit, long long withhold_tile);
 // The tile shapes (keys per thread) unsegmented passes can run with; [0] is
 // the default.
 constexpr int kOnesweepShapes[2] = {12, 8};
@@ -152,7 +156,8 @@ cudaError_t launch_seg_fill(const uint64_t *seg_offsets, uint64_t num_segs,
                             int num_sms, cudaStream_t s);
 
 // flags->error |= kErrOffsets unless seg_offsets[0] == 0, seg_offsets is
-// non-decreasing and seg_offsets[num_segs] == n.
+// non-decreasing, seg_offsets[num_segs] == n and no instance holds more than
+// 2^31 - 1 strings (local indices are 31-bit).
 cudaError_t launch_validate_segments(const uint64_t *seg_offsets, uint64_t num_segs,
                                      uint64_t n, DevFlags *flags, cudaStream_t s);
 
@@ -162,7 +167,16 @@ cudaError_t launch_validate_segments(const uint64_t *seg_offsets, uint64_t num_s
 struct Instances {
     const uint64_t *seg_offsets;  // NULL for a single sort
     uint64_t num_segs;
+    // The call's device error word (nullable).  Once an earlier kernel has
+    // set it (a wait that gave up leaves positions unwritten) the fix-up
+    // kernels do nothing: they would read string indices from those
+    // positions.
+    const unsigned int *stop = nullptr;
 };
+
+__device__ __forceinline__ bool stopped(const Instances &in) {
+    return in.stop != nullptr && *reinterpret_cast<const volatile unsigned int *>(in.stop) != 0u;
+}
 
 __device__ __forceinline__ uint64_t instance_base(const Instances &in, uint64_t pos) {
     if (in.seg_offsets == nullptr) return 0;

@@ -41,6 +41,12 @@ constexpr int kWideItems = 12;
 constexpr int items_for(bool has_seg) { return has_seg ? kItems : kWideItems; }
 static_assert(kWideItems * kThreads >= kSortTile, "look-back words are sized for tiles of kSortTile keys");
 
+// Bounded-wait test support (hs_test_bounded_waits): the look-back's poll
+// budget, and the id of a tile whose look-back words are never published (a
+// flag that nothing sets; -1: none).  Both are per device.
+__device__ unsigned int g_spin_limit = kSpinLimit;
+__device__ long long g_withhold_tile = -1;
+
 // Exclusive scan of one u32 per thread over the block.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -173,11 +179,13 @@ onesweep_kernel(const OnesweepArgs a) {
     }
     uint64_t *lb = a.lookback + tile * kBins;
     const uint32_t epoch = a.epoch;
+    const bool publish = (long long)tile != g_withhold_tile;
     // Publish this tile's counts as early as possible: later tiles can sum
     // past them before its global prefix is known.
 #pragma unroll
     for (int j = 0; j < kDpt; ++j)
-        st_relaxed(&lb[tid * kDpt + j], lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, total[j]));
+        if (publish)
+            st_relaxed(&lb[tid * kDpt + j], lb_word(epoch, tile == 0 ? kLbInclusive : kLbAggregate, total[j]));
 
     // Tile-local digit starts and the shared-memory scatter need no global
     // prefix, so they run before the look-back, which then overlaps with
@@ -225,6 +233,7 @@ onesweep_kernel(const OnesweepArgs a) {
             done[j] = false;
         }
         uint32_t spins = 0;
+        const uint32_t spin_limit = g_spin_limit;
         while (true) {
             bool all_done = true;
 #pragma unroll
@@ -260,7 +269,7 @@ onesweep_kernel(const OnesweepArgs a) {
                 progress |= used > 0;
             }
             if (!progress) {
-                if (++spins > kSpinLimit) {
+                if (++spins > spin_limit) {
                     atomicOr(&a.flags->error, kErrTimeout);
                     break;
                 }
@@ -269,7 +278,7 @@ onesweep_kernel(const OnesweepArgs a) {
         }
 #pragma unroll
         for (int j = 0; j < kDpt; ++j)
-            st_relaxed(&lb[tid * kDpt + j], lb_word(epoch, kLbInclusive, prefix[j] + total[j]));
+            if (publish) st_relaxed(&lb[tid * kDpt + j], lb_word(epoch, kLbInclusive, prefix[j] + total[j]));
     }
 #pragma unroll
     for (int j = 0; j < kDpt; ++j)
@@ -488,6 +497,13 @@ cudaError_t launch_onesweep(const OnesweepArgs &a, bool has_seg, bool digit_seg,
     }
 }
 
+cudaError_t set_wait_test(uint32_t spin_limit, long long withhold_tile) {
+    const uint32_t lim = spin_limit ? spin_limit : kSpinLimit;
+    cudaError_t e = cudaMemcpyToSymbol(g_spin_limit, &lim, sizeof(lim));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_withhold_tile, &withhold_tile, sizeof(withhold_tile));
+}
+
 cudaError_t launch_histogram(const uint64_t *keys, const uint32_t *segs, uint64_t n,
                              unsigned long long *hist, int num_sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -523,6 +539,7 @@ __global__ void validate_segments_kernel(const uint64_t *__restrict__ seg_offset
     bool bad = false;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < num_segs; i += stride) {
         bad |= seg_offsets[i] > seg_offsets[i + 1];
+        bad |= seg_offsets[i + 1] - seg_offsets[i] > kIdxMask;  // local indices are 31-bit
         if (i == 0) bad |= seg_offsets[0] != 0;
         if (i == num_segs - 1) bad |= seg_offsets[num_segs] != n;
     }

@@ -85,6 +85,23 @@ def test_argument_validation_without_gpu(lib):
     assert lib.hs_last_error() != b""
 
 
+def test_batched_rejects_an_oversize_instance_without_gpu(lib):
+    """Local indices are 31-bit.  With more strings than num_segs instances
+    of 2^31 - 1 can hold, some instance is too large: rejected on the host,
+    before the workspace check or any device work."""
+    import paper_2012_00866_gb300 as hs
+    vp = ctypes.c_void_p
+    n = 1 << 32                       # 2 instances hold at most 2^32 - 2 strings
+    st = lib.hs_argsort_batched(vp(16), vp(16), vp(16), 2, n, 0, vp(16), None, 0, None)
+    assert st == hs.ERR_INVALID_ARG
+    assert b"2^31" in lib.hs_last_error()
+    st = lib.hs_argsort_batched(vp(16), vp(16), vp(16), 1, 1 << 31, 0, vp(16), None, 0, None)
+    assert st == hs.ERR_INVALID_ARG
+    # at the limit the host check passes and the missing workspace is reported
+    st = lib.hs_argsort_batched(vp(16), vp(16), vp(16), 1, (1 << 31) - 1, 0, vp(16), None, 0, None)
+    assert st == hs.ERR_WORKSPACE
+
+
 def test_no_cpu_fallback_without_gpu():
     """The product path must fail loudly (not fall back) without a GPU."""
     import torch

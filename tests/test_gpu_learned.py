@@ -14,7 +14,7 @@ import torch
 
 import oracle
 import workloads
-from gpu_util import assert_oracle_equal, to_device
+from gpu_util import assert_oracle_equal, assert_stable_sorted, to_device
 from oracle import rmi_oracle as R
 
 pytestmark = pytest.mark.gpu
@@ -43,6 +43,55 @@ def test_learned_matches_oracle(cuda_lib, kind, index_u64):
     data, off = to_device(w)
     perm = hs.argsort_device(data, off, mode=hs.MODE_LEARNED, index_u64=index_u64)
     assert_oracle_equal(w, perm)
+
+
+@pytest.mark.parametrize("bits", [9, 21, 23, 24])
+@pytest.mark.parametrize("kind", [2, 5])
+def test_learned_forced_bucket_bits_match_oracle(cuda_lib, kind, bits):
+    """Above about 2.7e8 keys the learned path takes 23 or 24 bucket bits and
+    three 9-bit partition passes (the branch of the 1e9 skewed workload).
+    Forcing those widths at 1e6 strings checks that branch element by
+    element against the oracle, with the u64 permutation the 1e9 workload
+    uses; 9 bits (one pass, buckets far above the in-CTA bound) and 21 bits
+    (a partial last digit) cover the other widths."""
+    hs = cuda_lib
+    w = workloads.generate(kind, 1_000_003, 70 + kind)
+    data, off = to_device(w)
+    hs.learned_force_bucket_bits(bits)
+    try:
+        perm = hs.argsort_device(data, off, mode=hs.MODE_LEARNED, index_u64=True)
+        _, _, info = hs.learned_profile(data, off)
+    finally:
+        hs.learned_force_bucket_bits(0)
+    assert info["bits"] == bits
+    assert_oracle_equal(w, perm)
+
+
+@pytest.mark.slow
+def test_learned_3e8_crosses_to_wide_buckets(cuda_lib):
+    """3e8 skewed strings: the first size at which the learned path picks
+    more than 18 bucket bits on its own; checked by the property check."""
+    hs = cuda_lib
+    w = workloads.generate(5, 300_000_000, 4)
+    data, off = to_device(w)
+    perm = hs.argsort_device(data, off, mode=hs.MODE_LEARNED, index_u64=True)
+    del data, off
+    assert_stable_sorted(w, perm)
+
+
+@pytest.mark.slow
+def test_learned_full_skewed_1e9(cuda_lib):
+    """The learned arm of the 1e9 skewed workload as the bench runs it (u64
+    permutation, 24 bucket bits), checked by the property check (a
+    permutation, in order, equal strings by index), which fixes the stable
+    argsort uniquely."""
+    hs = cuda_lib
+    w = workloads.standard("skewed_1e9")
+    data, off = to_device(w)
+    perm = hs.argsort_device(data, off, mode=hs.MODE_LEARNED, index_u64=True)
+    del data, off
+    assert perm.dtype.itemsize == 8
+    assert_stable_sorted(w, perm)
 
 
 @pytest.mark.parametrize("case", ["equal_long", "few_distinct", "sorted", "byte8_fallback", "just_above_min"])

@@ -3,10 +3,11 @@ memory (for example code embedded in a host application that owns the GPU's
 memory pool, or code that must not trigger cudaMalloc's device-wide
 synchronisation).  Its scratch is a static device array inside the library.
 
-Checked through the C ABI against the existing hs_argsort entry point on two
-calls in a row: the second call gets a different, smaller input, so it runs on
-scratch that still holds the first call's contents.  The bar is the same as
-for every sort here: the permutations are integers and must be identical.
+Checked through the C ABI on two calls in a row, against the oracle's stable
+argsort and against the existing hs_argsort entry point: the second call gets
+a different, smaller input, so it runs on scratch that still holds the first
+call's contents.  The bar is the same as for every sort here: the
+permutations are integers and must be identical.
 This file is collected last so a failure here cannot hide the other tests."""
 
 import ctypes
@@ -16,7 +17,7 @@ import pytest
 import torch
 
 import workloads
-from gpu_util import to_device
+from gpu_util import assert_oracle_equal, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +43,7 @@ def _inputs():
     return first, second
 
 
-def test_noalloc_matches_hs_argsort_twice(cuda_lib):
+def test_noalloc_matches_oracle_and_hs_argsort_twice(cuda_lib):
     hs = cuda_lib
     lib = hs.load()
     first, second = _inputs()
@@ -52,6 +53,7 @@ def test_noalloc_matches_hs_argsort_twice(cuda_lib):
         ref = hs.argsort_device(data, off, index_u64=out_t == 1)
         st, perm = _noalloc(lib, data, off, w.n, out_t=out_t)
         assert st == hs.OK, lib.hs_last_error()
+        assert_oracle_equal(w, perm)
         assert torch.equal(perm, ref)
 
 
