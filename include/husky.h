@@ -283,7 +283,7 @@ HS_API hs_status hs_shutdown(void);
 HS_API hs_status hs_autotune(int mode);
 HS_API hs_status hs_autotune_choice(int layout, uint64_t n, int *items);
 
-/* Numeric coders.  Section 5 benchmarks Huskysort on Integer, Long and
+/* Numeric coders.  Section 6.1 and Table 4 benchmark Huskysort on Integer, Long and
  * Double arrays and Section 3.2 names a perfect coding for date-times (one
  * nanosecond over 128 years fits 64 bits); the paper gives no bit layout for
  * them.  Each value is coded here as an unsigned 64-bit key whose order is the
@@ -331,7 +331,7 @@ HS_API hs_status hs_argsort_numeric(const void *d_values, uint64_t n, int type,
                                     int out_t, void *d_perm, void *d_ws,
                                     size_t ws_bytes, void *stream);
 
-/* BigInteger coder.  Section 5 sorts BigInteger arrays; the paper gives no
+/* BigInteger coder.  Section 6.1 and Table 4 sort BigInteger arrays; the paper gives no
  * coder.  Value i is its minimal two's complement bytes, big-endian (Java's
  * BigInteger.toByteArray), at d_bytes[d_offsets[i] .. d_offsets[i+1]), at
  * most 32767 bytes.  Each is turned into the byte string header || value,

@@ -222,7 +222,7 @@ def string_compare(data: np.ndarray, offsets: np.ndarray, i: int, j: int) -> int
 
 # ---- numeric coders ---------------------------------------------------------
 #
-# The paper benchmarks Integer, Long and Double arrays (Section 5) and names a
+# The paper benchmarks Integer, Long and Double arrays (Section 6.1, Table 4) and names a
 # perfect date-time coding (Section 3.2) without giving bit layouts.  Two
 # plain definitions serve as the oracle: the order itself, written from each
 # type's compareTo semantics (integers by value; doubles as Double.compare:

@@ -1,4 +1,4 @@
-// BigInteger coder.  Section 5 sorts BigInteger arrays with Huskysort; the
+// BigInteger coder.  Section 6.1 and Table 4 sort BigInteger arrays with Huskysort; the
 // paper gives no coder for them.  A big integer here is its minimal two's
 // complement bytes, big-endian (Java's toByteArray).  A two-byte header that
 // orders by sign and length turns it into a byte string whose unsigned-byte
