@@ -65,12 +65,17 @@ HS_API hs_status hs_learned_profile(const uint8_t *d_bytes,
                                     void *d_ws, size_t ws_bytes, void *stream);
 
 /* Test support: the number of bucket-id bits the learned path uses.  By
- * default (bits = 0) it takes about n/256 buckets rounded to whole 9-bit
- * partition passes: 18 bits up to about 2.7e8 keys, 23 or 24 above.  A value
- * of 9..24 forces that many bits for every later learned sort in the process,
- * so that the three-pass branches can be checked at sizes the oracle sorts
- * quickly; the result never depends on it.  Workspace sizes follow the
- * setting.  HS_ERR_INVALID_ARG for other values. */
+ * default (bits = 0), for keys of the byte-range coder (the bucket id then
+ * rides above the key in one word), enough bits for an average bucket of at
+ * most about 2048 keys, up to 18 (two 9-bit partition passes); for ASCII7
+ * keys, about n/256 buckets rounded to whole partition passes: 18 bits up to
+ * about 2.7e8 keys, 23 or 24 above.  A value of 1..24 forces that many bits
+ * for every later learned sort in the process, so that each branch (one to
+ * three partition passes, buckets longer than the in-CTA window, a separate
+ * bucket array when the id does not fit above the key) can be checked at
+ * sizes the oracle sorts quickly; the result never depends on it.
+ * Workspace sizes follow the setting.  HS_ERR_INVALID_ARG for other
+ * values. */
 HS_API hs_status hs_learned_force_bucket_bits(int bits);
 
 #ifdef __cplusplus

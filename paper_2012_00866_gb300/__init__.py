@@ -157,8 +157,8 @@ def test_bounded_waits(spin_limit: int = 0, withhold_tile: int = -1):
 
 
 def learned_force_bucket_bits(bits: int):
-    """Test support: force the learned path's bucket-id bits (9..24), or 0
-    for its own choice (about n/256 buckets)."""
+    """Test support: force the learned path's bucket-id bits (1..24), or 0
+    for its own choice."""
     _check(load().hs_learned_force_bucket_bits(bits))
 
 

@@ -564,7 +564,7 @@ struct SortBufs {
 
 hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passes, int npasses,
                      bool segmented, const uint32_t *flag_bits, bool synth_first, void *final_out,
-                     OutMode final_mode, bool keep_keys, int pack_bits = 0) {
+                     OutMode final_mode, bool keep_keys, int pack_bits = 0, int digit_base = 0) {
     uint64_t *lb = c.at<uint64_t>(c.L.lb);
     const int layout = segmented ? -1 : (pack_bits > 0 ? 0 : 1);
     const int cls = size_class(n);
@@ -599,7 +599,7 @@ hs_status run_passes(Ctx &c, SortBufs &b, int *cur, uint64_t n, const int *passe
         a.flag_bits = flag_bits;
         a.n = n;
         a.pack_bits = pack_bits;
-        a.shift = digit_shift(p) + pack_bits;
+        a.shift = digit_shift(p) + pack_bits + digit_base;
         a.mask = digit_mask(p);
         a.bucket_base = c.at<unsigned long long>(c.L.bucket) + (size_t)p * kBins;
         a.lookback = lb;
@@ -657,7 +657,8 @@ struct Input {
 // perm_written: packed words whose last radix pass wrote the permutation
 // beside them (tie detection then only finds the runs).
 hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode, const Instances &inst0,
-                    bool *synced = nullptr, bool instance_in_key = false, bool perm_written = false) {
+                    bool *synced = nullptr, bool instance_in_key = false, bool perm_written = false,
+                    bool runs_queued = false) {
     if (synced) *synced = false;
     Instances inst = inst0;
     inst.stop = &c.d_flags->error;  // after a give-up the fix-up kernels do nothing
@@ -711,7 +712,8 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
     const double tie_bytes = mode == kTieKeyFlag ? 8.0 * n
                              : mode == kTiePacked ? 8.0 * n + (t.perm ? (in.perm_u64 ? 8.0 : 4.0) * n : 0.0)
                                                   : 8.0 * n + 4.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n;
-    HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
+    if (!runs_queued)  // else the caller's kernels queued the runs already
+        HS_TRY(c.timed(kKTieDetect, tie_bytes, [&] { return launch_tie_detect(t, mode, c.s); }), "tie detect");
     if (early && !perm_written) HS_TRY(cudaEventRecord(perm_done, c.s), "record tie detect");
     // Runs of copies of one string are final already; only the others go on
     // to refinement (queue B).
@@ -980,6 +982,145 @@ struct LearnedProfile {
     double info[4];
 };
 
+// Runs of the learned path too long for an in-CTA sort, queued in q_over
+// (c.h.qcount[kQOverflow] of them, positions in keys/vals): the payload goes
+// to the permutation as it stands (and key & kmask to big_keys_out when
+// given); the runs holding more than one key are gathered into ov.*[0],
+// sorted by a segmented radix sort over (run, key & kmask) and scattered
+// back: keys to sorted_keys_out, payload to the permutation.  The ov.*[1]
+// buffers are the passes' other side and may alias keys/vals (read only by
+// the gather).
+hs_status sort_oversize(Ctx &c, const Input &in, const uint64_t *keys, const uint32_t *vals, uint64_t kmask,
+                        uint64_t *big_keys_out, uint64_t *sorted_keys_out, SortBufs ov) {
+    const uint64_t n = in.n;
+    const Layout &L = c.L;
+    const uint64_t big = c.h.qcount[kQOverflow];
+    if (big == 0) return HS_OK;
+    if (big > L.cap_over) return fail(HS_ERR_INTERNAL, "overflow queue full");
+    RunEntry *q_over = c.at<RunEntry>(L.q_over);
+    RunEntry *q_mixed = c.at<RunEntry>(L.q_mixed);
+    unsigned long long *hist = c.at<unsigned long long>(L.hist);
+    unsigned long long *bucket = c.at<unsigned long long>(L.bucket);
+    unsigned long long *bb = c.at<unsigned long long>(L.over_base);
+    HS_TRY(c.timed(kKRunScan, 0.0, [&] { return launch_run_scan(q_over, big, bb, c.s); }), "big scan");
+    unsigned long long big_total = 0;
+    HS_TRY(cudaMemcpyAsync(&big_total, bb + big, 8, cudaMemcpyDeviceToHost, c.s), "big total");
+    HS_TRY(cudaStreamSynchronize(c.s), "big sync");
+    if (big_total > n) return fail(HS_ERR_INTERNAL, "oversize buckets overlap");
+    uint32_t *mixed = c.at<uint32_t>(L.big_mixed);
+    HS_TRY(cudaMemsetAsync(mixed, 0, big * 4, c.s), "memset mixed");
+    HS_TRY(c.timed(kKBucketSort, 20.0 * big_total, [&] {
+               return launch_big_buckets(q_over, big, bb, big_total, keys, vals, in.perm, in.perm_u64, mixed,
+                                         big_keys_out, kmask, c.s);
+           }),
+           "big buckets");
+    HS_TRY(c.timed(kKCollectMixed, 0.0, [&] { return launch_collect_mixed(q_over, big, mixed, q_mixed, L.cap_over, c.d_flags, c.s); }), "collect mixed");
+    HS_TRY(c.read_flags(), "mixed sync");
+    hs_status st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    const uint64_t over = c.h.qcount[kQMixed];
+    if (over == 0) return HS_OK;
+    unsigned long long *ob = c.at<unsigned long long>(L.mixed_base);
+    HS_TRY(c.timed(kKRunScan, 0.0, [&] { return launch_run_scan(q_mixed, over, ob, c.s); }), "overflow scan");
+    unsigned long long total = 0;
+    HS_TRY(cudaMemcpyAsync(&total, ob + over, 8, cudaMemcpyDeviceToHost, c.s), "overflow total");
+    HS_TRY(cudaStreamSynchronize(c.s), "overflow sync");
+    if (total > n) return fail(HS_ERR_INTERNAL, "overflow buckets overlap");
+    HS_TRY(c.timed(kKOverflow, 28.0 * total, [&] {
+               return launch_overflow_gather(q_mixed, over, ob, total, keys, vals, kmask, ov.keys[0], ov.segs[0],
+                                             ov.vals[0], c.s);
+           }),
+           "overflow gather");
+    HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
+    HS_TRY(c.timed(kKHistogram, 0.0, [&] { return launch_histogram(ov.keys[0], ov.segs[0], total, hist, c.sms, c.s); }), "overflow histogram");
+    HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, kHistPasses, total, bucket, c.d_flags, c.s); }), "overflow plan");
+    HS_TRY(c.read_flags(), "overflow plan sync");
+    int passes[kHistPasses], np = 0;
+    for (int p = 0; p < kHistPasses; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    int oc = 0;
+    st = run_passes(c, ov, &oc, total, passes, np, true, nullptr, false, nullptr, kOutVals, true);
+    if (st != HS_OK) return st;
+    HS_TRY(c.timed(kKOverflow, 28.0 * total, [&] {
+               return launch_overflow_scatter(q_mixed, ob, total, ov.keys[oc], ov.segs[oc], ov.vals[oc],
+                                              sorted_keys_out, in.perm, in.perm_u64, c.s);
+           }),
+           "overflow scatter");
+    return HS_OK;
+}
+
+// Bucket-id bits when the id sits above the key: an average bucket of at
+// most about 2048 keys (windows of the in-bucket sort hold 6144), and at
+// most 18 bits, two 9-bit partition passes.
+int composite_bits(uint64_t n) {
+    int bits = 1;
+    while (bits < 18 && (n >> bits) > 2048) ++bits;
+    return bits;
+}
+
+// Learned partition with the bucket id above a sort key of kb bits: compose,
+// one to three partition passes on the bucket digits (one word per element),
+// in-bucket sorts over windows of whole buckets (which write the
+// permutation and the sorted keys), the overflow sort for longer buckets,
+// then tie detection and the fix-up on the sorted keys.
+hs_status learned_composite(Ctx &c, const Input &in, SortBufs &b, RmiModel *model, int kb, int bits, bool perfect) {
+    const uint64_t n = in.n;
+    const Layout &L = c.L;
+    unsigned long long *hist = c.at<unsigned long long>(L.hist);
+    unsigned long long *bucket = c.at<unsigned long long>(L.bucket);
+    HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
+    HS_TRY(c.timed(kKRmiBucket, 16.0 * n, [&] {
+               return launch_rmi_compose(b.keys[0], n, model, bits, kb, hist, c.sms, c.s);
+           }),
+           "rmi compose");
+    const int nparts = (bits + kRadixBits - 1) / kRadixBits;
+    HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, nparts, n, bucket, c.d_flags, c.s); }), "bucket plan");
+    HS_TRY(c.read_flags(), "bucket plan sync");
+    hs_status st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    int passes[3], np = 0;
+    for (int p = 0; p < nparts; ++p)
+        if (c.h.active[p]) passes[np++] = p;
+    if (np == 0) passes[np++] = 0;  // one pass still writes the payload (the string index)
+    int cur = 0;
+    st = run_passes(c, b, &cur, n, passes, np, false, nullptr, true, nullptr, kOutVals, true, 0, kb);
+    if (st != HS_OK) return st;
+    unsigned int *ranges = nullptr;
+    HS_TRY(c.counter(&ranges), "counter");
+    const RunQueues rq{c.at<RunEntry>(L.q_small), c.at<RunEntry>(L.q_medium), c.at<RunEntry>(L.q_large_a),
+                       L.cap_small, L.cap_medium, L.cap_large, n};
+    const TileSortArgs t{b.keys[cur], b.vals[cur], in.perm, n, kb, perfect ? 0 : 1, ranges,
+                         c.at<RunEntry>(L.q_over), L.cap_over, rq, c.d_flags};
+    HS_TRY(c.timed(kKBucketSort, 12.0 * n + (in.perm_u64 ? 8.0 : 4.0) * n, [&] {
+               return launch_bucket_tile_sort(t, in.perm_u64, c.sms, c.s);
+           }),
+           "bucket tile sort");
+    HS_TRY(c.read_flags(), "tile sort sync");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    // Buckets longer than a window: sorted keys (bucket bits cleared) land in
+    // the other key buffer at their positions, then their tie runs are queued.
+    const uint64_t big = c.h.qcount[kQOverflow];
+    const uint64_t kmask = (1ull << kb) - 1;
+    st = sort_oversize(c, in, b.keys[cur], b.vals[cur], kmask, b.keys[cur ^ 1], b.keys[cur ^ 1],
+                       SortBufs{{c.at<uint64_t>(L.keys_extra), b.keys[cur]},
+                                {b.vals[cur ^ 1], b.vals[cur]},
+                                {b.segs[0], b.segs[1]}});
+    if (st != HS_OK) return st;
+    if (!perfect && big > 0)
+        HS_TRY(c.timed(kKTieDetect, 8.0 * big, [&] {
+                   return launch_oversize_ties(c.at<RunEntry>(L.q_over), big, b.keys[cur ^ 1], rq, c.d_flags, c.sms,
+                                               c.s);
+               }),
+               "oversize ties");
+    if (!perfect) {
+        st = run_fixup(c, in, b, cur ^ 1, kTieKeyFlag, Instances{nullptr, 0}, nullptr, false, false, true);
+        if (st != HS_OK) return st;
+    }
+    HS_TRY(c.read_flags(), "final sync");
+    return device_error_status(c.h);
+}
+
 hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, LearnedProfile *prof = nullptr) {
     Input in = in0;
     const uint64_t n = in.n;
@@ -1058,6 +1199,15 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
         prof->info[3] = losses[1];
         return HS_OK;
     }
+    // Byte-range keys leave room above them: the bucket id goes there and
+    // each partition pass moves one word and the payload.
+    if (used == HS_CODER_ALPHA) {
+        const int kb = kmax ? 64 - __builtin_clzll(kmax) : 1;
+        const int forced = g_forced_bucket_bits.load();
+        const int cbits = forced > 0 ? forced : composite_bits(n);
+        if (kb + cbits <= 64 && cbits <= 3 * kRadixBits && kb <= 64 - 13)  // 13: the in-window place field
+            return learned_composite(c, in, b, model, kb, cbits, perfect);
+    }
     HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
     HS_TRY(c.timed(kKRmiBucket, 16.0 * n, [&] {
                return launch_rmi_bucket(b.keys[0], n, model, bits, 0, b.segs[0], b.vals[0], hist, c.sms, c.s);
@@ -1088,64 +1238,11 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     HS_TRY(c.read_flags(), "bucket sort sync");
     st = device_error_status(c.h);
     if (st != HS_OK) return st;
-
-    // Oversize buckets: payload copied grid-wide; only the ones holding
-    // different keys (mixed) need the segmented sort.
-    const uint64_t big = c.h.qcount[kQOverflow];
-    uint64_t over = 0;
-    RunEntry *q_mixed = c.at<RunEntry>(L.q_mixed);
-    if (big > 0) {
-        unsigned long long *bb = c.at<unsigned long long>(L.over_base);
-        HS_TRY(c.timed(kKRunScan, 0.0, [&] { return launch_run_scan(q_over, big, bb, c.s); }), "big scan");
-        unsigned long long big_total = 0;
-        HS_TRY(cudaMemcpyAsync(&big_total, bb + big, 8, cudaMemcpyDeviceToHost, c.s), "big total");
-        HS_TRY(cudaStreamSynchronize(c.s), "big sync");
-        if (big_total > n) return fail(HS_ERR_INTERNAL, "oversize buckets overlap");
-        uint32_t *mixed = c.at<uint32_t>(L.big_mixed);
-        HS_TRY(cudaMemsetAsync(mixed, 0, big * 4, c.s), "memset mixed");
-        HS_TRY(c.timed(kKBucketSort, 20.0 * big_total, [&] {
-                   return launch_big_buckets(q_over, big, bb, big_total, b.keys[cur], b.vals[cur], in.perm,
-                                             in.perm_u64, mixed, c.s);
-               }),
-               "big buckets");
-        HS_TRY(c.timed(kKCollectMixed, 0.0, [&] { return launch_collect_mixed(q_over, big, mixed, q_mixed, L.cap_over, c.d_flags, c.s); }), "collect mixed");
-        HS_TRY(c.read_flags(), "mixed sync");
-        st = device_error_status(c.h);
-        if (st != HS_OK) return st;
-        over = c.h.qcount[kQMixed];
-    }
-    if (over > 0) {
-        q_over = q_mixed;
-        unsigned long long *ob = c.at<unsigned long long>(L.mixed_base);
-        HS_TRY(c.timed(kKRunScan, 0.0, [&] { return launch_run_scan(q_over, over, ob, c.s); }), "overflow scan");
-        unsigned long long total = 0;
-        HS_TRY(cudaMemcpyAsync(&total, ob + over, 8, cudaMemcpyDeviceToHost, c.s), "overflow total");
-        HS_TRY(cudaStreamSynchronize(c.s), "overflow sync");
-        if (total > n) return fail(HS_ERR_INTERNAL, "overflow buckets overlap");
-        SortBufs ov{{c.at<uint64_t>(L.keys_extra), b.keys[cur ^ 1]},
-                    {b.segs[cur ^ 1], b.segs[cur]},
-                    {b.vals[cur ^ 1], b.vals[cur]}};
-        HS_TRY(c.timed(kKOverflow, 28.0 * total, [&] {
-                   return launch_overflow_gather(q_over, over, ob, total, b.keys[cur], b.vals[cur], ov.keys[0],
-                                                 ov.segs[0], ov.vals[0], c.s);
-               }),
-               "overflow gather");
-        HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
-        HS_TRY(c.timed(kKHistogram, 0.0, [&] { return launch_histogram(ov.keys[0], ov.segs[0], total, hist, c.sms, c.s); }), "overflow histogram");
-        HS_TRY(c.timed(kKPlan, 0.0, [&] { return launch_plan(hist, kHistPasses, total, bucket, c.d_flags, c.s); }), "overflow plan");
-        HS_TRY(c.read_flags(), "overflow plan sync");
-        np = 0;
-        for (int p = 0; p < kHistPasses; ++p)
-            if (c.h.active[p]) passes[np++] = p;
-        int oc = 0;
-        st = run_passes(c, ov, &oc, total, passes, np, true, nullptr, false, nullptr, kOutVals, true);
-        if (st != HS_OK) return st;
-        HS_TRY(c.timed(kKOverflow, 28.0 * total, [&] {
-                   return launch_overflow_scatter(q_over, ob, total, ov.keys[oc], ov.segs[oc], ov.vals[oc],
-                                                  b.keys[cur], in.perm, in.perm_u64, c.s);
-               }),
-               "overflow scatter");
-    }
+    st = sort_oversize(c, in, b.keys[cur], b.vals[cur], ~0ull, nullptr, b.keys[cur],
+                       SortBufs{{c.at<uint64_t>(L.keys_extra), b.keys[cur ^ 1]},
+                                {b.vals[cur ^ 1], b.vals[cur]},
+                                {b.segs[cur ^ 1], b.segs[cur]}});
+    if (st != HS_OK) return st;
     if (!perfect) {
         st = run_fixup(c, in, b, cur, kTieKeyFlag, Instances{nullptr, 0});
         if (st != HS_OK) return st;
@@ -1702,8 +1799,7 @@ hs_status hs_test_bounded_waits(uint32_t spin_limit, int64_t withhold_tile) {
 
 hs_status hs_learned_force_bucket_bits(int bits) {
     g_last_error.clear();
-    if (bits != 0 && (bits < kRadixBits || bits > 24))
-        return fail(HS_ERR_INVALID_ARG, "bucket bits must be 0 or 9..24");
+    if (bits < 0 || bits > 24) return fail(HS_ERR_INVALID_ARG, "bucket bits must be 0 or 1..24");
     g_forced_bucket_bits.store(bits);
     return HS_OK;
 }

@@ -328,10 +328,12 @@ cudaError_t launch_rmi_leaves(const uint64_t *sorted_sample, const uint32_t *Xi,
                               RmiModel *model, cudaStream_t s);
 // Oversize buckets (from the bucket sort's queue): copy payload to perm and
 // flag buckets whose keys are not all equal (mixed[r] = 1, zeroed by caller).
+// keys_out (nullable): also write key & kmask there.
 cudaError_t launch_big_buckets(const RunEntry *big, uint64_t count,
                                const unsigned long long *base, uint64_t total,
                                const uint64_t *keys, const uint32_t *vals,
                                void *perm, int perm_u64, uint32_t *mixed,
+                               uint64_t *keys_out, uint64_t kmask,
                                cudaStream_t s);
 // Push the mixed ones to q_mixed (DevFlags::qcount[kQMixed]).
 cudaError_t launch_collect_mixed(const RunEntry *big, uint64_t count,
@@ -361,8 +363,48 @@ cudaError_t launch_bucket_sort(const unsigned long long *first,
 cudaError_t launch_overflow_gather(const RunEntry *runs, uint64_t count,
                                    const unsigned long long *run_base,
                                    uint64_t total, const uint64_t *keys,
-                                   const uint32_t *vals, uint64_t *ck,
-                                   uint32_t *cs, uint32_t *cv, cudaStream_t s);
+                                   const uint32_t *vals, uint64_t kmask,
+                                   uint64_t *ck, uint32_t *cs, uint32_t *cv,
+                                   cudaStream_t s);
+// Composite keys: keys[i] |= bucket(keys[i]) << kb (the trained model's
+// bucket of `bits` bits, kb + bits <= 64, every key below 2^kb), with the
+// bucket ids' 9-bit digit histograms accumulated into hist rows
+// 0..ceil(bits/9)-1.
+cudaError_t launch_rmi_compose(uint64_t *keys, uint64_t n, const RmiModel *model,
+                               int bits, int kb, unsigned long long *hist,
+                               int num_sms, cudaStream_t s);
+// Size-class run queues the fix-up reads (DevFlags::qcount[kQSmall],
+// [kQMedium], [kQLargeA]).
+struct RunQueues {
+    RunEntry *small, *medium, *large;
+    uint64_t cap_small, cap_medium, cap_large;
+    uint64_t perm_n;
+};
+// In-bucket sorts of composite keys grouped by bucket (key bits below kb,
+// kb <= 51): writes the payload in key order to perm; with ties set, queues
+// every run of equal keys whose bit 0 (not exact) is set; buckets longer than
+// one window are queued in overflow (DevFlags::qcount[kQOverflow]) and left
+// to the caller.
+struct TileSortArgs {
+    const uint64_t *keys_in;
+    const uint32_t *vals_in;
+    void *perm;
+    uint64_t n;
+    int kb;
+    int ties;
+    unsigned int *range_counter;  // zeroed
+    RunEntry *overflow;
+    uint64_t cap_overflow;
+    RunQueues q;
+    DevFlags *flags;
+};
+cudaError_t launch_bucket_tile_sort(const TileSortArgs &a, int perm_u64,
+                                    int num_sms, cudaStream_t s);
+// Tie runs inside the runs of `runs` (sorted keys, bit 0 = not exact).
+cudaError_t launch_oversize_ties(const RunEntry *runs, uint64_t count,
+                                 const uint64_t *keys, const RunQueues &q,
+                                 DevFlags *flags, int num_sms, cudaStream_t s);
+size_t tile_sort_smem_bytes();
 cudaError_t launch_overflow_scatter(const RunEntry *runs,
                                     const unsigned long long *run_base,
                                     uint64_t total, const uint64_t *ck,

@@ -454,6 +454,483 @@ rmi_bucket_kernel(const uint64_t *__restrict__ keys, uint64_t n, const RmiModel 
             if (s_hist[i]) atomicAdd(&hist[kKeyPasses * kBins + i], (unsigned long long)s_hist[i]);
 }
 
+// ---- composite keys: the bucket id above the key -------------------------------
+//
+// When the sort key has kb bits and the bucket id fits above it, the
+// partition moves one word per element, (bucket << kb) | key, instead of a
+// key and a separate bucket id.  Leaves are found through an index over the
+// top 12 feature bits: slice s of the 24-bit feature holds only the leaves
+// between the leaf of its first value and the leaf of the next slice's first
+// value (the threshold table is non-decreasing), so the bisection runs over
+// those few leaves instead of all 4096.
+constexpr int kAccelBits = 12;
+constexpr int kAccel = 1 << kAccelBits;
+constexpr int kAccelShift = kRmiFeatureBits - kAccelBits;
+constexpr int kCmpThreads = 512;
+constexpr int kCmpItems = 4;
+
+__device__ void build_accel(const uint32_t *s_thresh, uint16_t *s_accel) {
+    for (int sl = threadIdx.x; sl <= kAccel; sl += blockDim.x)
+        s_accel[sl] = (uint16_t)table_leaf(s_thresh, (uint32_t)sl << kAccelShift);
+}
+
+// table_leaf(X) restricted to the leaves of X's slice: the largest l in
+// [s_accel[s], s_accel[s + 1]] with l == 0 or thresh[l - 1] <= X.
+__device__ __forceinline__ uint32_t accel_leaf(const uint32_t *s_thresh, const uint16_t *s_accel, uint32_t X) {
+    const uint32_t sl = X >> kAccelShift;
+    uint32_t lo = s_accel[sl], hi = s_accel[sl + 1];
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (s_thresh[mid - 1] <= X) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// bucket_of (trained model) with the indexed leaf search: the same arithmetic.
+__device__ __forceinline__ uint32_t bucket_fast(const RmiModel &M, const uint32_t *s_thresh, const uint16_t *s_accel,
+                                                uint64_t key, uint64_t kmin, int shift, float B) {
+    const uint32_t X = feature_of(key, kmin, shift);
+    const uint32_t l = accel_leaf(s_thresh, s_accel, X);
+    const uint64_t kbase = __ldg(&M.kbase[l]);
+    const float xl = (float)(key >= kbase ? key - kbase : 0ull) * __ldg(&M.kscale[l]);
+    const float pos = fminf(fmaxf(fmaf(__ldg(&M.slope[l]), xl, __ldg(&M.icept[l])), __ldg(&M.lo[l])), __ldg(&M.hi[l]));
+    return (uint32_t)fminf(fmaxf(pos * B, 0.0f), B - 1.0f);
+}
+
+// keys[i] |= bucket(keys[i]) << kb in place, with the 9-bit digit histograms
+// of the bucket ids in hist rows 0..passes-1.  Four keys a thread are loaded
+// before any is bucketed, so their loads overlap.
+__global__ void __launch_bounds__(kCmpThreads)
+rmi_compose_kernel(uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__restrict__ model, int bits, int kb,
+                   unsigned long long *__restrict__ hist) {
+    __shared__ uint32_t s_thresh[kRmiLeaves];
+    __shared__ uint16_t s_accel[kAccel + 2];
+    __shared__ uint32_t s_hist[3 * kBins];
+    for (int i = threadIdx.x; i < kRmiLeaves; i += kCmpThreads) s_thresh[i] = model->thresh[i];
+    for (int i = threadIdx.x; i < 3 * kBins; i += kCmpThreads) s_hist[i] = 0;
+    __syncthreads();
+    build_accel(s_thresh, s_accel);
+    __syncthreads();
+    const uint64_t kmin = model->kmin;
+    const int shift = model->shift;
+    const float B = (float)(1u << bits);
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    constexpr uint64_t kGroup = (uint64_t)kCmpThreads * kCmpItems;
+    for (uint64_t g = (uint64_t)blockIdx.x * kGroup; g < n; g += (uint64_t)gridDim.x * kGroup) {
+        uint64_t key[kCmpItems];
+#pragma unroll
+        for (int k = 0; k < kCmpItems; ++k) {
+            const uint64_t i = g + (uint64_t)k * kCmpThreads + threadIdx.x;
+            key[k] = i < n ? keys[i] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < kCmpItems; ++k) {
+            const uint64_t i = g + (uint64_t)k * kCmpThreads + threadIdx.x;
+            const bool valid = i < n;
+            uint32_t b = 0;
+            if (valid) {
+                b = bucket_fast(*model, s_thresh, s_accel, key[k], kmin, shift, B);
+                keys[i] = key[k] | ((uint64_t)b << kb);
+            }
+            for (int p = 0; p < passes; ++p)
+                hist_add(s_hist + p * kBins, (b >> (kRadixBits * p)) & (kBins - 1), valid);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kBins; i += kCmpThreads)
+        if (s_hist[i]) atomicAdd(&hist[i], (unsigned long long)s_hist[i]);
+}
+
+// ---- in-bucket sorts over windows of whole buckets ------------------------------
+//
+// After the partition the composite keys are grouped by bucket in bucket
+// order, and the bucket is a non-decreasing function of the key, so sorting
+// any run of whole buckets by key alone puts it in its final order.  A CTA
+// claims ranges of kTsRange positions and takes every bucket that starts in
+// its range: it loads the next kTsWin keys, cuts them after the last bucket
+// that ends inside, and sorts that window in shared memory.  Each element
+// becomes one word, (key - min(window)) << 13 | its place in the window, so
+// the payload is fetched once, at the end; a stable LSD radix sort on the
+// key part, 9 bits a pass, takes as many passes as the window's key span
+// needs, the words held in registers between passes.  The CTA then writes
+// the permutation and queues the window's runs of equal keys that hold an
+// inexactly coded string for the fix-up (equal keys share a bucket, so no run
+// crosses a window).  A bucket longer than the window goes to the overflow
+// queue.
+constexpr int kTsThreads = 512;
+constexpr int kTsWarps = kTsThreads / 32;
+constexpr int kTsItems = 12;
+constexpr int kTsWin = kTsThreads * kTsItems;
+constexpr int kTsIdxBits = 13;
+constexpr int kTsBins = kBins;  // 9-bit digits, one per thread in the digit phase
+constexpr uint64_t kTsRange = 1ull << 18;
+static_assert(kTsWin <= 1 << kTsIdxBits, "the place field indexes the window");
+static_assert(kTsBins == kTsThreads, "one digit per thread");
+static_assert(32 * kTsItems < (1 << 16), "ranks within a warp fit 16 bits");
+constexpr int kTsMaxKeyBits = 64 - kTsIdxBits;  // key spans the words can hold
+
+// Per-warp digit counts are 16-bit (at most 32 * kTsItems per warp), two to a
+// word for the shared atomics; after the digit phase the same halves hold
+// each warp's offset within the digit (below kTsWin).  Ranks go to
+// shared memory rather than registers, which keeps two CTAs per SM.
+struct TsSmem {
+    uint64_t word[kTsWin];
+    uint32_t whist2[kTsWarps * kTsBins / 2];
+    uint16_t rank[kTsWin];
+    uint32_t dstart[kTsBins];
+    uint32_t heads[kTsWin / 32];
+    uint32_t wsum[kTsWarps];
+    unsigned long long kmin, kmax, found;
+    unsigned int cut, range_id;
+};
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kFull, v, o);
+        v = y < v ? y : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kFull, v, o);
+        v = y > v ? y : v;
+    }
+    return v;
+}
+
+// A run of equal keys [start, start + len) that needs the fix-up, to its
+// size-class queue.
+__device__ void queue_run(const RunQueues &q, DevFlags *flags, uint64_t start, uint64_t len) {
+    if (start >= q.perm_n || len > q.perm_n - start) {
+        atomicOr(&flags->error, kErrInternal);
+        return;
+    }
+    const RunEntry e{start, (unsigned)umin64(len, 0xFFFFFFFFull), 0u};
+    if (len <= kSmallMax) {
+        const unsigned long long i = atomicAdd(&flags->qcount[kQSmall], 1ull);
+        if (i < q.cap_small) q.small[i] = e; else atomicOr(&flags->error, kErrInternal);
+    } else if (len <= kMediumMax) {
+        const unsigned long long i = atomicAdd(&flags->qcount[kQMedium], 1ull);
+        if (i < q.cap_medium) q.medium[i] = e; else atomicOr(&flags->error, kErrInternal);
+    } else {
+        const unsigned long long i = atomicAdd(&flags->qcount[kQLargeA], 1ull);
+        if (i < q.cap_large && len < 0xFFFFFFFFull) q.large[i] = e; else atomicOr(&flags->error, kErrInternal);
+    }
+}
+
+// First position >= from whose bucket (key >> kb) is not b, or n.  Every key
+// at or after `from` has a bucket >= b.  Block-wide (all threads call it and
+// get the same value): one coalesced look at the next kTsWin keys, then, if
+// the bucket runs on past them, a galloping search and a bisection.
+__device__ uint64_t bucket_end(const uint64_t *__restrict__ keys, uint64_t n, int kb, uint64_t from, uint64_t b,
+                               TsSmem &s) {
+    if (threadIdx.x == 0) s.found = ~0ull;
+    __syncthreads();
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int k = 0; k < kTsItems; ++k) {
+        const uint64_t j = from + (uint64_t)k * kTsThreads + threadIdx.x;
+        if (j < n && (keys[j] >> kb) != b && j < best) best = j;
+    }
+    best = warp_min_u64(best);
+    if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&s.found, best);
+    __syncthreads();
+    unsigned long long f = s.found;
+    if (f == ~0ull) {
+        if (from + kTsWin >= n) {
+            f = n;
+        } else {
+            if (threadIdx.x == 0) {  // keys [from, from + kTsWin) are all in bucket b
+                uint64_t lo = from + kTsWin - 1, step = kTsWin, hi;
+                for (;;) {
+                    hi = lo + step;
+                    if (hi >= n) {
+                        hi = n;
+                        break;
+                    }
+                    if ((keys[hi] >> kb) != b) break;
+                    lo = hi;
+                    step <<= 1;
+                }
+                while (hi - lo > 1) {  // bucket(lo) == b, hi == n or bucket(hi) != b
+                    const uint64_t mid = lo + ((hi - lo) >> 1);
+                    if ((keys[mid] >> kb) == b) lo = mid; else hi = mid;
+                }
+                s.found = hi;
+            }
+            __syncthreads();
+            f = s.found;
+        }
+    }
+    __syncthreads();
+    return f;
+}
+
+// Exclusive scan of one u32 per thread over the block (kTsThreads).
+__device__ __forceinline__ uint32_t ts_exclusive_scan(uint32_t v, uint32_t *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+#pragma unroll
+    for (int w = 0; w < kTsWarps; ++w) pre += w < warp ? wsum[w] : 0u;
+    return pre + x - v;
+}
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kTsThreads, 2) bucket_tile_sort_kernel(const TileSortArgs a) {
+    extern __shared__ __align__(16) unsigned char ts_raw[];
+    TsSmem &s = *reinterpret_cast<TsSmem *>(ts_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t n = a.n;
+    const int kb = a.kb;
+    const uint64_t kmask = (1ull << kb) - 1;
+    IdxT *perm = static_cast<IdxT *>(a.perm);
+    const uint32_t wb = (uint32_t)warp * 32 * kTsItems;  // warp-striped: item k of lane l is element wb + 32k + l
+    uint32_t *mh2 = s.whist2 + warp * (kTsBins / 2);
+    const uint16_t *mh16 = reinterpret_cast<const uint16_t *>(mh2);
+    for (;;) {
+        if (tid == 0) {  // after an error elsewhere (a full queue) no more ranges are taken
+            const unsigned int err = *(volatile const unsigned int *)&a.flags->error;
+            s.range_id = err ? 0xFFFFFFFFu : atomicAdd(a.range_counter, 1u);
+        }
+        __syncthreads();
+        const uint64_t r0 = (uint64_t)s.range_id * kTsRange;
+        __syncthreads();
+        if (r0 >= n) break;
+        const uint64_t r1 = umin64(n, r0 + kTsRange);
+        // the bucket holding position r0 - 1 belongs to an earlier range
+        uint64_t pos = r0 == 0 ? 0 : bucket_end(a.keys_in, n, kb, r0, a.keys_in[r0 - 1] >> kb, s);
+        while (pos < r1) {
+            const uint64_t avail = umin64((uint64_t)kTsWin, n - pos);
+            if (tid == 0) {
+                s.cut = 0;
+                s.kmin = ~0ull;
+                s.kmax = 0;
+            }
+            uint64_t w[kTsItems];
+#pragma unroll
+            for (int k = 0; k < kTsItems; ++k) {
+                const uint32_t e = wb + k * 32 + lane;
+                w[k] = e < avail ? a.keys_in[pos + e] : ~0ull;
+            }
+            __syncthreads();
+            // e ends its bucket when the next element's bucket differs or
+            // there is no next element; the window is cut after the last such e
+            uint32_t mycut = 0;
+#pragma unroll
+            for (int k = 0; k < kTsItems; ++k) {
+                const uint32_t e = wb + k * 32 + lane;
+                uint64_t nxt = __shfl_down_sync(kFull, w[k], 1);
+                const uint64_t wrap = __shfl_sync(kFull, w[k + 1 < kTsItems ? k + 1 : k], 0);
+                if (lane == 31) nxt = wrap;
+                if (e < avail) {
+                    bool boundary = true;
+                    if (pos + e + 1 < n) {
+                        if (e + 1 >= avail || (lane == 31 && k == kTsItems - 1)) nxt = a.keys_in[pos + e + 1];
+                        boundary = (w[k] >> kb) != (nxt >> kb);
+                    }
+                    if (boundary) mycut = e + 1;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mycut = max(mycut, __shfl_xor_sync(kFull, mycut, o));
+            if (lane == 0 && mycut) atomicMax(&s.cut, mycut);
+            __syncthreads();
+            const uint32_t cut = s.cut;
+            if (cut == 0) {  // one bucket fills the window and goes on
+                const uint64_t b = a.keys_in[pos] >> kb;
+                const uint64_t end = bucket_end(a.keys_in, n, kb, pos + kTsWin, b, s);
+                if (tid == 0) {
+                    const unsigned long long q = atomicAdd(&a.flags->qcount[kQOverflow], 1ull);
+                    if (q < a.cap_overflow) a.overflow[q] = RunEntry{pos, (unsigned)(end - pos), 0u};
+                    else atomicOr(&a.flags->error, kErrInternal);
+                }
+                pos = end;
+                continue;
+            }
+            unsigned long long lo = ~0ull, hi = 0;
+#pragma unroll
+            for (int k = 0; k < kTsItems; ++k) {
+                const uint32_t e = wb + k * 32 + lane;
+                if (e < cut) {
+                    const uint64_t v = w[k] & kmask;
+                    lo = v < lo ? v : lo;
+                    hi = v > hi ? v : hi;
+                }
+            }
+            lo = warp_min_u64(lo);
+            hi = warp_max_u64(hi);
+            if (lane == 0 && lo != ~0ull) {
+                atomicMin(&s.kmin, lo);
+                atomicMax(&s.kmax, hi);
+            }
+            __syncthreads();
+            const uint64_t wmin = s.kmin;
+            const uint64_t span = s.kmax - wmin;
+            const int npass = span ? (64 - __clzll((long long)span) + kRadixBits - 1) / kRadixBits : 0;
+            // elements past the cut sort after every element of the window
+#pragma unroll
+            for (int k = 0; k < kTsItems; ++k) {
+                const uint32_t e = wb + k * 32 + lane;
+                w[k] = e < cut ? (((w[k] & kmask) - wmin) << kTsIdxBits) | e : ~0ull;
+            }
+            if (npass == 0) {  // one key value: the window is in order
+#pragma unroll
+                for (int k = 0; k < kTsItems; ++k) s.word[wb + k * 32 + lane] = w[k];
+                __syncthreads();
+            }
+            for (int q = 0; q < npass; ++q) {
+                const int sh = kTsIdxBits + q * kRadixBits;
+#pragma unroll
+                for (int i = 0; i < kTsWarps / 2; ++i) s.whist2[i * kTsThreads + tid] = 0;
+                __syncthreads();
+                // rank among the warp's earlier elements with the same digit,
+                // four matches in flight; each leader's add is ordered before
+                // the next item's by the __syncwarp (stability)
+#pragma unroll
+                for (int g = 0; g < kTsItems; g += 4) {
+                    unsigned peers[4], before[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        peers[u] = __match_any_sync(kFull, (unsigned)(w[g + u] >> sh) & (kTsBins - 1));
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned d = (unsigned)(w[g + u] >> sh) & (kTsBins - 1);
+                        before[u] = 0;
+                        if (lane == __ffs(peers[u]) - 1) {
+                            const unsigned half = 16 * (d & 1);
+                            before[u] = (atomicAdd(&mh2[d >> 1], (unsigned)__popc(peers[u]) << half) >> half) & 0xFFFFu;
+                        }
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned bb = __shfl_sync(kFull, before[u], __ffs(peers[u]) - 1);
+                        s.rank[wb + (g + u) * 32 + lane] = (uint16_t)(bb + __popc(peers[u] & lanemask_lt()));
+                    }
+                }
+                __syncthreads();
+                // digit tid: offsets over the warps (in place of the counts),
+                // then the window's digit start
+                uint32_t run = 0;
+                uint16_t *col = reinterpret_cast<uint16_t *>(s.whist2) + tid;
+#pragma unroll
+                for (int w2 = 0; w2 < kTsWarps; ++w2) {
+                    const uint32_t c = col[w2 * kTsBins];
+                    col[w2 * kTsBins] = (uint16_t)run;
+                    run += c;
+                }
+                s.dstart[tid] = ts_exclusive_scan(run, s.wsum);
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < kTsItems; ++k) {
+                    const unsigned d = (unsigned)(w[k] >> sh) & (kTsBins - 1);
+                    const uint32_t dst = s.dstart[d] + mh16[d] + s.rank[wb + k * 32 + lane];
+                    s.word[dst] = w[k];
+                }
+                __syncthreads();
+                if (q + 1 < npass) {
+#pragma unroll
+                    for (int k = 0; k < kTsItems; ++k) w[k] = s.word[wb + k * 32 + lane];
+                }
+            }
+            // permutation (payload fetched through the place field) and run heads
+            for (uint32_t c = warp; c < kTsWin / 32; c += kTsWarps) {
+                const uint32_t j = c * 32 + lane;
+                const bool v = j < cut;
+                const uint64_t wj = v ? s.word[j] : 0ull;
+                const uint64_t wp = (v && j > 0) ? s.word[j - 1] : 0ull;
+                const bool head = v && (j == 0 || (wj >> kTsIdxBits) != (wp >> kTsIdxBits));
+                const unsigned hb = __ballot_sync(kFull, head);
+                if (lane == 0) s.heads[c] = hb;
+                if (v) perm[pos + j] = (IdxT)a.vals_in[pos + (wj & ((1u << kTsIdxBits) - 1))];
+            }
+            if (a.ties) {
+                __syncthreads();
+                // a run needs the fix-up when it has two or more members and
+                // their key's not-exact bit (bit 0) is set
+                for (uint32_t c = warp; c * 32 < cut; c += kTsWarps) {
+                    const uint32_t j = c * 32 + lane;
+                    if (j < cut && ((s.heads[c] >> lane) & 1u)) {
+                        const uint64_t key = (s.word[j] >> kTsIdxBits) + wmin;
+                        if (key & 1ull) {
+                            uint32_t end = cut;
+                            const uint32_t later = lane == 31 ? 0u : (s.heads[c] & (~0u << (lane + 1)));
+                            if (later) {
+                                end = c * 32 + __ffs(later) - 1;
+                            } else {
+                                for (uint32_t c2 = c + 1; c2 * 32 < cut; ++c2)
+                                    if (s.heads[c2]) {
+                                        end = c2 * 32 + __ffs(s.heads[c2]) - 1;
+                                        break;
+                                    }
+                            }
+                            if (end > cut) end = cut;
+                            if (end - j >= 2) queue_run(a.q, a.flags, pos + j, end - j);
+                        }
+                    }
+                }
+            }
+            pos += cut;
+            __syncthreads();
+        }
+    }
+}
+
+// Runs of equal keys inside the overflow buckets (sorted keys, key bit 0 =
+// not exact): one CTA per bucket walks it in chunks, carrying the head of
+// the run open at each chunk's start.
+constexpr int kOtThreads = 512;
+
+__global__ void __launch_bounds__(kOtThreads)
+oversize_ties_kernel(const RunEntry *__restrict__ runs, uint64_t count, const uint64_t *__restrict__ keys,
+                     const RunQueues q, DevFlags *flags) {
+    __shared__ unsigned long long s_wmax[kOtThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
+        const uint64_t start = runs[r].start, len = runs[r].len;
+        unsigned long long open = start;  // head of the run open at the chunk start
+        for (uint64_t c0 = 0; c0 < len; c0 += kOtThreads) {
+            const uint64_t j = c0 + tid;
+            const bool v = j < len;
+            const uint64_t k = v ? keys[start + j] : 0ull;
+            const bool head = v && (j == 0 || keys[start + j - 1] != k);
+            const bool tail = v && (j + 1 == len || keys[start + j + 1] != k);
+            // inclusive max-scan of head positions over the chunk
+            unsigned long long h = head ? start + j : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(kFull, h, o);
+                if (lane >= o && y > h) h = y;
+            }
+            if (lane == 31) s_wmax[warp] = h;
+            __syncthreads();
+            unsigned long long pre = open;
+            for (int w2 = 0; w2 < warp; ++w2) pre = s_wmax[w2] > pre ? s_wmax[w2] : pre;
+            const unsigned long long run_head = h > pre ? h : pre;
+            if (tail && (k & 1ull)) {
+                const uint64_t rl = start + j - run_head + 1;
+                if (rl >= 2) queue_run(q, flags, run_head, rl);
+            }
+            unsigned long long all = open;
+            for (int w2 = 0; w2 < kOtThreads / 32; ++w2) all = s_wmax[w2] > all ? s_wmax[w2] : all;
+            __syncthreads();
+            open = all;
+        }
+    }
+}
+
 // first[b] / last[b]: positions of bucket b's first and last element after the
 // stable partition (buckets are contiguous and in increasing order).
 __global__ void bucket_bounds_kernel(const uint32_t *__restrict__ bk, uint64_t n, unsigned long long *__restrict__ first,
@@ -555,13 +1032,15 @@ bucket_sort_kernel(const unsigned long long *__restrict__ first, const unsigned 
     }
 }
 
-// Oversize buckets, flattened over their elements: payload -> perm, and a
-// flag for every bucket holding two different keys.
+// Oversize buckets, flattened over their elements: payload -> perm (and,
+// when keys_out is given, key & kmask -> keys_out), and a flag for every
+// bucket holding two different keys.
 template <typename IdxT>
 __global__ void big_bucket_kernel(const RunEntry *__restrict__ big, uint64_t count,
                                   const unsigned long long *__restrict__ base, uint64_t total,
                                   const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                                  IdxT *__restrict__ perm, uint32_t *__restrict__ mixed) {
+                                  IdxT *__restrict__ perm, uint32_t *__restrict__ mixed,
+                                  uint64_t *__restrict__ keys_out, uint64_t kmask) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {
         uint64_t lo = 0, hi = count;
@@ -572,6 +1051,7 @@ __global__ void big_bucket_kernel(const RunEntry *__restrict__ big, uint64_t cou
         const uint64_t start = big[lo].start;
         const uint64_t pos = start + (a - base[lo]);
         perm[pos] = (IdxT)vals[pos];
+        if (keys_out) keys_out[pos] = keys[pos] & kmask;
         if (keys[pos] != keys[start] && mixed[lo] == 0u) mixed[lo] = 1u;
     }
 }
@@ -584,12 +1064,13 @@ __global__ void collect_mixed_kernel(const RunEntry *__restrict__ big, uint64_t 
     if (q < cap) q_mixed[q] = big[r]; else atomicOr(&flags->error, kErrInternal);
 }
 
-// Overflow buckets: gather (key, bucket run id, payload) into compacted
-// arrays, and scatter the sorted result back.
+// Overflow buckets: gather (key & kmask, bucket run id, payload) into
+// compacted arrays, and scatter the sorted result back.
 __global__ void overflow_gather_kernel(const RunEntry *__restrict__ runs, uint64_t count,
                                        const unsigned long long *__restrict__ run_base, uint64_t total,
                                        const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                                       uint64_t *__restrict__ ck, uint32_t *__restrict__ cs, uint32_t *__restrict__ cv) {
+                                       uint64_t kmask, uint64_t *__restrict__ ck, uint32_t *__restrict__ cs,
+                                       uint32_t *__restrict__ cv) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += stride) {
         uint64_t lo = 0, hi = count;
@@ -598,7 +1079,7 @@ __global__ void overflow_gather_kernel(const RunEntry *__restrict__ runs, uint64
             if (run_base[mid] <= a) lo = mid; else hi = mid;
         }
         const uint64_t pos = runs[lo].start + (a - run_base[lo]);
-        ck[a] = keys[pos];
+        ck[a] = keys[pos] & kmask;
         cs[a] = (uint32_t)lo;
         cv[a] = vals[pos];
     }
@@ -688,15 +1169,15 @@ cudaError_t launch_rmi_leaves(const uint64_t *sorted_sample, const uint32_t *Xi,
 
 cudaError_t launch_big_buckets(const RunEntry *big, uint64_t count, const unsigned long long *base, uint64_t total,
                                const uint64_t *keys, const uint32_t *vals, void *perm, int perm_u64, uint32_t *mixed,
-                               cudaStream_t s) {
+                               uint64_t *keys_out, uint64_t kmask, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
     if (perm_u64)
         big_bucket_kernel<uint64_t><<<grid, 256, 0, s>>>(big, count, base, total, keys, vals,
-                                                         static_cast<uint64_t *>(perm), mixed);
+                                                         static_cast<uint64_t *>(perm), mixed, keys_out, kmask);
     else
         big_bucket_kernel<uint32_t><<<grid, 256, 0, s>>>(big, count, base, total, keys, vals,
-                                                         static_cast<uint32_t *>(perm), mixed);
+                                                         static_cast<uint32_t *>(perm), mixed, keys_out, kmask);
     return cudaGetLastError();
 }
 
@@ -767,11 +1248,11 @@ cudaError_t launch_bucket_sort(const unsigned long long *first, const unsigned l
 }
 
 cudaError_t launch_overflow_gather(const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
-                                   uint64_t total, const uint64_t *keys, const uint32_t *vals, uint64_t *ck,
-                                   uint32_t *cs, uint32_t *cv, cudaStream_t s) {
+                                   uint64_t total, const uint64_t *keys, const uint32_t *vals, uint64_t kmask,
+                                   uint64_t *ck, uint32_t *cs, uint32_t *cv, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
-    overflow_gather_kernel<<<grid, 256, 0, s>>>(runs, count, run_base, total, keys, vals, ck, cs, cv);
+    overflow_gather_kernel<<<grid, 256, 0, s>>>(runs, count, run_base, total, keys, vals, kmask, ck, cs, cv);
     return cudaGetLastError();
 }
 
@@ -786,6 +1267,49 @@ cudaError_t launch_overflow_scatter(const RunEntry *runs, const unsigned long lo
     else
         overflow_scatter_kernel<uint32_t><<<grid, 256, 0, s>>>(runs, run_base, total, ck, cs, cv, keys,
                                                                static_cast<uint32_t *>(perm));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rmi_compose(uint64_t *keys, uint64_t n, const RmiModel *model, int bits, int kb,
+                               unsigned long long *hist, int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (bits < 1 || bits > 3 * kRadixBits || kb < 1 || kb + bits > 64) return cudaErrorInvalidValue;
+    const uint64_t groups = (n + (uint64_t)kCmpThreads * kCmpItems - 1) / ((uint64_t)kCmpThreads * kCmpItems);
+    const unsigned grid = (unsigned)umin64(groups, (uint64_t)num_sms * 4);
+    rmi_compose_kernel<<<grid, kCmpThreads, 0, s>>>(keys, n, model, bits, kb, hist);
+    return cudaGetLastError();
+}
+
+size_t tile_sort_smem_bytes() { return sizeof(TsSmem); }
+
+cudaError_t launch_bucket_tile_sort(const TileSortArgs &a, int perm_u64, int num_sms, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    if (a.kb < 1 || a.kb > kTsMaxKeyBits) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(TsSmem);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(bucket_tile_sort_kernel<uint64_t>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bucket_tile_sort_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const uint64_t ranges = (a.n + kTsRange - 1) / kTsRange;
+    const unsigned grid = (unsigned)umin64(ranges, (uint64_t)num_sms * 2);
+    if (perm_u64)
+        bucket_tile_sort_kernel<uint64_t><<<grid, kTsThreads, smem, s>>>(a);
+    else
+        bucket_tile_sort_kernel<uint32_t><<<grid, kTsThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_oversize_ties(const RunEntry *runs, uint64_t count, const uint64_t *keys, const RunQueues &q,
+                                 DevFlags *flags, int num_sms, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64(count, (uint64_t)num_sms * 4);
+    oversize_ties_kernel<<<grid, kOtThreads, 0, s>>>(runs, count, keys, q, flags);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,27 @@ def test_learned_forced_bucket_bits_match_oracle(cuda_lib, kind, bits):
     assert_oracle_equal(w, perm)
 
 
+@pytest.mark.parametrize("bits", [1, 5, 12, 18])
+@pytest.mark.parametrize("kind", [2, 5])
+def test_learned_composite_bucket_widths(cuda_lib, kind, bits):
+    """Byte-range keys carry the bucket id above them (one word through the
+    partition), and the in-bucket sort works on windows of whole buckets,
+    queueing their tie runs itself.  With 1 or 5 bucket bits every bucket is
+    longer than a window, so the overflow sort and the tie runs found inside
+    it carry the whole result; 12 bits give windows of many buckets, 18 bits
+    windows of one or two.  Zipf words (kind 2) tie heavily past the 8 coded
+    chars; skewed strings (kind 5) have a hot first letter."""
+    hs = cuda_lib
+    w = workloads.generate(kind, 300_007, 90 + kind)
+    data, off = to_device(w)
+    hs.learned_force_bucket_bits(bits)
+    try:
+        perm = hs.argsort_device(data, off, mode=hs.MODE_LEARNED, index_u64=kind == 5)
+    finally:
+        hs.learned_force_bucket_bits(0)
+    assert_oracle_equal(w, perm)
+
+
 @pytest.mark.slow
 def test_learned_3e8_crosses_to_wide_buckets(cuda_lib):
     """3e8 skewed strings: the first size at which the learned path picks
