@@ -104,7 +104,7 @@ struct Layout {
     int bucket_bits;
     uint32_t m;  // sample size
     size_t model, samp_keys_a, samp_keys_b, samp_vals_a, samp_vals_b, samp_X, samp_x, samp_t;
-    size_t b_first, b_last, q_over, over_base, keys_extra, big_mixed, q_mixed, mixed_base;
+    size_t b_first, b_last, q_over, q_over2, over_base, keys_extra, big_mixed, q_mixed, mixed_base;
     uint64_t cap_over;
     // hs_argsort_host only: device copies of the host inputs and output
     size_t dev_bytes, dev_offsets, dev_perm;
@@ -169,6 +169,7 @@ Layout make_layout(uint64_t n, bool learned = false) {
         L.b_last = c.take(B * 8);
         L.cap_over = n / (kBucketCap + 1) + 1;
         L.q_over = c.take(L.cap_over * sizeof(RunEntry));
+        L.q_over2 = c.take(L.cap_over * sizeof(RunEntry));
         L.over_base = c.take((L.cap_over + 1) * 8);
         L.big_mixed = c.take(L.cap_over * 4);
         L.q_mixed = c.take(L.cap_over * sizeof(RunEntry));
@@ -982,22 +983,21 @@ struct LearnedProfile {
     double info[4];
 };
 
-// Runs of the learned path too long for an in-CTA sort, queued in q_over
-// (c.h.qcount[kQOverflow] of them, positions in keys/vals): the payload goes
+// Runs of the learned path too long for an in-CTA sort, `big` of them in
+// q_over (positions in keys/vals): the payload goes
 // to the permutation as it stands (and key & kmask to big_keys_out when
 // given); the runs holding more than one key are gathered into ov.*[0],
 // sorted by a segmented radix sort over (run, key & kmask) and scattered
 // back: keys to sorted_keys_out, payload to the permutation.  The ov.*[1]
 // buffers are the passes' other side and may alias keys/vals (read only by
 // the gather).
-hs_status sort_oversize(Ctx &c, const Input &in, const uint64_t *keys, const uint32_t *vals, uint64_t kmask,
-                        uint64_t *big_keys_out, uint64_t *sorted_keys_out, SortBufs ov) {
+hs_status sort_oversize(Ctx &c, const Input &in, const RunEntry *q_over, uint64_t big, const uint64_t *keys,
+                        const uint32_t *vals, uint64_t kmask, uint64_t *big_keys_out, uint64_t *sorted_keys_out,
+                        SortBufs ov) {
     const uint64_t n = in.n;
     const Layout &L = c.L;
-    const uint64_t big = c.h.qcount[kQOverflow];
     if (big == 0) return HS_OK;
     if (big > L.cap_over) return fail(HS_ERR_INTERNAL, "overflow queue full");
-    RunEntry *q_over = c.at<RunEntry>(L.q_over);
     RunEntry *q_mixed = c.at<RunEntry>(L.q_mixed);
     unsigned long long *hist = c.at<unsigned long long>(L.hist);
     unsigned long long *bucket = c.at<unsigned long long>(L.bucket);
@@ -1098,19 +1098,32 @@ hs_status learned_composite(Ctx &c, const Input &in, SortBufs &b, RmiModel *mode
     HS_TRY(c.read_flags(), "tile sort sync");
     st = device_error_status(c.h);
     if (st != HS_OK) return st;
-    // Buckets longer than a window: sorted keys (bucket bits cleared) land in
-    // the other key buffer at their positions, then their tie runs are queued.
+    // Buckets longer than a window: sorted whole in windows twice as long
+    // where they fit; the rest by the overflow sort, whose sorted keys (bucket
+    // bits cleared) land in the other key buffer, then their tie runs.
     const uint64_t big = c.h.qcount[kQOverflow];
+    uint64_t big2 = 0;
+    RunEntry *q_rest = c.at<RunEntry>(L.q_over2);
+    if (big > 0) {
+        if (big > L.cap_over) return fail(HS_ERR_INTERNAL, "overflow queue full");
+        const RunSortArgs ra{b.keys[cur], b.vals[cur], in.perm, kb, perfect ? 0 : 1, c.at<RunEntry>(L.q_over), big,
+                             q_rest, L.cap_over, rq, c.d_flags};
+        HS_TRY(c.timed(kKBucketSort, 0.0, [&] { return launch_bucket_run_sort(ra, in.perm_u64, c.sms, c.s); }),
+               "bucket run sort");
+        HS_TRY(c.read_flags(), "run sort sync");
+        st = device_error_status(c.h);
+        if (st != HS_OK) return st;
+        big2 = c.h.qcount[kQOverflow2];
+    }
     const uint64_t kmask = (1ull << kb) - 1;
-    st = sort_oversize(c, in, b.keys[cur], b.vals[cur], kmask, b.keys[cur ^ 1], b.keys[cur ^ 1],
+    st = sort_oversize(c, in, q_rest, big2, b.keys[cur], b.vals[cur], kmask, b.keys[cur ^ 1], b.keys[cur ^ 1],
                        SortBufs{{c.at<uint64_t>(L.keys_extra), b.keys[cur]},
                                 {b.vals[cur ^ 1], b.vals[cur]},
                                 {b.segs[0], b.segs[1]}});
     if (st != HS_OK) return st;
-    if (!perfect && big > 0)
-        HS_TRY(c.timed(kKTieDetect, 8.0 * big, [&] {
-                   return launch_oversize_ties(c.at<RunEntry>(L.q_over), big, b.keys[cur ^ 1], rq, c.d_flags, c.sms,
-                                               c.s);
+    if (!perfect && big2 > 0)
+        HS_TRY(c.timed(kKTieDetect, 8.0 * big2, [&] {
+                   return launch_oversize_ties(q_rest, big2, b.keys[cur ^ 1], rq, c.d_flags, c.sms, c.s);
                }),
                "oversize ties");
     if (!perfect) {
@@ -1205,7 +1218,7 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
         const int kb = kmax ? 64 - __builtin_clzll(kmax) : 1;
         const int forced = g_forced_bucket_bits.load();
         const int cbits = forced > 0 ? forced : composite_bits(n);
-        if (kb + cbits <= 64 && cbits <= 3 * kRadixBits && kb <= 64 - 13)  // 13: the in-window place field
+        if (kb + cbits <= 64 && cbits <= 3 * kRadixBits && kb <= kTsMaxKeyBits)
             return learned_composite(c, in, b, model, kb, cbits, perfect);
     }
     HS_TRY(cudaMemsetAsync(hist, 0, kHistPasses * kBins * 8, c.s), "memset hist");
@@ -1238,7 +1251,8 @@ hs_status argsort_learned(Ctx &c, const Input &in0, int coder, bool *fallback, L
     HS_TRY(c.read_flags(), "bucket sort sync");
     st = device_error_status(c.h);
     if (st != HS_OK) return st;
-    st = sort_oversize(c, in, b.keys[cur], b.vals[cur], ~0ull, nullptr, b.keys[cur],
+    st = sort_oversize(c, in, c.at<RunEntry>(L.q_over), c.h.qcount[kQOverflow], b.keys[cur], b.vals[cur], ~0ull,
+                       nullptr, b.keys[cur],
                        SortBufs{{c.at<uint64_t>(L.keys_extra), b.keys[cur ^ 1]},
                                 {b.vals[cur ^ 1], b.vals[cur]},
                                 {b.segs[cur ^ 1], b.segs[cur]}});

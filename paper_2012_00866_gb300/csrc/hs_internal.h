@@ -189,7 +189,7 @@ __device__ __forceinline__ uint64_t instance_base(const Instances &in, uint64_t 
 }
 
 // ---- fixup.cu ------------------------------------------------------------
-enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3, kQOverflow = 4, kQMixed = 5 };
+enum QueueId { kQSmall = 0, kQMedium = 1, kQLargeA = 2, kQLargeB = 3, kQOverflow = 4, kQMixed = 5, kQOverflow2 = 6 };
 constexpr uint32_t kSmallMax = 32;     // warp per run
 constexpr uint32_t kMediumMax = 2048;  // block per run
 
@@ -292,6 +292,7 @@ constexpr int kRmiFeatureBits = 24;
 constexpr uint64_t kRmiStride = 100;  // one sample per 100 keys (a 1% sample)
 constexpr uint64_t kRmiSeed = 0x5DEECE66Dull;
 constexpr int kBucketCap = 4096;      // largest bucket sorted inside one CTA
+constexpr int kRmiAccelBits = 12;     // leaf index over the top 12 feature bits
 
 // Model state (device, in the workspace).  thresh[l-1] = least feature X
 // routed to leaf >= l (l = 1..L-1); thresh[L-1] = 2^24.
@@ -308,6 +309,15 @@ struct RmiModel {
     int shift;
     int pad1;
     float loss0, loss1;  // training loss before / after the gradient steps
+    // For the bucket kernels: leaf l's parameters in one 32-byte record, and
+    // accel[s] = the leaf of feature s << (24 - kRmiAccelBits) (s up to
+    // 2^kRmiAccelBits inclusive), so the leaf of feature X lies in
+    // [accel[X >> 12], accel[(X >> 12) + 1]].
+    struct alignas(32) LeafPk {
+        unsigned long long kbase;
+        float kscale, slope, icept, lo, hi, pad;
+    } leafpk[kRmiLeaves];
+    uint16_t accel[(1 << kRmiAccelBits) + 8];
 };
 
 cudaError_t launch_rmi_sample(const uint64_t *keys, uint64_t n, uint64_t seed,
@@ -380,11 +390,13 @@ struct RunQueues {
     uint64_t cap_small, cap_medium, cap_large;
     uint64_t perm_n;
 };
+// Widest key (bits below the bucket id) the in-bucket sorts take.
+constexpr int kTsMaxKeyBits = 50;
 // In-bucket sorts of composite keys grouped by bucket (key bits below kb,
-// kb <= 51): writes the payload in key order to perm; with ties set, queues
-// every run of equal keys whose bit 0 (not exact) is set; buckets longer than
-// one window are queued in overflow (DevFlags::qcount[kQOverflow]) and left
-// to the caller.
+// kb <= kTsMaxKeyBits): writes the payload in key order to perm; with ties
+// set, queues every run of equal keys whose bit 0 (not exact) is set; buckets
+// longer than one window are queued in overflow (DevFlags::qcount[kQOverflow])
+// and left to the caller.
 struct TileSortArgs {
     const uint64_t *keys_in;
     const uint32_t *vals_in;
@@ -400,11 +412,27 @@ struct TileSortArgs {
 };
 cudaError_t launch_bucket_tile_sort(const TileSortArgs &a, int perm_u64,
                                     int num_sms, cudaStream_t s);
+// The queued buckets, each sorted whole in a window of 12288 (as above);
+// longer ones go to rest (DevFlags::qcount[kQOverflow2]).
+struct RunSortArgs {
+    const uint64_t *keys_in;
+    const uint32_t *vals_in;
+    void *perm;
+    int kb;
+    int ties;
+    const RunEntry *runs;
+    uint64_t count;
+    RunEntry *rest;
+    uint64_t cap_rest;
+    RunQueues q;
+    DevFlags *flags;
+};
+cudaError_t launch_bucket_run_sort(const RunSortArgs &a, int perm_u64,
+                                   int num_sms, cudaStream_t s);
 // Tie runs inside the runs of `runs` (sorted keys, bit 0 = not exact).
 cudaError_t launch_oversize_ties(const RunEntry *runs, uint64_t count,
                                  const uint64_t *keys, const RunQueues &q,
                                  DevFlags *flags, int num_sms, cudaStream_t s);
-size_t tile_sort_smem_bytes();
 cudaError_t launch_overflow_scatter(const RunEntry *runs,
                                     const unsigned long long *run_base,
                                     uint64_t total, const uint64_t *ck,

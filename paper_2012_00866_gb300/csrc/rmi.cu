@@ -462,16 +462,30 @@ rmi_bucket_kernel(const uint64_t *__restrict__ keys, uint64_t n, const RmiModel 
 // top 12 feature bits: slice s of the 24-bit feature holds only the leaves
 // between the leaf of its first value and the leaf of the next slice's first
 // value (the threshold table is non-decreasing), so the bisection runs over
-// those few leaves instead of all 4096.
-constexpr int kAccelBits = 12;
-constexpr int kAccel = 1 << kAccelBits;
-constexpr int kAccelShift = kRmiFeatureBits - kAccelBits;
+// those few leaves instead of all 4096; each leaf's parameters are one
+// 32-byte record.
+constexpr int kAccel = 1 << kRmiAccelBits;
+constexpr int kAccelShift = kRmiFeatureBits - kRmiAccelBits;
 constexpr int kCmpThreads = 512;
 constexpr int kCmpItems = 4;
+using LeafPk = RmiModel::LeafPk;
+static_assert(sizeof(LeafPk) == 32, "one leaf record is two 16-byte loads");
 
-__device__ void build_accel(const uint32_t *s_thresh, uint16_t *s_accel) {
-    for (int sl = threadIdx.x; sl <= kAccel; sl += blockDim.x)
-        s_accel[sl] = (uint16_t)table_leaf(s_thresh, (uint32_t)sl << kAccelShift);
+// The index and the leaf records, once per model (after the leaf fits).
+__global__ void rmi_pack_kernel(RmiModel *model) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= (uint32_t)kAccel) model->accel[i] = (uint16_t)table_leaf(model->thresh, i << kAccelShift);
+    if (i < (uint32_t)kRmiLeaves) {
+        LeafPk r;
+        r.kbase = model->kbase[i];
+        r.kscale = model->kscale[i];
+        r.slope = model->slope[i];
+        r.icept = model->icept[i];
+        r.lo = model->lo[i];
+        r.hi = model->hi[i];
+        r.pad = 0.f;
+        model->leafpk[i] = r;
+    }
 }
 
 // table_leaf(X) restricted to the leaves of X's slice: the largest l in
@@ -487,13 +501,18 @@ __device__ __forceinline__ uint32_t accel_leaf(const uint32_t *s_thresh, const u
 }
 
 // bucket_of (trained model) with the indexed leaf search: the same arithmetic.
-__device__ __forceinline__ uint32_t bucket_fast(const RmiModel &M, const uint32_t *s_thresh, const uint16_t *s_accel,
-                                                uint64_t key, uint64_t kmin, int shift, float B) {
+__device__ __forceinline__ uint32_t bucket_fast(const LeafPk *__restrict__ pk, const uint32_t *s_thresh,
+                                                const uint16_t *s_accel, uint64_t key, uint64_t kmin, int shift,
+                                                float B) {
     const uint32_t X = feature_of(key, kmin, shift);
     const uint32_t l = accel_leaf(s_thresh, s_accel, X);
-    const uint64_t kbase = __ldg(&M.kbase[l]);
-    const float xl = (float)(key >= kbase ? key - kbase : 0ull) * __ldg(&M.kscale[l]);
-    const float pos = fminf(fmaxf(fmaf(__ldg(&M.slope[l]), xl, __ldg(&M.icept[l])), __ldg(&M.lo[l])), __ldg(&M.hi[l]));
+    const ulonglong2 r0 = __ldg(reinterpret_cast<const ulonglong2 *>(pk + l));
+    const float4 r1 = __ldg(reinterpret_cast<const float4 *>(pk + l) + 1);
+    const uint64_t kbase = r0.x;
+    const float kscale = __uint_as_float((unsigned)r0.y), slope = __uint_as_float((unsigned)(r0.y >> 32));
+    const float icept = r1.x, lo = r1.y, hi = r1.z;
+    const float xl = (float)(key >= kbase ? key - kbase : 0ull) * kscale;
+    const float pos = fminf(fmaxf(fmaf(slope, xl, icept), lo), hi);
     return (uint32_t)fminf(fmaxf(pos * B, 0.0f), B - 1.0f);
 }
 
@@ -503,18 +522,20 @@ __device__ __forceinline__ uint32_t bucket_fast(const RmiModel &M, const uint32_
 __global__ void __launch_bounds__(kCmpThreads)
 rmi_compose_kernel(uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__restrict__ model, int bits, int kb,
                    unsigned long long *__restrict__ hist) {
-    __shared__ uint32_t s_thresh[kRmiLeaves];
-    __shared__ uint16_t s_accel[kAccel + 2];
-    __shared__ uint32_t s_hist[3 * kBins];
+    extern __shared__ __align__(16) unsigned char cmp_smem[];
+    uint32_t *s_thresh = reinterpret_cast<uint32_t *>(cmp_smem);
+    uint16_t *s_accel = reinterpret_cast<uint16_t *>(s_thresh + kRmiLeaves);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_accel + kAccel + 8);
     for (int i = threadIdx.x; i < kRmiLeaves; i += kCmpThreads) s_thresh[i] = model->thresh[i];
+    for (int i = threadIdx.x; i < (kAccel + 8) / 8; i += kCmpThreads)
+        reinterpret_cast<uint4 *>(s_accel)[i] = reinterpret_cast<const uint4 *>(model->accel)[i];
     for (int i = threadIdx.x; i < 3 * kBins; i += kCmpThreads) s_hist[i] = 0;
-    __syncthreads();
-    build_accel(s_thresh, s_accel);
     __syncthreads();
     const uint64_t kmin = model->kmin;
     const int shift = model->shift;
     const float B = (float)(1u << bits);
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    const LeafPk *pk = model->leafpk;
     constexpr uint64_t kGroup = (uint64_t)kCmpThreads * kCmpItems;
     for (uint64_t g = (uint64_t)blockIdx.x * kGroup; g < n; g += (uint64_t)gridDim.x * kGroup) {
         uint64_t key[kCmpItems];
@@ -526,14 +547,11 @@ rmi_compose_kernel(uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__re
 #pragma unroll
         for (int k = 0; k < kCmpItems; ++k) {
             const uint64_t i = g + (uint64_t)k * kCmpThreads + threadIdx.x;
-            const bool valid = i < n;
-            uint32_t b = 0;
-            if (valid) {
-                b = bucket_fast(*model, s_thresh, s_accel, key[k], kmin, shift, B);
+            if (i < n) {
+                const uint32_t b = bucket_fast(pk, s_thresh, s_accel, key[k], kmin, shift, B);
                 keys[i] = key[k] | ((uint64_t)b << kb);
+                for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p * kBins + ((b >> (kRadixBits * p)) & (kBins - 1))], 1u);
             }
-            for (int p = 0; p < passes; ++p)
-                hist_add(s_hist + p * kBins, (b >> (kRadixBits * p)) & (kBins - 1), valid);
         }
     }
     __syncthreads();
@@ -547,42 +565,48 @@ rmi_compose_kernel(uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__re
 // order, and the bucket is a non-decreasing function of the key, so sorting
 // any run of whole buckets by key alone puts it in its final order.  A CTA
 // claims ranges of kTsRange positions and takes every bucket that starts in
-// its range: it loads the next kTsWin keys, cuts them after the last bucket
+// its range: it loads the next window of keys, cuts it after the last bucket
 // that ends inside, and sorts that window in shared memory.  Each element
-// becomes one word, (key - min(window)) << 13 | its place in the window, so
-// the payload is fetched once, at the end; a stable LSD radix sort on the
-// key part, 9 bits a pass, takes as many passes as the window's key span
-// needs, the words held in registers between passes.  The CTA then writes
-// the permutation and queues the window's runs of equal keys that hold an
-// inexactly coded string for the fix-up (equal keys share a bucket, so no run
-// crosses a window).  A bucket longer than the window goes to the overflow
-// queue.
-constexpr int kTsThreads = 512;
-constexpr int kTsWarps = kTsThreads / 32;
-constexpr int kTsItems = 12;
-constexpr int kTsWin = kTsThreads * kTsItems;
-constexpr int kTsIdxBits = 13;
-constexpr int kTsBins = kBins;  // 9-bit digits, one per thread in the digit phase
+// becomes one word, (key - min(window)) << place bits | its place in the
+// window, so the payload is fetched once, at the end; a stable LSD radix
+// sort on the key part, 9 bits a pass, takes as many passes as the window's
+// key span needs, the words held in registers between passes.  The CTA then
+// writes the permutation and queues the window's runs of equal keys that
+// hold an inexactly coded string for the fix-up (equal keys share a bucket,
+// so no run crosses a window).  A bucket longer than the window is queued;
+// a second kernel with windows twice as long (one CTA per SM) sorts those it
+// can hold, and the overflow sort takes the rest.
 constexpr uint64_t kTsRange = 1ull << 18;
-static_assert(kTsWin <= 1 << kTsIdxBits, "the place field indexes the window");
-static_assert(kTsBins == kTsThreads, "one digit per thread");
-static_assert(32 * kTsItems < (1 << 16), "ranks within a warp fit 16 bits");
-constexpr int kTsMaxKeyBits = 64 - kTsIdxBits;  // key spans the words can hold
 
-// Per-warp digit counts are 16-bit (at most 32 * kTsItems per warp), two to a
-// word for the shared atomics; after the digit phase the same halves hold
-// each warp's offset within the digit (below kTsWin).  Ranks go to
-// shared memory rather than registers, which keeps two CTAs per SM.
-struct TsSmem {
-    uint64_t word[kTsWin];
-    uint32_t whist2[kTsWarps * kTsBins / 2];
-    uint16_t rank[kTsWin];
-    uint32_t dstart[kTsBins];
-    uint32_t heads[kTsWin / 32];
-    uint32_t wsum[kTsWarps];
-    unsigned long long kmin, kmax, found;
-    unsigned int cut, range_id;
+template <int THREADS, int ITEMS, bool RANK_REGS>
+struct TsShape {
+    static constexpr bool kRankRegs = RANK_REGS;  // ranks in registers (else in shared memory)
+    static constexpr int kThreads = THREADS;
+    static constexpr int kWarps = THREADS / 32;
+    static constexpr int kItems = ITEMS;
+    static constexpr int kWin = THREADS * ITEMS;
+    static constexpr int kIdxBits = kWin <= (1 << 13) ? 13 : 14;
+    static_assert(kWin <= (1 << kIdxBits), "the place field indexes the window");
+    static_assert(THREADS % 32 == 0 && ITEMS % 4 == 0, "whole warps, whole groups of four items");
+    static_assert(kWin < (1 << 16), "per-warp counts and offsets within a digit fit 16 bits");
+    // Per-warp digit counts are 16-bit, two to a word for the shared
+    // atomics; after the digit phase the same halves hold each warp's first
+    // place for the digit in the window.  Ranks go to shared memory rather
+    // than registers, which keeps the register count at 64.
+    struct Smem {
+        uint64_t word[kWin];
+        uint32_t whist2[kWarps * kBins / 2];
+        uint16_t rank[kWin];
+        uint32_t heads[kWin / 32];
+        uint32_t wsum[kWarps];
+        unsigned long long kmin, kmax, found;
+        unsigned int cut, job;
+    };
 };
+using TsMain = TsShape<512, 12, true>;   // windows cut from ranges, two CTAs per SM
+using TsBig = TsShape<1024, 12, false>;  // one oversize bucket at a time, one CTA per SM
+static_assert(64 - TsBig::kIdxBits >= kTsMaxKeyBits && 64 - TsMain::kIdxBits >= kTsMaxKeyBits,
+              "every shape's words hold a key span of kTsMaxKeyBits");
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
 #pragma unroll
@@ -622,18 +646,27 @@ __device__ void queue_run(const RunQueues &q, DevFlags *flags, uint64_t start, u
     }
 }
 
+// A bucket longer than a window, to a queue of RunEntry (count in *count).
+__device__ void queue_bucket(RunEntry *qb, unsigned long long *count, uint64_t cap, DevFlags *flags, uint64_t start,
+                             uint64_t len) {
+    const unsigned long long i = atomicAdd(count, 1ull);
+    if (i < cap && len < 0xFFFFFFFFull) qb[i] = RunEntry{start, (unsigned)len, 0u};
+    else atomicOr(&flags->error, kErrInternal);
+}
+
 // First position >= from whose bucket (key >> kb) is not b, or n.  Every key
 // at or after `from` has a bucket >= b.  Block-wide (all threads call it and
-// get the same value): one coalesced look at the next kTsWin keys, then, if
-// the bucket runs on past them, a galloping search and a bisection.
+// get the same value): one coalesced look at the next window of keys, then,
+// if the bucket runs on past them, a galloping search and a bisection.
+template <class S>
 __device__ uint64_t bucket_end(const uint64_t *__restrict__ keys, uint64_t n, int kb, uint64_t from, uint64_t b,
-                               TsSmem &s) {
+                               typename S::Smem &s) {
     if (threadIdx.x == 0) s.found = ~0ull;
     __syncthreads();
     unsigned long long best = ~0ull;
 #pragma unroll
-    for (int k = 0; k < kTsItems; ++k) {
-        const uint64_t j = from + (uint64_t)k * kTsThreads + threadIdx.x;
+    for (int k = 0; k < S::kItems; ++k) {
+        const uint64_t j = from + (uint64_t)k * S::kThreads + threadIdx.x;
         if (j < n && (keys[j] >> kb) != b && j < best) best = j;
     }
     best = warp_min_u64(best);
@@ -641,11 +674,11 @@ __device__ uint64_t bucket_end(const uint64_t *__restrict__ keys, uint64_t n, in
     __syncthreads();
     unsigned long long f = s.found;
     if (f == ~0ull) {
-        if (from + kTsWin >= n) {
+        if (from + S::kWin >= n) {
             f = n;
         } else {
-            if (threadIdx.x == 0) {  // keys [from, from + kTsWin) are all in bucket b
-                uint64_t lo = from + kTsWin - 1, step = kTsWin, hi;
+            if (threadIdx.x == 0) {  // keys [from, from + kWin) are all in bucket b
+                uint64_t lo = from + S::kWin - 1, step = S::kWin, hi;
                 for (;;) {
                     hi = lo + step;
                     if (hi >= n) {
@@ -670,7 +703,8 @@ __device__ uint64_t bucket_end(const uint64_t *__restrict__ keys, uint64_t n, in
     return f;
 }
 
-// Exclusive scan of one u32 per thread over the block (kTsThreads).
+// Exclusive scan of one u32 per thread over the block.
+template <class S>
 __device__ __forceinline__ uint32_t ts_exclusive_scan(uint32_t v, uint32_t *wsum) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -683,44 +717,195 @@ __device__ __forceinline__ uint32_t ts_exclusive_scan(uint32_t v, uint32_t *wsum
     __syncthreads();
     uint32_t pre = 0;
 #pragma unroll
-    for (int w = 0; w < kTsWarps; ++w) pre += w < warp ? wsum[w] : 0u;
+    for (int w = 0; w < S::kWarps; ++w) pre += w < warp ? wsum[w] : 0u;
     return pre + x - v;
 }
 
+// Sorts elements [0, cut) of a window held in w (item k of lane l of warp wp
+// is element 32 * ITEMS * wp + 32k + l; w[k] its composite key, anything at
+// or past cut), writes their payload in key order to perm[pos ..] and, with
+// ties set, queues the window's runs of equal keys whose bit 0 (not exact)
+// is set.  On entry s.kmin = ~0 and s.kmax = 0 are visible to every thread;
+// returns after a barrier.
+template <class S, typename IdxT>
+__device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint64_t pos, uint32_t cut,
+                            uint64_t kmask, const uint32_t *__restrict__ vals_in, IdxT *__restrict__ perm,
+                            bool ties, const RunQueues &q, DevFlags *flags) {
+    constexpr int IB = S::kIdxBits;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t wb = (uint32_t)warp * 32 * S::kItems;
+    uint32_t *mh2 = s.whist2 + warp * (kBins / 2);
+    const uint16_t *mh16 = reinterpret_cast<const uint16_t *>(mh2);
+
+    unsigned long long lo = ~0ull, hi = 0;
+#pragma unroll
+    for (int k = 0; k < S::kItems; ++k) {
+        const uint32_t e = wb + k * 32 + lane;
+        if (e < cut) {
+            const uint64_t v = w[k] & kmask;
+            lo = v < lo ? v : lo;
+            hi = v > hi ? v : hi;
+        }
+    }
+    lo = warp_min_u64(lo);
+    hi = warp_max_u64(hi);
+    if (lane == 0 && lo != ~0ull) {
+        atomicMin(&s.kmin, lo);
+        atomicMax(&s.kmax, hi);
+    }
+    __syncthreads();
+    const uint64_t wmin = s.kmin;
+    const uint64_t span = s.kmax - wmin;
+    const int npass = span ? (64 - __clzll((long long)span) + kRadixBits - 1) / kRadixBits : 0;
+    // elements past the cut sort after every element of the window
+#pragma unroll
+    for (int k = 0; k < S::kItems; ++k) {
+        const uint32_t e = wb + k * 32 + lane;
+        w[k] = e < cut ? (((w[k] & kmask) - wmin) << IB) | e : ~0ull;
+    }
+    if (npass == 0) {  // one key value: the window is in order
+#pragma unroll
+        for (int k = 0; k < S::kItems; ++k) s.word[wb + k * 32 + lane] = w[k];
+        __syncthreads();
+    }
+    for (int qp = 0; qp < npass; ++qp) {
+        const int sh = IB + qp * kRadixBits;
+        for (int i = tid; i < S::kWarps * kBins / 2; i += S::kThreads) s.whist2[i] = 0;
+        __syncthreads();
+        // rank among the warp's earlier elements with the same digit, four
+        // matches in flight; each leader's add is ordered before the next
+        // item's by the __syncwarp (stability)
+        uint32_t rankp[S::kItems / 2];
+#pragma unroll
+        for (int k = 0; k < S::kItems / 2; ++k) rankp[k] = 0;
+#pragma unroll
+        for (int g = 0; g < S::kItems; g += 4) {
+            unsigned peers[4], before[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) peers[u] = __match_any_sync(kFull, (unsigned)(w[g + u] >> sh) & (kBins - 1));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned d = (unsigned)(w[g + u] >> sh) & (kBins - 1);
+                before[u] = 0;
+                if (lane == __ffs(peers[u]) - 1) {
+                    const unsigned half = 16 * (d & 1);
+                    before[u] = (atomicAdd(&mh2[d >> 1], (unsigned)__popc(peers[u]) << half) >> half) & 0xFFFFu;
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const unsigned bb = __shfl_sync(kFull, before[u], __ffs(peers[u]) - 1);
+                const unsigned rk = bb + __popc(peers[u] & lanemask_lt());
+                if (S::kRankRegs) rankp[(g + u) / 2] |= rk << (16 * ((g + u) & 1));
+                else s.rank[wb + (g + u) * 32 + lane] = (uint16_t)rk;
+            }
+        }
+        __syncthreads();
+        // digit tid: offsets over the warps (in place of the counts), then
+        // the window's digit start
+        uint32_t run = 0;
+        if (tid < kBins) {
+            uint16_t *col = reinterpret_cast<uint16_t *>(s.whist2) + tid;
+#pragma unroll
+            for (int w2 = 0; w2 < S::kWarps; ++w2) {
+                const uint32_t c = col[w2 * kBins];
+                col[w2 * kBins] = (uint16_t)run;
+                run += c;
+            }
+        }
+        const uint32_t ds = ts_exclusive_scan<S>(run, s.wsum);
+        if (tid < kBins) {  // each warp's place for the digit, window-wide
+            uint16_t *col = reinterpret_cast<uint16_t *>(s.whist2) + tid;
+#pragma unroll
+            for (int w2 = 0; w2 < S::kWarps; ++w2) col[w2 * kBins] = (uint16_t)(col[w2 * kBins] + ds);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < S::kItems; ++k) {
+            const unsigned d = (unsigned)(w[k] >> sh) & (kBins - 1);
+            const uint32_t rk = S::kRankRegs ? (rankp[k / 2] >> (16 * (k & 1))) & 0xFFFFu : s.rank[wb + k * 32 + lane];
+            s.word[mh16[d] + rk] = w[k];
+        }
+        __syncthreads();
+        if (qp + 1 < npass) {
+#pragma unroll
+            for (int k = 0; k < S::kItems; ++k) w[k] = s.word[wb + k * 32 + lane];
+        }
+    }
+    // permutation (payload fetched through the place field) and run heads
+    for (uint32_t c = warp; c < S::kWin / 32; c += S::kWarps) {
+        const uint32_t j = c * 32 + lane;
+        const bool v = j < cut;
+        const uint64_t wj = v ? s.word[j] : 0ull;
+        const uint64_t wp = (v && j > 0) ? s.word[j - 1] : 0ull;
+        const bool head = v && (j == 0 || (wj >> IB) != (wp >> IB));
+        const unsigned hb = __ballot_sync(kFull, head);
+        if (lane == 0) s.heads[c] = hb;
+        if (v) perm[pos + j] = (IdxT)vals_in[pos + (wj & ((1u << IB) - 1))];
+    }
+    if (ties) {
+        __syncthreads();
+        // a run needs the fix-up when it has two or more members and their
+        // key's not-exact bit (bit 0) is set
+        for (uint32_t c = warp; c * 32 < cut; c += S::kWarps) {
+            const uint32_t j = c * 32 + lane;
+            if (j < cut && ((s.heads[c] >> lane) & 1u)) {
+                const uint64_t key = (s.word[j] >> IB) + wmin;
+                if (key & 1ull) {
+                    uint32_t end = cut;
+                    const uint32_t later = lane == 31 ? 0u : (s.heads[c] & (~0u << (lane + 1)));
+                    if (later) {
+                        end = c * 32 + __ffs(later) - 1;
+                    } else {
+                        for (uint32_t c2 = c + 1; c2 * 32 < cut; ++c2)
+                            if (s.heads[c2]) {
+                                end = c2 * 32 + __ffs(s.heads[c2]) - 1;
+                                break;
+                            }
+                    }
+                    if (end > cut) end = cut;
+                    if (end - j >= 2) queue_run(q, flags, pos + j, end - j);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <typename IdxT>
-__global__ void __launch_bounds__(kTsThreads, 2) bucket_tile_sort_kernel(const TileSortArgs a) {
+__global__ void __launch_bounds__(TsMain::kThreads, 2) bucket_tile_sort_kernel(const TileSortArgs a) {
+    using S = TsMain;
     extern __shared__ __align__(16) unsigned char ts_raw[];
-    TsSmem &s = *reinterpret_cast<TsSmem *>(ts_raw);
+    S::Smem &s = *reinterpret_cast<S::Smem *>(ts_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t n = a.n;
     const int kb = a.kb;
     const uint64_t kmask = (1ull << kb) - 1;
     IdxT *perm = static_cast<IdxT *>(a.perm);
-    const uint32_t wb = (uint32_t)warp * 32 * kTsItems;  // warp-striped: item k of lane l is element wb + 32k + l
-    uint32_t *mh2 = s.whist2 + warp * (kTsBins / 2);
-    const uint16_t *mh16 = reinterpret_cast<const uint16_t *>(mh2);
+    const uint32_t wb = (uint32_t)warp * 32 * S::kItems;
     for (;;) {
         if (tid == 0) {  // after an error elsewhere (a full queue) no more ranges are taken
             const unsigned int err = *(volatile const unsigned int *)&a.flags->error;
-            s.range_id = err ? 0xFFFFFFFFu : atomicAdd(a.range_counter, 1u);
+            s.job = err ? 0xFFFFFFFFu : atomicAdd(a.range_counter, 1u);
         }
         __syncthreads();
-        const uint64_t r0 = (uint64_t)s.range_id * kTsRange;
+        const uint64_t r0 = (uint64_t)s.job * kTsRange;
         __syncthreads();
         if (r0 >= n) break;
         const uint64_t r1 = umin64(n, r0 + kTsRange);
         // the bucket holding position r0 - 1 belongs to an earlier range
-        uint64_t pos = r0 == 0 ? 0 : bucket_end(a.keys_in, n, kb, r0, a.keys_in[r0 - 1] >> kb, s);
+        uint64_t pos = r0 == 0 ? 0 : bucket_end<S>(a.keys_in, n, kb, r0, a.keys_in[r0 - 1] >> kb, s);
         while (pos < r1) {
-            const uint64_t avail = umin64((uint64_t)kTsWin, n - pos);
+            const uint64_t avail = umin64((uint64_t)S::kWin, n - pos);
             if (tid == 0) {
                 s.cut = 0;
                 s.kmin = ~0ull;
                 s.kmax = 0;
             }
-            uint64_t w[kTsItems];
+            uint64_t w[S::kItems];
 #pragma unroll
-            for (int k = 0; k < kTsItems; ++k) {
+            for (int k = 0; k < S::kItems; ++k) {
                 const uint32_t e = wb + k * 32 + lane;
                 w[k] = e < avail ? a.keys_in[pos + e] : ~0ull;
             }
@@ -729,15 +914,15 @@ __global__ void __launch_bounds__(kTsThreads, 2) bucket_tile_sort_kernel(const T
             // there is no next element; the window is cut after the last such e
             uint32_t mycut = 0;
 #pragma unroll
-            for (int k = 0; k < kTsItems; ++k) {
+            for (int k = 0; k < S::kItems; ++k) {
                 const uint32_t e = wb + k * 32 + lane;
                 uint64_t nxt = __shfl_down_sync(kFull, w[k], 1);
-                const uint64_t wrap = __shfl_sync(kFull, w[k + 1 < kTsItems ? k + 1 : k], 0);
+                const uint64_t wrap = __shfl_sync(kFull, w[k + 1 < S::kItems ? k + 1 : k], 0);
                 if (lane == 31) nxt = wrap;
                 if (e < avail) {
                     bool boundary = true;
                     if (pos + e + 1 < n) {
-                        if (e + 1 >= avail || (lane == 31 && k == kTsItems - 1)) nxt = a.keys_in[pos + e + 1];
+                        if (e + 1 >= avail || (lane == 31 && k == S::kItems - 1)) nxt = a.keys_in[pos + e + 1];
                         boundary = (w[k] >> kb) != (nxt >> kb);
                     }
                     if (boundary) mycut = e + 1;
@@ -750,147 +935,55 @@ __global__ void __launch_bounds__(kTsThreads, 2) bucket_tile_sort_kernel(const T
             const uint32_t cut = s.cut;
             if (cut == 0) {  // one bucket fills the window and goes on
                 const uint64_t b = a.keys_in[pos] >> kb;
-                const uint64_t end = bucket_end(a.keys_in, n, kb, pos + kTsWin, b, s);
-                if (tid == 0) {
-                    const unsigned long long q = atomicAdd(&a.flags->qcount[kQOverflow], 1ull);
-                    if (q < a.cap_overflow) a.overflow[q] = RunEntry{pos, (unsigned)(end - pos), 0u};
-                    else atomicOr(&a.flags->error, kErrInternal);
-                }
+                const uint64_t end = bucket_end<S>(a.keys_in, n, kb, pos + S::kWin, b, s);
+                if (tid == 0)
+                    queue_bucket(a.overflow, &a.flags->qcount[kQOverflow], a.cap_overflow, a.flags, pos, end - pos);
                 pos = end;
                 continue;
             }
-            unsigned long long lo = ~0ull, hi = 0;
-#pragma unroll
-            for (int k = 0; k < kTsItems; ++k) {
-                const uint32_t e = wb + k * 32 + lane;
-                if (e < cut) {
-                    const uint64_t v = w[k] & kmask;
-                    lo = v < lo ? v : lo;
-                    hi = v > hi ? v : hi;
-                }
-            }
-            lo = warp_min_u64(lo);
-            hi = warp_max_u64(hi);
-            if (lane == 0 && lo != ~0ull) {
-                atomicMin(&s.kmin, lo);
-                atomicMax(&s.kmax, hi);
-            }
-            __syncthreads();
-            const uint64_t wmin = s.kmin;
-            const uint64_t span = s.kmax - wmin;
-            const int npass = span ? (64 - __clzll((long long)span) + kRadixBits - 1) / kRadixBits : 0;
-            // elements past the cut sort after every element of the window
-#pragma unroll
-            for (int k = 0; k < kTsItems; ++k) {
-                const uint32_t e = wb + k * 32 + lane;
-                w[k] = e < cut ? (((w[k] & kmask) - wmin) << kTsIdxBits) | e : ~0ull;
-            }
-            if (npass == 0) {  // one key value: the window is in order
-#pragma unroll
-                for (int k = 0; k < kTsItems; ++k) s.word[wb + k * 32 + lane] = w[k];
-                __syncthreads();
-            }
-            for (int q = 0; q < npass; ++q) {
-                const int sh = kTsIdxBits + q * kRadixBits;
-#pragma unroll
-                for (int i = 0; i < kTsWarps / 2; ++i) s.whist2[i * kTsThreads + tid] = 0;
-                __syncthreads();
-                // rank among the warp's earlier elements with the same digit,
-                // four matches in flight; each leader's add is ordered before
-                // the next item's by the __syncwarp (stability)
-#pragma unroll
-                for (int g = 0; g < kTsItems; g += 4) {
-                    unsigned peers[4], before[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        peers[u] = __match_any_sync(kFull, (unsigned)(w[g + u] >> sh) & (kTsBins - 1));
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const unsigned d = (unsigned)(w[g + u] >> sh) & (kTsBins - 1);
-                        before[u] = 0;
-                        if (lane == __ffs(peers[u]) - 1) {
-                            const unsigned half = 16 * (d & 1);
-                            before[u] = (atomicAdd(&mh2[d >> 1], (unsigned)__popc(peers[u]) << half) >> half) & 0xFFFFu;
-                        }
-                        __syncwarp();
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const unsigned bb = __shfl_sync(kFull, before[u], __ffs(peers[u]) - 1);
-                        s.rank[wb + (g + u) * 32 + lane] = (uint16_t)(bb + __popc(peers[u] & lanemask_lt()));
-                    }
-                }
-                __syncthreads();
-                // digit tid: offsets over the warps (in place of the counts),
-                // then the window's digit start
-                uint32_t run = 0;
-                uint16_t *col = reinterpret_cast<uint16_t *>(s.whist2) + tid;
-#pragma unroll
-                for (int w2 = 0; w2 < kTsWarps; ++w2) {
-                    const uint32_t c = col[w2 * kTsBins];
-                    col[w2 * kTsBins] = (uint16_t)run;
-                    run += c;
-                }
-                s.dstart[tid] = ts_exclusive_scan(run, s.wsum);
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < kTsItems; ++k) {
-                    const unsigned d = (unsigned)(w[k] >> sh) & (kTsBins - 1);
-                    const uint32_t dst = s.dstart[d] + mh16[d] + s.rank[wb + k * 32 + lane];
-                    s.word[dst] = w[k];
-                }
-                __syncthreads();
-                if (q + 1 < npass) {
-#pragma unroll
-                    for (int k = 0; k < kTsItems; ++k) w[k] = s.word[wb + k * 32 + lane];
-                }
-            }
-            // permutation (payload fetched through the place field) and run heads
-            for (uint32_t c = warp; c < kTsWin / 32; c += kTsWarps) {
-                const uint32_t j = c * 32 + lane;
-                const bool v = j < cut;
-                const uint64_t wj = v ? s.word[j] : 0ull;
-                const uint64_t wp = (v && j > 0) ? s.word[j - 1] : 0ull;
-                const bool head = v && (j == 0 || (wj >> kTsIdxBits) != (wp >> kTsIdxBits));
-                const unsigned hb = __ballot_sync(kFull, head);
-                if (lane == 0) s.heads[c] = hb;
-                if (v) perm[pos + j] = (IdxT)a.vals_in[pos + (wj & ((1u << kTsIdxBits) - 1))];
-            }
-            if (a.ties) {
-                __syncthreads();
-                // a run needs the fix-up when it has two or more members and
-                // their key's not-exact bit (bit 0) is set
-                for (uint32_t c = warp; c * 32 < cut; c += kTsWarps) {
-                    const uint32_t j = c * 32 + lane;
-                    if (j < cut && ((s.heads[c] >> lane) & 1u)) {
-                        const uint64_t key = (s.word[j] >> kTsIdxBits) + wmin;
-                        if (key & 1ull) {
-                            uint32_t end = cut;
-                            const uint32_t later = lane == 31 ? 0u : (s.heads[c] & (~0u << (lane + 1)));
-                            if (later) {
-                                end = c * 32 + __ffs(later) - 1;
-                            } else {
-                                for (uint32_t c2 = c + 1; c2 * 32 < cut; ++c2)
-                                    if (s.heads[c2]) {
-                                        end = c2 * 32 + __ffs(s.heads[c2]) - 1;
-                                        break;
-                                    }
-                            }
-                            if (end > cut) end = cut;
-                            if (end - j >= 2) queue_run(a.q, a.flags, pos + j, end - j);
-                        }
-                    }
-                }
-            }
+            sort_window<S, IdxT>(s, w, pos, cut, kmask, a.vals_in, perm, a.ties != 0, a.q, a.flags);
             pos += cut;
-            __syncthreads();
         }
     }
 }
 
+// The buckets the range kernel found longer than its window, one at a time
+// in windows twice as long; longer ones go on to `rest`.
+template <typename IdxT>
+__global__ void __launch_bounds__(TsBig::kThreads, 1) bucket_run_sort_kernel(const RunSortArgs a) {
+    using S = TsBig;
+    extern __shared__ __align__(16) unsigned char ts_raw[];
+    S::Smem &s = *reinterpret_cast<S::Smem *>(ts_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t kmask = (1ull << a.kb) - 1;
+    IdxT *perm = static_cast<IdxT *>(a.perm);
+    const uint32_t wb = (uint32_t)warp * 32 * S::kItems;
+    for (uint64_t r = blockIdx.x; r < a.count; r += gridDim.x) {
+        const uint64_t pos = a.runs[r].start;
+        const uint32_t len = a.runs[r].len;
+        if (len > (uint32_t)S::kWin) {
+            if (tid == 0) queue_bucket(a.rest, &a.flags->qcount[kQOverflow2], a.cap_rest, a.flags, pos, len);
+            continue;
+        }
+        if (tid == 0) {
+            s.kmin = ~0ull;
+            s.kmax = 0;
+        }
+        uint64_t w[S::kItems];
+#pragma unroll
+        for (int k = 0; k < S::kItems; ++k) {
+            const uint32_t e = wb + k * 32 + lane;
+            w[k] = e < len ? a.keys_in[pos + e] : ~0ull;
+        }
+        __syncthreads();
+        sort_window<S, IdxT>(s, w, pos, len, kmask, a.vals_in, perm, a.ties != 0, a.q, a.flags);
+    }
+}
+
 // Runs of equal keys inside the overflow buckets (sorted keys, key bit 0 =
-// not exact): one CTA per bucket walks it in chunks, carrying the head of
-// the run open at each chunk's start.
+// not exact): a bucket whose first and last keys agree is one run; any other
+// is walked by one CTA in chunks, carrying the head of the run open at each
+// chunk's start.
 constexpr int kOtThreads = 512;
 
 __global__ void __launch_bounds__(kOtThreads)
@@ -900,6 +993,12 @@ oversize_ties_kernel(const RunEntry *__restrict__ runs, uint64_t count, const ui
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint64_t r = blockIdx.x; r < count; r += gridDim.x) {
         const uint64_t start = runs[r].start, len = runs[r].len;
+        if (len == 0) continue;
+        const uint64_t k0 = keys[start];
+        if (keys[start + len - 1] == k0) {  // sorted: one key value, one run
+            if (tid == 0 && len >= 2 && (k0 & 1ull)) queue_run(q, flags, start, len);
+            continue;
+        }
         unsigned long long open = start;  // head of the run open at the chunk start
         for (uint64_t c0 = 0; c0 < len; c0 += kOtThreads) {
             const uint64_t j = c0 + tid;
@@ -1164,6 +1263,7 @@ cudaError_t launch_rmi_leaves(const uint64_t *sorted_sample, const uint32_t *Xi,
     rmi_leaf_input_kernel<<<(m + 255) / 256, 256, 0, s>>>(sorted_sample, Xi, m, model, xf);
     rmi_leaf_fit_kernel<<<kRmiLeaves / 8, 256, 0, s>>>(xf, tf, model->leaf_start, m, kRmiLeaves, model->slope,
                                                         model->icept, model->lo, model->hi);
+    rmi_pack_kernel<<<(kAccel + 1 + 255) / 256, 256, 0, s>>>(model);
     return cudaGetLastError();
 }
 
@@ -1276,32 +1376,59 @@ cudaError_t launch_rmi_compose(uint64_t *keys, uint64_t n, const RmiModel *model
     if (bits < 1 || bits > 3 * kRadixBits || kb < 1 || kb + bits > 64) return cudaErrorInvalidValue;
     const uint64_t groups = (n + (uint64_t)kCmpThreads * kCmpItems - 1) / ((uint64_t)kCmpThreads * kCmpItems);
     const unsigned grid = (unsigned)umin64(groups, (uint64_t)num_sms * 4);
-    rmi_compose_kernel<<<grid, kCmpThreads, 0, s>>>(keys, n, model, bits, kb, hist);
+    constexpr size_t smem = kRmiLeaves * 4 + (kAccel + 8) * 2 + 3 * kBins * 4;
+    static_assert(((kAccel + 8) * 2) % 16 == 0, "the histogram stays 4-byte aligned");
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(rmi_compose_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    rmi_compose_kernel<<<grid, kCmpThreads, smem, s>>>(keys, n, model, bits, kb, hist);
     return cudaGetLastError();
 }
 
-size_t tile_sort_smem_bytes() { return sizeof(TsSmem); }
+template <class S, typename K64, typename K32>
+cudaError_t set_smem_once(bool &done, K64 k64, K32 k32) {
+    if (done) return cudaSuccess;
+    const int smem = (int)sizeof(typename S::Smem);
+    cudaError_t e = cudaFuncSetAttribute(k64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
 
 cudaError_t launch_bucket_tile_sort(const TileSortArgs &a, int perm_u64, int num_sms, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.kb < 1 || a.kb > kTsMaxKeyBits) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(TsSmem);
     static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(bucket_tile_sort_kernel<uint64_t>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(bucket_tile_sort_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = set_smem_once<TsMain>(configured, bucket_tile_sort_kernel<uint64_t>,
+                                          bucket_tile_sort_kernel<uint32_t>);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(TsMain::Smem);
     const uint64_t ranges = (a.n + kTsRange - 1) / kTsRange;
     const unsigned grid = (unsigned)umin64(ranges, (uint64_t)num_sms * 2);
     if (perm_u64)
-        bucket_tile_sort_kernel<uint64_t><<<grid, kTsThreads, smem, s>>>(a);
+        bucket_tile_sort_kernel<uint64_t><<<grid, TsMain::kThreads, smem, s>>>(a);
     else
-        bucket_tile_sort_kernel<uint32_t><<<grid, kTsThreads, smem, s>>>(a);
+        bucket_tile_sort_kernel<uint32_t><<<grid, TsMain::kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_run_sort(const RunSortArgs &a, int perm_u64, int num_sms, cudaStream_t s) {
+    if (a.count == 0) return cudaSuccess;
+    if (a.kb < 1 || a.kb > kTsMaxKeyBits) return cudaErrorInvalidValue;
+    static bool configured = false;
+    cudaError_t e = set_smem_once<TsBig>(configured, bucket_run_sort_kernel<uint64_t>,
+                                         bucket_run_sort_kernel<uint32_t>);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(TsBig::Smem);
+    const unsigned grid = (unsigned)umin64(a.count, (uint64_t)num_sms);
+    if (perm_u64)
+        bucket_run_sort_kernel<uint64_t><<<grid, TsBig::kThreads, smem, s>>>(a);
+    else
+        bucket_run_sort_kernel<uint32_t><<<grid, TsBig::kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
