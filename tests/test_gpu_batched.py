@@ -108,6 +108,19 @@ def test_batched_2000_instances(cuda_lib):
     assert oracle.check_sorted_batched(w.bytes, w.offsets, w.seg_offsets, got) == -1
 
 
+@pytest.mark.slow
+def test_batched_20000_instances_literal_size(cuda_lib):
+    """The batched workload at its literal size: 20,000 instances of
+    log-uniform sizes 100..1e6, about 2.17e9 strings in one call (more than
+    2^31 positions; each instance's local indices stay below 2^31), checked
+    instance by instance by the oracle's property check."""
+    hs = cuda_lib
+    w = workloads.standard("batched_20000")
+    assert w.n > 2**31 and len(w.seg_offsets) == 20_001
+    got = _run(hs, w, w.seg_offsets)
+    assert oracle.check_sorted_batched(w.bytes, w.offsets, w.seg_offsets, got) == -1
+
+
 @pytest.mark.parametrize("num_segs", [3, 511, 20_000, 300_000])
 def test_instance_id_packed_into_the_key(cuda_lib, num_segs):
     """Lowercase strings (the byte-range coder's 5 bits, a 41-bit key) with the
