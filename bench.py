@@ -195,11 +195,16 @@ def profile_traffic(key: str):
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             data = json.load(f)
-        digest = sources_digest()
     except OSError:
         return None
     entry = data.get(key)
-    if not entry or entry.get("sources_sha256") != digest:
+    if not entry:
+        return None
+    try:
+        digest = sources_digest(entry.get("sources", TRAFFIC_SOURCES))
+    except OSError:
+        return None
+    if entry.get("sources_sha256") != digest:
         return None
     return entry.get("dram_bytes_per_launch")
 
@@ -408,7 +413,8 @@ def _batched_block(hs, args, device, flush, stream):
                                               "ms_per_step": round(single_ms, 4)},
             "vs_loop": round(loop_ms / ms, 2), "vs_one_plain_sort": round(single_ms / ms, 3),
             "parity": {"instances_checked_against_oracle": checked, "instances_differing": bad},
-            "roofline": _roofline(kstats, args.steps, ms, "batched_20000"),
+            "roofline": _roofline(kstats, args.steps, ms,
+                                  "batched_20000" + (f"@{args.batched_scale:g}" if args.batched_scale != 1.0 else "")),
             "gpu_launches": int(sum(v["launches"] for v in kstats.values()) / args.steps),
             "stages": _stages(kstats, args.steps)}
 

@@ -41,12 +41,14 @@ hs_status fail_cuda(cudaError_t e, const char *where) {
 enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
-    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKCopies, kKNumKinds
+    kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKCopies,
+    kKBucketRun, kKBigBuckets, kKOversizeTies, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
-    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test", "copies_filter"};
+    "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test", "copies_filter",
+    "bucket_run_sort", "big_buckets", "oversize_ties"};
 
 struct StatsTable {
     std::mutex mu;
@@ -1009,7 +1011,7 @@ hs_status sort_oversize(Ctx &c, const Input &in, const RunEntry *q_over, uint64_
     if (big_total > n) return fail(HS_ERR_INTERNAL, "oversize buckets overlap");
     uint32_t *mixed = c.at<uint32_t>(L.big_mixed);
     HS_TRY(cudaMemsetAsync(mixed, 0, big * 4, c.s), "memset mixed");
-    HS_TRY(c.timed(kKBucketSort, 20.0 * big_total, [&] {
+    HS_TRY(c.timed(kKBigBuckets, 20.0 * big_total, [&] {
                return launch_big_buckets(q_over, big, bb, big_total, keys, vals, in.perm, in.perm_u64, mixed,
                                          big_keys_out, kmask, c.s);
            }),
@@ -1108,7 +1110,7 @@ hs_status learned_composite(Ctx &c, const Input &in, SortBufs &b, RmiModel *mode
         if (big > L.cap_over) return fail(HS_ERR_INTERNAL, "overflow queue full");
         const RunSortArgs ra{b.keys[cur], b.vals[cur], in.perm, kb, perfect ? 0 : 1, c.at<RunEntry>(L.q_over), big,
                              q_rest, L.cap_over, rq, c.d_flags};
-        HS_TRY(c.timed(kKBucketSort, 0.0, [&] { return launch_bucket_run_sort(ra, in.perm_u64, c.sms, c.s); }),
+        HS_TRY(c.timed(kKBucketRun, 0.0, [&] { return launch_bucket_run_sort(ra, in.perm_u64, c.sms, c.s); }),
                "bucket run sort");
         HS_TRY(c.read_flags(), "run sort sync");
         st = device_error_status(c.h);
@@ -1122,7 +1124,7 @@ hs_status learned_composite(Ctx &c, const Input &in, SortBufs &b, RmiModel *mode
                                 {b.segs[0], b.segs[1]}});
     if (st != HS_OK) return st;
     if (!perfect && big2 > 0)
-        HS_TRY(c.timed(kKTieDetect, 8.0 * big2, [&] {
+        HS_TRY(c.timed(kKOversizeTies, 0.0, [&] {
                    return launch_oversize_ties(q_rest, big2, b.keys[cur ^ 1], rq, c.d_flags, c.sms, c.s);
                }),
                "oversize ties");
