@@ -283,3 +283,41 @@ def bigint_argsort(data: np.ndarray, offsets: np.ndarray) -> np.ndarray:
 def bigint_bytes(x: int) -> bytes:
     """The minimal two's complement big-endian bytes of x (toByteArray)."""
     return x.to_bytes(((x if x >= 0 else ~x).bit_length() + 8) // 8, "big", signed=True)
+
+
+# ---- BigDecimal -----------------------------------------------------------------
+#
+# The paper benchmarks BigDecimal arrays (Section 6.1, Table 4) without giving
+# a coder.  A value here is its decimal text in the form Java's
+# BigDecimal(String) accepts: an optional sign, digits with at most one
+# decimal point and at least one digit, then optionally an exponent
+# [eE][+-]digits.  The order is compareTo's: numeric value with the scale
+# ignored (1.0 equals 1.00), and the sort is stable, so equal values keep
+# index order.  The oracle is that definition written out: each text's exact
+# rational value (Python's Fraction), then Python's stable sort.
+
+import re as _re
+from fractions import Fraction as _Fraction
+
+_DECIMAL_TEXT = _re.compile(r"[+-]?(?:[0-9]+\.?[0-9]*|\.[0-9]+)(?:[eE][+-]?[0-9]+)?")
+
+
+def bigdecimal_value(text: bytes) -> _Fraction:
+    """The exact value of one decimal text; ValueError outside the grammar."""
+    s = bytes(text).decode("ascii")
+    if not _DECIMAL_TEXT.fullmatch(s):
+        raise ValueError(f"not a decimal: {s!r}")
+    mant, _, exp = s.replace("E", "e").partition("e")
+    sign = -1 if mant.startswith("-") else 1
+    mant = mant.lstrip("+-")
+    whole, _, frac = mant.partition(".")
+    digits = int((whole + frac) or "0")
+    scale = len(frac) - (int(exp) if exp else 0)
+    return sign * _Fraction(digits, 1) / _Fraction(10) ** scale if scale >= 0 else \
+        sign * _Fraction(digits * 10 ** (-scale), 1)
+
+
+def bigdecimal_argsort(data: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """Stable argsort of decimal texts by numeric value."""
+    v = [bigdecimal_value(data[int(offsets[i]):int(offsets[i + 1])].tobytes()) for i in range(offsets.size - 1)]
+    return np.array(sorted(range(len(v)), key=v.__getitem__), dtype=np.int64)
