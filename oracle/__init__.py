@@ -317,7 +317,20 @@ def bigdecimal_value(text: bytes) -> _Fraction:
         sign * _Fraction(digits * 10 ** (-scale), 1)
 
 
+def bigdecimal_key(text: bytes):
+    """A sort key equal to the text's exact value for comparisons: Python's
+    Decimal, which compares finite values exactly and keeps the exponent
+    apart from the digits, so exponents near 10^9 cost nothing (the Fraction
+    of 1E+999999999 would be a billion-digit integer).  ValueError outside
+    the grammar."""
+    import decimal
+    s = bytes(text).decode("ascii")
+    if not _DECIMAL_TEXT.fullmatch(s):
+        raise ValueError(f"not a decimal: {s!r}")
+    return decimal.Decimal(s)
+
+
 def bigdecimal_argsort(data: np.ndarray, offsets: np.ndarray) -> np.ndarray:
     """Stable argsort of decimal texts by numeric value."""
-    v = [bigdecimal_value(data[int(offsets[i]):int(offsets[i + 1])].tobytes()) for i in range(offsets.size - 1)]
+    v = [bigdecimal_key(data[int(offsets[i]):int(offsets[i + 1])].tobytes()) for i in range(offsets.size - 1)]
     return np.array(sorted(range(len(v)), key=v.__getitem__), dtype=np.int64)

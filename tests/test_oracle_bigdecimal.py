@@ -69,8 +69,48 @@ def test_agrees_with_the_decimal_module():
         assert oracle.bigdecimal_value(text) == Fraction(decimal.Decimal(text.decode())), text
 
 
+def test_sort_key_orders_as_the_exact_values():
+    """The sort key (Decimal) orders and equates texts exactly as their
+    Fraction values do, on random texts with moderate exponents."""
+    rng = random.Random(11)
+    texts = []
+    for _ in range(600):
+        whole = "".join(rng.choice("0123456789") for _ in range(rng.randint(0, 6)))
+        frac = "".join(rng.choice("0123456789") for _ in range(rng.randint(0, 6)))
+        mant = (whole or "0") + ("." + frac if frac else "")
+        exp = f"E{rng.randint(-30, 30)}" if rng.random() < 0.5 else ""
+        texts.append((rng.choice(["", "-"]) + mant + exp).encode())
+    for a, b in zip(texts, texts[1:] + texts[:1]):
+        fa, fb = oracle.bigdecimal_value(a), oracle.bigdecimal_value(b)
+        ka, kb = oracle.bigdecimal_key(a), oracle.bigdecimal_key(b)
+        assert (fa < fb) == (ka < kb) and (fa == fb) == (ka == kb), (a, b)
+
+
+def test_extreme_exponents_ordered_by_hand():
+    # ascending; texts on one line are equal values
+    groups = [
+        [b"-1E+999999999", b"-10E+999999998"],
+        [b"-9.99E+999999998"],
+        [b"-1"],
+        [b"-1E-999999999"],
+        [b"0", b"0E+999999999"],
+        [b"1E-999999999", b"0.1E-999999998"],
+        [b"2E-999999999"],
+        [b"1"],
+        [b"9.99E+999999998"],
+        [b"1E+999999999"],
+    ]
+    order = [t for g in groups for t in g]
+    shuffled = order[::-1]
+    data, off = _pack(shuffled)
+    got = [shuffled[i] for i in oracle.bigdecimal_argsort(data, off)]
+    assert got == [t for g in groups for t in sorted(g, key=shuffled.index)]
+
+
 @pytest.mark.parametrize("text", [b"", b"-", b"+", b".", b"1e", b"1E+", b"1.2.3", b"1e5.5", b" 1", b"1 ",
                                   b"1_000", b"abc", b"0x10", b"inf", b"NaN", b"--1", b"1e--2", b"e5"])
 def test_texts_outside_the_grammar(text):
     with pytest.raises(ValueError):
         oracle.bigdecimal_value(text)
+    with pytest.raises(ValueError):
+        oracle.bigdecimal_key(text)
