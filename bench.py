@@ -596,9 +596,59 @@ def run_ours(args, rank, world, local):
 
 # name: (type, n, seed).  f64: normal values over many decades with 1% of
 # +-0, +-infinity, NaN and subnormals; datetime: ns instants over 1900..2100
-# with repeats; i32: full-range integers.
+# with repeats; i32: full-range integers; bigint and bigdecimal: byte strings
+# (see their generators below).
 NUMERIC = {"f64_1e8": ("f64", 100_000_000, 11), "datetime_1e8": ("datetime", 100_000_000, 12),
-           "i32_1e8": ("i32", 100_000_000, 13), "bigint_1e7": ("bigint", 10_000_000, 14)}
+           "i32_1e8": ("i32", 100_000_000, 13), "bigint_1e7": ("bigint", 10_000_000, 14),
+           "bigdecimal_1e7": ("bigdecimal", 10_000_000, 15)}
+BYTES_KINDS = ("bigint", "bigdecimal")  # values given as byte strings in the strings' data model
+
+
+def bigdecimal_workload(n, seed):
+    """n decimal texts (the form Java's BigDecimal(String) accepts): a minus
+    sign on 45%, 1..20 digits, a point inside the digits on 70%, an exponent
+    E[+-]d or E[+-]dd on 30%; 10% repeats of earlier texts."""
+    import workloads
+    rng = np.random.default_rng(seed)
+    width = 1 + 20 + 1 + 4
+    neg = (rng.random(n) < 0.45).astype(np.int64)
+    m = rng.integers(1, 21, size=n)
+    hasdot = (rng.random(n) < 0.7) & (m >= 2)
+    q = np.where(hasdot, rng.integers(1, np.maximum(m, 2)), m)
+    hasexp = rng.random(n) < 0.3
+    ed = rng.integers(1, 3, size=n)
+    chars = np.zeros((n, width), np.uint8)
+    rows = np.arange(n)
+    chars[rows[neg == 1], 0] = ord("-")
+    digits = rng.integers(ord("0"), ord("9") + 1, size=(n, 20), dtype=np.uint8)
+    for k in range(20):
+        ok = k < m
+        col = neg + k + (hasdot & (k >= q))
+        chars[rows[ok], col[ok]] = digits[ok, k]
+    chars[rows[hasdot], (neg + q)[hasdot]] = ord(".")
+    e0 = neg + m + hasdot
+    chars[rows[hasexp], e0[hasexp]] = ord("E")
+    chars[rows[hasexp], (e0 + 1)[hasexp]] = np.where(rng.random(int(hasexp.sum())) < 0.5, ord("+"), ord("-"))
+    for k in range(2):
+        ok = hasexp & (k < ed)
+        chars[rows[ok], (e0 + 2 + k)[ok]] = rng.integers(ord("0"), ord("9") + 1, size=int(ok.sum()))
+    rep = rng.random(n) < 0.1
+    src = rng.integers(0, n, size=n)
+    rep &= ~rep[src]
+    chars[rep] = chars[src[rep]]
+    keep = chars != 0
+    lens = keep.sum(axis=1).astype(np.uint64)
+    off = np.zeros(n + 1, np.uint64)
+    np.cumsum(lens, out=off[1:])
+    return workloads.Workload(chars[keep], off)
+
+
+def bytes_workload(kind, n, seed):
+    return bigint_workload(n, seed) if kind == "bigint" else bigdecimal_workload(n, seed)
+
+
+def bytes_argsort(hs, kind):
+    return hs.argsort_bigint if kind == "bigint" else hs.argsort_bigdecimal
 
 
 def bigint_workload(n, seed):
@@ -660,8 +710,8 @@ def run_numeric(args, rank, world, local):
         hs.autotune(0)
     kind = NUMERIC[args.workload][0]
     index_u64 = args.index == "u64"
-    if kind == "bigint":
-        bw = bigint_workload(max(2, int(NUMERIC[args.workload][1] * args.scale)), NUMERIC[args.workload][2])
+    if kind in BYTES_KINDS:
+        bw = bytes_workload(kind, max(2, int(NUMERIC[args.workload][1] * args.scale)), NUMERIC[args.workload][2])
         n = bw.offsets.size - 1
         v = None
         xb = torch.from_numpy(bw.bytes).to(device)
@@ -674,8 +724,8 @@ def run_numeric(args, rank, world, local):
     stream = torch.cuda.current_stream(device)
 
     def step():
-        if kind == "bigint":
-            return hs.argsort_bigint(xb, xo, index_u64=index_u64)
+        if kind in BYTES_KINDS:
+            return bytes_argsort(hs, kind)(xb, xo, index_u64=index_u64)
         return hs.argsort_numeric(x, type=t, index_u64=index_u64)
 
     for _ in range(args.warmup):
@@ -719,14 +769,14 @@ def run_numeric(args, rank, world, local):
 
     # end to end through the public call: pinned host values in, host permutation out
     h_perm = torch.empty(n, dtype=torch.int64 if index_u64 else torch.int32).pin_memory()
-    if kind == "bigint":
+    if kind in BYTES_KINDS:
         hb = torch.from_numpy(bw.bytes).pin_memory()
         ho = torch.from_numpy(bw.offsets.view(np.int64)).pin_memory()
         h2d = int(bw.bytes.nbytes + bw.offsets.nbytes)
 
         def host_call():
-            return hs.argsort_bigint(hb.to(device, non_blocking=True), ho.to(device, non_blocking=True),
-                                     index_u64=index_u64)
+            return bytes_argsort(hs, kind)(hb.to(device, non_blocking=True), ho.to(device, non_blocking=True),
+                                           index_u64=index_u64)
     else:
         h_vals = torch.from_numpy(v).pin_memory()
         h2d = int(v.nbytes)
@@ -765,12 +815,12 @@ def run_numeric(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        if kind == "bigint":
-            m = min(n, 1_000_000)
+        if kind in BYTES_KINDS:
+            m = min(n, 1_000_000 if kind == "bigint" else 300_000)
             t0 = time.perf_counter()
-            oracle.bigint_argsort(bw.bytes, bw.offsets[: m + 1])
+            (oracle.bigint_argsort if kind == "bigint" else oracle.bigdecimal_argsort)(bw.bytes, bw.offsets[: m + 1])
             dt = time.perf_counter() - t0
-            how = "Python int sort (one thread)"
+            how = "Python int sort (one thread)" if kind == "bigint" else "Python Decimal sort (one thread)"
         else:
             m = min(n, CPU_SAMPLE_MAX)
             t0 = time.perf_counter()
@@ -804,10 +854,12 @@ def run_reference(args, rank, world, local):
     import workloads
     threads = os.cpu_count() or 1
     if args.workload in NUMERIC:
-        if NUMERIC[args.workload][0] == "bigint":
-            bw = bigint_workload(max(2, int(NUMERIC[args.workload][1] * args.scale)), NUMERIC[args.workload][2])
-            m = min(bw.offsets.size - 1, 1_000_000)
-            sort = lambda: oracle.bigint_argsort(bw.bytes, bw.offsets[: m + 1])
+        kind = NUMERIC[args.workload][0]
+        if kind in BYTES_KINDS:
+            bw = bytes_workload(kind, max(2, int(NUMERIC[args.workload][1] * args.scale)), NUMERIC[args.workload][2])
+            m = min(bw.offsets.size - 1, 1_000_000 if kind == "bigint" else 300_000)
+            fn = oracle.bigint_argsort if kind == "bigint" else oracle.bigdecimal_argsort
+            sort = lambda: fn(bw.bytes, bw.offsets[: m + 1])
             v = np.zeros(bw.offsets.size - 1)
         else:
             v, t = numeric_values(args.workload, args.scale)

@@ -350,6 +350,30 @@ HS_API hs_status hs_argsort_bigint(const uint8_t *d_bytes,
                                    void *d_perm, void *d_ws, size_t ws_bytes,
                                    void *stream);
 
+/* BigDecimal coder.  Section 6.1 and Table 4 sort BigDecimal arrays; the
+ * paper gives no coder.  Value i is its decimal text at
+ * d_bytes[d_offsets[i] .. d_offsets[i+1]), in the form Java's
+ * BigDecimal(String) accepts: an optional '+' or '-', digits with at most
+ * one '.' and at least one digit, then optionally 'e' or 'E', an optional
+ * sign and the exponent's digits (its value below 10^9); at most 32767 bytes.
+ * With the value written as 0.d1 d2 .. dk x 10^X (d1 and dk nonzero) each
+ * text becomes the byte string 0x02 (zero); 0x03, X + 2^39 in 5 big-endian
+ * bytes, then the digits (positive); or 0x01, the complement of X + 2^39,
+ * each digit d as '9' - d, then 0xFF (negative).  Unsigned-byte order of
+ * these strings is numeric order, and values equal under compareTo (1.0 and
+ * 1.00) give equal strings; hs_argsort's path sorts them with the byte
+ * coder.  d_perm (device, uint32 or uint64 by out_t) receives the stable
+ * argsort by value.  total_bytes: the size of the byte buffer.  Returns
+ * HS_ERR_INVALID_ARG if a text is outside that form or too long, or its
+ * offsets decrease or pass total_bytes. */
+HS_API hs_status hs_bigdecimal_workspace_size(uint64_t n, uint64_t total_bytes,
+                                              int out_t, size_t *out);
+HS_API hs_status hs_argsort_bigdecimal(const uint8_t *d_bytes,
+                                       const uint64_t *d_offsets, uint64_t n,
+                                       uint64_t total_bytes, int out_t,
+                                       void *d_perm, void *d_ws,
+                                       size_t ws_bytes, void *stream);
+
 /* Test support for the bounded device-side waits.  A radix pass's tiles wait
  * on the counts that earlier tiles publish (decoupled look-back); each wait
  * gives up after a poll budget, records HS_ERR_TIMEOUT and lets its kernel

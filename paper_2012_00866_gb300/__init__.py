@@ -47,6 +47,7 @@ EXPORTS = ("hs_encode", "hs_argsort", "hs_argsort_batched", "hs_workspace_size",
            "hs_argsort_noalloc", "hs_argsort_host", "hs_host_workspace_size", "hs_shutdown",
            "hs_last_error", "hs_version", "hs_encode_numeric", "hs_numeric_workspace_size", "hs_argsort_numeric",
            "hs_autotune", "hs_autotune_choice", "hs_bigint_workspace_size", "hs_argsort_bigint",
+           "hs_bigdecimal_workspace_size", "hs_argsort_bigdecimal",
            "hs_rmi_grad", "hs_rmi_leaf_fit", "hs_rmi_sample_indices", "hs_learned_profile",
            "hs_learned_force_bucket_bits", "hs_test_bounded_waits")
 
@@ -111,6 +112,10 @@ def load(path: str | None = None):
     lib.hs_bigint_workspace_size.argtypes = [u64, u64, ci, ctypes.POINTER(ctypes.c_size_t)]
     lib.hs_argsort_bigint.restype = ci
     lib.hs_argsort_bigint.argtypes = [vp, vp, u64, u64, ci, vp, vp, ctypes.c_size_t, vp]
+    lib.hs_bigdecimal_workspace_size.restype = ci
+    lib.hs_bigdecimal_workspace_size.argtypes = [u64, u64, ci, ctypes.POINTER(ctypes.c_size_t)]
+    lib.hs_argsort_bigdecimal.restype = ci
+    lib.hs_argsort_bigdecimal.argtypes = [vp, vp, u64, u64, ci, vp, vp, ctypes.c_size_t, vp]
     lib.hs_autotune.restype = ci
     lib.hs_autotune.argtypes = [ci]
     lib.hs_autotune_choice.restype = ci
@@ -243,6 +248,21 @@ def _numeric_input(values: torch.Tensor, type):
     if values.element_size() != width:
         raise ValueError(f"numeric type {type} needs {width}-byte elements")
     return values, type
+
+
+def argsort_bigdecimal(data: torch.Tensor, offsets: torch.Tensor, index_u64: bool = False,
+                       stream=None) -> torch.Tensor:
+    """Stable argsort of decimal texts (the form Java's BigDecimal(String)
+    accepts) by numeric value, in the strings' data model."""
+    data, offsets = _as_device_inputs(data, offsets)
+    n = offsets.numel() - 1
+    out = torch.empty(max(n, 0), dtype=torch.int64 if index_u64 else torch.int32, device=offsets.device)
+    need = ctypes.c_size_t(0)
+    _check(load().hs_bigdecimal_workspace_size(n, data.numel(), U64 if index_u64 else U32, ctypes.byref(need)))
+    ws = workspace(need.value, offsets.device)
+    _check(load().hs_argsort_bigdecimal(_ptr(data), _ptr(offsets), n, data.numel(), U64 if index_u64 else U32,
+                                        _ptr(out), _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return out
 
 
 def argsort_bigint(data: torch.Tensor, offsets: torch.Tensor, index_u64: bool = False,

@@ -42,13 +42,13 @@ enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
     kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKCopies,
-    kKBucketRun, kKBigBuckets, kKOversizeTies, kKNumKinds
+    kKBucketRun, kKBigBuckets, kKOversizeTies, kKDecimal, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
     "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test", "copies_filter",
-    "bucket_run_sort", "big_buckets", "oversize_ties"};
+    "bucket_run_sort", "big_buckets", "oversize_ties", "decimal_encode"};
 
 struct StatsTable {
     std::mutex mu;
@@ -1446,6 +1446,73 @@ BigLayout bigint_layout(uint64_t n, uint64_t total_bytes) {
     b.enc_offsets = b.enc_bytes + up(b.enc_cap + 16);
     b.total = b.enc_offsets + up(8 * (n + 1));
     return b;
+}
+
+// BigDecimal: the sort workspace, then the encoded strings (at most 7 bytes
+// longer than the text: class byte, 5 exponent bytes, terminator; the sign,
+// point and exponent characters are not copied), their offsets and the tile
+// totals of the length pass.
+struct DecLayout {
+    size_t sort_bytes, enc_bytes, enc_offsets, tile_sum, total;
+    uint64_t enc_cap;
+};
+DecLayout bigdecimal_layout(uint64_t n, uint64_t total_bytes) {
+    auto up = [](size_t x) { return (x + kAlign - 1) / kAlign * kAlign; };
+    DecLayout d{};
+    d.sort_bytes = up(make_layout(n).total);
+    d.enc_cap = total_bytes + 7 * n;
+    d.enc_bytes = d.sort_bytes;
+    d.enc_offsets = d.enc_bytes + up(d.enc_cap + 16);
+    d.tile_sum = d.enc_offsets + up(8 * (n + 1));
+    d.total = d.tile_sum + up(8 * (bigdecimal_tiles(n) + 1));
+    return d;
+}
+
+hs_status hs_bigdecimal_workspace_size(uint64_t n, uint64_t total_bytes, int out_t, size_t *out) {
+    g_last_error.clear();
+    if (!out) return fail(HS_ERR_INVALID_ARG, "out is NULL");
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    *out = bigdecimal_layout(n, total_bytes).total;
+    return HS_OK;
+}
+
+hs_status hs_argsort_bigdecimal(const uint8_t *d_bytes, const uint64_t *d_offsets, uint64_t n, uint64_t total_bytes,
+                                int out_t, void *d_perm, void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (out_t != HS_U32 && out_t != HS_U64) return fail(HS_ERR_INVALID_ARG, "bad index type");
+    if (n > HS_MAX_N) return fail(HS_ERR_INVALID_ARG, "n exceeds HS_MAX_N");
+    if (n == 0) return HS_OK;
+    if (!d_bytes || !d_offsets || !d_perm) return fail(HS_ERR_INVALID_ARG, "null pointer");
+    const DecLayout dl = bigdecimal_layout(n, total_bytes);
+    if (d_ws == nullptr || ws_bytes < dl.total)
+        return fail(HS_ERR_WORKSPACE, "workspace smaller than hs_bigdecimal_workspace_size()");
+    Ctx c;
+    hs_status st;
+    if (!make_ctx(c, d_ws, dl.sort_bytes, n, stream, &st)) return st;
+    uint8_t *eb = c.at<uint8_t>(dl.enc_bytes);
+    uint64_t *eo = c.at<uint64_t>(dl.enc_offsets);
+    unsigned long long *ts = c.at<unsigned long long>(dl.tile_sum);
+    HS_TRY(cudaMemsetAsync(c.ws, 0, c.L.control_end, c.s), "memset control");
+    // algorithmic bytes: each pass reads the offsets and the text; the second
+    // also writes the encoded strings (at most 7 bytes longer) and offsets
+    HS_TRY(c.timed(kKDecimal, 8.0 * (n + 1) + (double)total_bytes, [&] {
+               return launch_bigdecimal_lengths(d_bytes, d_offsets, n, total_bytes, ts, c.d_flags, c.s);
+           }, 2),
+           "bigdecimal lengths");
+    HS_TRY(c.read_flags(), "bigdecimal sync");
+    if (c.h.error & kErrOffsets)
+        return fail(HS_ERR_INVALID_ARG,
+                    "a value is not a decimal text, is longer than 32767 bytes, or its offsets decrease or pass "
+                    "total_bytes");
+    st = device_error_status(c.h);
+    if (st != HS_OK) return st;
+    HS_TRY(c.timed(kKDecimal, 16.0 * (n + 1) + 2.0 * (double)total_bytes, [&] {
+               return launch_bigdecimal_write(d_bytes, d_offsets, n, total_bytes, ts, eb, dl.enc_cap, eo, c.d_flags,
+                                              c.s);
+           }),
+           "bigdecimal write");
+    Input in{eb, eo, n, 9, d_perm, out_t == HS_U64 ? 1 : 0};
+    return argsort_plain(c, in, HS_CODER_BYTE8);
 }
 
 hs_status hs_bigint_workspace_size(uint64_t n, uint64_t total_bytes, int out_t, size_t *out) {

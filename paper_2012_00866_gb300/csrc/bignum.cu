@@ -45,7 +45,291 @@ bigint_encode_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restri
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags->error, kErrOffsets);
 }
 
+// ---- BigDecimal coder ----------------------------------------------------------
+//
+// Section 6.1 and Table 4 sort BigDecimal arrays with Huskysort; the paper
+// gives no coder.  A value here is its decimal text (an optional sign, digits
+// with at most one decimal point, an optional exponent [eE][+-]digits: the
+// form Java's BigDecimal(String) accepts).  With the value written as
+// 0.d1 d2 ... dk x 10^X (d1 != 0, no trailing zero digit) the byte string
+//   zero      0x02
+//   positive  0x03, X + 2^39 (5 bytes, big-endian), the digits '0'..'9'
+//   negative  0x01, ~(X + 2^39) (5 bytes), each digit as '9' - d, then 0xFF
+// has unsigned-byte order equal to numeric order, and equal values (1.0 and
+// 1.00) give equal strings, as compareTo wants.  Among positives a larger X
+// is larger, and at equal X the digits compare as decimal fractions (a
+// shorter one that is a prefix is smaller); negatives reverse both, the 0xFF
+// terminator putting a prefix (a smaller magnitude) after its extensions.
+// Three kernels: each value's encoded length and a tile total; an exclusive
+// scan of the tile totals; each tile's offsets and bytes.
+
+constexpr int kDecThreads = 256;
+constexpr int kDecPer = 4;                       // values a thread, consecutive
+constexpr int kDecTile = kDecThreads * kDecPer;  // values a tile
+constexpr int64_t kDecMaxExp = 999999999;        // |exponent| below 10^9
+constexpr int64_t kDecBias = 1ll << 39;
+constexpr uint32_t kDecStage = 24576;            // a tile's text bytes staged in shared memory
+
+struct DecForm {
+    bool ok;
+    int cls;                 // 0 negative, 1 zero, 2 positive
+    int64_t X;               // the value is 0.d1 d2 ... dk x 10^X
+    uint32_t mstart, mend;   // the mantissa's characters (digits and at most one '.')
+    uint32_t z, k;           // leading zero digits, then the k digits kept
+};
+
+__device__ DecForm dec_parse(const uint8_t *__restrict__ s, uint32_t len) {
+    DecForm f{};
+    uint32_t i = 0;
+    bool neg = false;
+    if (i < len && (s[i] == '+' || s[i] == '-')) {
+        neg = s[i] == '-';
+        ++i;
+    }
+    f.mstart = i;
+    // one pass over the mantissa: digits t (p before the point), the number
+    // of leading zero digits z and the position of the last nonzero one
+    uint32_t t = 0, p = 0, z = 0, last = 0;
+    bool dot = false, seen = false;
+    for (; i < len; ++i) {
+        const uint8_t c = s[i];
+        const bool digit = (unsigned)(c - '0') < 10u;
+        const bool point = c == '.' && !dot;
+        if (!digit && !point) break;
+        dot |= point;
+        const bool nz = digit && c != '0';
+        t += digit;
+        p += digit && !dot;
+        z = (nz && !seen) ? t - 1 : z;
+        seen |= nz;
+        last = nz ? t : last;
+    }
+    f.mend = i;
+    if (t == 0) return f;
+    int64_t ex = 0;
+    if (i < len && (s[i] == 'e' || s[i] == 'E')) {
+        ++i;
+        bool eneg = false;
+        if (i < len && (s[i] == '+' || s[i] == '-')) {
+            eneg = s[i] == '-';
+            ++i;
+        }
+        uint32_t nd = 0;
+        for (; i < len && s[i] >= '0' && s[i] <= '9'; ++i, ++nd) {
+            ex = ex * 10 + (s[i] - '0');
+            if (ex > kDecMaxExp) return f;
+        }
+        if (nd == 0) return f;
+        if (eneg) ex = -ex;
+    }
+    if (i != len) return f;
+    f.ok = true;
+    if (!seen) {
+        f.cls = 1;
+        return f;
+    }
+    f.cls = neg ? 0 : 2;
+    f.z = z;
+    f.k = last - z;
+    f.X = (int64_t)p - (int64_t)z + ex;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t dec_len(const DecForm &f) {
+    return f.cls == 1 ? 1u : (f.cls == 2 ? 6u + f.k : 7u + f.k);
+}
+
+__device__ void dec_write(const uint8_t *__restrict__ s, const DecForm &f, uint8_t *__restrict__ out) {
+    if (f.cls == 1) {
+        out[0] = 0x02;
+        return;
+    }
+    const bool neg = f.cls == 0;
+    out[0] = neg ? 0x01 : 0x03;
+    uint64_t e = (uint64_t)(f.X + kDecBias);
+    if (neg) e = ~e & ((1ull << 40) - 1);
+    for (int b = 0; b < 5; ++b) out[1 + b] = (uint8_t)(e >> (8 * (4 - b)));
+    uint32_t idx = 0, w = 6;
+    for (uint32_t j = f.mstart; j < f.mend && idx < f.z + f.k; ++j) {
+        const uint8_t c = s[j];
+        if (c == '.') continue;
+        if (idx >= f.z) out[w++] = neg ? (uint8_t)('9' - c + '0') : c;
+        ++idx;
+    }
+    if (neg) out[w] = 0xFFu;
+}
+
+// Value i's text, or false when its offsets decrease, pass the buffer, or
+// the text is longer than kDecMaxLen.
+__device__ __forceinline__ bool dec_text(const uint64_t *__restrict__ offsets, uint64_t i, uint64_t total,
+                                         uint64_t *o, uint32_t *len) {
+    const uint64_t a = offsets[i], b = offsets[i + 1];
+    if (b < a || b > total || b - a > kDecMaxLen) return false;
+    *o = a;
+    *len = (uint32_t)(b - a);
+    return true;
+}
+
+// Copies the tile's text bytes (strings t0 .. t0 + cnt - 1, contiguous when
+// their offsets are in order) into s_text with coalesced loads; returns the
+// first byte's offset, or ~0 when they do not fit (or the offsets are out of
+// order), in which case every string is read from global memory.  Ends with a
+// barrier.
+__device__ uint64_t dec_stage(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                              uint64_t t0, uint64_t cnt, uint64_t total, uint8_t *s_text, uint32_t *span) {
+    const uint64_t lo = offsets[t0], hi = offsets[t0 + cnt];
+    const bool fits = lo <= hi && hi <= total && hi - lo <= kDecStage;
+    if (fits)
+        for (uint64_t k = threadIdx.x; k < hi - lo; k += kDecThreads) s_text[k] = bytes[lo + k];
+    __syncthreads();
+    *span = fits ? (uint32_t)(hi - lo) : 0u;
+    return fits ? lo : ~0ull;
+}
+
+// Where value i's text is read from: the stage when it lies inside the
+// staged bytes [lo, lo + span).
+__device__ __forceinline__ const uint8_t *dec_src(const uint8_t *__restrict__ bytes, const uint8_t *s_text,
+                                                  uint64_t lo, uint32_t span, uint64_t o, uint32_t len) {
+    return (lo != ~0ull && o >= lo && o - lo + len <= span) ? s_text + (o - lo) : bytes + o;
+}
+
+// Exclusive scan over the block of one u64 per thread; *block_total: the sum.
+__device__ uint64_t dec_block_scan(uint64_t v, uint64_t *block_total) {
+    __shared__ unsigned long long s_w[kDecThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    unsigned long long pre = 0, all = 0;
+    for (int w = 0; w < kDecThreads / 32; ++w) {
+        pre += w < warp ? s_w[w] : 0ull;
+        all += s_w[w];
+    }
+    __syncthreads();
+    *block_total = all;
+    return pre + x - v;
+}
+
+__global__ void __launch_bounds__(kDecThreads)
+dec_len_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets, uint64_t n, uint64_t total,
+               unsigned long long *__restrict__ tile_sum, DevFlags *flags) {
+    __shared__ uint8_t s_text[kDecStage];
+    const uint64_t t0 = (uint64_t)blockIdx.x * kDecTile;
+    uint32_t span;
+    const uint64_t lo = dec_stage(bytes, offsets, t0, umin64(kDecTile, n - t0), total, s_text, &span);
+    const uint64_t i0 = t0 + (uint64_t)threadIdx.x * kDecPer;
+    uint64_t sum = 0;
+    bool bad = false;
+    for (int q = 0; q < kDecPer; ++q) {
+        const uint64_t i = i0 + q;
+        if (i >= n) break;
+        uint64_t o;
+        uint32_t len;
+        if (!dec_text(offsets, i, total, &o, &len)) {
+            bad = true;
+            continue;
+        }
+        const DecForm f = dec_parse(dec_src(bytes, s_text, lo, span, o, len), len);
+        bad |= !f.ok;
+        sum += f.ok ? dec_len(f) : 0u;
+    }
+    uint64_t all;
+    dec_block_scan(sum, &all);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = all;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags->error, kErrOffsets);
+}
+
+// Exclusive scan of the tile totals in place (one CTA, chunks of its size);
+// the grand total goes to tile_sum[tiles].
+__global__ void __launch_bounds__(kDecThreads) dec_scan_kernel(unsigned long long *__restrict__ tile_sum,
+                                                               uint64_t tiles) {
+    uint64_t carry = 0;
+    for (uint64_t c0 = 0; c0 < tiles; c0 += kDecThreads) {
+        const uint64_t t = c0 + threadIdx.x;
+        const uint64_t v = t < tiles ? tile_sum[t] : 0ull;
+        uint64_t all;
+        const uint64_t ex = dec_block_scan(v, &all);
+        if (t < tiles) tile_sum[t] = carry + ex;
+        carry += all;
+    }
+    if (threadIdx.x == 0) tile_sum[tiles] = carry;
+}
+
+__global__ void __launch_bounds__(kDecThreads)
+dec_write_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets, uint64_t n, uint64_t total,
+                 const unsigned long long *__restrict__ tile_base, uint8_t *__restrict__ out_bytes, uint64_t out_cap,
+                 uint64_t *__restrict__ out_offsets, DevFlags *flags) {
+    __shared__ uint8_t s_text[kDecStage];
+    const uint64_t t0 = (uint64_t)blockIdx.x * kDecTile;
+    uint32_t span;
+    const uint64_t lo = dec_stage(bytes, offsets, t0, umin64(kDecTile, n - t0), total, s_text, &span);
+    const uint64_t i0 = t0 + (uint64_t)threadIdx.x * kDecPer;
+    uint32_t lens[kDecPer];
+    uint64_t sum = 0;
+    for (int q = 0; q < kDecPer; ++q) {
+        const uint64_t i = i0 + q;
+        lens[q] = 0;
+        uint64_t o;
+        uint32_t len;
+        if (i < n && dec_text(offsets, i, total, &o, &len)) {
+            const DecForm f = dec_parse(dec_src(bytes, s_text, lo, span, o, len), len);
+            lens[q] = f.ok ? dec_len(f) : 0u;
+        }
+        sum += lens[q];
+    }
+    uint64_t all;
+    uint64_t dst = tile_base[blockIdx.x] + dec_block_scan(sum, &all);
+    bool bad = false;
+    for (int q = 0; q < kDecPer; ++q) {
+        const uint64_t i = i0 + q;
+        if (i >= n) break;
+        out_offsets[i] = dst;
+        if (lens[q]) {
+            if (dst + lens[q] > out_cap) {
+                bad = true;
+            } else {
+                uint64_t o;
+                uint32_t len;
+                dec_text(offsets, i, total, &o, &len);
+                const uint8_t *src = dec_src(bytes, s_text, lo, span, o, len);
+                dec_write(src, dec_parse(src, len), out_bytes + dst);
+            }
+        }
+        dst += lens[q];
+        if (i + 1 == n) out_offsets[n] = dst;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags->error, kErrInternal);
+}
+
 }  // namespace
+
+cudaError_t launch_bigdecimal_lengths(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t total,
+                                      unsigned long long *tile_sum, DevFlags *flags, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t tiles = (n + kDecTile - 1) / kDecTile;
+    dec_len_kernel<<<(unsigned)tiles, kDecThreads, 0, s>>>(bytes, offsets, n, total, tile_sum, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dec_scan_kernel<<<1, kDecThreads, 0, s>>>(tile_sum, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bigdecimal_write(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t total,
+                                    const unsigned long long *tile_base, uint8_t *out_bytes, uint64_t out_cap,
+                                    uint64_t *out_offsets, DevFlags *flags, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t tiles = (n + kDecTile - 1) / kDecTile;
+    dec_write_kernel<<<(unsigned)tiles, kDecThreads, 0, s>>>(bytes, offsets, n, total, tile_base, out_bytes, out_cap,
+                                                             out_offsets, flags);
+    return cudaGetLastError();
+}
+
+uint64_t bigdecimal_tiles(uint64_t n) { return (n + kDecTile - 1) / kDecTile; }
 
 cudaError_t launch_bigint_encode(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint8_t *out_bytes,
                                  uint64_t out_cap, uint64_t *out_offsets, DevFlags *flags, int num_sms,

@@ -24,4 +24,27 @@ cudaError_t launch_bigint_encode(const uint8_t *bytes, const uint64_t *offsets, 
                                  uint64_t out_cap, uint64_t *out_offsets, DevFlags *flags, int num_sms,
                                  cudaStream_t s);
 
+// BigDecimal texts longer than this many bytes are rejected.
+constexpr uint64_t kDecMaxLen = 32767;
+
+// BigDecimal coder, step 1: checks each of n decimal texts (bytes
+// offsets[i] .. offsets[i+1] of a buffer of `total` bytes) and computes the
+// length of its order-preserving byte string; tile_sum (bigdecimal_tiles(n)
+// + 1 entries) receives the exclusive scan of the per-tile totals, the grand
+// total last.  A text outside the grammar, offsets that decrease or pass the
+// buffer, or a text longer than kDecMaxLen set flags->error |= kErrOffsets.
+cudaError_t launch_bigdecimal_lengths(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t total,
+                                      unsigned long long *tile_sum, DevFlags *flags, cudaStream_t s);
+// Step 2 (once step 1 reported no error): writes each value's byte string to
+// out_bytes at out_offsets[i] (out_offsets[n] closes the last), placed by the
+// scanned tile totals.  For the value 0.d1 .. dk x 10^X (d1, dk nonzero) the
+// string is 0x02 for zero; 0x03, X + 2^39 in 5 big-endian bytes and the
+// digits '0'..'9' for a positive value; 0x01, the complement of X + 2^39 in
+// 5 bytes, each digit as '9' - d, then 0xFF for a negative value.  Their
+// unsigned-byte order is numeric order, and equal values give equal strings.
+cudaError_t launch_bigdecimal_write(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t total,
+                                    const unsigned long long *tile_base, uint8_t *out_bytes, uint64_t out_cap,
+                                    uint64_t *out_offsets, DevFlags *flags, cudaStream_t s);
+uint64_t bigdecimal_tiles(uint64_t n);
+
 }  // namespace hs
