@@ -761,7 +761,7 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
                        return launch_small_runs(in.bytes, in.offsets, in.perm, in.perm_u64, q_small,
                                                 &c.d_flags->qcount[kQSmall], small0, c.L.cap_small, n, inst,
                                                 in.prefix_len, c.sms, c.s, early ? c.d_flags : nullptr);
-                   }),
+                   }, 2),
                    "small runs");
         return HS_OK;
     };

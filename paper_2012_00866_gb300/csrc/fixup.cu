@@ -304,7 +304,40 @@ tie_detect_kernel(const TieArgs a) {
     }
 }
 
-// ---- 2..32: warp per run ---------------------------------------------------
+// ---- 2: thread per run ------------------------------------------------------
+// Pairs are most of the small runs on long text (two strings that share the
+// coded prefix), and each is a chain of dependent loads (the entry, the two
+// indices, their offsets, the bytes), so a thread per pair keeps 32 times as
+// many of them in flight as a warp per run.  The order is the warp kernel's:
+// by the strings from the window offset on, then by index.
+
+template <typename IdxT>
+__global__ void __launch_bounds__(256)
+pair_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                 IdxT *__restrict__ perm, const RunEntry *__restrict__ q,
+                 const unsigned long long *__restrict__ qcount, uint64_t first, uint64_t cap, uint64_t perm_n,
+                 Instances inst, int prefix_len, DevFlags *dirty) {
+    if (stopped(inst)) return;
+    const uint64_t count = umin64(*qcount, cap);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = first + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < count; r += stride) {
+        const RunEntry e = q[r];
+        if (e.len != 2 || e.start >= perm_n || perm_n - e.start < 2) continue;
+        const uint64_t base = instance_base(inst, e.start);
+        const IdxT i0 = perm[e.start], i1 = perm[e.start + 1];
+        const uint64_t o0 = offsets[base + i0], l0 = offsets[base + i0 + 1] - o0;
+        const uint64_t o1 = offsets[base + i1], l1 = offsets[base + i1 + 1] - o1;
+        const uint64_t from = min(window_offset(prefix_len, e.depth), min(l0, l1));
+        const int c = compare_from(bytes + o0, l0, bytes + o1, l1, from);
+        if (c > 0 || (c == 0 && i1 < i0)) {
+            perm[e.start] = i1;
+            perm[e.start + 1] = i0;
+            mark_dirty(dirty, e.start, 2);
+        }
+    }
+}
+
+// ---- 3..32: warp per run ----------------------------------------------------
 
 template <typename IdxT>
 __global__ void __launch_bounds__(256)
@@ -320,6 +353,7 @@ small_runs_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict_
     for (uint64_t r = first + warp_id; r < count; r += nwarps) {
         const RunEntry e = q[r];
         if (e.len > kSmallMax || e.start >= perm_n || e.len > perm_n - e.start) continue;  // never queued
+        if (e.len == 2) continue;  // pair_runs_kernel's
         const bool mine = (uint32_t)lane < e.len;
         const uint64_t base = instance_base(inst, e.start);  // string index of local index 0
         IdxT idx = 0;
@@ -824,12 +858,17 @@ cudaError_t launch_small_runs(const uint8_t *bytes, const uint64_t *offsets, voi
                               uint64_t perm_n, Instances inst, int prefix_len, int num_sms, cudaStream_t s,
                               DevFlags *dirty) {
     const unsigned grid = (unsigned)num_sms * 8;
-    if (perm_u64)
+    if (perm_u64) {
+        pair_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q, qcount,
+                                                        first, cap, perm_n, inst, prefix_len, dirty);
         small_runs_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint64_t *>(perm), q,
                                                          qcount, first, cap, perm_n, inst, prefix_len, dirty);
-    else
+    } else {
+        pair_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q, qcount,
+                                                        first, cap, perm_n, inst, prefix_len, dirty);
         small_runs_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<uint32_t *>(perm), q,
                                                          qcount, first, cap, perm_n, inst, prefix_len, dirty);
+    }
     return cudaGetLastError();
 }
 
