@@ -304,6 +304,109 @@ tie_detect_kernel(const TieArgs a) {
     }
 }
 
+// ---- tie detection without a scan (unsegmented keys, flag in bit 0) ------------
+// A run needing work is a run of two or more equal keys with bit 0 (not
+// exact) set; all its members share bit 0.  Its head is the position whose
+// key differs from the predecessor's and equals the successor's.  Each head's
+// thread finds the run's end by a galloping search over the sorted keys (the
+// first larger key) and queues the run; every other position costs one
+// comparison with a neighbour, so the pass is one streaming read of the keys
+// with no look-back.  Used when the permutation is already written and no
+// segment ids break runs (instance ids, when there are any, are in the key).
+
+constexpr int kHeadThreads = 256;
+constexpr int kHeadItems = 8;  // keys a thread; a warp takes 256 consecutive keys, all loads in flight together
+
+// The end of the run of key k that starts at j (keys[j + 1] == k): the first
+// position after it, by a galloping search and a bisection.
+__device__ uint64_t run_end(const uint64_t *__restrict__ keys, uint64_t n, uint64_t j, uint64_t k) {
+    uint64_t lo = j + 1, hi, step = 2;
+    for (;;) {
+        hi = lo + step;
+        if (hi >= n) {
+            hi = n;
+            break;
+        }
+        if (keys[hi] != k) break;
+        lo = hi;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {  // keys[lo] == k; hi == n or keys[hi] != k
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (keys[mid] == k) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+// Small runs (the common kind) are gathered in shared memory and queued a
+// batch at a time, one counter update per batch: with millions of runs, one
+// atomic per run on the queue's single counter serialises.
+constexpr int kHeadBatch = 2048;  // buffered small runs; a block iteration finds at most 1024
+
+__device__ void flush_small(const TieArgs &a, RunEntry *s_runs, unsigned int *s_cnt, unsigned long long *s_base) {
+    __syncthreads();
+    const unsigned int cnt = *s_cnt;
+    if (cnt) {
+        if (threadIdx.x == 0) *s_base = atomicAdd(&a.flags->qcount[kQSmall], (unsigned long long)cnt);
+        __syncthreads();
+        const unsigned long long base = *s_base;
+        for (unsigned int t = threadIdx.x; t < cnt; t += kHeadThreads) {
+            if (base + t < a.cap_small) a.q_small[base + t] = s_runs[t];
+            else atomicOr(&a.flags->error, kErrInternal);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *s_cnt = 0;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kHeadThreads) tie_heads_kernel(const TieArgs a) {
+    __shared__ RunEntry s_runs[kHeadBatch];
+    __shared__ unsigned int s_cnt;
+    __shared__ unsigned long long s_base;
+    const uint64_t n = a.n;
+    const uint64_t *__restrict__ keys = a.keys;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint64_t kChunk = 32 * kHeadItems;
+    constexpr uint64_t kBlockKeys = kChunk * (kHeadThreads / 32);
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (uint64_t bb = (uint64_t)blockIdx.x * kBlockKeys; bb < n; bb += (uint64_t)gridDim.x * kBlockKeys) {
+        const uint64_t base = bb + (uint64_t)warp * kChunk;
+        uint64_t key[kHeadItems];
+#pragma unroll
+        for (int k = 0; k < kHeadItems; ++k) {
+            const uint64_t j = base + k * 32 + lane;
+            key[k] = j < n ? keys[j] : 0ull;
+        }
+        // the neighbours just outside the warp's chunk
+        const uint64_t before = (lane == 0 && base > 0 && base - 1 < n) ? keys[base - 1] : 0ull;
+        const uint64_t after = (lane == 31 && base + kChunk < n) ? keys[base + kChunk] : 0ull;
+#pragma unroll
+        for (int k = 0; k < kHeadItems; ++k) {
+            const uint64_t j = base + k * 32 + lane;
+            uint64_t prev = __shfl_up_sync(kFull, key[k], 1);
+            const uint64_t wrap_prev = __shfl_sync(kFull, key[k > 0 ? k - 1 : 0], 31);
+            uint64_t next = __shfl_down_sync(kFull, key[k], 1);
+            const uint64_t wrap_next = __shfl_sync(kFull, key[k + 1 < kHeadItems ? k + 1 : k], 0);
+            if (lane == 0) prev = k > 0 ? wrap_prev : before;
+            if (lane == 31) next = k + 1 < kHeadItems ? wrap_next : after;
+            if (j >= n) continue;
+            const uint64_t kk = key[k];
+            if (!(kk & 1ull)) continue;                        // exact: copies, already in index order
+            if (j > 0 && prev == kk) continue;                 // not the head of its run
+            if (j + 1 >= n || next != kk) continue;            // a single key
+            const uint64_t len = run_end(keys, n, j, kk) - j;
+            if (len <= kSmallMax) s_runs[atomicAdd(&s_cnt, 1u)] = RunEntry{j, (unsigned)len, 0u};
+            else push_run(a, j, len, 0);
+        }
+        // at most kHeadBatch / 2 runs an iteration: flush once half full
+        __syncthreads();
+        if (s_cnt >= kHeadBatch / 2) flush_small(a, s_runs, &s_cnt, &s_base);
+    }
+    flush_small(a, s_runs, &s_cnt, &s_base);
+}
+
 // ---- 2: thread per run ------------------------------------------------------
 // Pairs are most of the small runs on long text (two strings that share the
 // coded prefix), and each is a chain of dependent loads (the entry, the two
@@ -841,7 +944,14 @@ cudaError_t launch_tie_detect(const TieArgs &a, TieMode mode, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     const unsigned tiles = (unsigned)((a.n + kTieTile - 1) / kTieTile);
     switch (mode) {
-        case kTieKeyFlag: tie_detect_kernel<kTieKeyFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
+        case kTieKeyFlag:
+            if (a.segs == nullptr && a.runs == nullptr) {
+                const uint64_t blocks = (a.n + kHeadThreads * kHeadItems - 1) / (kHeadThreads * kHeadItems);
+                tie_heads_kernel<<<(unsigned)umin64(blocks, 152ull * 8), kHeadThreads, 0, s>>>(a);
+            } else {
+                tie_detect_kernel<kTieKeyFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a);
+            }
+            break;
         case kTieValFlag: tie_detect_kernel<kTieValFlag><<<tiles, kTieThreads, kTieSmem, s>>>(a); break;
         case kTiePacked:
             if (a.bits == nullptr || a.pack_bits <= 0 || a.pack_bits > 63 || a.segs != nullptr)
