@@ -599,9 +599,10 @@ struct TsShape {
         uint32_t whist2[kWarps * kBins / 2];
         uint16_t rank[kWin];
         uint32_t heads[kWin / 32];
+        RunEntry runs[512];  // the window's small tie runs, queued together
         uint32_t wsum[kWarps];
-        unsigned long long kmin, kmax, found;
-        unsigned int cut, job;
+        unsigned long long kmin, kmax, found, rbase;
+        unsigned int cut, job, nruns;
     };
 };
 // Two CTAs per SM: measured faster than 12288-key windows at one CTA per
@@ -868,12 +869,30 @@ __device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint6
                             }
                     }
                     if (end > cut) end = cut;
-                    if (end - j >= 2) queue_run(q, flags, pos + j, end - j);
+                    const uint32_t len = end - j;
+                    if (len >= 2) {
+                        // small runs wait in shared memory: one queue update a window
+                        const unsigned int slot = len <= kSmallMax ? atomicAdd(&s.nruns, 1u) : ~0u;
+                        if (slot < 512u) s.runs[slot] = RunEntry{pos + j, len, 0u};
+                        else queue_run(q, flags, pos + j, len);
+                    }
                 }
+            }
+        }
+        __syncthreads();
+        const unsigned int cnt = min(s.nruns, 512u);
+        if (cnt) {
+            if (tid == 0) s.rbase = atomicAdd(&flags->qcount[kQSmall], (unsigned long long)cnt);
+            __syncthreads();
+            const unsigned long long rb = s.rbase;
+            for (unsigned int t = tid; t < cnt; t += S::kThreads) {
+                if (rb + t < q.cap_small) q.small[rb + t] = s.runs[t];
+                else atomicOr(&flags->error, kErrInternal);
             }
         }
     }
     __syncthreads();
+    if (tid == 0) s.nruns = 0;
 }
 
 template <typename IdxT>
@@ -887,6 +906,7 @@ __global__ void __launch_bounds__(TsMain::kThreads, TsMain::kMinBlocks) bucket_t
     const uint64_t kmask = (1ull << kb) - 1;
     IdxT *perm = static_cast<IdxT *>(a.perm);
     const uint32_t wb = (uint32_t)warp * 32 * S::kItems;
+    if (tid == 0) s.nruns = 0;
     for (;;) {
         if (tid == 0) {  // after an error elsewhere (a full queue) no more ranges are taken
             const unsigned int err = *(volatile const unsigned int *)&a.flags->error;
@@ -961,6 +981,7 @@ __global__ void __launch_bounds__(TsBig::kThreads, TsBig::kMinBlocks) bucket_run
     const uint64_t kmask = (1ull << a.kb) - 1;
     IdxT *perm = static_cast<IdxT *>(a.perm);
     const uint32_t wb = (uint32_t)warp * 32 * S::kItems;
+    if (tid == 0) s.nruns = 0;
     for (uint64_t r = blockIdx.x; r < a.count; r += gridDim.x) {
         const uint64_t pos = a.runs[r].start;
         const uint32_t len = a.runs[r].len;
