@@ -21,6 +21,8 @@
 //             leaf l fitted by least squares (FP64 sums), slope >= 0, output
 //             clamped to the band [c_l, c_{l+1}] of sample fractions;
 //   bucket    min(B - 1, floor(clamp(a_l x + b_l, c_l, c_{l+1}) B)).
+#include <type_traits>
+
 #include "hs_internal.h"
 
 namespace hs {
@@ -777,34 +779,48 @@ __device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint6
         for (int i = tid; i < S::kWarps * kBins / 2; i += S::kThreads) s.whist2[i] = 0;
         __syncthreads();
         // rank among the warp's earlier elements with the same digit, four
-        // matches in flight; each leader's add is ordered before the next
-        // item's by the __syncwarp (stability)
+        // peer masks in flight (the match instruction, or ballots when the
+        // warp's first item holds many distinct digits, prefer_ballots: each
+        // form unrolled on its own); each leader's add is ordered before the
+        // next item's by the __syncwarp (stability)
         uint32_t rankp[S::kItems / 2];
 #pragma unroll
         for (int k = 0; k < S::kItems / 2; ++k) rankp[k] = 0;
+        unsigned peers0 = 0;
+        auto rank_items = [&](auto by_ballots) {
+            constexpr bool BALLOTS = decltype(by_ballots)::value;
 #pragma unroll
-        for (int g = 0; g < S::kItems; g += 4) {
-            unsigned peers[4], before[4];
+            for (int g = 0; g < S::kItems; g += 4) {
+                unsigned peers[4], before[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) peers[u] = __match_any_sync(kFull, (unsigned)(w[g + u] >> sh) & (kBins - 1));
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const unsigned d = (unsigned)(w[g + u] >> sh) & (kBins - 1);
-                before[u] = 0;
-                if (lane == __ffs(peers[u]) - 1) {
-                    const unsigned half = 16 * (d & 1);
-                    before[u] = (atomicAdd(&mh2[d >> 1], (unsigned)__popc(peers[u]) << half) >> half) & 0xFFFFu;
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned d = (unsigned)(w[g + u] >> sh) & (kBins - 1);
+                    peers[u] = g + u == 0 ? peers0 : BALLOTS ? match_by_ballots(d, kRadixBits) : __match_any_sync(kFull, d);
                 }
-                __syncwarp();
-            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const unsigned bb = __shfl_sync(kFull, before[u], __ffs(peers[u]) - 1);
-                const unsigned rk = bb + __popc(peers[u] & lanemask_lt());
-                if (S::kRankRegs) rankp[(g + u) / 2] |= rk << (16 * ((g + u) & 1));
-                else s.rank[wb + (g + u) * 32 + lane] = (uint16_t)rk;
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned d = (unsigned)(w[g + u] >> sh) & (kBins - 1);
+                    before[u] = 0;
+                    if (lane == __ffs(peers[u]) - 1) {
+                        const unsigned half = 16 * (d & 1);
+                        before[u] = (atomicAdd(&mh2[d >> 1], (unsigned)__popc(peers[u]) << half) >> half) & 0xFFFFu;
+                    }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned bb = __shfl_sync(kFull, before[u], __ffs(peers[u]) - 1);
+                    const unsigned rk = bb + __popc(peers[u] & lanemask_lt());
+                    if (S::kRankRegs) rankp[(g + u) / 2] |= rk << (16 * ((g + u) & 1));
+                    else s.rank[wb + (g + u) * 32 + lane] = (uint16_t)rk;
+                }
             }
-        }
+        };
+        peers0 = __match_any_sync(kFull, (unsigned)(w[0] >> sh) & (kBins - 1));  // also item 0's mask
+        if (prefer_ballots(peers0, kRadixBits))
+            rank_items(std::true_type{});
+        else
+            rank_items(std::false_type{});
         __syncthreads();
         // digit tid: offsets over the warps (in place of the counts), then
         // the window's digit start

@@ -17,6 +17,8 @@
 // fit one word together, that word alone.  Tile ids come from an atomic
 // counter, so every tile a CTA waits on is already running; each wait is
 // bounded and reports kErrTimeout.
+#include <type_traits>
+
 #include "hs_internal.h"
 
 namespace hs {
@@ -65,35 +67,34 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return wsum + x - v;
 }
 
-// PACKED: each element is one word (key << pack_bits) | index; no payload
-// is loaded, staged or stored.  ITEMS keys per thread.
-template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED, int ITEMS>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
-onesweep_kernel(const OnesweepArgs a) {
+// Shared-memory layout of one onesweep CTA (the dynamic part holds the tile).
+struct OsShared {
+    uint64_t *keys;
+    uint32_t *vals;
+    uint32_t *segs;
+    uint32_t *whist;                 // kWarps x kBins warp counts, then warp offsets
+    unsigned long long *gbase;       // per digit: global start minus tile-local start
+    uint32_t *scan;                  // kWarps
+    uint32_t *dstart;                // kBins tile-local digit starts
+};
+
+// One tile.  FULL: the tile holds TILE elements, so no element needs a
+// bounds test and the write-out runs as ITEMS unrolled rounds; the last,
+// partial tile takes the general form.  PACKED: each element is one word
+// (key << pack_bits) | index; no payload is loaded, staged or stored.
+template <bool FULL, bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED, int ITEMS>
+__device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsShared &s, const uint64_t tile) {
     constexpr int TILE = kThreads * ITEMS;
     constexpr int RBITS = (32 * ITEMS <= 256 && !SYNTH) ? 8 : 16;  // rank bits (ranks < 32 * ITEMS; SYNTH: + a flag)
     constexpr int RPR = 32 / RBITS;
     constexpr uint32_t RMASK = (1u << (SYNTH ? RBITS - 1 : RBITS)) - 1;  // SYNTH: top bit is the flag
     static_assert(ITEMS % 4 == 0, "tile must be whole groups of four items");
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
-    uint32_t *s_segs = s_vals + (PACKED ? 0 : TILE);
-    uint32_t *s_whist = s_segs + (HAS_SEG ? TILE : 0);
-    unsigned long long *s_gbase = reinterpret_cast<unsigned long long *>(s_whist + kWarps * kBins);
-    __shared__ uint32_t s_scan[kWarps];
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_dstart[kBins];
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-    for (int i = tid; i < kWarps * kBins; i += kThreads) s_whist[i] = 0;
-    __syncthreads();
-    const uint64_t tile = s_tile;
     const uint64_t n = a.n;
     const uint64_t tile_base = tile * TILE;
     const int shift = a.shift;
     const unsigned mask = a.mask;
+    const int nbits = 32 - __clz(mask);  // digit width of this pass
 
     // Warp-striped load: warp w owns elements [w*32*ITEMS, (w+1)*32*ITEMS)
     // of the tile, item k of lane l is element w*32*ITEMS + k*32 + l, so
@@ -102,80 +103,102 @@ onesweep_kernel(const OnesweepArgs a) {
     // at the scatter instead of being held; their not-exact bit waits in the
     // top bit of the item's 16-bit rank slot (ranks stay below 32 * ITEMS).
     static_assert(!SYNTH || (RBITS == 16 && 32 * ITEMS < (1 << 15)), "synthesised flags ride in 16-bit rank slots");
+    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS;
+    // elements of this warp inside the input (all of them in a full tile)
+    const uint32_t wcount = FULL ? 32u * ITEMS : (uint32_t)(n > wbase ? umin64(n - wbase, 32u * ITEMS) : 0);
     uint64_t key[ITEMS];
     uint32_t val[ITEMS];
     uint32_t seg[ITEMS];
     uint32_t rankp[ITEMS / RPR] = {};
-    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * ITEMS;
+    {
+        const uint64_t *kin = a.keys_in + wbase + lane;
+        const uint32_t *vin = PACKED || SYNTH ? nullptr : a.vals_in + wbase + lane;
+        const uint32_t *sin = HAS_SEG ? a.segs_in + wbase + lane : nullptr;
+        const uint32_t *fin = SYNTH ? a.flag_bits + (wbase >> 5) : nullptr;  // one word per item, warp-uniform
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        const uint64_t e = wbase + k * 32 + lane;
-        const bool valid = e < n;
-        key[k] = valid ? a.keys_in[e] : 0;
-        val[k] = (PACKED || SYNTH || !valid) ? 0u : a.vals_in[e];
-        if (SYNTH && valid && a.flag_bits)
-            rankp[k / RPR] |= ((a.flag_bits[e >> 5] >> lane) & 1u) << (RBITS * (k % RPR) + RBITS - 1);
-        seg[k] = (HAS_SEG && valid) ? a.segs_in[e] : 0;
+        for (int k = 0; k < ITEMS; ++k) {
+            const bool valid = FULL || (uint32_t)(k * 32 + lane) < wcount;
+            key[k] = valid ? kin[k * 32] : 0;
+            val[k] = (PACKED || SYNTH || !valid) ? 0u : vin[k * 32];
+            if (SYNTH && valid && a.flag_bits)
+                rankp[k / RPR] |= ((fin[k] >> lane) & 1u) << (RBITS * (k % RPR) + RBITS - 1);
+            seg[k] = (HAS_SEG && valid) ? sin[k * 32] : 0;
+        }
     }
+    auto digit_of = [&](int k) -> unsigned {
+        return DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
+    };
 
-    // Ranking, four items at a time: the warp matches of the four are
-    // independent and issue back to back; then for each item the lowest lane
-    // of every equal-digit group (leader) advances the warp's count by the
-    // group size with one shared atomic (the __syncwarp orders the groups of
-    // consecutive items on the same counter), and the counts before the
-    // adds are broadcast to the groups last.
-    uint32_t *my_hist = s_whist + warp * kBins;
+    // Ranking, four items at a time: the peer masks of the four (lanes
+    // with the same digit) are independent and issue back to back; then for
+    // each item the lowest lane of every equal-digit group (leader) advances
+    // the warp's count by the group size with one shared atomic (the
+    // __syncwarp orders the groups of consecutive items on the same
+    // counter), and the counts before the adds are broadcast to the groups
+    // last.  The masks come from the match instruction, or from ballots when
+    // the warp's first item holds many distinct digits (prefer_ballots);
+    // each form is unrolled on its own, with no branch between the groups.
+    uint32_t *my_hist = s.whist + warp * kBins;
+    unsigned peers0 = 0;
+    auto rank_items = [&](auto by_ballots) {
+        constexpr bool BALLOTS = decltype(by_ballots)::value;
 #pragma unroll
-    for (int g = 0; g < ITEMS; g += 4) {
-        unsigned peers[4], before[4];
+        for (int g = 0; g < ITEMS; g += 4) {
+            unsigned peers[4], before[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = g + q;
-            const bool valid = wbase + k * 32 + lane < n;
-            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-            peers[q] = match_digit(d, __ballot_sync(kFull, valid));
+            for (int q = 0; q < 4; ++q) {
+                const int k = g + q;
+                if (FULL && k == 0) {
+                    peers[q] = peers0;
+                } else if (BALLOTS) {
+                    peers[q] = match_by_ballots(digit_of(k), nbits);
+                } else if (FULL) {
+                    peers[q] = __match_any_sync(kFull, digit_of(k));
+                } else {
+                    const bool valid = (uint32_t)(k * 32 + lane) < wcount;
+                    peers[q] = match_digit(digit_of(k), __ballot_sync(kFull, valid));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = g + q;
+                const bool valid = FULL || (uint32_t)(k * 32 + lane) < wcount;
+                before[q] = 0;
+                if (valid && lane == __ffs(peers[q]) - 1)
+                    before[q] = atomicAdd(&my_hist[digit_of(k)], (unsigned)__popc(peers[q]));
+                __syncwarp();
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = g + q;
+                const bool valid = FULL || (uint32_t)(k * 32 + lane) < wcount;
+                const int leader = valid ? __ffs(peers[q]) - 1 : lane;
+                const unsigned b = __shfl_sync(kFull, before[q], leader);
+                rankp[k / RPR] |= (b + __popc(peers[q] & lanemask_lt())) << (RBITS * (k % RPR));
+            }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = g + q;
-            const bool valid = wbase + k * 32 + lane < n;
-            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
-            before[q] = 0;
-            if (valid && lane == __ffs(peers[q]) - 1) before[q] = atomicAdd(&my_hist[d], (unsigned)__popc(peers[q]));
-            __syncwarp();
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = g + q;
-            const bool valid = wbase + k * 32 + lane < n;
-            const int leader = valid ? __ffs(peers[q]) - 1 : lane;
-            const unsigned b = __shfl_sync(kFull, before[q], leader);
-            rankp[k / RPR] |= (b + __popc(peers[q] & lanemask_lt())) << (RBITS * (k % RPR));
-        }
+    };
+    if constexpr (FULL) {
+        peers0 = __match_any_sync(kFull, digit_of(0));  // also item 0's mask
+        if (prefer_ballots(peers0, nbits))
+            rank_items(std::true_type{});
+        else
+            rank_items(std::false_type{});
+    } else {
+        rank_items(std::false_type{});  // the last, partial tile
     }
     __syncthreads();
 
-    // Thread t owns digits t*kDpt .. t*kDpt + kDpt - 1: their tile counts,
-    // and the exclusive per-warp offsets in place of the warp counts.
+    // Thread t owns digits t*kDpt .. t*kDpt + kDpt - 1: their tile counts
+    // first, then (after the tile-local digit starts are known) each warp's
+    // start for the digit inside the staged tile in place of its count.
     uint32_t total[kDpt];
 #pragma unroll
     for (int j = 0; j < kDpt; ++j) total[j] = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-        uint32_t *h = s_whist + w * kBins + tid * kDpt;
-        if (kDpt == 2) {
-            const uint2 c = *reinterpret_cast<const uint2 *>(h);
-            *reinterpret_cast<uint2 *>(h) = make_uint2(total[0], total[kDpt - 1]);
-            total[0] += c.x;
-            total[kDpt - 1] += c.y;
-        } else {
 #pragma unroll
-            for (int j = 0; j < kDpt; ++j) {
-                const uint32_t c = h[j];
-                h[j] = total[j];
-                total[j] += c;
-            }
-        }
+        for (int j = 0; j < kDpt; ++j) total[j] += s.whist[w * kBins + tid * kDpt + j];
     }
     uint64_t *lb = a.lookback + tile * kBins;
     const uint32_t epoch = a.epoch;
@@ -194,27 +217,39 @@ onesweep_kernel(const OnesweepArgs a) {
 #pragma unroll
     for (int j = 0; j < kDpt; ++j) mine += total[j];
     uint32_t dstart[kDpt];
-    dstart[0] = block_exclusive_scan(mine, s_scan);
+    dstart[0] = block_exclusive_scan(mine, s.scan);
 #pragma unroll
     for (int j = 1; j < kDpt; ++j) dstart[j] = dstart[j - 1] + total[j - 1];
+    {
+        uint32_t run[kDpt];
 #pragma unroll
-    for (int j = 0; j < kDpt; ++j) s_dstart[tid * kDpt + j] = dstart[j];
+        for (int j = 0; j < kDpt; ++j) run[j] = dstart[j];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+#pragma unroll
+            for (int j = 0; j < kDpt; ++j) {
+                uint32_t *h = s.whist + w * kBins + tid * kDpt + j;
+                const uint32_t c = *h;
+                *h = run[j];
+                run[j] += c;
+            }
+        }
+    }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const uint64_t e = wbase + k * 32 + lane;
-        if (e < n) {
-            const unsigned d = DIGIT_SEG ? ((seg[k] >> shift) & mask) : (unsigned)((key[k] >> shift) & mask);
+        if (FULL || (uint32_t)(k * 32 + lane) < wcount) {
+            const unsigned d = digit_of(k);
             const uint32_t r = (rankp[k / RPR] >> (RBITS * (k % RPR))) & RMASK;
-            const uint32_t p = my_hist[d] + s_dstart[d] + r;
-            s_keys[p] = key[k];
+            const uint32_t p = my_hist[d] + r;
+            s.keys[p] = key[k];
             if (SYNTH) {
                 const uint32_t bit = (rankp[k / RPR] >> (RBITS * (k % RPR) + RBITS - 1)) & 1u;
-                s_vals[p] = (uint32_t)e | (bit << 31);
+                s.vals[p] = ((uint32_t)wbase + (uint32_t)(k * 32 + lane)) | (bit << 31);
             } else if (!PACKED) {
-                s_vals[p] = val[k];
+                s.vals[p] = val[k];
             }
-            if (HAS_SEG) s_segs[p] = seg[k];
+            if (HAS_SEG) s.segs[p] = seg[k];
         }
     }
 
@@ -282,18 +317,17 @@ onesweep_kernel(const OnesweepArgs a) {
     }
 #pragma unroll
     for (int j = 0; j < kDpt; ++j)
-        s_gbase[tid * kDpt + j] = a.bucket_base[tid * kDpt + j] + prefix[j] - dstart[j];
+        s.gbase[tid * kDpt + j] = a.bucket_base[tid * kDpt + j] + prefix[j] - dstart[j];
     __syncthreads();
 
-    const int cnt = (int)umin64(TILE, n - tile_base);
-    for (int i = tid; i < cnt; i += kThreads) {
-        const uint64_t k = s_keys[i];
-        const uint32_t sg = HAS_SEG ? s_segs[i] : 0;
+    // Write-out in tile order: element i of the staged tile goes to its
+    // digit's global start plus i, so equal digits leave as runs.
+    auto emit = [&](int i, uint64_t k, uint32_t sg) {
         const unsigned d = DIGIT_SEG ? ((sg >> shift) & mask) : (unsigned)((k >> shift) & mask);
-        const uint64_t pos = s_gbase[d] + (uint64_t)i;
+        const uint64_t pos = s.gbase[d] + (uint64_t)i;
         if (pos >= n) {
             atomicOr(&a.flags->error, kErrInternal);
-            continue;
+            return;
         }
         if (PACKED) {
             const uint64_t idx = k & ((1ull << a.pack_bits) - 1);
@@ -302,18 +336,61 @@ onesweep_kernel(const OnesweepArgs a) {
                 static_cast<uint32_t *>(a.vals_out)[pos] = (uint32_t)idx;
             else if (OUT == kOutPerm64)
                 static_cast<uint64_t *>(a.vals_out)[pos] = idx;
-            continue;
+            return;
         }
         if (a.keys_out) a.keys_out[pos] = k;
         if (HAS_SEG) a.segs_out[pos] = sg;
-        const uint32_t v = s_vals[i];
+        const uint32_t v = s.vals[i];
         if (OUT == kOutVals)
             static_cast<uint32_t *>(a.vals_out)[pos] = v;
         else if (OUT == kOutPerm32)
             static_cast<uint32_t *>(a.vals_out)[pos] = v & kIdxMask;
         else
             static_cast<uint64_t *>(a.vals_out)[pos] = (uint64_t)(v & kIdxMask);
+    };
+    if (FULL) {
+        // every thread owns ITEMS elements: their shared loads issue together
+        uint64_t k[ITEMS];
+        uint32_t sg[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            k[j] = s.keys[j * kThreads + tid];
+            sg[j] = HAS_SEG ? s.segs[j * kThreads + tid] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) emit(j * kThreads + tid, k[j], sg[j]);
+    } else {
+        const int cnt = (int)umin64(TILE, n - tile_base);
+        for (int i = tid; i < cnt; i += kThreads) emit(i, s.keys[i], HAS_SEG ? s.segs[i] : 0);
     }
+}
+
+template <bool HAS_SEG, bool DIGIT_SEG, bool SYNTH, int OUT, bool PACKED, int ITEMS>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+onesweep_kernel(const OnesweepArgs a) {
+    constexpr int TILE = kThreads * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_scan[kWarps];
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_dstart[kBins];
+    OsShared s;
+    s.keys = reinterpret_cast<uint64_t *>(smem);
+    s.vals = reinterpret_cast<uint32_t *>(s.keys + TILE);
+    s.segs = s.vals + (PACKED ? 0 : TILE);
+    s.whist = s.segs + (HAS_SEG ? TILE : 0);
+    s.gbase = reinterpret_cast<unsigned long long *>(s.whist + kWarps * kBins);
+    s.scan = s_scan;
+    s.dstart = s_dstart;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    for (int i = tid; i < kWarps * kBins; i += kThreads) s.whist[i] = 0;
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    if ((tile + 1) * TILE <= a.n)
+        onesweep_tile<true, HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, ITEMS>(a, s, tile);
+    else
+        onesweep_tile<false, HAS_SEG, DIGIT_SEG, SYNTH, OUT, PACKED, ITEMS>(a, s, tile);
 }
 
 size_t onesweep_smem(bool has_seg, bool packed, int items) {
