@@ -341,16 +341,18 @@ def argsort_device(data: torch.Tensor, offsets: torch.Tensor,
 
 def argsort(data: torch.Tensor, offsets: torch.Tensor, mode: int = MODE_PLAIN,
             coder: int = CODER_AUTO, index_u64: bool = False,
-            device="cuda", stream=None) -> torch.Tensor:
+            device="cuda", stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
     """Stable argsort of strings held in host or device tensors.
 
     Device inputs are sorted on the device (hs_argsort) and the permutation
     stays there.  Host inputs go through hs_argsort_host: the library copies
     them in chunks (overlapped with the encoder), sorts on the device and
     copies the permutation back into a pinned host tensor, which is
-    returned.  Pinned inputs give the full transfer speed."""
+    returned (`out`, when given: a pinned host tensor of n int32, or int64
+    with index_u64, reused across calls).  Pinned inputs give the full
+    transfer speed."""
     if data.is_cuda and offsets.is_cuda:
-        return argsort_device(data, offsets, mode, coder, index_u64, stream=stream)
+        return argsort_device(data, offsets, mode, coder, index_u64, out=out, stream=stream)
     if data.is_cuda or offsets.is_cuda:
         raise ValueError("bytes and offsets must both be on the host or both on the device")
     if data.dtype != torch.uint8:
@@ -361,7 +363,10 @@ def argsort(data: torch.Tensor, offsets: torch.Tensor, mode: int = MODE_PLAIN,
     offsets = offsets.contiguous()
     n = offsets.numel() - 1
     dt = torch.int64 if index_u64 else torch.int32
-    out = torch.empty(max(n, 0), dtype=dt, pin_memory=True)
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=dt, pin_memory=True)
+    elif out.dtype != dt or out.numel() != max(n, 0) or out.is_cuda or not out.is_pinned():
+        raise ValueError("out must be a pinned host tensor of n indices of the output type")
     if n <= 0:
         return out
     lib = load()

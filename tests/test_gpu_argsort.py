@@ -288,6 +288,29 @@ def test_host_inputs_roundtrip(cuda_lib):
     assert_oracle_equal(w, perm)
 
 
+@pytest.mark.parametrize("index_u64", [False, True])
+def test_host_inputs_into_a_reused_pinned_output(cuda_lib, index_u64):
+    """The host entry point writes into a caller's pinned tensor, call after
+    call; a tensor of the wrong type or size, or not pinned, is refused."""
+    hs = cuda_lib
+    import torch
+    dt = torch.int64 if index_u64 else torch.int32
+    out = None
+    for seed in (5, 6):
+        w = workloads.generate(2, 100_000, seed)
+        data = torch.from_numpy(w.bytes).pin_memory()
+        off = torch.from_numpy(w.offsets.view(np.int64)).pin_memory()
+        if out is None:
+            out = torch.full((w.n,), -1, dtype=dt).pin_memory()
+        got = hs.argsort(data, off, index_u64=index_u64, out=out)
+        assert got.data_ptr() == out.data_ptr()
+        assert_oracle_equal(w, out)
+    for bad in (torch.empty(w.n, dtype=dt), torch.empty(w.n + 1, dtype=dt).pin_memory(),
+                torch.empty(w.n, dtype=torch.int32 if index_u64 else torch.int64).pin_memory()):
+        with pytest.raises(ValueError):
+            hs.argsort(data, off, index_u64=index_u64, out=bad)
+
+
 @pytest.mark.parametrize("n_copies", [40, 3000, 70_001])
 @pytest.mark.parametrize("odd", ["none", "smaller", "greater", "longer", "shorter"])
 def test_runs_of_copies_with_one_odd_member(cuda_lib, n_copies, odd):
