@@ -465,10 +465,12 @@ rmi_bucket_kernel(const uint64_t *__restrict__ keys, uint64_t n, const RmiModel 
 // between the leaf of its first value and the leaf of the next slice's first
 // value (the threshold table is non-decreasing), so the bisection runs over
 // those few leaves instead of all 4096; each leaf's parameters are one
-// 32-byte record.
+// 32-byte record.  The compose kernel holds all 4096 records (128 KB) in
+// shared memory, one CTA of 1024 threads per SM: from L1/L2 the records'
+// loads were its longest waits.
 constexpr int kAccel = 1 << kRmiAccelBits;
 constexpr int kAccelShift = kRmiFeatureBits - kRmiAccelBits;
-constexpr int kCmpThreads = 512;
+constexpr int kCmpThreads = 1024;
 constexpr int kCmpItems = 4;
 using LeafPk = RmiModel::LeafPk;
 static_assert(sizeof(LeafPk) == 32, "one leaf record is two 16-byte loads");
@@ -502,14 +504,15 @@ __device__ __forceinline__ uint32_t accel_leaf(const uint32_t *s_thresh, const u
     return lo;
 }
 
-// bucket_of (trained model) with the indexed leaf search: the same arithmetic.
-__device__ __forceinline__ uint32_t bucket_fast(const LeafPk *__restrict__ pk, const uint32_t *s_thresh,
+// bucket_of (trained model) with the indexed leaf search: the same
+// arithmetic.  pk: the leaf records in shared memory.
+__device__ __forceinline__ uint32_t bucket_fast(const LeafPk *pk, const uint32_t *s_thresh,
                                                 const uint16_t *s_accel, uint64_t key, uint64_t kmin, int shift,
                                                 float B) {
     const uint32_t X = feature_of(key, kmin, shift);
     const uint32_t l = accel_leaf(s_thresh, s_accel, X);
-    const ulonglong2 r0 = __ldg(reinterpret_cast<const ulonglong2 *>(pk + l));
-    const float4 r1 = __ldg(reinterpret_cast<const float4 *>(pk + l) + 1);
+    const ulonglong2 r0 = *reinterpret_cast<const ulonglong2 *>(pk + l);
+    const float4 r1 = *(reinterpret_cast<const float4 *>(pk + l) + 1);
     const uint64_t kbase = r0.x;
     const float kscale = __uint_as_float((unsigned)r0.y), slope = __uint_as_float((unsigned)(r0.y >> 32));
     const float icept = r1.x, lo = r1.y, hi = r1.z;
@@ -525,9 +528,12 @@ __global__ void __launch_bounds__(kCmpThreads)
 rmi_compose_kernel(uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__restrict__ model, int bits, int kb,
                    unsigned long long *__restrict__ hist) {
     extern __shared__ __align__(16) unsigned char cmp_smem[];
-    uint32_t *s_thresh = reinterpret_cast<uint32_t *>(cmp_smem);
+    LeafPk *s_leaf = reinterpret_cast<LeafPk *>(cmp_smem);
+    uint32_t *s_thresh = reinterpret_cast<uint32_t *>(s_leaf + kRmiLeaves);
     uint16_t *s_accel = reinterpret_cast<uint16_t *>(s_thresh + kRmiLeaves);
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_accel + kAccel + 8);
+    for (int i = threadIdx.x; i < kRmiLeaves * 2; i += kCmpThreads)
+        reinterpret_cast<uint4 *>(s_leaf)[i] = reinterpret_cast<const uint4 *>(model->leafpk)[i];
     for (int i = threadIdx.x; i < kRmiLeaves; i += kCmpThreads) s_thresh[i] = model->thresh[i];
     for (int i = threadIdx.x; i < (kAccel + 8) / 8; i += kCmpThreads)
         reinterpret_cast<uint4 *>(s_accel)[i] = reinterpret_cast<const uint4 *>(model->accel)[i];
@@ -537,7 +543,7 @@ rmi_compose_kernel(uint64_t *__restrict__ keys, uint64_t n, const RmiModel *__re
     const int shift = model->shift;
     const float B = (float)(1u << bits);
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    const LeafPk *pk = model->leafpk;
+    const LeafPk *pk = s_leaf;
     constexpr uint64_t kGroup = (uint64_t)kCmpThreads * kCmpItems;
     for (uint64_t g = (uint64_t)blockIdx.x * kGroup; g < n; g += (uint64_t)gridDim.x * kGroup) {
         uint64_t key[kCmpItems];
@@ -1415,8 +1421,8 @@ cudaError_t launch_rmi_compose(uint64_t *keys, uint64_t n, const RmiModel *model
     if (n == 0) return cudaSuccess;
     if (bits < 1 || bits > 3 * kRadixBits || kb < 1 || kb + bits > 64) return cudaErrorInvalidValue;
     const uint64_t groups = (n + (uint64_t)kCmpThreads * kCmpItems - 1) / ((uint64_t)kCmpThreads * kCmpItems);
-    const unsigned grid = (unsigned)umin64(groups, (uint64_t)num_sms * 4);
-    constexpr size_t smem = kRmiLeaves * 4 + (kAccel + 8) * 2 + 3 * kBins * 4;
+    const unsigned grid = (unsigned)umin64(groups, (uint64_t)num_sms);  // one CTA per SM (shared memory)
+    constexpr size_t smem = kRmiLeaves * sizeof(LeafPk) + kRmiLeaves * 4 + (kAccel + 8) * 2 + 3 * kBins * 4;
     static_assert(((kAccel + 8) * 2) % 16 == 0, "the histogram stays 4-byte aligned");
     static bool configured = false;
     if (!configured) {
