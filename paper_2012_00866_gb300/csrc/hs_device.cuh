@@ -101,30 +101,31 @@ __device__ __forceinline__ unsigned match_digit(unsigned d, unsigned active) {
     return __match_any_sync(kFull, d) & active;
 }
 
-// The same peer mask from one ballot per digit bit (bits 0..nbits-1 of d,
-// nbits <= 9).  Its cost is fixed, where the match instruction's grows with
-// the number of distinct values the warp holds (see prefer_ballots).  Call
-// with the full warp converged.
-__device__ __forceinline__ unsigned match_by_ballots(unsigned d, int nbits) {
+// The same peer mask from one ballot per digit bit, for digits below 2^9.
+// Always nine ballots: where a pass's digits are narrower, their upper bits
+// are 0 in every lane, those ballots are 0 and change nothing, and a
+// runtime bound on the loop measured 10% slower in onesweep.  Its cost is
+// fixed, where the match instruction's grows with the number of distinct
+// values the warp holds (see prefer_ballots).  Call with the full warp
+// converged.
+__device__ __forceinline__ unsigned match_by_ballots(unsigned d) {
     unsigned diff = 0;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        if (j < nbits) {
-            const unsigned t = 0u - ((d >> j) & 1u);  // all ones where bit j is set
-            diff |= __ballot_sync(kFull, t != 0u) ^ t;
-        }
+    for (int j = 0; j < kRadixBits; ++j) {
+        const unsigned t = 0u - ((d >> j) & 1u);  // all ones where bit j is set
+        diff |= __ballot_sync(kFull, t != 0u) ^ t;
     }
     return ~diff;
 }
 
 // Whether a warp ranks its items with ballots rather than the match
 // instruction, from the match result `peers` of one of its items: the
-// leaders of the equal-digit groups count the warp's distinct digits.
-// Measured on GB300, the two forms cost the same at about 2.3 distinct
-// digits per digit bit.  Call with the full warp converged.
-__device__ __forceinline__ bool prefer_ballots(unsigned peers, int nbits) {
-    const unsigned distinct = __popc(__ballot_sync(kFull, (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)));
-    return 10u * distinct >= 23u * (unsigned)nbits;
+// leaders of the equal-digit groups count the warp's distinct digits, and
+// at kBallotDistinct or more the nine ballots cost less (measured on
+// GB300).  Call with the full warp converged.
+constexpr unsigned kBallotDistinct = 21;
+__device__ __forceinline__ bool prefer_ballots(unsigned peers) {
+    return (unsigned)__popc(__ballot_sync(kFull, (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))) >= kBallotDistinct;
 }
 
 // Shared-memory histogram increment of digit d: when the whole warp holds

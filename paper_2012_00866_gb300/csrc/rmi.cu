@@ -801,7 +801,7 @@ __device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint6
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const unsigned d = (unsigned)(w[g + u] >> sh) & (kBins - 1);
-                    peers[u] = g + u == 0 ? peers0 : BALLOTS ? match_by_ballots(d, kRadixBits) : __match_any_sync(kFull, d);
+                    peers[u] = g + u == 0 ? peers0 : BALLOTS ? match_by_ballots(d) : __match_any_sync(kFull, d);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -823,7 +823,7 @@ __device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint6
             }
         };
         peers0 = __match_any_sync(kFull, (unsigned)(w[0] >> sh) & (kBins - 1));  // also item 0's mask
-        if (prefer_ballots(peers0, kRadixBits))
+        if (prefer_ballots(peers0))
             rank_items(std::true_type{});
         else
             rank_items(std::false_type{});

@@ -94,7 +94,6 @@ __device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsSha
     const uint64_t tile_base = tile * TILE;
     const int shift = a.shift;
     const unsigned mask = a.mask;
-    const int nbits = 32 - __clz(mask);  // digit width of this pass
 
     // Warp-striped load: warp w owns elements [w*32*ITEMS, (w+1)*32*ITEMS)
     // of the tile, item k of lane l is element w*32*ITEMS + k*32 + l, so
@@ -151,7 +150,7 @@ __device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsSha
                 if (FULL && k == 0) {
                     peers[q] = peers0;
                 } else if (BALLOTS) {
-                    peers[q] = match_by_ballots(digit_of(k), nbits);
+                    peers[q] = match_by_ballots(digit_of(k));
                 } else if (FULL) {
                     peers[q] = __match_any_sync(kFull, digit_of(k));
                 } else {
@@ -180,7 +179,7 @@ __device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsSha
     };
     if constexpr (FULL) {
         peers0 = __match_any_sync(kFull, digit_of(0));  // also item 0's mask
-        if (prefer_ballots(peers0, nbits))
+        if (prefer_ballots(peers0))
             rank_items(std::true_type{});
         else
             rank_items(std::false_type{});
