@@ -321,7 +321,9 @@ __device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsSha
 
     // Write-out in tile order: element i of the staged tile goes to its
     // digit's global start plus i, so equal digits leave as runs.
-    auto emit = [&](int i, uint64_t k, uint32_t sg) {
+    // KEYS (compile time): the keys go out too (keys_out set).
+    auto emit = [&](int i, uint64_t k, uint32_t sg, auto keys_tag) {
+        constexpr bool KEYS = decltype(keys_tag)::value;
         const unsigned d = DIGIT_SEG ? ((sg >> shift) & mask) : (unsigned)((k >> shift) & mask);
         const uint64_t pos = s.gbase[d] + (uint64_t)i;
         if (pos >= n) {
@@ -330,14 +332,14 @@ __device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsSha
         }
         if (PACKED) {
             const uint64_t idx = k & ((1ull << a.pack_bits) - 1);
-            if (OUT == kOutVals || a.keys_out) a.keys_out[pos] = k;
+            if (OUT == kOutVals || KEYS) a.keys_out[pos] = k;
             if (OUT == kOutPerm32)
                 static_cast<uint32_t *>(a.vals_out)[pos] = (uint32_t)idx;
             else if (OUT == kOutPerm64)
                 static_cast<uint64_t *>(a.vals_out)[pos] = idx;
             return;
         }
-        if (a.keys_out) a.keys_out[pos] = k;
+        if (KEYS) a.keys_out[pos] = k;
         if (HAS_SEG) a.segs_out[pos] = sg;
         const uint32_t v = s.vals[i];
         if (OUT == kOutVals)
@@ -356,11 +358,22 @@ __device__ __forceinline__ void onesweep_tile(const OnesweepArgs &a, const OsSha
             k[j] = s.keys[j * kThreads + tid];
             sg[j] = HAS_SEG ? s.segs[j * kThreads + tid] : 0;
         }
+        auto emit_all = [&](auto keys_tag) {
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) emit(j * kThreads + tid, k[j], sg[j]);
+            for (int j = 0; j < ITEMS; ++j) emit(j * kThreads + tid, k[j], sg[j], keys_tag);
+        };
+        if (a.keys_out)
+            emit_all(std::true_type{});
+        else
+            emit_all(std::false_type{});
     } else {
         const int cnt = (int)umin64(TILE, n - tile_base);
-        for (int i = tid; i < cnt; i += kThreads) emit(i, s.keys[i], HAS_SEG ? s.segs[i] : 0);
+        for (int i = tid; i < cnt; i += kThreads) {
+            if (a.keys_out)
+                emit(i, s.keys[i], HAS_SEG ? s.segs[i] : 0, std::true_type{});
+            else
+                emit(i, s.keys[i], HAS_SEG ? s.segs[i] : 0, std::false_type{});
+        }
     }
 }
 
