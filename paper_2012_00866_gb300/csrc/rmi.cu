@@ -733,6 +733,29 @@ __device__ __forceinline__ uint32_t ts_exclusive_scan(uint32_t v, uint32_t *wsum
     return pre + x - v;
 }
 
+// The CTA's small tie runs gathered in shared memory go to the small-run
+// queue with one global atomic for all of them.  Call with every thread,
+// after a barrier that follows the last write to s.runs.
+template <class S>
+__device__ void flush_runs(typename S::Smem &s, const RunQueues &q, DevFlags *flags) {
+    const unsigned int cnt = min(s.nruns, 512u);
+    if (cnt) {
+        if (threadIdx.x == 0) s.rbase = atomicAdd(&flags->qcount[kQSmall], (unsigned long long)cnt);
+        __syncthreads();
+        const unsigned long long rb = s.rbase;
+        for (unsigned int t = threadIdx.x; t < cnt; t += S::kThreads) {
+            if (rb + t < q.cap_small) q.small[rb + t] = s.runs[t];
+            else atomicOr(&flags->error, kErrInternal);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s.nruns = 0;
+}
+
+// Windows keep adding small runs to the CTA's buffer until it is half full;
+// a run that finds it full goes to the queue on its own.
+constexpr unsigned kRunFlushAt = 256;
+
 // Sorts elements [0, cut) of a window held in w (item k of lane l of warp wp
 // is element 32 * ITEMS * wp + 32k + l; w[k] its composite key, anything at
 // or past cut), writes their payload in key order to perm[pos ..] and, with
@@ -893,7 +916,7 @@ __device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint6
                     if (end > cut) end = cut;
                     const uint32_t len = end - j;
                     if (len >= 2) {
-                        // small runs wait in shared memory: one queue update a window
+                        // small runs wait in shared memory: one queue update for many windows
                         const unsigned int slot = len <= kSmallMax ? atomicAdd(&s.nruns, 1u) : ~0u;
                         if (slot < 512u) s.runs[slot] = RunEntry{pos + j, len, 0u};
                         else queue_run(q, flags, pos + j, len);
@@ -902,19 +925,9 @@ __device__ void sort_window(typename S::Smem &s, uint64_t (&w)[S::kItems], uint6
             }
         }
         __syncthreads();
-        const unsigned int cnt = min(s.nruns, 512u);
-        if (cnt) {
-            if (tid == 0) s.rbase = atomicAdd(&flags->qcount[kQSmall], (unsigned long long)cnt);
-            __syncthreads();
-            const unsigned long long rb = s.rbase;
-            for (unsigned int t = tid; t < cnt; t += S::kThreads) {
-                if (rb + t < q.cap_small) q.small[rb + t] = s.runs[t];
-                else atomicOr(&flags->error, kErrInternal);
-            }
-        }
+        if (s.nruns >= kRunFlushAt) flush_runs<S>(s, q, flags);  // the same value in every thread
     }
     __syncthreads();
-    if (tid == 0) s.nruns = 0;
 }
 
 template <typename IdxT>
@@ -990,6 +1003,7 @@ __global__ void __launch_bounds__(TsMain::kThreads, TsMain::kMinBlocks) bucket_t
             pos += cut;
         }
     }
+    if (a.ties) flush_runs<S>(s, a.q, a.flags);
 }
 
 // The buckets the range kernel found longer than its window, one at a time
@@ -1024,6 +1038,8 @@ __global__ void __launch_bounds__(TsBig::kThreads, TsBig::kMinBlocks) bucket_run
         __syncthreads();
         sort_window<S, IdxT>(s, w, pos, len, kmask, a.vals_in, perm, a.ties != 0, a.q, a.flags);
     }
+    __syncthreads();
+    if (a.ties) flush_runs<S>(s, a.q, a.flags);
 }
 
 // Runs of equal keys inside the overflow buckets (sorted keys, key bit 0 =
