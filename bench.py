@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -180,11 +181,19 @@ TRAFFIC_SOURCES = ["paper_2012_00866_gb300/csrc/sort.cu", "paper_2012_00866_gb30
                    "paper_2012_00866_gb300/csrc/hs_internal.h"]
 
 
+def _code_only(src: str) -> str:
+    """C/CUDA source without comments and blank lines: the digest follows
+    the code, so an edited comment does not void a capture."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.strip() for line in src.split("\n") if line.strip())
+
+
 def sources_digest(paths=TRAFFIC_SOURCES):
     h = hashlib.sha256()
     for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()
 
 

@@ -94,9 +94,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 
 // Lanes of the warp whose radix digit equals this lane's, restricted to
-// `active`.  Call with the full warp converged (lanes outside `active` pass
-// any digit).  The hardware match instruction measured faster here than one
-// ballot per digit bit.
+// `active`, from the hardware match instruction.  Call with the full warp
+// converged (lanes outside `active` pass any digit).  Its cost grows with the
+// number of distinct digits in the warp; match_by_ballots below costs the
+// same always.
 __device__ __forceinline__ unsigned match_digit(unsigned d, unsigned active) {
     return __match_any_sync(kFull, d) & active;
 }

@@ -6,7 +6,8 @@
 // Each pass is a single "onesweep" kernel (Adinets and Merrill, 2022): the
 // global digit offsets come from histograms computed up front (fused into the
 // encoder), each CTA ranks a tile of keys with warp-private digit counters
-// (lanes with equal digits found by a warp match), publishes its per-digit
+// (lanes with equal digits found by the warp match instruction, or by nine
+// ballots where the warp holds many distinct digits), publishes its per-digit
 // counts, scatters the tile into shared memory in digit order, resolves its
 // global prefix by decoupled look-back over earlier tiles, and writes the
 // tile out so that runs of equal digits leave as coalesced stores.  Digits
