@@ -20,6 +20,7 @@
 #include "husky_learned.h"
 #include "hs_internal.h"
 #include "hs_bignum.h"
+#include "hs_fixup.h"
 
 namespace hs {
 namespace {
@@ -42,13 +43,13 @@ enum KernelKind {
     kKEncode, kKPlan, kKOnesweep, kKIdentity, kKTieDetect, kKSmallRuns, kKMediumRuns,
     kKRunScan, kKRefineKeys, kKPushConstant, kKHistogram, kKSegFill, kKRmiSample, kKRmiFit, kKRmiBucket,
     kKBucketBounds, kKBucketSort, kKOverflow, kKRmiTable, kKRmiLeaves, kKDistinctLarge, kKCollectMixed, kKValidate, kKAlphabet, kKPairs, kKSorted, kKCopies,
-    kKBucketRun, kKBigBuckets, kKOversizeTies, kKDecimal, kKNumKinds
+    kKBucketRun, kKBigBuckets, kKOversizeTies, kKDecimal, kKWindowDense, kKNumKinds
 };
 const char *const kKindNames[kKNumKinds] = {
     "encode", "plan", "onesweep", "identity", "tie_detect", "small_runs", "medium_runs",
     "run_scan", "refine_keys", "push_constant_runs", "histogram", "seg_fill", "rmi_sample", "rmi_train",
     "rmi_bucket", "bucket_bounds", "bucket_sort", "overflow", "rmi_table", "rmi_leaves", "distinct_large", "collect_mixed", "validate", "alphabet", "pairs_ordered", "sorted_test", "copies_filter",
-    "bucket_run_sort", "big_buckets", "oversize_ties", "decimal_encode"};
+    "bucket_run_sort", "big_buckets", "oversize_ties", "decimal_encode", "window_dense"};
 
 struct StatsTable {
     std::mutex mu;
@@ -809,10 +810,25 @@ hs_status run_fixup(Ctx &c, const Input &in, SortBufs &b, int cur, TieMode mode,
         if (total > n) return fail(HS_ERR_INTERNAL, "large runs overlap (run descriptors inconsistent)");
         SortBufs r = b;
         int rc = 0;
-        HS_TRY(c.timed(kKRefineKeys, 32.0 * total, [&] {
-                   return launch_refine_keys(in.bytes, in.offsets, in.perm, in.perm_u64, q_large[li], large,
-                                             run_base, total, inst, in.prefix_len, r.keys[0], r.segs[0],
-                                             r.vals[0], c.d_flags, c.s);
+        // Every run of a round is at the same depth: runs enter at depth 0
+        // and each round moves the ones it keeps one window on.  When the
+        // runs hold most of the strings, one pass in string order writes
+        // every string's window key to a dense array (r.keys[1], free until
+        // the sort below), and the refinement gathers one word a member
+        // from it instead of the member's offsets and bytes.
+        const uint32_t depth = (uint32_t)(rounds - 1);
+        uint64_t *win = nullptr;
+        if (total * 5 >= n * 2) {
+            win = r.keys[1];
+            HS_TRY(c.timed(kKWindowDense, 32.0 * n, [&] {
+                       return launch_window_dense(in.bytes, in.offsets, n, in.prefix_len, depth, win, c.sms, c.s);
+                   }),
+                   "window keys");
+        }
+        HS_TRY(c.timed(kKRefineKeys, (win ? 28.0 : 32.0) * total, [&] {
+                   return launch_refine_keys_win(in.bytes, in.offsets, in.perm, in.perm_u64, q_large[li], large,
+                                                 run_base, total, inst, in.prefix_len, win, depth, r.keys[0],
+                                                 r.segs[0], r.vals[0], c.d_flags, c.s);
                }),
                "refine keys");
         HS_TRY(c.read_flags(), "refine sync");

@@ -15,6 +15,7 @@
 //                   segmented radix sort by (run, key), and tie detection
 //                   again on the result (driven from the host).
 #include "hs_internal.h"
+#include "hs_fixup.h"
 
 namespace hs {
 namespace {
@@ -868,13 +869,30 @@ __global__ void run_scan_kernel(const RunEntry *__restrict__ runs, uint64_t coun
     if (tid == 0) run_base[count] = s_carry;
 }
 
+// The window keys of every string at one refinement depth, in string order.
+// Offsets are read coalesced and the bytes nearly so (consecutive threads
+// take consecutive strings); the refinement then gathers one word a member
+// from here instead of a member's offsets and bytes from scattered sectors.
+__global__ void window_dense_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
+                                    uint64_t n, int prefix_len, uint32_t depth, uint64_t *__restrict__ win) {
+    const uint64_t o = window_offset(prefix_len, depth);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t off = offsets[i];
+        win[i] = window_key(bytes + off, offsets[i + 1] - off, o, prefix_len);
+    }
+}
+
+// win (nullable): window keys of all strings at depth win_depth; runs at
+// that depth read their members' keys there.
 template <typename IdxT>
 __global__ void refine_keys_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__ offsets,
                                    const IdxT *__restrict__ perm, const RunEntry *__restrict__ runs,
                                    uint64_t count, const unsigned long long *__restrict__ run_base,
-                                   uint64_t total, Instances inst, int prefix_len, uint64_t *__restrict__ keys,
-                                   uint32_t *__restrict__ segs, uint32_t *__restrict__ vals,
-                                   DevFlags *flags) {
+                                   uint64_t total, Instances inst, int prefix_len,
+                                   const uint64_t *__restrict__ win, uint32_t win_depth,
+                                   uint64_t *__restrict__ keys, uint32_t *__restrict__ segs,
+                                   uint32_t *__restrict__ vals, DevFlags *flags) {
     if (stopped(inst)) return;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     bool nonconst = false;
@@ -887,14 +905,20 @@ __global__ void refine_keys_kernel(const uint8_t *__restrict__ bytes, const uint
         }
         const RunEntry r = runs[lo];
         const uint64_t pos = r.start + (a - run_base[lo]);
-        const uint64_t o = window_offset(prefix_len, r.depth);
         const uint64_t base = instance_base(inst, r.start);
         const IdxT idx = perm[pos];
-        const uint64_t off = offsets[base + idx];
-        const uint64_t k = window_key(bytes + off, offsets[base + idx + 1] - off, o, prefix_len);
         const uint64_t g0 = base + perm[r.start];
-        const uint64_t off0 = offsets[g0];
-        const uint64_t k0 = window_key(bytes + off0, offsets[g0 + 1] - off0, o, prefix_len);
+        uint64_t k, k0;
+        if (win != nullptr && r.depth == win_depth) {
+            k = win[base + idx];
+            k0 = win[g0];
+        } else {
+            const uint64_t o = window_offset(prefix_len, r.depth);
+            const uint64_t off = offsets[base + idx];
+            k = window_key(bytes + off, offsets[base + idx + 1] - off, o, prefix_len);
+            const uint64_t off0 = offsets[g0];
+            k0 = window_key(bytes + off0, offsets[g0 + 1] - off0, o, prefix_len);
+        }
         nonconst |= k != k0;
         keys[a] = k;
         segs[a] = (uint32_t)lo;
@@ -1038,20 +1062,37 @@ cudaError_t launch_run_scan(const RunEntry *runs, uint64_t count, unsigned long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_keys(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
-                               const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
-                               uint64_t total, Instances inst, int prefix_len, uint64_t *keys, uint32_t *segs,
-                               uint32_t *vals, DevFlags *flags, cudaStream_t s) {
+cudaError_t launch_refine_keys_win(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                                   const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
+                                   uint64_t total, Instances inst, int prefix_len, const uint64_t *win,
+                                   uint32_t win_depth, uint64_t *keys, uint32_t *segs, uint32_t *vals,
+                                   DevFlags *flags, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     const unsigned grid = (unsigned)umin64((total + 255) / 256, 152ull * 16);
     if (perm_u64)
         refine_keys_kernel<uint64_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint64_t *>(perm),
-                                                          runs, count, run_base, total, inst, prefix_len, keys,
-                                                          segs, vals, flags);
+                                                          runs, count, run_base, total, inst, prefix_len, win,
+                                                          win_depth, keys, segs, vals, flags);
     else
         refine_keys_kernel<uint32_t><<<grid, 256, 0, s>>>(bytes, offsets, static_cast<const uint32_t *>(perm),
-                                                          runs, count, run_base, total, inst, prefix_len, keys,
-                                                          segs, vals, flags);
+                                                          runs, count, run_base, total, inst, prefix_len, win,
+                                                          win_depth, keys, segs, vals, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_keys(const uint8_t *bytes, const uint64_t *offsets, const void *perm, int perm_u64,
+                               const RunEntry *runs, uint64_t count, const unsigned long long *run_base,
+                               uint64_t total, Instances inst, int prefix_len, uint64_t *keys, uint32_t *segs,
+                               uint32_t *vals, DevFlags *flags, cudaStream_t s) {
+    return launch_refine_keys_win(bytes, offsets, perm, perm_u64, runs, count, run_base, total, inst, prefix_len,
+                                  nullptr, 0, keys, segs, vals, flags, s);
+}
+
+cudaError_t launch_window_dense(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, int prefix_len,
+                                uint32_t depth, uint64_t *win, int num_sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)umin64((n + 255) / 256, (uint64_t)num_sms * 8);
+    window_dense_kernel<<<grid, 256, 0, s>>>(bytes, offsets, n, prefix_len, depth, win);
     return cudaGetLastError();
 }
 
