@@ -357,12 +357,13 @@ HS_API hs_status hs_argsort_bigint(const uint8_t *d_bytes,
  * one '.' and at least one digit, then optionally 'e' or 'E', an optional
  * sign and the exponent's digits (its value below 10^9); at most 32767 bytes.
  * With the value written as 0.d1 d2 .. dk x 10^X (d1 and dk nonzero) each
- * text becomes the byte string 0x02 (zero); 0x03, X + 2^39 in 5 big-endian
- * bytes, then the digits (positive); or 0x01, the complement of X + 2^39,
- * each digit d as '9' - d, then 0xFF (negative).  Unsigned-byte order of
- * these strings is numeric order, and values equal under compareTo (1.0 and
- * 1.00) give equal strings; hs_argsort's path sorts them with the byte
- * coder.  d_perm (device, uint32 or uint64 by out_t) receives the stable
+ * text becomes a byte string: a class byte (zero; or the sign and whether
+ * |X| < 2^23), the exponent in 3 bytes (|X| < 2^23) or 5, complemented for
+ * negatives, then the digits two to a byte (99 minus the pair for negatives,
+ * which end with 0xFF).  Unsigned-byte order of these strings is numeric
+ * order, and values equal under compareTo (1.0 and 1.00) give equal strings;
+ * hs_argsort's path sorts them with the byte coder, whose 8-byte prefix
+ * holds up to 8 digits.  d_perm (device, uint32 or uint64 by out_t) receives the stable
  * argsort by value.  total_bytes: the size of the byte buffer.  Returns
  * HS_ERR_INVALID_ARG if a text is outside that form or too long, or its
  * offsets decrease or pass total_bytes. */

@@ -51,15 +51,24 @@ bigint_encode_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restri
 // gives no coder.  A value here is its decimal text (an optional sign, digits
 // with at most one decimal point, an optional exponent [eE][+-]digits: the
 // form Java's BigDecimal(String) accepts).  With the value written as
-// 0.d1 d2 ... dk x 10^X (d1 != 0, no trailing zero digit) the byte string
-//   zero      0x02
-//   positive  0x03, X + 2^39 (5 bytes, big-endian), the digits '0'..'9'
-//   negative  0x01, ~(X + 2^39) (5 bytes), each digit as '9' - d, then 0xFF
-// has unsigned-byte order equal to numeric order, and equal values (1.0 and
-// 1.00) give equal strings, as compareTo wants.  Among positives a larger X
-// is larger, and at equal X the digits compare as decimal fractions (a
-// shorter one that is a prefix is smaller); negatives reverse both, the 0xFF
-// terminator putting a prefix (a smaller magnitude) after its extensions.
+// 0.d1 d2 ... dk x 10^X (d1 != 0, no trailing zero digit) the byte string is
+// a class byte, the exponent, and the digits two to a byte:
+//   class     0x00 / 0x01 / 0x02 negative with X >= 2^23 / |X| < 2^23 /
+//             X < -2^23; 0x03 zero (alone); 0x04 / 0x05 / 0x06 positive with
+//             X < -2^23 / |X| < 2^23 / X >= 2^23
+//   exponent  X + 2^23 in 3 big-endian bytes (|X| < 2^23), else X + 2^39 in
+//             5; complemented for negatives
+//   digits    each pair d(2i-1) d(2i) as the byte 10 d(2i-1) + d(2i) (an odd
+//             last digit paired with 0), as 99 minus that for negatives,
+//             which end with 0xFF
+// Its unsigned-byte order is numeric order, and equal values (1.0 and 1.00)
+// give equal strings, as compareTo wants.  Among positives of one class a
+// larger X is larger, and at equal X the digits compare as decimal
+// fractions: pairs compare as two digits do, and a shorter string that is a
+// prefix is smaller (no trailing zero digits, so the longer one continues
+// with a nonzero digit); negatives reverse both, the 0xFF terminator putting
+// a prefix (a smaller magnitude) after its extensions.  The first 8 bytes,
+// which the byte coder turns into the sort key, hold up to 8 digits.
 // Three kernels: each value's encoded length and a tile total; an exclusive
 // scan of the tile totals; each tile's offsets and bytes.
 
@@ -67,7 +76,8 @@ constexpr int kDecThreads = 256;
 constexpr int kDecPer = 4;                       // values a thread, consecutive
 constexpr int kDecTile = kDecThreads * kDecPer;  // values a tile
 constexpr int64_t kDecMaxExp = 999999999;        // |exponent| below 10^9
-constexpr int64_t kDecBias = 1ll << 39;
+constexpr int64_t kDecBias = 1ll << 39;            // 5-byte exponents
+constexpr int64_t kDecSmall = 1ll << 23;           // |X| below this: 3-byte exponents
 constexpr uint32_t kDecStage = 24576;            // a tile's text bytes staged in shared memory
 
 struct DecForm {
@@ -135,27 +145,43 @@ __device__ DecForm dec_parse(const uint8_t *__restrict__ s, uint32_t len) {
     return f;
 }
 
+__device__ __forceinline__ bool dec_small(const DecForm &f) { return f.X > -kDecSmall && f.X < kDecSmall; }
+
 __device__ __forceinline__ uint32_t dec_len(const DecForm &f) {
-    return f.cls == 1 ? 1u : (f.cls == 2 ? 6u + f.k : 7u + f.k);
+    if (f.cls == 1) return 1u;
+    return 1u + (dec_small(f) ? 3u : 5u) + (f.k + 1) / 2 + (f.cls == 0 ? 1u : 0u);
 }
 
 __device__ void dec_write(const uint8_t *__restrict__ s, const DecForm &f, uint8_t *__restrict__ out) {
     if (f.cls == 1) {
-        out[0] = 0x02;
+        out[0] = 0x03;
         return;
     }
-    const bool neg = f.cls == 0;
-    out[0] = neg ? 0x01 : 0x03;
-    uint64_t e = (uint64_t)(f.X + kDecBias);
-    if (neg) e = ~e & ((1ull << 40) - 1);
-    for (int b = 0; b < 5; ++b) out[1 + b] = (uint8_t)(e >> (8 * (4 - b)));
-    uint32_t idx = 0, w = 6;
+    const bool neg = f.cls == 0, small = dec_small(f);
+    const uint32_t band = small ? 1u : (f.X < 0 ? 0u : 2u);  // tiny, small or huge |value| scale
+    out[0] = (uint8_t)(neg ? 2u - band : 4u + band);
+    const int nb = small ? 3 : 5;
+    uint64_t e = (uint64_t)(f.X + (small ? kDecSmall : kDecBias));
+    if (neg) e = ~e & ((1ull << (8 * nb)) - 1);
+    for (int b = 0; b < nb; ++b) out[1 + b] = (uint8_t)(e >> (8 * (nb - 1 - b)));
+    uint32_t idx = 0, w = 1 + nb, pending = 0;
+    bool half = false;  // a first digit of a pair is pending
     for (uint32_t j = f.mstart; j < f.mend && idx < f.z + f.k; ++j) {
         const uint8_t c = s[j];
         if (c == '.') continue;
-        if (idx >= f.z) out[w++] = neg ? (uint8_t)('9' - c + '0') : c;
+        if (idx >= f.z) {
+            const uint32_t d = c - '0';
+            if (half) {
+                const uint32_t v = 10 * pending + d;
+                out[w++] = (uint8_t)(neg ? 99u - v : v);
+            } else {
+                pending = d;
+            }
+            half = !half;
+        }
         ++idx;
     }
+    if (half) out[w++] = (uint8_t)(neg ? 99u - 10 * pending : 10 * pending);
     if (neg) out[w] = 0xFFu;
 }
 

@@ -38,10 +38,13 @@ cudaError_t launch_bigdecimal_lengths(const uint8_t *bytes, const uint64_t *offs
 // Step 2 (once step 1 reported no error): writes each value's byte string to
 // out_bytes at out_offsets[i] (out_offsets[n] closes the last), placed by the
 // scanned tile totals.  For the value 0.d1 .. dk x 10^X (d1, dk nonzero) the
-// string is 0x02 for zero; 0x03, X + 2^39 in 5 big-endian bytes and the
-// digits '0'..'9' for a positive value; 0x01, the complement of X + 2^39 in
-// 5 bytes, each digit as '9' - d, then 0xFF for a negative value.  Their
-// unsigned-byte order is numeric order, and equal values give equal strings.
+// string is a class byte (0x03 for zero, alone; 0x04..0x06 for positives
+// with X < -2^23, |X| < 2^23, X >= 2^23; 0x02..0x00 for negatives likewise),
+// the exponent (X + 2^23 in 3 big-endian bytes when |X| < 2^23, else X + 2^39
+// in 5; complemented for negatives), and the digits two to a byte (10 a + b,
+// an odd last digit paired with 0; 99 minus that for negatives, which end
+// with 0xFF).  Their unsigned-byte order is numeric order, and equal values
+// give equal strings.
 cudaError_t launch_bigdecimal_write(const uint8_t *bytes, const uint64_t *offsets, uint64_t n, uint64_t total,
                                     const unsigned long long *tile_base, uint8_t *out_bytes, uint64_t out_cap,
                                     uint64_t *out_offsets, DevFlags *flags, cudaStream_t s);
