@@ -79,6 +79,7 @@ constexpr int64_t kDecMaxExp = 999999999;        // |exponent| below 10^9
 constexpr int64_t kDecBias = 1ll << 39;            // 5-byte exponents
 constexpr int64_t kDecSmall = 1ll << 23;           // |X| below this: 3-byte exponents
 constexpr uint32_t kDecStage = 24576;            // a tile's text bytes staged in shared memory
+constexpr uint32_t kDecOutStage = 20480;         // a tile's output bytes, gathered before one coalesced copy
 
 struct DecForm {
     bool ok;
@@ -291,10 +292,16 @@ dec_write_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__
                  const unsigned long long *__restrict__ tile_base, uint8_t *__restrict__ out_bytes, uint64_t out_cap,
                  uint64_t *__restrict__ out_offsets, DevFlags *flags) {
     __shared__ uint8_t s_text[kDecStage];
+    __shared__ __align__(16) uint8_t s_out[kDecOutStage];
     const uint64_t t0 = (uint64_t)blockIdx.x * kDecTile;
     uint32_t span;
     const uint64_t lo = dec_stage(bytes, offsets, t0, umin64(kDecTile, n - t0), total, s_text, &span);
     const uint64_t i0 = t0 + (uint64_t)threadIdx.x * kDecPer;
+    // The tile's strings are contiguous in the output: when they fit the
+    // stage they are written there and leave in one coalesced copy, instead
+    // of each thread's bytes going out to its own scattered sectors.
+    const uint64_t out0 = tile_base[blockIdx.x], out1 = tile_base[blockIdx.x + 1];
+    const bool staged_out = out1 >= out0 && out1 - out0 <= kDecOutStage && out1 <= out_cap;
     uint32_t lens[kDecPer];
     uint64_t sum = 0;
     for (int q = 0; q < kDecPer; ++q) {
@@ -323,12 +330,15 @@ dec_write_kernel(const uint8_t *__restrict__ bytes, const uint64_t *__restrict__
                 uint32_t len;
                 dec_text(offsets, i, total, &o, &len);
                 const uint8_t *src = dec_src(bytes, s_text, lo, span, o, len);
-                dec_write(src, dec_parse(src, len), out_bytes + dst);
+                dec_write(src, dec_parse(src, len), staged_out ? s_out + (dst - out0) : out_bytes + dst);
             }
         }
         dst += lens[q];
         if (i + 1 == n) out_offsets[n] = dst;
     }
+    __syncthreads();
+    if (staged_out)
+        for (uint64_t k = threadIdx.x; k < out1 - out0; k += kDecThreads) out_bytes[out0 + k] = s_out[k];
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&flags->error, kErrInternal);
 }
 
